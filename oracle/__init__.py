@@ -1,0 +1,19 @@
+"""FP64 CPU oracle for Electric Vertex Splitting (EVS) and the Virtual Transmission Method (VTM).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously-correct reference that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it.  The product path (``paper_0807_1949_gb300``) never imports,
+calls or links it, and it shares no code with the product beyond the seeded input generators
+in ``paper_0807_1949_gb300/inputs.py`` (which hold none of the method's arithmetic).
+
+Modules, each following the paper in its own order and notation:
+
+* ``evs``      — §4 (EVS steps 1-4, eq. 4.1-4.4; App. 2 splitting identities).
+* ``vtm``      — §5 (eq. 5.6-5.8 and Table 1): local SPD systems, the (u, omega) iteration,
+                 assembly of the solution, FP64 residual, direct solve.
+* ``matching`` — §7.1 (Def. 7.1 input impedance, impedance matching).
+* ``theory``   — App. 3 (the port-space iteration operator of eq. A3.8) and the closed-form
+                 reflection of a single transmission line (§2 eq. 2.1 with §7.1).
+
+Pins (what fixes each function independently of itself) are listed in each module header.
+"""

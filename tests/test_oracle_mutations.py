@@ -1,0 +1,103 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that a pin catches each one.
+
+A pin that a dropped term, a wrong sign, a missing exchange or a wrong share would still pass is
+no pin; these tests run the pins of test_oracle.py against deliberately broken oracles.
+"""
+import numpy as np
+import pytest
+
+import test_oracle as T
+from conftest import load_golden
+from oracle import evs, matching, theory
+from oracle import vtm as ovtm
+
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except (AssertionError, np.linalg.LinAlgError, ValueError):
+        return True
+    return False
+
+
+def test_dropped_line_admittance_is_caught(monkeypatch):
+    """eq. 5.8 without the Z^{-1} port term."""
+    monkeypatch.setattr(ovtm, "local_matrix", lambda split, ends, j: split.subgraphs[j].A.tocsr())
+    assert _fails(T.test_example_5_1_local_matrices, load_golden)
+    assert _fails(T.test_example_5_1_converges_to_direct_solution, load_golden)
+
+
+def test_missing_exchange_is_caught(monkeypatch):
+    """Table 1 step 5 forgotten: every end reads its own old values instead of its twin's."""
+    orig = ovtm.ends_of
+
+    def no_exchange(split, Z):
+        e = orig(split, Z)
+        e.twin = np.arange(len(e.twin))
+        return e
+
+    monkeypatch.setattr(ovtm, "ends_of", no_exchange)
+    assert _fails(T.test_example_5_1_converges_to_direct_solution, load_golden)
+    assert _fails(T.test_a38_operator_reproduces_iteration, 0)
+
+
+def test_asymmetric_impedance_is_caught(monkeypatch):
+    """The two ends of one line must see the same Z (Table 1 step 1)."""
+    orig = ovtm.ends_of
+
+    def skewed(split, Z):
+        e = orig(split, Z)
+        e.Z = e.Z.copy()
+        e.Z[1::2] *= 2.0
+        return e
+
+    monkeypatch.setattr(ovtm, "ends_of", skewed)
+    assert _fails(T.test_example_5_1_local_matrices, load_golden)
+
+
+def test_unsplit_source_is_caught(monkeypatch):
+    """Step 3 forgetting to split b_i between the copies of a boundary vertex."""
+    monkeypatch.setattr(evs.SplitGraph, "local_rhs",
+                        lambda self, b, j: np.atleast_2d(b)[:, self.subgraphs[j].vertices].astype(float))
+    assert _fails(T.test_config1_oracle_reaches_1e10)
+
+
+def test_unsplit_edge_is_caught(monkeypatch):
+    """Step 3 forgetting to split an edge along the boundary (KCL broken)."""
+    orig = evs.split_by_owners
+
+    def keep_edges(A, owners, pairs):
+        s = orig(A, owners, pairs)
+        for g in s.subgraphs:
+            g.A = g.A.tolil()
+            for r in range(g.A.shape[0]):
+                for c in range(g.A.shape[1]):
+                    if r != c and g.A[r, c] != 0 and len(owners[g.vertices[r]]) > 1 and len(owners[g.vertices[c]]) > 1:
+                        g.A[r, c] = g.A[r, c] * 2
+            g.A = g.A.tocsr()
+        return s
+
+    monkeypatch.setattr(evs, "split_by_owners", keep_edges)
+    assert _fails(T.test_equal_share_rule_on_example_3_1)
+
+
+def test_input_impedance_without_inverse_is_caught(monkeypatch):
+    """Def. 7.1 read as 1 / a_cc instead of (Ã^{-1})_cc."""
+    import scipy.sparse as sp
+    monkeypatch.setattr(matching, "input_impedance_open",
+                        lambda A, c: 1.0 / (A.toarray() if sp.issparse(A) else np.asarray(A))[c, c])
+    assert _fails(T.test_example_7_1_input_impedances, load_golden)
+
+
+def test_operator_without_exchange_is_caught(monkeypatch):
+    """eq. A3.8 with J = I: the operator no longer reproduces the iteration."""
+    orig_block = np.block
+
+    def fake_block(rows):
+        out = orig_block(rows)
+        if out.shape[0] == out.shape[1] and np.all(np.diag(out) == 0) and np.allclose(out, out.T):
+            return np.eye(out.shape[0])
+        return out
+
+    monkeypatch.setattr(theory.np, "block", fake_block)
+    assert _fails(T.test_a38_operator_reproduces_iteration, 0)
