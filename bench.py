@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative residual 1e-8 of the Virtual Transmission Method on one GB300.
+
+Workload (default "poisson3d-128"): 3D 7-point variable-coefficient Poisson operator on a 128^3
+vertex grid (2,097,152 unknowns), node coefficients log-normal (sigma = 1, seed 0), Dirichlet
+boundary; Electric Vertex Splitting into 8x8x8 = 512 cubic subgraphs (cut planes every 16
+nodes, shared); uniform line impedance Z = 1; b i.i.d. uniform[-1, 1].  The product path uses
+FP32 band factors and FP32 sweeps inside FP64 defect correction (residual b - A x in FP64 on the
+device).  The plain method (FP64 factors and sweeps, no correction) is timed beside it.
+
+One step = one vtm_solve from zero waves to max relative residual <= 1e-8 (every sweep gathers
+the twins' waves, builds the port right-hand side, runs the forward and back substitution over
+all subgraphs and emits the outgoing waves; the FP64 residual is checked every 10 sweeps).
+The factorisation (vtm_setup) happens once, before the timed region, and is reported as
+setup_ms.  The factor (2.7 GB FP32) is far larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vtm|reference] [--workload W]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: dims, block, sigma, rtol
+    "poisson3d-128": dict(dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0, rtol=1e-8),
+    "laplace2d-32": dict(dims=(32, 32), block=(16, 16), sigma=0.0, rtol=1e-8),
+}
+METRIC = "time to rel. residual 1e-8 (learned-Z batched vs plain VTM) on 1 GB300; HBM GB/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
+    p.add_argument("--workload", default="poisson3d-128", choices=list(WORKLOADS))
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+
+def oracle_sweep_sample(workload: str, sweeps: int) -> dict:
+    """Time the FP64 oracle's own sweep (oracle.vtm.VTM.sweep) on a bounded sample.
+
+    The sample is a grid of 2x2(x2) blocks of exactly the workload's block shape (so every
+    subgraph has the workload's size and bandwidth), split and iterated by the oracle as it is.
+    Returns seconds per subgraph-sweep; the factorisation is excluded (paid once, like vtm_setup).
+    """
+    import numpy as np
+
+    from oracle import evs
+    from oracle import vtm as ovtm
+    from paper_0807_1949_gb300 import inputs
+
+    w = WORKLOADS[workload]
+    dims = tuple(min(d, 2 * s + 1) for d, s in zip(w["dims"], w["block"]))
+    A = inputs.grid_poisson(dims, sigma=w["sigma"], seed=0)
+    b = inputs.rhs_uniform(A.n, 1, seed=0)
+    split = evs.split_grid(A, dims, w["block"])
+    m = ovtm.VTM(split, 1.0)
+    st = m.initial_state()
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        st = m.sweep(st, b)
+    dt = time.perf_counter() - t0
+    nb = [max(1, -(-(d - 1) // s)) if d > 1 else 1 for d, s in zip(w["dims"], w["block"])]
+    total = int(np.prod(nb))
+    return dict(sec_per_piece_sweep=dt / (sweeps * len(split.subgraphs)), total_pieces=total,
+                sample=len(split.subgraphs), sample_dims=dims, sweeps=sweeps, seconds=dt)
+
+
+def cpu_baseline(workload: str, sweeps_to_tol: int, sweeps=6) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-child",
+           json.dumps(dict(workload=workload, sweeps=sweeps))]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        return dict(value=None, unit="ms", cores=1, kind="oracle", error=out.stderr[-300:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    per_sweep_ms = r["sec_per_piece_sweep"] * r["total_pieces"] * 1e3
+    return dict(value=round(per_sweep_ms * sweeps_to_tol, 3), unit="ms", cores=1, kind="oracle",
+                per_sweep_ms=round(per_sweep_ms, 3),
+                sample=(f"FP64 oracle, {r['sweeps']} sweeps of a {r['sample_dims']} grid = {r['sample']} subgraphs of "
+                        f"the workload's block shape ({r['seconds']:.1f} s), scaled to {r['total_pieces']} subgraphs "
+                        f"and to {sweeps_to_tol} sweeps (plain FP64 method's count to 1e-8); factorisation excluded"))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_traffic(kernel_src: str, workload: str):
+    """Measured DRAM bytes per sweep launch from a committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(kernel_src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        e = d.get(workload)
+        if e and e.get("kernel_sha") == h:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "vtm" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- arms
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    ksweeps = reference_sweeps(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sweep_sample(args.workload, 1)
+    t0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        info = oracle_sweep_sample(args.workload, 2)
+        vals.append(info["sec_per_piece_sweep"] * info["total_pieces"] * ksweeps * 1e3)
+    dt = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": w["dims"], "block": w["block"], "sigma": w["sigma"],
+                   "rtol": w["rtol"], "z": 1.0, "sweeps_to_tol": ksweeps},
+        "cpu_baseline": {"value": round(v, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": (f"each step: FP64 oracle, {info['sweeps']} sweeps of a {info['sample_dims']} grid "
+                                    f"({info['sample']} subgraphs of the workload's block shape), scaled to "
+                                    f"{info['total_pieces']} subgraphs and {ksweeps} sweeps; wall {dt:.1f} s for "
+                                    f"{args.steps} steps")},
+        "e2e": {"value": round(v, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def reference_sweeps(workload: str) -> int:
+    """Sweeps the plain FP64 method needs to reach 1e-8 on this workload (oracle-written file)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_sweeps.json")
+    try:
+        with open(path) as f:
+            return int(json.load(f)[workload]["sweeps"])
+    except Exception:
+        return -1
+
+
+def run_vtm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_0807_1949_gb300 import inputs, vtm
+
+    w = WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    A = inputs.grid_poisson(w["dims"], sigma=w["sigma"], seed=0)
+    b = inputs.rhs_uniform(A.n, 1, seed=0)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    part = vtm.partition_evs(A, "grid", dims=w["dims"], block=w["block"])
+    t_part = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    solver = vtm.Solver(part, z=1.0, precision="fp32", nrhs=1, stream=stream, check_every=10)
+    sinfo = solver.info()
+    bd = torch.tensor(b, device="cuda")
+    xd = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+
+    # ---- warm-up and timed steps (device timing on the solver's stream)
+    for _ in range(args.warmup):
+        solver.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        stats.append(solver.solve(bd, xd, rtol=w["rtol"], maxit=100000))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ws, ms)
+    x = xd.cpu().numpy()
+    rel = float(np.linalg.norm(b[0] - A.to_scipy() @ x[0]) / np.linalg.norm(b[0]))
+    sweeps = stats[-1].sweeps
+    launches = sum(s.launches for s in stats)
+
+    # ---- dominant kernel: one sweep launch, CUDA events around back-to-back sweeps
+    solver.set_rhs(bd)
+    solver.reset()
+    nsw = 40
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    solver.iterate(nsw)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = k0.elapsed_time(k1) / nsw
+    elem = 4
+    alg_bytes = (2 * sinfo.band_entries * elem + sinfo.ncopies * elem + 2 * sinfo.nends * elem
+                 + sinfo.nends * 8)
+    pk = peaks()
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc", "sweep.cu"), args.workload)
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    bh = torch.tensor(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.solve(bh, xh, rtol=w["rtol"], maxit=100000)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = max_over_ranks(ws, statistics.median(e2e))
+
+    # ---- plain method (FP64 factors, no correction), same workload
+    plain = None
+    if not args.no_plain:
+        del solver
+        torch.cuda.empty_cache()
+        ps = vtm.Solver(part, z=1.0, precision="fp64", nrhs=1, stream=stream, check_every=10)
+        ps.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pst = ps.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"ms": round(p0.elapsed_time(p1), 3), "sweeps": pst.sweeps, "setup_ms": round(ps.info().setup_ms, 1),
+                 "precision": "fp64", "z": 1.0}
+        del ps
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        ks = plain["sweeps"] if plain else sweeps
+        cpu = cpu_baseline(args.workload, ks)
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f64 residual + defect correction)", "data": "synthetic",
+        "config": {"workload": args.workload, "dims": w["dims"], "block": w["block"], "sigma": w["sigma"],
+                   "rtol": w["rtol"], "z": 1.0, "pieces": sinfo.npieces, "nrhs": 1,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (FP32 factor %.2f GB)" % (sinfo.factor_bytes / 1e9),
+                   "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,
+                   "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
+                   "partition_ms": round(t_part * 1e3, 1), "plain": plain},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep<float,1>", "achieved": round(achieved, 1),
+                     "peak": pk["hbm_gbs"], "peak_source": pk["source"], "unit": "GB/s",
+                     "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
+                     "alg_bytes_per_launch": int(alg_bytes), "launch_ms": round(sweep_ms, 4)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(A.n * 8),
+                "d2h_bytes_per_step": int(A.n * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.cpu_child:
+        p = json.loads(args.cpu_child)
+        print(json.dumps(oracle_sweep_sample(p["workload"], p["sweeps"])))
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_vtm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * vtm.h — C ABI of the GB300 (sm_103a) Virtual Transmission Method library.
+ *
+ * The library solves A x = b for a sparse symmetric positive-definite A (§1, §3 eq. 3.1: A is
+ * viewed as an electric graph with vertex weights a_ii, edge weights a_ij, current sources b_i
+ * and potentials x_i).  It splits the graph by Electric Vertex Splitting (§4, steps 1-4), joins
+ * every pair of facing copies with a virtual transmission line of impedance Z (§5), factors each
+ * subsystem's local SPD matrix once (eq. 5.8) and iterates Table 1: every sweep solves all
+ * subsystems with the incident waves of the previous sweep and exchanges the outgoing waves
+ * between twins (Neighbor-To-Neighbor, §1, Table 1 steps 3-5).
+ *
+ * Conventions for every entry point:
+ *  - Return value: VTM_OK (0) or a vtm_status error code; the thread-local message of the last
+ *    failure is returned by vtm_last_error().  No entry point aborts or throws.
+ *  - Ownership: the caller owns every array it passes; the library copies what it keeps.
+ *    Opaque handles are released with the matching *_destroy call (NULL is accepted).
+ *  - Host pointers are marked "host", device pointers "device" (memory of the current CUDA
+ *    device, e.g. a torch tensor's data_ptr()).  Pointers marked "host or device" are
+ *    classified with cudaPointerGetAttributes.
+ *  - Right-hand sides and solutions are column-major n x nrhs with leading dimension ld >= n:
+ *    element (i, r) is at p[i + r*ld].
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Work is queued on
+ *    it; calls that return host data synchronise it.
+ */
+#ifndef VTM_H
+#define VTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VTM_VERSION_MAJOR 0
+#define VTM_VERSION_MINOR 1
+
+typedef enum vtm_status {
+  VTM_OK = 0,
+  VTM_ERR_INVALID = 1,        /* bad argument, size or handle                                   */
+  VTM_ERR_NOT_SYMMETRIC = 2,  /* A is not symmetric (§3 requires a_ij = a_ji)                   */
+  VTM_ERR_NOT_CONFORMAL = 3,  /* a boundary vertex is not weakly diagonally dominant, so the
+                                 equal-share split cannot make the pieces SNND (Cor. 4.1)        */
+  VTM_ERR_NOT_SPD = 4,        /* a local matrix of eq. 5.8 had a non-positive Cholesky pivot     */
+  VTM_ERR_NOT_CONVERGED = 5,  /* maxit sweeps without reaching rtol                              */
+  VTM_ERR_DIVERGED = 6,       /* residual became NaN/Inf or grew without bound                   */
+  VTM_ERR_TIMEOUT = 7,        /* a bounded device wait ran out (kernel returned early)           */
+  VTM_ERR_CUDA = 8,           /* a CUDA runtime call failed                                      */
+  VTM_ERR_OOM = 9             /* device or host allocation failed                                */
+} vtm_status;
+
+/* Symmetric sparse matrix, full storage (both triangles), host memory.
+ * rowptr: n+1 int64; col: nnz int32 (sorted ascending within a row, no duplicates);
+ * val: nnz float64.  Must be symmetric with a positive diagonal. */
+typedef struct vtm_csr {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} vtm_csr;
+
+/* ----------------------------------------------------------------------------------------------
+ * Partition (Electric Vertex Splitting, §4)
+ * --------------------------------------------------------------------------------------------*/
+
+enum vtm_partition_kind {
+  /* Grid cut into blocks that SHARE their cut lines/planes (§9's testbenches are 2D grids cut into
+   * blocks; Fig. 7 gives the 2- and 3-level splits).  Vertex id = x + dims[0]*(y + dims[1]*z).
+   * Along an axis of extent m with spacing s the cut coordinates are s, 2s, ...; block q covers
+   * [q*s, min((q+1)*s, m-1)].  Subgraph id of block (qx,qy,qz) = qx + Bx*(qy + By*qz).
+   * Lines: hypercube rule — the copies of a vertex in two blocks that differ along exactly one
+   * axis are joined by one line (1 line per copy on a face, 2 on an edge line, 3 at a corner). */
+  VTM_PART_GRID = 1,
+  /* Owner sets given per vertex; the lines are given explicitly. */
+  VTM_PART_OWNERS = 2,
+  /* A complete split given explicitly: copies, local matrices Ã_j, source shares and lines
+   * (any conformal scheme, e.g. the uneven shares of Example 4.1). */
+  VTM_PART_EXPLICIT = 3
+};
+
+/* Split rule of GRID and OWNERS (§4 step 3; the paper leaves the shares open, this is the
+ * library's rule): edge (i,j) goes to every subgraph in O(i)∩O(j) with weight a_ij/|O(i)∩O(j)|;
+ * the copy of a boundary vertex i gets a_ii^(c) = sum_{j!=i} |a_ij^(c)| + delta_i/|O(i)| with
+ * delta_i = a_ii - sum_{j!=i}|a_ij| (delta_i < -64 eps a_ii => VTM_ERR_NOT_CONFORMAL; rounding-
+ * level negatives count as 0); inner vertices keep a_ii; b_i is shared as b_i/|O(i)|.
+ * Copies inside a subgraph are ordered by ascending global vertex id. */
+typedef struct vtm_partition_spec {
+  int32_t kind;             /* vtm_partition_kind */
+  /* GRID */
+  int32_t dims[3];          /* grid extents; use 1 for unused axes                           */
+  int32_t block[3];         /* cut spacing per axis (>= 1)                                   */
+  /* OWNERS */
+  int32_t npieces;          /* number of subgraphs (OWNERS, EXPLICIT)                        */
+  const int64_t* owner_ptr; /* host, n+1: owners of vertex i are owner_piece[owner_ptr[i]..]  */
+  const int32_t* owner_piece; /* host, sorted ascending per vertex, values in [0, npieces)    */
+  int64_t nlines;           /* OWNERS: lines as (vertex, piece_a, piece_b) triples            */
+  const int64_t* line_vertex;
+  const int32_t* line_piece_a;
+  const int32_t* line_piece_b;
+  /* EXPLICIT: C copies numbered piece by piece */
+  const int64_t* piece_ptr;   /* host, npieces+1: copies of piece j are piece_ptr[j]..piece_ptr[j+1]-1 */
+  const int64_t* copy_vertex; /* host, C: parent vertex of each copy                             */
+  const double* copy_share;   /* host, C: b̃_c = copy_share[c] * b[copy_vertex[c]]              */
+  const int64_t* local_rowptr;/* host, C+1: row c of Ã (its piece's local matrix)                */
+  const int32_t* local_col;   /* host: LOCAL column index within the piece (0-based)             */
+  const double* local_val;    /* host                                                            */
+  int64_t ncopy_lines;        /* EXPLICIT: lines as pairs of copy ids                            */
+  const int64_t* line_copy_a;
+  const int64_t* line_copy_b;
+} vtm_partition_spec;
+
+typedef struct vtm_partition vtm_partition;
+
+typedef struct vtm_partition_info {
+  int64_t n;          /* vertices of A                       */
+  int32_t npieces;    /* subgraphs N                         */
+  int64_t ncopies;    /* total local unknowns                */
+  int64_t nlines;     /* virtual transmission lines          */
+  int64_t nboundary;  /* vertices with two or more copies    */
+  int64_t max_piece;  /* largest subgraph (local unknowns)   */
+} vtm_partition_info;
+
+/* §4 steps 1-4.  A: host CSR (copied).  On success *out owns the split.
+ * Errors: VTM_ERR_INVALID (bad spec / an edge in no common subgraph / a line between copies
+ * that do not exist), VTM_ERR_NOT_SYMMETRIC, VTM_ERR_NOT_CONFORMAL. */
+int vtm_partition_evs(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition** out);
+int vtm_partition_get_info(const vtm_partition* p, vtm_partition_info* info);
+/* Subgraph j (eq. 4.4): copies' parent vertices (host, n_j int64), shares (host, n_j double) and
+ * Ã_j in local CSR (rowptr n_j+1 int64, col int32, val double).  Any output may be NULL; call
+ * first with NULL arrays to read *n_j and *nnz_j. */
+int vtm_partition_get_piece(const vtm_partition* p, int32_t j, int64_t* n_j, int64_t* nnz_j,
+                            int64_t* vertices, double* shares, int64_t* rowptr, int32_t* col,
+                            double* val);
+/* Lines as (piece_a, local_a, piece_b, local_b) quadruples, host int64 array of 4*nlines. */
+int vtm_partition_get_lines(const vtm_partition* p, int64_t* quads);
+void vtm_partition_destroy(vtm_partition* p);
+
+/* ----------------------------------------------------------------------------------------------
+ * Solver setup (Table 1 steps 1-2, eq. 5.8 factored once, §8)
+ * --------------------------------------------------------------------------------------------*/
+
+enum vtm_z_mode {
+  VTM_Z_UNIFORM = 0,   /* every line has impedance z_uniform (Example 5.1 style)            */
+  VTM_Z_EXPLICIT = 1   /* z_lines[t] per line, in the order of vtm_partition_get_lines      */
+};
+
+enum vtm_precision {
+  VTM_FP64 = 0,        /* factor, substitution and waves in FP64                              */
+  VTM_FP32 = 1         /* factor, substitution and waves in FP32; FP64 residual and defect
+                          correction around the sweeps (outer refinement)                     */
+};
+
+typedef struct vtm_setup_opts {
+  int32_t z_mode;          /* vtm_z_mode                                                     */
+  double z_uniform;        /* UNIFORM: impedance (> 0)                                       */
+  const double* z_lines;   /* EXPLICIT: host, nlines values (> 0)                            */
+  int32_t precision;       /* vtm_precision                                                  */
+  int32_t nrhs;            /* right-hand sides solved together (1..8)                        */
+  int32_t check_every;     /* sweeps between residual checks in vtm_solve (0 = 10)           */
+  double inner_reduction;  /* FP32: restart the defect correction once the inner residual has
+                              dropped by this factor (0 = 1e-4); ignored for FP64            */
+} vtm_setup_opts;
+
+typedef struct vtm_solver vtm_solver;
+
+typedef struct vtm_solver_info {
+  int32_t npieces;
+  int64_t ncopies;
+  int64_t nends;               /* 2 * nlines                                                  */
+  int32_t nrhs;
+  int32_t precision;
+  int32_t block_rows;          /* substitution block height (rows per staged slab)            */
+  int64_t factor_entries;      /* stored band entries (with padding)                          */
+  int64_t band_entries;        /* structurally in-band entries sum_j (n_j (w_j+1) - w_j(w_j+1)/2) */
+  int64_t factor_bytes;        /* stored factor bytes                                         */
+  int64_t max_halfband;        /* max_j w_j                                                   */
+  double setup_ms;             /* wall time of vtm_setup                                      */
+  double factor_ms;            /* device time of the factorisation kernels                    */
+} vtm_solver_info;
+
+/* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the
+ * device once (banded Cholesky), allocate the wave and vector buffers.  `p` is not retained.
+ * Errors: VTM_ERR_INVALID, VTM_ERR_NOT_SPD, VTM_ERR_OOM, VTM_ERR_CUDA. */
+int vtm_setup(const vtm_partition* p, const vtm_setup_opts* opts, void* cuda_stream, vtm_solver** out);
+int vtm_solver_get_info(const vtm_solver* s, vtm_solver_info* info);
+void vtm_solver_destroy(vtm_solver* s);
+
+/* ----------------------------------------------------------------------------------------------
+ * Iteration (Table 1 steps 3-5)
+ * --------------------------------------------------------------------------------------------*/
+
+/* Split b into the subsystems' sources b̃_j (§4 step 3, eq. 4.4) for vtm_iterate.
+ * b: host or device, column-major n x nrhs, leading dimension ldb.  Waves are not touched. */
+int vtm_set_rhs(vtm_solver* s, const double* b, int64_t ldb);
+/* Zero every wave (Table 1 step 2 with u^0 = omega^0 = 0). */
+int vtm_reset(vtm_solver* s);
+/* Run `sweeps` synchronous sweeps on the solver's stream (asynchronous): each sweep gathers the
+ * incident wave of every line end from its twin (w_in[e] = w_out_prev[twin(e)]), solves every
+ * K_j x_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8) with the stored factor, and emits
+ * w_out[e] = 2 u_e - w_in[e] (the left side u - Z omega of eq. 5.6 seen from the twin). */
+int vtm_iterate(vtm_solver* s, int32_t sweeps);
+
+/* Solve A x = b to max_r ||b_r - A x_r||_2 / ||b_r||_2 <= rtol (FP64 residual on the device,
+ * checked every check_every sweeps), from zero waves.  FP32 solvers wrap the sweeps in FP64
+ * defect correction.  b, x: host or device, column-major n x nrhs, leading dimension ld.
+ * st may be NULL.  Returns VTM_ERR_NOT_CONVERGED after maxit sweeps (x holds the last iterate),
+ * VTM_ERR_DIVERGED on NaN/Inf. */
+typedef struct vtm_stats {
+  int32_t sweeps;          /* total sweeps                                        */
+  int32_t checks;          /* residual evaluations                                */
+  int32_t restarts;        /* defect-correction restarts                          */
+  double rel_residual;     /* final max_r relative residual (FP64)                */
+  double solve_ms;         /* wall time of the call                               */
+  int32_t launches;        /* kernels of this library launched by the call        */
+} vtm_stats;
+int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int32_t maxit,
+              vtm_stats* st);
+
+/* Checkpoint / inspection.  Waves: outgoing waves of the last sweep, host, nends x nrhs
+ * column-major (end order of vtm_partition_get_lines: end 2t = side a of line t, 2t+1 = side b).
+ * Copies: the last local solutions, host, ncopies x nrhs column-major, copies numbered piece by
+ * piece in local order.  vtm_get_copies needs a sweep to have run since vtm_reset. */
+int vtm_get_state(vtm_solver* s, double* waves);
+int vtm_set_state(vtm_solver* s, const double* waves);
+int vtm_get_copies(vtm_solver* s, double* copies);
+
+const char* vtm_last_error(void);
+int vtm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VTM_H */

@@ -269,3 +269,22 @@ def kcl_residual(split: SplitGraph, A) -> float:
         tot = tot + P @ g.A @ P.T
     d = (tot - A).tocoo()
     return float(np.max(np.abs(d.data))) if d.nnz else 0.0
+
+
+def grid_piece_line_count(dims, block, piece: int) -> np.ndarray:
+    """Number of lines at each local copy of a grid subgraph (hypercube rule of Fig. 7).
+
+    A copy has one line per axis along which its vertex is shared by two blocks.
+    Local order: ascending global vertex id, as in ``split_grid_piece``.
+    """
+    dims = tuple(dims) + (1,) * (3 - len(dims))
+    block = tuple(block) + (1,) * (3 - len(block))
+    per_axis = [grid_axis_blocks(dims[a], block[a]) for a in range(3)]
+    nblk = tuple(1 + max(max(t) for t in per_axis[a]) for a in range(3))
+    q = (piece % nblk[0], (piece // nblk[0]) % nblk[1], piece // (nblk[0] * nblk[1]))
+    rng = [[c for c in range(dims[a]) if q[a] in per_axis[a][c]] for a in range(3)]
+    zz, yy, xx = np.meshgrid(rng[2], rng[1], rng[0], indexing="ij")
+    cnt = np.zeros(xx.size, dtype=np.int64)
+    for a, coord in enumerate((xx.ravel(), yy.ravel(), zz.ravel())):
+        cnt += np.array([len(per_axis[a][c]) == 2 for c in coord], dtype=np.int64)
+    return cnt

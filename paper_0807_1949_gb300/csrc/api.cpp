@@ -1,0 +1,199 @@
+// C ABI entry points (include/vtm.h): argument checks, error codes and thread-local messages.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace vtm {
+void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition* p);
+vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void* cuda_stream);
+void solver_set_rhs(vtm_solver* s, const double* b, int64_t ldb);
+void reset_waves(vtm_solver* s);
+void solver_iterate(vtm_solver* s, int k);
+int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int maxit, vtm_stats* st);
+void solver_get_state(vtm_solver* s, double* waves);
+void solver_set_state(vtm_solver* s, const double* waves);
+void solver_get_copies(vtm_solver* s, double* out);
+void solver_get_info(const vtm_solver* s, vtm_solver_info* info);
+void solver_destroy(vtm_solver* s);
+
+static thread_local std::string g_last_error;
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace vtm
+
+using vtm::Error;
+
+template <class F>
+static int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    vtm::g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    vtm::g_last_error = "host allocation failed";
+    return VTM_ERR_OOM;
+  } catch (const std::exception& e) {
+    vtm::g_last_error = e.what();
+    return VTM_ERR_INVALID;
+  } catch (...) {
+    vtm::g_last_error = "unknown error";
+    return VTM_ERR_INVALID;
+  }
+}
+
+extern "C" {
+
+int vtm_partition_evs(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition** out) {
+  return guarded([&] {
+    if (!out) vtm::fail(VTM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    vtm_partition* p = new vtm_partition();
+    try {
+      vtm::build_partition(A, spec, p);
+    } catch (...) {
+      delete p;
+      throw;
+    }
+    *out = p;
+    return VTM_OK;
+  });
+}
+
+int vtm_partition_get_info(const vtm_partition* p, vtm_partition_info* info) {
+  return guarded([&] {
+    if (!p || !info) vtm::fail(VTM_ERR_INVALID, "null argument");
+    info->n = p->n;
+    info->npieces = p->npieces;
+    info->ncopies = p->piece_ptr.empty() ? 0 : p->piece_ptr.back();
+    info->nlines = (int64_t)p->line_a.size();
+    info->nboundary = p->nboundary;
+    int64_t mx = 0;
+    for (int32_t j = 0; j < p->npieces; ++j) mx = std::max(mx, p->piece_ptr[j + 1] - p->piece_ptr[j]);
+    info->max_piece = mx;
+    return VTM_OK;
+  });
+}
+
+int vtm_partition_get_piece(const vtm_partition* p, int32_t j, int64_t* n_j, int64_t* nnz_j, int64_t* vertices,
+                            double* shares, int64_t* rowptr, int32_t* col, double* val) {
+  return guarded([&] {
+    if (!p || j < 0 || j >= p->npieces) vtm::fail(VTM_ERR_INVALID, "bad partition or piece index");
+    const int64_t c0 = p->piece_ptr[j], c1 = p->piece_ptr[j + 1];
+    const int64_t k0 = p->l_rowptr[c0], k1 = p->l_rowptr[c1];
+    if (n_j) *n_j = c1 - c0;
+    if (nnz_j) *nnz_j = k1 - k0;
+    if (vertices) std::memcpy(vertices, p->copy_vertex.data() + c0, (c1 - c0) * sizeof(int64_t));
+    if (shares) std::memcpy(shares, p->copy_share.data() + c0, (c1 - c0) * sizeof(double));
+    if (rowptr)
+      for (int64_t c = c0; c <= c1; ++c) rowptr[c - c0] = p->l_rowptr[c] - k0;
+    if (col) std::memcpy(col, p->l_col.data() + k0, (k1 - k0) * sizeof(int32_t));
+    if (val) std::memcpy(val, p->l_val.data() + k0, (k1 - k0) * sizeof(double));
+    return VTM_OK;
+  });
+}
+
+int vtm_partition_get_lines(const vtm_partition* p, int64_t* quads) {
+  return guarded([&] {
+    if (!p || !quads) vtm::fail(VTM_ERR_INVALID, "null argument");
+    auto piece_of = [&](int64_t c) {
+      return (int64_t)(std::upper_bound(p->piece_ptr.begin(), p->piece_ptr.end(), c) - p->piece_ptr.begin() - 1);
+    };
+    for (size_t t = 0; t < p->line_a.size(); ++t) {
+      const int64_t a = p->line_a[t], b = p->line_b[t];
+      const int64_t ja = piece_of(a), jb = piece_of(b);
+      quads[4 * t + 0] = ja;
+      quads[4 * t + 1] = a - p->piece_ptr[ja];
+      quads[4 * t + 2] = jb;
+      quads[4 * t + 3] = b - p->piece_ptr[jb];
+    }
+    return VTM_OK;
+  });
+}
+
+void vtm_partition_destroy(vtm_partition* p) { delete p; }
+
+int vtm_setup(const vtm_partition* p, const vtm_setup_opts* opts, void* cuda_stream, vtm_solver** out) {
+  return guarded([&] {
+    if (!out) vtm::fail(VTM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    *out = vtm::create_solver(p, opts, cuda_stream);
+    return VTM_OK;
+  });
+}
+
+int vtm_solver_get_info(const vtm_solver* s, vtm_solver_info* info) {
+  return guarded([&] {
+    if (!s || !info) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::solver_get_info(s, info);
+    return VTM_OK;
+  });
+}
+
+void vtm_solver_destroy(vtm_solver* s) {
+  if (s) vtm::solver_destroy(s);
+}
+
+int vtm_set_rhs(vtm_solver* s, const double* b, int64_t ldb) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_set_rhs(s, b, ldb);
+    return VTM_OK;
+  });
+}
+
+int vtm_reset(vtm_solver* s) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::reset_waves(s);
+    return VTM_OK;
+  });
+}
+
+int vtm_iterate(vtm_solver* s, int32_t sweeps) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_iterate(s, sweeps);
+    return VTM_OK;
+  });
+}
+
+int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int32_t maxit, vtm_stats* st) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    return vtm::solver_solve(s, b, x, ld, rtol, maxit, st);
+  });
+}
+
+int vtm_get_state(vtm_solver* s, double* waves) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_get_state(s, waves);
+    return VTM_OK;
+  });
+}
+
+int vtm_set_state(vtm_solver* s, const double* waves) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_set_state(s, waves);
+    return VTM_OK;
+  });
+}
+
+int vtm_get_copies(vtm_solver* s, double* copies) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_get_copies(s, copies);
+    return VTM_OK;
+  });
+}
+
+const char* vtm_last_error(void) { return vtm::g_last_error.c_str(); }
+
+int vtm_version(void) { return VTM_VERSION_MAJOR * 100 + VTM_VERSION_MINOR; }
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Device-side layout shared by the CUDA kernels of libvtm (sm_103a).
+//
+// Band storage of a subgraph's factor (eq. 5.8, factored once, §8): n_pad rows (n_j rounded up to
+// kNB with identity rows), each row Wp entries, RIGHT-aligned so that entry p of row i holds
+// column i - (Wp-1) + p (p = Wp-1 is the diagonal).  Columns left of the band (or negative) hold
+// zeros.  After the factorisation every kNB x kNB diagonal block holds the INVERSE of the
+// Cholesky block L_KK (lower triangular), so the substitution is matrix-vector work only.
+// Wp >= kNB so that a full diagonal block always fits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vtm {
+
+constexpr int kNB = 32;            // rows per block (slab) of the substitution and factorisation
+constexpr int kSweepThreads = 256; // 8 threads per slab row
+
+// Status word written by kernels (0 = ok); values are vtm_status codes.
+constexpr int kStatusNotSpd = 4;
+constexpr int kStatusTimeout = 7;
+
+struct PieceDesc {
+  int64_t factor_off;  // element offset of row 0 of this piece's band
+  int64_t copy_off;    // first copy (global copy id) of the piece
+  int32_t n;           // local unknowns n_j
+  int32_t n_pad;       // n_j rounded up to kNB
+  int32_t Wp;          // stored row width (>= w_j + 1, >= kNB)
+  int32_t w;           // half-bandwidth w_j
+  int32_t port_off;    // first port (index into port arrays)
+  int32_t nports;
+  int32_t end_off;     // first (sorted) line end of the piece
+  int32_t nends;
+};
+
+// ------------------------------------------------------------------ PTX wrappers (sm_90+)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// 1D bulk copy global -> shared (TMA engine), completion counted on `bar` in bytes.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (each poll may suspend the
+// thread for a hardware-defined slice), returning false so that the caller can record a timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long limit) {
+  for (long it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_g8(T v) {
+  // sum over the 8 consecutive lanes of a group (lane bits 0..2)
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+}  // namespace vtm

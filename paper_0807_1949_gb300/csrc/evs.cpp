@@ -1,0 +1,405 @@
+// Electric Vertex Splitting (§4 steps 1-4, App. 2) — host implementation behind vtm_partition_evs.
+//
+// Split rule (the paper leaves the shares open, §4 "plenty of ways"): an edge (i,j) goes to every
+// subgraph of O(i)∩O(j) with weight a_ij/|O(i)∩O(j)|; a boundary copy gets
+// sum_{j!=i}|a_ij^(c)| + delta_i/|O(i)|, delta_i = a_ii - sum_{j!=i}|a_ij| (weak diagonal
+// dominance keeps every piece SNND, Cor. 4.1); inner vertices keep a_ii; b_i is shared equally.
+// Grid lines follow the hypercube of Fig. 7.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "internal.h"
+
+namespace {
+
+using vtm::fail;
+
+constexpr double kExcessTol = 64.0 * 2.220446049250313e-16;
+
+double boundary_excess(double aii, double offabs) {
+  double d = aii - offabs;
+  if (d < 0) {
+    if (d >= -kExcessTol * std::fabs(aii)) return 0.0;
+    fail(VTM_ERR_NOT_CONFORMAL, "boundary vertex is not weakly diagonally dominant (delta_i < 0)");
+  }
+  return d;
+}
+
+void copy_and_check_matrix(const vtm_csr* A, vtm_partition* p) {
+  if (!A || A->n <= 0 || !A->rowptr || !A->col || !A->val) fail(VTM_ERR_INVALID, "A: null or empty matrix");
+  const int64_t n = A->n;
+  if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) fail(VTM_ERR_INVALID, "A: rowptr inconsistent with nnz");
+  p->n = n;
+  p->a_rowptr.assign(A->rowptr, A->rowptr + n + 1);
+  p->a_col.assign(A->col, A->col + A->nnz);
+  p->a_val.assign(A->val, A->val + A->nnz);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t lo = A->rowptr[i], hi = A->rowptr[i + 1];
+    if (hi < lo) fail(VTM_ERR_INVALID, "A: rowptr not monotone");
+    bool diag = false;
+    for (int64_t k = lo; k < hi; ++k) {
+      int32_t j = A->col[k];
+      if (j < 0 || j >= n) fail(VTM_ERR_INVALID, "A: column index out of range");
+      if (k > lo && A->col[k - 1] >= j) fail(VTM_ERR_INVALID, "A: columns not strictly ascending in a row");
+      if (j == i) {
+        diag = true;
+        if (!(A->val[k] > 0)) fail(VTM_ERR_INVALID, "A: non-positive diagonal");
+        continue;
+      }
+      // symmetric partner
+      const int32_t* b = A->col + A->rowptr[j];
+      const int32_t* e = A->col + A->rowptr[j + 1];
+      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+      if (f == e || *f != i || A->val[A->rowptr[j] + (f - b)] != A->val[k])
+        fail(VTM_ERR_NOT_SYMMETRIC, "A is not symmetric");
+    }
+    if (!diag) fail(VTM_ERR_INVALID, "A: missing diagonal entry");
+  }
+}
+
+template <class F>
+void parallel_for(int64_t count, F&& f) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (count < 64 || nt == 1) {
+    for (int64_t i = 0; i < count; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::vector<vtm::Error> errs(nt);
+  std::vector<char> bad(nt, 0);
+  for (unsigned t = 0; t < nt; ++t) {
+    th.emplace_back([&, t] {
+      try {
+        for (int64_t i = t; i < count; i += nt) f(i);
+      } catch (const vtm::Error& e) {
+        errs[t] = e;
+        bad[t] = 1;
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+  for (unsigned t = 0; t < nt; ++t)
+    if (bad[t]) throw errs[t];
+}
+
+// ----------------------------------------------------------------------------------- GRID
+
+struct Axis {
+  int m = 1, s = 1, nb = 1;
+  // blocks containing coordinate c form the range [lo(c), hi(c)]
+  // block q covers [q*s, min((q+1)*s, m-1)]; a cut coordinate c = q*s (q >= 1) is shared by
+  // blocks q-1 and q when block q exists.
+  int lo(int c) const {
+    int q = c / s;
+    return (c % s == 0 && c > 0) ? q - 1 : std::min(q, nb - 1);
+  }
+  int hi(int c) const {
+    int q = c / s;
+    if (c % s == 0 && c > 0) return q <= nb - 1 ? q : q - 1;
+    return std::min(q, nb - 1);
+  }
+  int lo_of_block(int q) const { return q * s; }
+  int hi_of_block(int q) const { return std::min((q + 1) * s, m - 1); }
+};
+
+void build_grid(const vtm_partition_spec* sp, vtm_partition* p) {
+  Axis ax[3];
+  int64_t nn = 1;
+  for (int a = 0; a < 3; ++a) {
+    int m = sp->dims[a], s = sp->block[a];
+    if (m < 1 || s < 1) fail(VTM_ERR_INVALID, "grid: dims and block must be >= 1");
+    ax[a].m = m;
+    ax[a].s = s;
+    ax[a].nb = (m > 1) ? (int)((m - 1 + s - 1) / s) : 1;
+    if (ax[a].nb < 1) ax[a].nb = 1;
+    nn *= m;
+  }
+  if (nn != p->n) fail(VTM_ERR_INVALID, "grid: dims do not match n");
+  const int nx = ax[0].m, ny = ax[1].m;
+  const int Bx = ax[0].nb, By = ax[1].nb, Bz = ax[2].nb;
+  const int64_t np = (int64_t)Bx * By * Bz;
+  if (np > INT32_MAX) fail(VTM_ERR_INVALID, "grid: too many blocks");
+  p->npieces = (int32_t)np;
+  // copies per piece
+  p->piece_ptr.assign(np + 1, 0);
+  std::vector<int> ext(np * 3), org(np * 3);
+  for (int64_t j = 0; j < np; ++j) {
+    int q[3] = {(int)(j % Bx), (int)((j / Bx) % By), (int)(j / ((int64_t)Bx * By))};
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      org[j * 3 + a] = ax[a].lo_of_block(q[a]);
+      ext[j * 3 + a] = ax[a].hi_of_block(q[a]) - org[j * 3 + a] + 1;
+      cnt *= ext[j * 3 + a];
+    }
+    p->piece_ptr[j + 1] = p->piece_ptr[j] + cnt;
+  }
+  const int64_t C = p->piece_ptr[np];
+  p->copy_vertex.resize(C);
+  p->copy_share.resize(C);
+  auto nown = [&](int x, int y, int z) {
+    return (int64_t)(ax[0].hi(x) - ax[0].lo(x) + 1) * (ax[1].hi(y) - ax[1].lo(y) + 1) * (ax[2].hi(z) - ax[2].lo(z) + 1);
+  };
+  auto common1 = [&](const Axis& A, int c, int d) {
+    int lo = std::max(A.lo(c), A.lo(d)), hi = std::min(A.hi(c), A.hi(d));
+    return hi >= lo ? hi - lo + 1 : 0;
+  };
+  // pass 1: row counts
+  std::vector<int64_t> rowcnt(C + 1, 0);
+  parallel_for(np, [&](int64_t j) {
+    const int* o = &org[j * 3];
+    const int* e = &ext[j * 3];
+    int64_t c = p->piece_ptr[j];
+    for (int z = 0; z < e[2]; ++z)
+      for (int y = 0; y < e[1]; ++y)
+        for (int x = 0; x < e[0]; ++x, ++c) {
+          int gx = o[0] + x, gy = o[1] + y, gz = o[2] + z;
+          int64_t v = gx + (int64_t)nx * (gy + (int64_t)ny * gz);
+          p->copy_vertex[c] = v;
+          p->copy_share[c] = 1.0 / (double)nown(gx, gy, gz);
+          int64_t cnt = 0;
+          for (int64_t k = p->a_rowptr[v]; k < p->a_rowptr[v + 1]; ++k) {
+            int64_t u = p->a_col[k];
+            if (u == v) { ++cnt; continue; }
+            int ux = (int)(u % nx), uy = (int)((u / nx) % ny), uz = (int)(u / ((int64_t)nx * ny));
+            if (ux >= o[0] && ux < o[0] + e[0] && uy >= o[1] && uy < o[1] + e[1] && uz >= o[2] && uz < o[2] + e[2]) ++cnt;
+          }
+          rowcnt[c + 1] = cnt;
+        }
+  });
+  p->l_rowptr.resize(C + 1);
+  p->l_rowptr[0] = 0;
+  for (int64_t c = 0; c < C; ++c) p->l_rowptr[c + 1] = p->l_rowptr[c] + rowcnt[c + 1];
+  p->l_col.resize(p->l_rowptr[C]);
+  p->l_val.resize(p->l_rowptr[C]);
+  // pass 2: values (step 3)
+  parallel_for(np, [&](int64_t j) {
+    const int* o = &org[j * 3];
+    const int* e = &ext[j * 3];
+    for (int64_t c = p->piece_ptr[j]; c < p->piece_ptr[j + 1]; ++c) {
+      int64_t v = p->copy_vertex[c];
+      int gx = (int)(v % nx), gy = (int)((v / nx) % ny), gz = (int)(v / ((int64_t)nx * ny));
+      int64_t nv = nown(gx, gy, gz);
+      int64_t pos = p->l_rowptr[c];
+      int64_t diagpos = -1;
+      double offabs = 0.0, inpiece = 0.0, aii = 0.0;
+      for (int64_t k = p->a_rowptr[v]; k < p->a_rowptr[v + 1]; ++k) {
+        int64_t u = p->a_col[k];
+        double a = p->a_val[k];
+        if (u == v) {
+          aii = a;
+          diagpos = pos;
+          p->l_col[pos++] = (int32_t)(c - p->piece_ptr[j]);
+          continue;
+        }
+        offabs += std::fabs(a);
+        int ux = (int)(u % nx), uy = (int)((u / nx) % ny), uz = (int)(u / ((int64_t)nx * ny));
+        int64_t cm = (int64_t)common1(ax[0], gx, ux) * common1(ax[1], gy, uy) * common1(ax[2], gz, uz);
+        if (cm == 0) fail(VTM_ERR_INVALID, "grid: an edge of A lies in no common block");
+        if (ux >= o[0] && ux < o[0] + e[0] && uy >= o[1] && uy < o[1] + e[1] && uz >= o[2] && uz < o[2] + e[2]) {
+          double sh = a / (double)cm;
+          int32_t lc = (ux - o[0]) + e[0] * ((uy - o[1]) + e[1] * (uz - o[2]));
+          p->l_col[pos] = lc;
+          p->l_val[pos++] = sh;
+          inpiece += std::fabs(sh);
+        }
+      }
+      if (nv == 1) p->l_val[diagpos] = aii;
+      else p->l_val[diagpos] = inpiece + boundary_excess(aii, offabs) / (double)nv;
+    }
+  });
+  // step 4: hypercube lines; and boundary count
+  int64_t nbnd = 0;
+  auto copy_id = [&](int qx, int qy, int qz, int gx, int gy, int gz) {
+    int64_t j = qx + (int64_t)Bx * (qy + (int64_t)By * qz);
+    const int* o = &org[j * 3];
+    const int* e = &ext[j * 3];
+    return p->piece_ptr[j] + (gx - o[0]) + (int64_t)e[0] * ((gy - o[1]) + (int64_t)e[1] * (gz - o[2]));
+  };
+  for (int gz = 0; gz < ax[2].m; ++gz)
+    for (int gy = 0; gy < ax[1].m; ++gy)
+      for (int gx = 0; gx < ax[0].m; ++gx) {
+        int lo[3] = {ax[0].lo(gx), ax[1].lo(gy), ax[2].lo(gz)};
+        int hi[3] = {ax[0].hi(gx), ax[1].hi(gy), ax[2].hi(gz)};
+        if (lo[0] == hi[0] && lo[1] == hi[1] && lo[2] == hi[2]) continue;
+        ++nbnd;
+        for (int a = 0; a < 3; ++a) {
+          if (lo[a] == hi[a]) continue;
+          int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+          for (int q1 = lo[b1]; q1 <= hi[b1]; ++q1)
+            for (int q2 = lo[b2]; q2 <= hi[b2]; ++q2) {
+              int qa[3], qb[3];
+              qa[a] = lo[a];
+              qb[a] = hi[a];
+              qa[b1] = qb[b1] = q1;
+              qa[b2] = qb[b2] = q2;
+              p->line_a.push_back(copy_id(qa[0], qa[1], qa[2], gx, gy, gz));
+              p->line_b.push_back(copy_id(qb[0], qb[1], qb[2], gx, gy, gz));
+            }
+        }
+      }
+  p->nboundary = nbnd;
+}
+
+// ----------------------------------------------------------------------------------- OWNERS
+
+void build_owners(const vtm_partition_spec* sp, vtm_partition* p) {
+  const int64_t n = p->n;
+  const int32_t np = sp->npieces;
+  if (np < 1 || !sp->owner_ptr || !sp->owner_piece) fail(VTM_ERR_INVALID, "owners: missing owner sets");
+  if (sp->owner_ptr[0] != 0) fail(VTM_ERR_INVALID, "owners: owner_ptr[0] != 0");
+  p->npieces = np;
+  std::vector<std::vector<int64_t>> verts(np);
+  int64_t nbnd = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t lo = sp->owner_ptr[i], hi = sp->owner_ptr[i + 1];
+    if (hi <= lo) fail(VTM_ERR_INVALID, "owners: a vertex has no owner");
+    if (hi - lo > 1) ++nbnd;
+    for (int64_t k = lo; k < hi; ++k) {
+      int32_t q = sp->owner_piece[k];
+      if (q < 0 || q >= np || (k > lo && sp->owner_piece[k - 1] >= q)) fail(VTM_ERR_INVALID, "owners: bad or unsorted owner list");
+      verts[q].push_back(i);
+    }
+  }
+  p->nboundary = nbnd;
+  p->piece_ptr.assign(np + 1, 0);
+  for (int32_t q = 0; q < np; ++q) p->piece_ptr[q + 1] = p->piece_ptr[q] + (int64_t)verts[q].size();
+  const int64_t C = p->piece_ptr[np];
+  p->copy_vertex.resize(C);
+  p->copy_share.resize(C);
+  auto owners = [&](int64_t i) { return std::make_pair(sp->owner_piece + sp->owner_ptr[i], sp->owner_piece + sp->owner_ptr[i + 1]); };
+  auto local_of = [&](int32_t q, int64_t v) -> int64_t {
+    auto& vs = verts[q];
+    auto it = std::lower_bound(vs.begin(), vs.end(), v);
+    if (it == vs.end() || *it != v) return -1;
+    return it - vs.begin();
+  };
+  auto ncommon = [&](int64_t i, int64_t j) {
+    auto a = owners(i), b = owners(j);
+    int64_t c = 0;
+    const int32_t *x = a.first, *y = b.first;
+    while (x < a.second && y < b.second) {
+      if (*x == *y) { ++c; ++x; ++y; }
+      else if (*x < *y) ++x;
+      else ++y;
+    }
+    return c;
+  };
+  std::vector<int64_t> rowcnt(C + 1, 0);
+  for (int32_t q = 0; q < np; ++q)
+    for (size_t l = 0; l < verts[q].size(); ++l) {
+      int64_t c = p->piece_ptr[q] + (int64_t)l, v = verts[q][l];
+      p->copy_vertex[c] = v;
+      p->copy_share[c] = 1.0 / (double)(sp->owner_ptr[v + 1] - sp->owner_ptr[v]);
+      int64_t cnt = 0;
+      for (int64_t k = p->a_rowptr[v]; k < p->a_rowptr[v + 1]; ++k)
+        if (p->a_col[k] == v || local_of(q, p->a_col[k]) >= 0) ++cnt;
+      rowcnt[c + 1] = cnt;
+    }
+  p->l_rowptr.resize(C + 1);
+  p->l_rowptr[0] = 0;
+  for (int64_t c = 0; c < C; ++c) p->l_rowptr[c + 1] = p->l_rowptr[c] + rowcnt[c + 1];
+  p->l_col.resize(p->l_rowptr[C]);
+  p->l_val.resize(p->l_rowptr[C]);
+  for (int32_t q = 0; q < np; ++q)
+    for (size_t l = 0; l < verts[q].size(); ++l) {
+      int64_t c = p->piece_ptr[q] + (int64_t)l, v = verts[q][l];
+      int64_t nv = sp->owner_ptr[v + 1] - sp->owner_ptr[v];
+      int64_t pos = p->l_rowptr[c], diagpos = -1;
+      double offabs = 0, inpiece = 0, aii = 0;
+      for (int64_t k = p->a_rowptr[v]; k < p->a_rowptr[v + 1]; ++k) {
+        int64_t u = p->a_col[k];
+        double a = p->a_val[k];
+        if (u == v) {
+          aii = a;
+          diagpos = pos;
+          p->l_col[pos++] = (int32_t)l;
+          continue;
+        }
+        offabs += std::fabs(a);
+        int64_t cm = ncommon(v, u);
+        if (cm == 0) fail(VTM_ERR_INVALID, "owners: an edge of A lies in no common subgraph");
+        int64_t lu = local_of(q, u);
+        if (lu >= 0) {
+          double sh = a / (double)cm;
+          p->l_col[pos] = (int32_t)lu;
+          p->l_val[pos++] = sh;
+          inpiece += std::fabs(sh);
+        }
+      }
+      p->l_val[diagpos] = (nv == 1) ? aii : inpiece + boundary_excess(aii, offabs) / (double)nv;
+    }
+  for (int64_t t = 0; t < sp->nlines; ++t) {
+    int64_t v = sp->line_vertex[t];
+    if (v < 0 || v >= n) fail(VTM_ERR_INVALID, "owners: line vertex out of range");
+    int32_t qa = sp->line_piece_a[t], qb = sp->line_piece_b[t];
+    if (qa < 0 || qa >= np || qb < 0 || qb >= np || qa == qb) fail(VTM_ERR_INVALID, "owners: bad line pieces");
+    int64_t la = local_of(qa, v), lb = local_of(qb, v);
+    if (la < 0 || lb < 0) fail(VTM_ERR_INVALID, "owners: line joins a copy that does not exist");
+    p->line_a.push_back(p->piece_ptr[qa] + la);
+    p->line_b.push_back(p->piece_ptr[qb] + lb);
+  }
+}
+
+// ----------------------------------------------------------------------------------- EXPLICIT
+
+void build_explicit(const vtm_partition_spec* sp, vtm_partition* p) {
+  const int32_t np = sp->npieces;
+  if (np < 1 || !sp->piece_ptr || !sp->copy_vertex || !sp->copy_share || !sp->local_rowptr || !sp->local_col || !sp->local_val)
+    fail(VTM_ERR_INVALID, "explicit: missing arrays");
+  p->npieces = np;
+  p->piece_ptr.assign(sp->piece_ptr, sp->piece_ptr + np + 1);
+  if (p->piece_ptr[0] != 0) fail(VTM_ERR_INVALID, "explicit: piece_ptr[0] != 0");
+  for (int32_t q = 0; q < np; ++q)
+    if (p->piece_ptr[q + 1] < p->piece_ptr[q]) fail(VTM_ERR_INVALID, "explicit: piece_ptr not monotone");
+  const int64_t C = p->piece_ptr[np];
+  p->copy_vertex.assign(sp->copy_vertex, sp->copy_vertex + C);
+  p->copy_share.assign(sp->copy_share, sp->copy_share + C);
+  p->l_rowptr.assign(sp->local_rowptr, sp->local_rowptr + C + 1);
+  if (p->l_rowptr[0] != 0) fail(VTM_ERR_INVALID, "explicit: local_rowptr[0] != 0");
+  const int64_t nnz = p->l_rowptr[C];
+  p->l_col.assign(sp->local_col, sp->local_col + nnz);
+  p->l_val.assign(sp->local_val, sp->local_val + nnz);
+  std::vector<int64_t> cnt(p->n, 0);
+  for (int32_t q = 0; q < np; ++q) {
+    int64_t nq = p->piece_ptr[q + 1] - p->piece_ptr[q];
+    for (int64_t c = p->piece_ptr[q]; c < p->piece_ptr[q + 1]; ++c) {
+      if (p->copy_vertex[c] < 0 || p->copy_vertex[c] >= p->n) fail(VTM_ERR_INVALID, "explicit: copy vertex out of range");
+      cnt[p->copy_vertex[c]]++;
+      for (int64_t k = p->l_rowptr[c]; k < p->l_rowptr[c + 1]; ++k)
+        if (p->l_col[k] < 0 || p->l_col[k] >= nq) fail(VTM_ERR_INVALID, "explicit: local column out of range");
+    }
+  }
+  int64_t nbnd = 0;
+  for (int64_t i = 0; i < p->n; ++i) {
+    if (cnt[i] == 0) fail(VTM_ERR_INVALID, "explicit: a vertex has no copy");
+    if (cnt[i] > 1) ++nbnd;
+  }
+  p->nboundary = nbnd;
+  for (int64_t t = 0; t < sp->ncopy_lines; ++t) {
+    int64_t a = sp->line_copy_a[t], b = sp->line_copy_b[t];
+    if (a < 0 || a >= C || b < 0 || b >= C || a == b || p->copy_vertex[a] != p->copy_vertex[b])
+      fail(VTM_ERR_INVALID, "explicit: a line must join two copies of the same vertex");
+    p->line_a.push_back(a);
+    p->line_b.push_back(b);
+  }
+}
+
+}  // namespace
+
+namespace vtm {
+void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition* p) {
+  if (!spec) fail(VTM_ERR_INVALID, "null partition spec");
+  copy_and_check_matrix(A, p);
+  switch (spec->kind) {
+    case VTM_PART_GRID: build_grid(spec, p); break;
+    case VTM_PART_OWNERS: build_owners(spec, p); break;
+    case VTM_PART_EXPLICIT: build_explicit(spec, p); break;
+    default: fail(VTM_ERR_INVALID, "unknown partition kind");
+  }
+  // every copy that has a line must sit in a piece; pieces must be non-empty
+  for (int32_t q = 0; q < p->npieces; ++q)
+    if (p->piece_ptr[q + 1] == p->piece_ptr[q]) fail(VTM_ERR_INVALID, "a subgraph is empty");
+}
+}  // namespace vtm

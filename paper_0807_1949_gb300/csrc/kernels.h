@@ -1,0 +1,67 @@
+// Host-callable launchers of the libvtm CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "device.cuh"
+
+namespace vtm {
+
+// Arguments of one VTM sweep (Table 1 steps 3-5) over all subgraphs.
+template <typename T>
+struct SweepArgs {
+  const PieceDesc* pieces;
+  const T* factor;             // band factors (see device.cuh)
+  const T* bt;                 // b̃: copies x R, R contiguous
+  T* xc;                       // local solutions: copies x R (written when write_x)
+  const T* wprev;              // outgoing waves of the previous sweep: ends x R
+  T* wnext;                    // outgoing waves of this sweep
+  const int32_t* port_local;   // per port: local row of the port copy
+  const int32_t* port_end_ptr; // per port: first (sorted) end; nports_total + 1 entries
+  const int32_t* twin;         // per end: the twin end of the same line
+  const T* invz;               // per end: 1 / Z_e
+  int* status;                 // kernel status word (0 = ok)
+  int write_x;
+  int stages;                  // staged slabs in flight (>= 2)
+  int slot_elems;              // ring slot stride in elements (kNB * max Wp)
+  int ys_elems;                // (max Wp - 1 + max n_pad) * R
+  int win_elems;               // (max ends per piece) * R
+  long wait_limit;             // bounded mbarrier polls before a timeout is recorded
+};
+
+size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
+template <typename T>
+cudaError_t sweep_configure(int R, size_t smem);
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+
+// Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T into the (zeroed) band storage (eq. 5.8).
+template <typename T>
+cudaError_t launch_build_band(int64_t ncopies, const int32_t* copy_piece, const PieceDesc* pieces,
+                              const int64_t* l_rowptr, const int32_t* l_col, const double* l_val,
+                              const int32_t* port_of_copy, const int32_t* port_end_ptr, const double* invz,
+                              int npieces, int max_pad_rows, T* band, int* status, cudaStream_t st);
+// Banded Cholesky of every K_j in place; each diagonal block replaced by its inverse.
+template <typename T>
+cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, cudaStream_t st);
+
+// b̃_c = share_c * src[vertex(c)]  (§4 step 3), into T precision, R contiguous.
+template <typename T>
+cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, const double* share,
+                         const double* src, int64_t ld, T* bt, cudaStream_t st);
+// xt[i] = xbase[i] + mean over the copies of i of xc (xbase may be NULL).
+template <typename T>
+cudaError_t launch_assemble(int64_t n, int R, const int64_t* vc_ptr, const int64_t* vc_copy, const T* xc,
+                            const double* xbase, double* xt, int64_t ld, cudaStream_t st);
+// res = b - A x (res may be NULL); norms[r] += ||res_r||^2.
+cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
+                            const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
+                            double* norms, cudaStream_t st);
+// norms[r] += ||v_r||^2
+cudaError_t launch_sqnorm(int64_t n, int R, const double* v, int64_t ld, double* norms, cudaStream_t st);
+// dst[i + r*ldd] = src[i + r*lds]
+cudaError_t launch_copy2d(int64_t n, int R, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st);
+
+}  // namespace vtm

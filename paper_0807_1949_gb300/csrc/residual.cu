@@ -1,0 +1,153 @@
+// Vector kernels around the sweeps: source splitting (§4 step 3), assembly of the solution from the
+// copies (mean of the copies; at the fixed point all copies agree, Thm 4.1), and the FP64 residual
+// b - A x with per-right-hand-side squared norms (the convergence test of Table 1 step 6).
+#include "kernels.h"
+
+namespace vtm {
+
+namespace {
+constexpr int kMaxR = 8;
+constexpr int kBS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of R values per thread, accumulated into norms[r] with one atomic per block.
+__device__ void block_accumulate(const double* v, int R, double* norms) {
+  __shared__ double red[kBS / 32][kMaxR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r) {
+    if (r >= R) break;
+    const double s = warp_sum(v[r]);
+    if (lane == 0) red[warp][r] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) {
+      if (r >= R) break;
+      double s = lane < kBS / 32 ? red[lane][r] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) atomicAdd(&norms[r], s);
+    }
+  }
+}
+}  // namespace
+
+template <typename T>
+__global__ void k_split(int64_t ncopies, int R, const int64_t* __restrict__ copy_vertex, const double* __restrict__ share,
+                        const double* __restrict__ src, int64_t ld, T* __restrict__ bt) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncopies) return;
+  const int64_t v = copy_vertex[c];
+  const double s = share[c];
+  for (int r = 0; r < R; ++r) bt[c * R + r] = (T)(s * src[v + r * ld]);
+}
+
+template <typename T>
+__global__ void k_assemble(int64_t n, int R, const int64_t* __restrict__ vc_ptr, const int64_t* __restrict__ vc_copy,
+                           const T* __restrict__ xc, const double* __restrict__ xbase, double* __restrict__ xt, int64_t ld) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t lo = vc_ptr[i], hi = vc_ptr[i + 1];
+  const double inv = 1.0 / (double)(hi - lo);
+  for (int r = 0; r < R; ++r) {
+    double s = 0.0;
+    for (int64_t k = lo; k < hi; ++k) s += (double)xc[vc_copy[k] * R + r];
+    xt[i + r * ld] = (xbase ? xbase[i + r * ld] : 0.0) + s * inv;
+  }
+}
+
+__global__ void k_residual(int64_t n, int R, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ b, int64_t ldb,
+                           const double* __restrict__ x, int64_t ldx, double* __restrict__ res, int64_t ldr,
+                           double* norms) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double sq[kMaxR];
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r) sq[r] = 0.0;
+  if (i < n) {
+    const int64_t lo = rowptr[i], hi = rowptr[i + 1];
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) {
+      if (r >= R) break;
+      double ax = 0.0;
+      for (int64_t k = lo; k < hi; ++k) ax += val[k] * x[col[k] + r * ldx];
+      const double ri = b[i + r * ldb] - ax;
+      if (res) res[i + r * ldr] = ri;
+      sq[r] = ri * ri;
+    }
+  }
+  block_accumulate(sq, R, norms);
+}
+
+__global__ void k_sqnorm(int64_t n, int R, const double* __restrict__ v, int64_t ld, double* norms) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double sq[kMaxR];
+#pragma unroll
+  for (int r = 0; r < kMaxR; ++r) sq[r] = 0.0;
+  if (i < n)
+#pragma unroll
+    for (int r = 0; r < kMaxR; ++r) {
+      if (r >= R) break;
+      const double t = v[i + r * ld];
+      sq[r] = t * t;
+    }
+  block_accumulate(sq, R, norms);
+}
+
+__global__ void k_copy2d(int64_t n, int R, const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int r = 0; r < R; ++r) dst[i + r * ldd] = src[i + r * lds];
+}
+
+static unsigned nblocks(int64_t n) { return (unsigned)((n + kBS - 1) / kBS); }
+
+template <typename T>
+cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, const double* share, const double* src,
+                         int64_t ld, T* bt, cudaStream_t st) {
+  if (ncopies > 0) k_split<T><<<nblocks(ncopies), kBS, 0, st>>>(ncopies, R, copy_vertex, share, src, ld, bt);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_assemble(int64_t n, int R, const int64_t* vc_ptr, const int64_t* vc_copy, const T* xc,
+                            const double* xbase, double* xt, int64_t ld, cudaStream_t st) {
+  k_assemble<T><<<nblocks(n), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
+                            const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
+                            double* norms, cudaStream_t st) {
+  if (R > kMaxR) return cudaErrorInvalidValue;
+  k_residual<<<nblocks(n), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqnorm(int64_t n, int R, const double* v, int64_t ld, double* norms, cudaStream_t st) {
+  if (R > kMaxR) return cudaErrorInvalidValue;
+  k_sqnorm<<<nblocks(n), kBS, 0, st>>>(n, R, v, ld, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(int64_t n, int R, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st) {
+  k_copy2d<<<nblocks(n), kBS, 0, st>>>(n, R, src, lds, dst, ldd);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_split<float>(int64_t, int, const int64_t*, const double*, const double*, int64_t, float*,
+                                         cudaStream_t);
+template cudaError_t launch_split<double>(int64_t, int, const int64_t*, const double*, const double*, int64_t, double*,
+                                          cudaStream_t);
+template cudaError_t launch_assemble<float>(int64_t, int, const int64_t*, const int64_t*, const float*, const double*,
+                                            double*, int64_t, cudaStream_t);
+template cudaError_t launch_assemble<double>(int64_t, int, const int64_t*, const int64_t*, const double*,
+                                             const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace vtm

@@ -1,0 +1,611 @@
+// Solver setup and drivers behind vtm_setup / vtm_iterate / vtm_solve (host side).
+//
+// Setup (Table 1 steps 1-2, eq. 5.8): plan the band layout of every subgraph, sort the line ends
+// by subgraph and port, upload Ã_j, assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T on the device and
+// factor it once.  Iteration (Table 1 steps 3-5): one k_sweep launch per sweep, ping-ponging the
+// two wave buffers (the N2N exchange is the twin-indexed read of the previous buffer).
+// Solve: sweeps plus the FP64 residual every check_every sweeps; FP32 solvers restart the sweeps
+// on the FP64 residual (defect correction) once the inner residual has dropped enough or stalls.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace vtm {
+
+#define VTM_CUDA(call)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) fail(VTM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  void alloc(size_t b) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = b;
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      fail(e == cudaErrorMemoryAllocation ? VTM_ERR_OOM : VTM_ERR_CUDA,
+           std::string("cudaMalloc(") + std::to_string(b) + "): " + cudaGetErrorString(e));
+    }
+  }
+  void swap(DevBuf& o) {
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+  }
+  template <class U>
+  U* as() const {
+    return static_cast<U*>(p);
+  }
+};
+
+template <class U>
+static void upload(DevBuf& d, const std::vector<U>& h, cudaStream_t st) {
+  d.alloc(h.size() * sizeof(U));
+  if (!h.empty()) VTM_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(U), cudaMemcpyHostToDevice, st));
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace vtm
+
+using namespace vtm;
+
+struct vtm_solver {
+  int precision = VTM_FP64;
+  int R = 1;
+  int check_every = 10;
+  double inner_reduction = 1e-4;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0, C = 0, E = 0;
+  int32_t npieces = 0, nports = 0;
+  size_t elem = 8;
+
+  DevBuf pieces, factor, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status;
+  DevBuf a_rowptr, a_col, a_val, vc_ptr, vc_copy, copy_vertex, share;
+  DevBuf vb, vx, vxt, vr, vrt, norms;
+  double* h_norms = nullptr;  // pinned: [R] residual^2, [R] b^2 ... plus status
+  int cur = 0;                // wave buffer holding the last outgoing waves
+  bool have_copies = false;
+  int64_t launches = 0;       // kernels launched since creation (for accounting)
+
+  std::vector<int32_t> api_to_int;  // end 2t+side -> internal (sorted) end
+  int stages = 2;
+  size_t sweep_smem = 0;
+  int slot_elems = 0, ys_elems = 0, win_elems = 0;
+  long wait_limit = 1L << 22;
+  vtm_solver_info info{};
+
+  ~vtm_solver() {
+    if (h_norms) cudaFreeHost(h_norms);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace vtm {
+
+static void check_status(vtm_solver* s) {
+  int st = 0;
+  VTM_CUDA(cudaMemcpyAsync(&st, s->status.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+  if (st == kStatusTimeout) fail(VTM_ERR_TIMEOUT, "a bounded device wait ran out in the sweep kernel");
+  if (st == kStatusNotSpd) fail(VTM_ERR_NOT_SPD, "a local matrix K_j had a non-positive Cholesky pivot");
+  if (st != 0) fail(VTM_ERR_INVALID, "device status " + std::to_string(st));
+}
+
+template <typename T>
+static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s) {
+  cudaStream_t st = s->stream;
+  const int32_t np = p->npieces;
+  const int64_t C = p->piece_ptr[np];
+  const int64_t nl = (int64_t)p->line_a.size();
+  s->n = p->n;
+  s->C = C;
+  s->E = 2 * nl;
+  s->npieces = np;
+  s->elem = sizeof(T);
+
+  // ---- impedances per line
+  std::vector<double> Z(nl);
+  for (int64_t t = 0; t < nl; ++t) {
+    double z = (o->z_mode == VTM_Z_EXPLICIT) ? o->z_lines[t] : o->z_uniform;
+    if (!(z > 0) || !std::isfinite(z)) fail(VTM_ERR_INVALID, "line impedances must be positive and finite");
+    Z[t] = z;
+  }
+
+  // ---- ends sorted by (copy, line, side); copies are grouped by subgraph in local order
+  std::vector<int64_t> end_copy(2 * nl);
+  for (int64_t t = 0; t < nl; ++t) {
+    end_copy[2 * t] = p->line_a[t];
+    end_copy[2 * t + 1] = p->line_b[t];
+  }
+  std::vector<int32_t> order(2 * nl);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return end_copy[a] < end_copy[b]; });
+  s->api_to_int.assign(2 * nl, 0);
+  for (int64_t k = 0; k < 2 * nl; ++k) s->api_to_int[order[k]] = (int32_t)k;
+  std::vector<int32_t> twin(2 * nl);
+  std::vector<double> invz(2 * nl);
+  for (int64_t k = 0; k < 2 * nl; ++k) {
+    const int32_t api = order[k];
+    twin[k] = s->api_to_int[api ^ 1];
+    invz[k] = 1.0 / Z[api >> 1];
+  }
+  // ports: distinct copies among the sorted ends
+  std::vector<int32_t> port_local, port_end_ptr;
+  std::vector<int32_t> port_of_copy(C, -1);
+  std::vector<int32_t> copy_piece(C);
+  for (int32_t j = 0; j < np; ++j)
+    for (int64_t c = p->piece_ptr[j]; c < p->piece_ptr[j + 1]; ++c) copy_piece[c] = j;
+  std::vector<PieceDesc> pd(np);
+  for (int32_t j = 0; j < np; ++j) {
+    pd[j].nports = 0;
+    pd[j].nends = 0;
+    pd[j].port_off = 0;
+    pd[j].end_off = 0;
+  }
+  {
+    int64_t k = 0;
+    int32_t lastpiece = -1;
+    while (k < 2 * nl) {
+      const int64_t c = end_copy[order[k]];
+      const int32_t j = copy_piece[c];
+      if (j != lastpiece) {
+        pd[j].port_off = (int32_t)port_local.size();
+        pd[j].end_off = (int32_t)k;
+        lastpiece = j;
+      }
+      port_of_copy[c] = (int32_t)port_local.size();
+      port_local.push_back((int32_t)(c - p->piece_ptr[j]));
+      port_end_ptr.push_back((int32_t)k);
+      int64_t k2 = k;
+      while (k2 < 2 * nl && end_copy[order[k2]] == c) ++k2;
+      pd[j].nports++;
+      pd[j].nends += (int32_t)(k2 - k);
+      k = k2;
+    }
+    port_end_ptr.push_back((int32_t)(2 * nl));
+  }
+  s->nports = (int32_t)port_local.size();
+  // pieces without ports still need a valid port_off/end_off
+  for (int32_t j = 0; j < np; ++j)
+    if (pd[j].nports == 0) {
+      pd[j].port_off = 0;
+      pd[j].end_off = 0;
+    }
+
+  // ---- band layout
+  const int wmod = (sizeof(T) == 4) ? 32 : 16, wrem = (sizeof(T) == 4) ? 8 : 4;
+  int64_t foff = 0, band_entries = 0;
+  int max_w = 0, max_Wp = 0, max_pad = 0, max_ends = 0;
+  for (int32_t j = 0; j < np; ++j) {
+    const int64_t n_j = p->piece_ptr[j + 1] - p->piece_ptr[j];
+    if (n_j > (1 << 30)) fail(VTM_ERR_INVALID, "subgraph too large");
+    int w = 0;
+    for (int64_t c = p->piece_ptr[j]; c < p->piece_ptr[j + 1]; ++c) {
+      const int64_t l = c - p->piece_ptr[j];
+      for (int64_t k = p->l_rowptr[c]; k < p->l_rowptr[c + 1]; ++k) w = std::max<int64_t>(w, std::llabs(l - p->l_col[k]));
+    }
+    int Wp = std::max(w + 1, kNB);
+    while (Wp % wmod != wrem) ++Wp;
+    const int n_pad = (int)((n_j + kNB - 1) / kNB) * kNB;
+    pd[j].factor_off = foff;
+    pd[j].copy_off = p->piece_ptr[j];
+    pd[j].n = (int32_t)n_j;
+    pd[j].n_pad = n_pad;
+    pd[j].Wp = Wp;
+    pd[j].w = w;
+    foff += (int64_t)n_pad * Wp;
+    band_entries += n_j * (w + 1) - (int64_t)w * (w + 1) / 2;
+    max_w = std::max(max_w, w);
+    max_Wp = std::max(max_Wp, Wp);
+    max_pad = std::max(max_pad, n_pad);
+    max_ends = std::max(max_ends, pd[j].nends);
+  }
+
+  // ---- sweep shared-memory plan
+  const int R = s->R;
+  s->slot_elems = kNB * max_Wp;
+  s->ys_elems = (max_Wp - 1 + max_pad) * R;
+  s->win_elems = std::max(1, max_ends) * R;
+  const size_t kSmemMax = 227 * 1024;
+  int stages = 4;
+  while (stages >= 2 && sweep_smem_bytes(sizeof(T), R, stages, s->slot_elems, s->ys_elems, s->win_elems) > kSmemMax) --stages;
+  if (stages < 2)
+    fail(VTM_ERR_INVALID, "a subgraph is too large for the shared-memory sweep (n_j, bandwidth or nrhs too big)");
+  s->stages = stages;
+  s->sweep_smem = sweep_smem_bytes(sizeof(T), R, stages, s->slot_elems, s->ys_elems, s->win_elems);
+  VTM_CUDA(sweep_configure<T>(R, s->sweep_smem));
+
+  // ---- vertex -> copies (for assembly)
+  std::vector<int64_t> vc_ptr(p->n + 1, 0), vc_copy(C);
+  for (int64_t c = 0; c < C; ++c) vc_ptr[p->copy_vertex[c] + 1]++;
+  for (int64_t i = 0; i < p->n; ++i) vc_ptr[i + 1] += vc_ptr[i];
+  {
+    std::vector<int64_t> fill(vc_ptr.begin(), vc_ptr.end() - 1);
+    for (int64_t c = 0; c < C; ++c) vc_copy[fill[p->copy_vertex[c]]++] = c;
+  }
+
+  // ---- device buffers
+  upload(s->pieces, pd, st);
+  upload(s->port_local, port_local, st);
+  upload(s->port_end_ptr, port_end_ptr, st);
+  upload(s->twin, twin, st);
+  {
+    std::vector<T> iz(invz.begin(), invz.end());
+    upload(s->invz_t, iz, st);
+  }
+  upload(s->a_rowptr, p->a_rowptr, st);
+  upload(s->a_col, p->a_col, st);
+  upload(s->a_val, p->a_val, st);
+  upload(s->vc_ptr, vc_ptr, st);
+  upload(s->vc_copy, vc_copy, st);
+  upload(s->copy_vertex, p->copy_vertex, st);
+  upload(s->share, p->copy_share, st);
+  s->status.alloc(sizeof(int));
+  VTM_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
+
+  // local matrices and factor
+  {
+    DevBuf d_piece, d_rowptr, d_col, d_val, d_poc, d_invz;
+    upload(d_piece, copy_piece, st);
+    upload(d_rowptr, p->l_rowptr, st);
+    upload(d_col, p->l_col, st);
+    upload(d_val, p->l_val, st);
+    upload(d_poc, port_of_copy, st);
+    upload(d_invz, invz, st);
+    s->factor.alloc((size_t)foff * sizeof(T));
+    VTM_CUDA(cudaMemsetAsync(s->factor.p, 0, (size_t)foff * sizeof(T), st));
+    VTM_CUDA(launch_build_band<T>(C, d_piece.as<int32_t>(), s->pieces.as<PieceDesc>(), d_rowptr.as<int64_t>(),
+                                  d_col.as<int32_t>(), d_val.as<double>(), d_poc.as<int32_t>(),
+                                  s->port_end_ptr.as<int32_t>(), d_invz.as<double>(), np, max_pad,
+                                  s->factor.as<T>(), s->status.as<int>(), st));
+    cudaEvent_t e0, e1;
+    VTM_CUDA(cudaEventCreate(&e0));
+    VTM_CUDA(cudaEventCreate(&e1));
+    VTM_CUDA(cudaEventRecord(e0, st));
+    cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), np, max_w, s->factor.as<T>(), s->status.as<int>(), st);
+    VTM_CUDA(cudaEventRecord(e1, st));
+    VTM_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (fe == cudaErrorInvalidValue) fail(VTM_ERR_INVALID, "bandwidth too large for the factorisation kernel");
+    VTM_CUDA(fe);
+    s->info.factor_ms = ms;
+    check_status(s);
+  }
+
+  // vectors
+  s->bt.alloc((size_t)C * R * sizeof(T));
+  s->xc.alloc((size_t)C * R * sizeof(T));
+  for (int b = 0; b < 2; ++b) {
+    s->w[b].alloc((size_t)std::max<int64_t>(1, s->E) * R * sizeof(T));
+    VTM_CUDA(cudaMemsetAsync(s->w[b].p, 0, s->w[b].bytes, st));
+  }
+  VTM_CUDA(cudaMemsetAsync(s->bt.p, 0, s->bt.bytes, st));
+  VTM_CUDA(cudaMemsetAsync(s->xc.p, 0, s->xc.bytes, st));
+  const size_t nv = (size_t)p->n * R * sizeof(double);
+  s->vb.alloc(nv);
+  s->vx.alloc(nv);
+  s->vxt.alloc(nv);
+  s->vr.alloc(nv);
+  s->vrt.alloc(nv);
+  s->norms.alloc(4 * 8 * sizeof(double));
+  VTM_CUDA(cudaMallocHost(&s->h_norms, 4 * 8 * sizeof(double)));
+  VTM_CUDA(cudaStreamSynchronize(st));
+
+  s->info.npieces = np;
+  s->info.ncopies = C;
+  s->info.nends = s->E;
+  s->info.nrhs = R;
+  s->info.precision = s->precision;
+  s->info.block_rows = kNB;
+  s->info.factor_entries = foff;
+  s->info.band_entries = band_entries;
+  s->info.factor_bytes = foff * (int64_t)sizeof(T);
+  s->info.max_halfband = max_w;
+}
+
+template <typename T>
+static SweepArgs<T> sweep_args(vtm_solver* s, int write_x) {
+  SweepArgs<T> a;
+  a.pieces = s->pieces.as<PieceDesc>();
+  a.factor = s->factor.as<T>();
+  a.bt = s->bt.as<T>();
+  a.xc = s->xc.as<T>();
+  a.wprev = s->w[s->cur].as<T>();
+  a.wnext = s->w[s->cur ^ 1].as<T>();
+  a.port_local = s->port_local.as<int32_t>();
+  a.port_end_ptr = s->port_end_ptr.as<int32_t>();
+  a.twin = s->twin.as<int32_t>();
+  a.invz = s->invz_t.as<T>();
+  a.status = s->status.as<int>();
+  a.write_x = write_x;
+  a.stages = s->stages;
+  a.slot_elems = s->slot_elems;
+  a.ys_elems = s->ys_elems;
+  a.win_elems = s->win_elems;
+  a.wait_limit = s->wait_limit;
+  return a;
+}
+
+template <typename T>
+static void sweeps_typed(vtm_solver* s, int k) {
+  for (int i = 0; i < k; ++i) {
+    SweepArgs<T> a = sweep_args<T>(s, i == k - 1);
+    VTM_CUDA(launch_sweep<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
+    s->cur ^= 1;
+    s->launches++;
+  }
+  if (k > 0) s->have_copies = true;
+}
+
+void run_sweeps(vtm_solver* s, int k) {
+  if (s->precision == VTM_FP32) sweeps_typed<float>(s, k);
+  else sweeps_typed<double>(s, k);
+}
+
+void reset_waves(vtm_solver* s) {
+  for (int b = 0; b < 2; ++b) VTM_CUDA(cudaMemsetAsync(s->w[b].p, 0, s->w[b].bytes, s->stream));
+  s->cur = 0;
+  s->have_copies = false;
+}
+
+static void split_rhs(vtm_solver* s, const double* src, int64_t ld) {
+  s->launches++;
+  if (s->precision == VTM_FP32)
+    VTM_CUDA(launch_split<float>(s->C, s->R, s->copy_vertex.as<int64_t>(), s->share.as<double>(), src, ld,
+                                 s->bt.as<float>(), s->stream));
+  else
+    VTM_CUDA(launch_split<double>(s->C, s->R, s->copy_vertex.as<int64_t>(), s->share.as<double>(), src, ld,
+                                  s->bt.as<double>(), s->stream));
+}
+
+static void assemble(vtm_solver* s, const double* xbase, double* xt) {
+  s->launches++;
+  if (s->precision == VTM_FP32)
+    VTM_CUDA(launch_assemble<float>(s->n, s->R, s->vc_ptr.as<int64_t>(), s->vc_copy.as<int64_t>(),
+                                    s->xc.as<float>(), xbase, xt, s->n, s->stream));
+  else
+    VTM_CUDA(launch_assemble<double>(s->n, s->R, s->vc_ptr.as<int64_t>(), s->vc_copy.as<int64_t>(),
+                                     s->xc.as<double>(), xbase, xt, s->n, s->stream));
+}
+
+vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void* cuda_stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!p || !o) fail(VTM_ERR_INVALID, "null partition or options");
+  if (o->precision != VTM_FP32 && o->precision != VTM_FP64) fail(VTM_ERR_INVALID, "unknown precision");
+  if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8)) fail(VTM_ERR_INVALID, "nrhs must be 1, 2, 4 or 8");
+  if (o->z_mode != VTM_Z_UNIFORM && o->z_mode != VTM_Z_EXPLICIT) fail(VTM_ERR_INVALID, "unknown z_mode");
+  if (o->z_mode == VTM_Z_EXPLICIT && !o->z_lines && !p->line_a.empty()) fail(VTM_ERR_INVALID, "z_lines is NULL");
+  std::unique_ptr<vtm_solver> s(new vtm_solver());
+  s->precision = o->precision;
+  s->R = o->nrhs;
+  s->check_every = o->check_every > 0 ? o->check_every : 10;
+  s->inner_reduction = o->inner_reduction > 0 ? o->inner_reduction : 1e-4;
+  if (cuda_stream) {
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    VTM_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  if (s->precision == VTM_FP32) setup_typed<float>(p, o, s.get());
+  else setup_typed<double>(p, o, s.get());
+  s->info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return s.release();
+}
+
+void solver_set_rhs(vtm_solver* s, const double* b, int64_t ldb) {
+  if (!b || ldb < s->n) fail(VTM_ERR_INVALID, "b: null or ldb < n");
+  const double* src = b;
+  if (!is_device_ptr(b)) {
+    for (int r = 0; r < s->R; ++r)
+      VTM_CUDA(cudaMemcpyAsync(s->vb.as<double>() + r * s->n, b + r * ldb, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    src = s->vb.as<double>();
+    ldb = s->n;
+  }
+  split_rhs(s, src, ldb);
+}
+
+void solver_iterate(vtm_solver* s, int k) {
+  if (k < 0) fail(VTM_ERR_INVALID, "negative sweep count");
+  run_sweeps(s, k);
+}
+
+static void read_norms(vtm_solver* s, int cnt) {
+  VTM_CUDA(cudaMemcpyAsync(s->h_norms, s->norms.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int maxit, vtm_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = s->launches;
+  if (!b || !x || ld < s->n || !(rtol > 0) || maxit < 1) fail(VTM_ERR_INVALID, "vtm_solve: bad arguments");
+  const int R = s->R;
+  const int64_t n = s->n;
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  cudaStream_t st = s->stream;
+  double* db = s->vb.as<double>();
+  if (bdev) {
+    VTM_CUDA(launch_copy2d(n, R, b, ld, db, n, st));
+    s->launches++;
+  } else
+    for (int r = 0; r < R; ++r)
+      VTM_CUDA(cudaMemcpyAsync(db + r * n, b + r * ld, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  double* norms = s->norms.as<double>();
+  VTM_CUDA(cudaMemsetAsync(norms, 0, 2 * 8 * sizeof(double), st));
+  VTM_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
+  VTM_CUDA(launch_sqnorm(n, R, db, n, norms + 8, st));
+  VTM_CUDA(launch_copy2d(n, R, db, n, s->vr.as<double>(), n, st));
+  s->launches += 2;
+  read_norms(s, 16);
+  std::vector<double> bn(R);
+  for (int r = 0; r < R; ++r) bn[r] = std::sqrt(s->h_norms[8 + r]) > 0 ? std::sqrt(s->h_norms[8 + r]) : 1.0;
+
+  double* xacc = s->vx.as<double>();   // accepted solution
+  double* xt = s->vxt.as<double>();    // trial solution
+  double* rcur = s->vr.as<double>();   // residual the current inner solve works on
+  double* rt = s->vrt.as<double>();    // trial residual
+  VTM_CUDA(cudaMemsetAsync(xacc, 0, n * R * sizeof(double), st));
+  std::vector<double> rcur_norm(bn);
+  split_rhs(s, rcur, n);
+  reset_waves(s);
+
+  const bool refine = (s->precision == VTM_FP32);
+  const int m = s->check_every;
+  int sweeps = 0, checks = 0, restarts = 0, inner_sweeps = 0;
+  double prev_inner = INFINITY, rel = INFINITY;
+  int status = VTM_ERR_NOT_CONVERGED;
+  bool trial_fresh = false;  // xt holds the assembled iterate of the last check
+  while (sweeps < maxit) {
+    const int k = std::min(m, maxit - sweeps);
+    run_sweeps(s, k);
+    sweeps += k;
+    inner_sweeps += k;
+    assemble(s, xacc, xt);
+    VTM_CUDA(cudaMemsetAsync(norms, 0, 8 * sizeof(double), st));
+    VTM_CUDA(launch_residual(n, R, s->a_rowptr.as<int64_t>(), s->a_col.as<int32_t>(), s->a_val.as<double>(), db, n,
+                             xt, n, rt, n, norms, st));
+    s->launches++;
+    read_norms(s, 8);
+    ++checks;
+    check_status(s);
+    rel = 0;
+    double inner = 0;
+    bool bad = false;
+    for (int r = 0; r < R; ++r) {
+      const double rn = std::sqrt(s->h_norms[r]);
+      if (!std::isfinite(rn)) bad = true;
+      rel = std::max(rel, rn / bn[r]);
+      inner = std::max(inner, rn / rcur_norm[r]);
+    }
+    if (bad) {
+      status = VTM_ERR_DIVERGED;
+      break;
+    }
+    trial_fresh = true;
+    if (rel <= rtol) {
+      s->vx.swap(s->vxt);
+      xacc = s->vx.as<double>();
+      status = VTM_OK;
+      break;
+    }
+    if (refine && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
+      // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
+      s->vx.swap(s->vxt);
+      s->vr.swap(s->vrt);
+      xacc = s->vx.as<double>();
+      xt = s->vxt.as<double>();
+      rcur = s->vr.as<double>();
+      rt = s->vrt.as<double>();
+      for (int r = 0; r < R; ++r) rcur_norm[r] = std::max(std::sqrt(s->h_norms[r]), 1e-300);
+      split_rhs(s, rcur, n);
+      reset_waves(s);
+      ++restarts;
+      inner_sweeps = 0;
+      prev_inner = INFINITY;
+      trial_fresh = false;
+      continue;
+    }
+    prev_inner = inner;
+  }
+  if (status != VTM_OK && trial_fresh) {
+    // return the iterate of the last check
+    s->vx.swap(s->vxt);
+    xacc = s->vx.as<double>();
+  }
+  if (xdev) {
+    VTM_CUDA(launch_copy2d(n, R, xacc, n, x, ld, st));
+    s->launches++;
+  } else
+    for (int r = 0; r < R; ++r)
+      VTM_CUDA(cudaMemcpyAsync(x + r * ld, xacc + r * n, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VTM_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->sweeps = sweeps;
+    stats->checks = checks;
+    stats->restarts = restarts;
+    stats->rel_residual = rel;
+    stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = (int32_t)(s->launches - launches0);
+  }
+  if (status == VTM_ERR_NOT_CONVERGED) set_last_error("vtm_solve: maxit reached before rtol");
+  if (status == VTM_ERR_DIVERGED) set_last_error("vtm_solve: residual is not finite");
+  return status;
+}
+
+template <typename T>
+static void get_state_typed(vtm_solver* s, double* waves) {
+  std::vector<T> h((size_t)s->E * s->R);
+  VTM_CUDA(cudaMemcpyAsync(h.data(), s->w[s->cur].p, h.size() * sizeof(T), cudaMemcpyDeviceToHost, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+  for (int64_t e = 0; e < s->E; ++e)
+    for (int r = 0; r < s->R; ++r) waves[e + r * s->E] = (double)h[(size_t)s->api_to_int[e] * s->R + r];
+}
+
+template <typename T>
+static void set_state_typed(vtm_solver* s, const double* waves) {
+  std::vector<T> h((size_t)s->E * s->R);
+  for (int64_t e = 0; e < s->E; ++e)
+    for (int r = 0; r < s->R; ++r) h[(size_t)s->api_to_int[e] * s->R + r] = (T)waves[e + r * s->E];
+  VTM_CUDA(cudaMemcpyAsync(s->w[s->cur].p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+template <typename T>
+static void get_copies_typed(vtm_solver* s, double* out) {
+  std::vector<T> h((size_t)s->C * s->R);
+  VTM_CUDA(cudaMemcpyAsync(h.data(), s->xc.p, h.size() * sizeof(T), cudaMemcpyDeviceToHost, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+  for (int64_t c = 0; c < s->C; ++c)
+    for (int r = 0; r < s->R; ++r) out[c + r * s->C] = (double)h[(size_t)c * s->R + r];
+}
+
+void solver_get_state(vtm_solver* s, double* waves) {
+  if (!waves) fail(VTM_ERR_INVALID, "null waves");
+  if (s->precision == VTM_FP32) get_state_typed<float>(s, waves);
+  else get_state_typed<double>(s, waves);
+}
+void solver_set_state(vtm_solver* s, const double* waves) {
+  if (!waves) fail(VTM_ERR_INVALID, "null waves");
+  if (s->precision == VTM_FP32) set_state_typed<float>(s, waves);
+  else set_state_typed<double>(s, waves);
+}
+void solver_get_copies(vtm_solver* s, double* out) {
+  if (!out) fail(VTM_ERR_INVALID, "null output");
+  if (!s->have_copies) fail(VTM_ERR_INVALID, "no sweep has run since the last reset");
+  if (s->precision == VTM_FP32) get_copies_typed<float>(s, out);
+  else get_copies_typed<double>(s, out);
+}
+void solver_get_info(const vtm_solver* s, vtm_solver_info* info) { *info = s->info; }
+void solver_destroy(vtm_solver* s) { delete s; }
+
+}  // namespace vtm

@@ -1,0 +1,226 @@
+// One VTM sweep over all subgraphs (Table 1 steps 3-5; eq. 5.6, 5.8), one CTA per subgraph.
+//
+// Per subgraph j the CTA
+//   1. gathers the incident wave of each line end from its twin, w_in[e] = w_prev[twin(e)]
+//      (the N2N exchange), and forms r_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8 right side);
+//   2. streams the band factor of K_j from HBM in kNB-row slabs with the TMA bulk-copy engine
+//      (cp.async.bulk into a ring of shared-memory stages tracked by mbarriers) and runs the
+//      forward substitution L y = r (dot-product form) and the back substitution L^T x = y
+//      (column/axpy form) with the diagonal blocks stored as inverses;
+//   3. emits w_out[e] = 2 x_c - w_in[e] for every end (u - Z omega of eq. 5.6, written as the
+//      single wave that the twin receives next sweep).
+// The vector state of the subgraph (y / x, n_pad + Wp - 1 rows x R) stays in shared memory.
+#include "kernels.h"
+
+namespace vtm {
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const PieceDesc pd = a.pieces[blockIdx.x];
+  const int S = a.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  T* ring = reinterpret_cast<T*>(smem + 128);
+  T* ys = ring + (size_t)S * a.slot_elems;
+  T* win = ys + a.ys_elems;
+  T* tb = win + a.win_elems;
+
+  const int Wp = pd.Wp;
+  const int off = Wp - 1;  // ys row of column 0
+  const int nblk = pd.n_pad / kNB;
+  const int total = 2 * nblk;
+  const uint32_t slab_bytes = (uint32_t)(kNB * Wp * sizeof(T));
+  const T* fbase = a.factor + pd.factor_off;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  auto issue = [&](int s) {
+    const int kb = s < nblk ? s : total - 1 - s;
+    const int slot = s % S;
+    mbar_arrive_expect_tx(&bars[slot], slab_bytes);
+    bulk_copy_g2s(ring + (size_t)slot * a.slot_elems, fbase + (size_t)kb * kNB * Wp, slab_bytes, &bars[slot]);
+  };
+  if (tid == 0)
+    for (int s = 0; s < S && s < total; ++s) issue(s);
+
+  // ---- prologue: r_j = b̃_j + sum_e w_in[e] / Z_e at the port rows
+  for (int i = tid; i < off * R; i += kSweepThreads) ys[i] = T(0);
+  const T* btp = a.bt + (size_t)pd.copy_off * R;
+  for (int i = tid; i < pd.n_pad * R; i += kSweepThreads) ys[(size_t)off * R + i] = (i < pd.n * R) ? btp[i] : T(0);
+  __syncthreads();
+  for (int q = tid; q < pd.nports; q += kSweepThreads) {
+    const int l = a.port_local[pd.port_off + q];
+    const int e0 = a.port_end_ptr[pd.port_off + q], e1 = a.port_end_ptr[pd.port_off + q + 1];
+    T acc[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
+    for (int e = e0; e < e1; ++e) {
+      const int tw = a.twin[e];
+      const T iz = a.invz[e];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const T w = a.wprev[(size_t)tw * R + rr];
+        win[(e - pd.end_off) * R + rr] = w;
+        acc[rr] += w * iz;
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) ys[(size_t)(off + l) * R + rr] += acc[rr];
+  }
+  __syncthreads();
+
+  // ---- forward (s < nblk) then backward (s >= nblk) over the staged slabs
+  const int rg = tid >> 3, g = tid & 7;
+  int s = 0;
+  for (; s < total; ++s) {
+    const int slot = s % S;
+    if (!mbar_wait_bounded(&bars[slot], (uint32_t)((s / S) & 1), a.wait_limit)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const T* L = ring + (size_t)slot * a.slot_elems;
+    if (s < nblk) {
+      const int k0 = s * kNB;
+      // t_r = r_r - sum_{col < k0} L[r][col] y_col
+      const T* Lr = L + rg * Wp;
+      const int pend = off - rg;
+      const T* yb = ys + (size_t)(k0 + rg) * R;
+      T acc[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
+      for (int p = g; p < pend; p += 8) {
+        const T l = Lr[p];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc[rr] += l * yb[(size_t)p * R + rr];
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = warp_sum_g8(acc[rr]);
+      if (g == 0)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) tb[rg * R + rr] = ys[(size_t)(k0 + rg + off) * R + rr] - acc[rr];
+      __syncthreads();
+      // y_B = inv(L_KK) t
+      T acc2[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc2[rr] = T(0);
+      for (int c = g; c <= rg; c += 8) {
+        const T l = Lr[off - rg + c];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc2[rr] += l * tb[c * R + rr];
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc2[rr] = warp_sum_g8(acc2[rr]);
+      if (g == 0)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + rg + off) * R + rr] = acc2[rr];
+    } else {
+      const int k0 = (total - 1 - s) * kNB;
+      // x_B = inv(L_KK)^T y_B      (thread (rg = column c, g))
+      T acc[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
+      for (int r = rg + g; r < kNB; r += 8) {
+        const T l = L[r * Wp + off - r + rg];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc[rr] += l * ys[(size_t)(k0 + r + off) * R + rr];
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] = warp_sum_g8(acc[rr]);
+      if (g == 0)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) tb[rg * R + rr] = acc[rr];
+      __syncthreads();
+      if (tid < kNB)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + tid + off) * R + rr] = tb[tid * R + rr];
+      // y_col -= sum_r L[k0 + r][col] x_r for the Wp-1 columns left of the block
+      for (int co = tid; co < off; co += kSweepThreads) {
+        T acc3[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc3[rr] = T(0);
+        const int rmax = co < kNB - 1 ? co : kNB - 1;
+        for (int r = 0; r <= rmax; ++r) {
+          const T l = L[r * Wp + co - r];
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) acc3[rr] += l * tb[r * R + rr];
+        }
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + co) * R + rr] -= acc3[rr];
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && s + S < total) {
+      fence_proxy_async_smem();
+      issue(s + S);
+    }
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      atomicExch(a.status, kStatusTimeout);
+      // drain the copies still in flight (bounded) before the CTA leaves
+      for (int s2 = s; s2 < total && s2 < s + S; ++s2)
+        mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), a.wait_limit);
+    }
+    return;
+  }
+
+  // ---- epilogue: w_out[e] = 2 x_c - w_in[e]; local solution
+  for (int q = tid; q < pd.nports; q += kSweepThreads) {
+    const int l = a.port_local[pd.port_off + q];
+    const int e0 = a.port_end_ptr[pd.port_off + q], e1 = a.port_end_ptr[pd.port_off + q + 1];
+    for (int e = e0; e < e1; ++e)
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+        a.wnext[(size_t)e * R + rr] = T(2) * ys[(size_t)(off + l) * R + rr] - win[(e - pd.end_off) * R + rr];
+  }
+  if (a.write_x) {
+    T* xp = a.xc + (size_t)pd.copy_off * R;
+    for (int i = tid; i < pd.n * R; i += kSweepThreads) xp[i] = ys[(size_t)off * R + i];
+  }
+}
+
+size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems) {
+  return 128 + elem * ((size_t)stages * slot_elems + ys_elems + win_elems + (size_t)kNB * R);
+}
+
+template <typename T, int R>
+static cudaError_t configure_one(size_t smem) {
+  return cudaFuncSetAttribute(k_sweep<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+cudaError_t sweep_configure(int R, size_t smem) {
+  switch (R) {
+    case 1: return configure_one<T, 1>(smem);
+    case 2: return configure_one<T, 2>(smem);
+    case 4: return configure_one<T, 4>(smem);
+    case 8: return configure_one<T, 8>(smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+  dim3 grid(npieces), block(kSweepThreads);
+  switch (R) {
+    case 1: k_sweep<T, 1><<<grid, block, smem, st>>>(a); break;
+    case 2: k_sweep<T, 2><<<grid, block, smem, st>>>(a); break;
+    case 4: k_sweep<T, 4><<<grid, block, smem, st>>>(a); break;
+    case 8: k_sweep<T, 8><<<grid, block, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t sweep_configure<float>(int, size_t);
+template cudaError_t sweep_configure<double>(int, size_t);
+template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, size_t, cudaStream_t);
+
+}  // namespace vtm

@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libvtm (include/vtm.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch is used by callers for
+device memory and streams; device tensors are passed as raw pointers (``tensor.data_ptr()``) and
+streams as ``torch.cuda.Stream.cuda_stream``.  Importing this module loads the library and fails
+loudly when it has not been built (``python -m paper_0807_1949_gb300.build``).
+
+The names mirror the C ABI: ``partition_evs`` -> ``vtm_partition_evs``, ``Solver`` wraps
+``vtm_setup`` / ``vtm_iterate`` / ``vtm_solve`` / ``vtm_get_state`` ... .
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libvtm.so")
+
+VTM_OK = 0
+STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SYMMETRIC", 3: "NOT_CONFORMAL", 4: "NOT_SPD", 5: "NOT_CONVERGED",
+          6: "DIVERGED", 7: "TIMEOUT", 8: "CUDA", 9: "OOM"}
+PART_GRID, PART_OWNERS, PART_EXPLICIT = 1, 2, 3
+Z_UNIFORM, Z_EXPLICIT = 0, 1
+FP64, FP32 = 0, 1
+
+
+class VTMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vtm error {code} ({STATUS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _CSR(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class _Spec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dims", C.c_int32 * 3), ("block", C.c_int32 * 3), ("npieces", C.c_int32),
+                ("owner_ptr", C.c_void_p), ("owner_piece", C.c_void_p), ("nlines", C.c_int64),
+                ("line_vertex", C.c_void_p), ("line_piece_a", C.c_void_p), ("line_piece_b", C.c_void_p),
+                ("piece_ptr", C.c_void_p), ("copy_vertex", C.c_void_p), ("copy_share", C.c_void_p),
+                ("local_rowptr", C.c_void_p), ("local_col", C.c_void_p), ("local_val", C.c_void_p),
+                ("ncopy_lines", C.c_int64), ("line_copy_a", C.c_void_p), ("line_copy_b", C.c_void_p)]
+
+
+class PartitionInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("npieces", C.c_int32), ("ncopies", C.c_int64), ("nlines", C.c_int64),
+                ("nboundary", C.c_int64), ("max_piece", C.c_int64)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("z_mode", C.c_int32), ("z_uniform", C.c_double), ("z_lines", C.c_void_p), ("precision", C.c_int32),
+                ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double)]
+
+
+class SolverInfo(C.Structure):
+    _fields_ = [("npieces", C.c_int32), ("ncopies", C.c_int64), ("nends", C.c_int64), ("nrhs", C.c_int32),
+                ("precision", C.c_int32), ("block_rows", C.c_int32), ("factor_entries", C.c_int64),
+                ("band_entries", C.c_int64), ("factor_bytes", C.c_int64), ("max_halfband", C.c_int64),
+                ("setup_ms", C.c_double), ("factor_ms", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("checks", C.c_int32), ("restarts", C.c_int32), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("launches", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libvtm.so is not built ({_LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_0807_1949_gb300.build")
+    try:  # make torch's CUDA runtime the one the library binds to, when torch is present
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    lib = C.CDLL(_LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "vtm_partition_evs": (C.c_int, [vp, vp, vp]),
+        "vtm_partition_get_info": (C.c_int, [vp, vp]),
+        "vtm_partition_get_piece": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "vtm_partition_get_lines": (C.c_int, [vp, vp]),
+        "vtm_partition_destroy": (None, [vp]),
+        "vtm_setup": (C.c_int, [vp, vp, vp, vp]),
+        "vtm_solver_get_info": (C.c_int, [vp, vp]),
+        "vtm_solver_destroy": (None, [vp]),
+        "vtm_set_rhs": (C.c_int, [vp, vp, i64]),
+        "vtm_reset": (C.c_int, [vp]),
+        "vtm_iterate": (C.c_int, [vp, i32]),
+        "vtm_solve": (C.c_int, [vp, vp, vp, i64, dbl, i32, vp]),
+        "vtm_get_state": (C.c_int, [vp, vp]),
+        "vtm_set_state": (C.c_int, [vp, vp]),
+        "vtm_get_copies": (C.c_int, [vp, vp]),
+        "vtm_last_error": (C.c_char_p, []),
+        "vtm_version": (C.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _check(code: int, allow=()):
+    if code != VTM_OK and code not in allow:
+        raise VTMError(code, _lib.vtm_last_error().decode())
+    return code
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+class Partition:
+    """Handle of a split electric graph (vtm_partition)."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.vtm_partition_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> PartitionInfo:
+        i = PartitionInfo()
+        _check(_lib.vtm_partition_get_info(self._h, C.byref(i)))
+        return i
+
+    def piece(self, j: int):
+        """(vertices, shares, local CSR (rowptr, col, val)) of subgraph j."""
+        nj, nnz = C.c_int64(), C.c_int64()
+        _check(_lib.vtm_partition_get_piece(self._h, j, C.byref(nj), C.byref(nnz), None, None, None, None, None))
+        v = np.empty(nj.value, np.int64)
+        s = np.empty(nj.value, np.float64)
+        rp = np.empty(nj.value + 1, np.int64)
+        col = np.empty(nnz.value, np.int32)
+        val = np.empty(nnz.value, np.float64)
+        _check(_lib.vtm_partition_get_piece(self._h, j, None, None, _ptr(v), _ptr(s), _ptr(rp), _ptr(col), _ptr(val)))
+        return v, s, (rp, col, val)
+
+    def lines(self) -> np.ndarray:
+        """(nlines, 4) int64: (piece_a, local_a, piece_b, local_b)."""
+        q = np.empty((self.info().nlines, 4), np.int64)
+        _check(_lib.vtm_partition_get_lines(self._h, _ptr(q)))
+        return q
+
+
+def _csr_struct(A):
+    rowptr, col, val = _arr(A.rowptr, np.int64), _arr(A.col, np.int32), _arr(A.val, np.float64)
+    s = _CSR(n=A.n, nnz=len(val), rowptr=rowptr.ctypes.data, col=col.ctypes.data, val=val.ctypes.data)
+    return s, (rowptr, col, val)
+
+
+def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, lines=None, explicit=None) -> Partition:
+    """vtm_partition_evs.  A: object with n, rowptr, col, val (inputs.CSR).
+
+    kind="grid":     dims=(nx, ny[, nz]), block=(sx, sy[, sz]).
+    kind="owners":   owners=list of sorted piece tuples per vertex, lines=[(vertex, pa, pb), ...].
+    kind="explicit": explicit=dict(piece_ptr, copy_vertex, copy_share, local_rowptr, local_col, local_val,
+                     line_copy_a, line_copy_b).
+    """
+    csr, keep = _csr_struct(A)
+    sp = _Spec()
+    hold = [keep]
+    if kind == "grid":
+        d = list(dims) + [1] * (3 - len(dims))
+        b = list(block) + [1] * (3 - len(block))
+        sp.kind = PART_GRID
+        sp.dims[:] = d
+        sp.block[:] = b
+    elif kind == "owners":
+        ptr = np.zeros(len(owners) + 1, np.int64)
+        ptr[1:] = np.cumsum([len(o) for o in owners])
+        pieces = _arr(np.concatenate([np.asarray(o, np.int32) for o in owners]), np.int32)
+        lv = _arr([t[0] for t in lines], np.int64)
+        la = _arr([t[1] for t in lines], np.int32)
+        lb = _arr([t[2] for t in lines], np.int32)
+        hold += [ptr, pieces, lv, la, lb]
+        sp.kind = PART_OWNERS
+        sp.npieces = int(pieces.max()) + 1
+        sp.owner_ptr, sp.owner_piece = ptr.ctypes.data, pieces.ctypes.data
+        sp.nlines, sp.line_vertex, sp.line_piece_a, sp.line_piece_b = len(lv), lv.ctypes.data, la.ctypes.data, lb.ctypes.data
+    elif kind == "explicit":
+        e = {k: v for k, v in explicit.items()}
+        arrs = dict(piece_ptr=_arr(e["piece_ptr"], np.int64), copy_vertex=_arr(e["copy_vertex"], np.int64),
+                    copy_share=_arr(e["copy_share"], np.float64), local_rowptr=_arr(e["local_rowptr"], np.int64),
+                    local_col=_arr(e["local_col"], np.int32), local_val=_arr(e["local_val"], np.float64),
+                    line_copy_a=_arr(e["line_copy_a"], np.int64), line_copy_b=_arr(e["line_copy_b"], np.int64))
+        hold.append(arrs)
+        sp.kind = PART_EXPLICIT
+        sp.npieces = len(arrs["piece_ptr"]) - 1
+        for k in ("piece_ptr", "copy_vertex", "copy_share", "local_rowptr", "local_col", "local_val",
+                  "line_copy_a", "line_copy_b"):
+            setattr(sp, k, arrs[k].ctypes.data)
+        sp.ncopy_lines = len(arrs["line_copy_a"])
+    else:
+        raise ValueError(kind)
+    h = C.c_void_p()
+    _check(_lib.vtm_partition_evs(C.byref(csr), C.byref(sp), C.byref(h)))
+    return Partition(h.value)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _data_ptr(x):
+    """(pointer, keepalive) of a torch tensor (host or device) or numpy array, float64 contiguous."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+            raise ValueError("tensors must be contiguous float64")
+        return C.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a.ctypes.data_as(C.c_void_p), a
+
+
+class Solver:
+    """vtm_setup / vtm_iterate / vtm_solve on one partition.
+
+    z: scalar (uniform) or per-line array (order of Partition.lines()).
+    precision: "fp64" or "fp32".  nrhs: 1, 2, 4 or 8.
+    Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
+    """
+
+    def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
+                 check_every: int = 10, inner_reduction: float = 0.0):
+        o = _Opts()
+        zarr = None
+        if np.ndim(z) == 0:
+            o.z_mode, o.z_uniform = Z_UNIFORM, float(z)
+        else:
+            zarr = _arr(z, np.float64)
+            o.z_mode, o.z_lines = Z_EXPLICIT, zarr.ctypes.data
+        o.precision = {"fp64": FP64, "fp32": FP32}[precision]
+        o.nrhs = nrhs
+        o.check_every = check_every
+        o.inner_reduction = inner_reduction
+        self.nrhs = nrhs
+        self.n = part.info().n
+        h = C.c_void_p()
+        _check(_lib.vtm_setup(part.handle, C.byref(o), _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self._zkeep = zarr
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.vtm_solver_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def info(self) -> SolverInfo:
+        i = SolverInfo()
+        _check(_lib.vtm_solver_get_info(self._h, C.byref(i)))
+        return i
+
+    def set_rhs(self, b):
+        p, keep = _data_ptr(b)
+        _check(_lib.vtm_set_rhs(self._h, p, self.n))
+
+    def reset(self):
+        _check(_lib.vtm_reset(self._h))
+
+    def iterate(self, sweeps: int):
+        _check(_lib.vtm_iterate(self._h, int(sweeps)))
+
+    def solve(self, b, x, rtol: float = 1e-10, maxit: int = 10000, raise_on_fail: bool = True) -> Stats:
+        pb, kb = _data_ptr(b)
+        px, kx = _data_ptr(x)
+        st = Stats()
+        code = _lib.vtm_solve(self._h, pb, px, self.n, float(rtol), int(maxit), C.byref(st))
+        if raise_on_fail:
+            _check(code)
+        st.status = code
+        return st
+
+    def get_state(self) -> np.ndarray:
+        """Outgoing waves of the last sweep, (nrhs, nends), end 2t / 2t+1 = sides a / b of line t."""
+        ne = self.info().nends
+        w = np.empty((self.nrhs, ne), np.float64)
+        _check(_lib.vtm_get_state(self._h, _ptr(w)))
+        return w
+
+    def set_state(self, waves):
+        w = _arr(waves, np.float64)
+        _check(_lib.vtm_set_state(self._h, _ptr(w)))
+
+    def copies(self) -> np.ndarray:
+        """Last local solutions, (nrhs, ncopies), copies piece by piece in local order."""
+        nc = self.info().ncopies
+        x = np.empty((self.nrhs, nc), np.float64)
+        _check(_lib.vtm_get_copies(self._h, _ptr(x)))
+        return x
+
+
+def version() -> int:
+    return _lib.vtm_version()

@@ -24,3 +24,14 @@ def load_golden(name):
 @pytest.fixture
 def golden():
     return load_golden
+
+
+@pytest.fixture(scope="session")
+def vtmlib():
+    """The built C-ABI library's Python binding (builds it in-tree with nvcc if missing)."""
+    from paper_0807_1949_gb300 import build as _build
+
+    _build.build()
+    from paper_0807_1949_gb300 import vtm
+
+    return vtm

@@ -1,0 +1,121 @@
+"""Host-side logic of the C-ABI library on CPU: exports, EVS partition parity with the oracle.
+
+vtm_partition_evs runs on the host only (no device crossing), so its split is compared here with
+the oracle's independent split, element by element.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import evs
+from paper_0807_1949_gb300 import inputs
+from conftest import ROOT
+
+
+def test_library_exports_every_declared_symbol(vtmlib):
+    hdr = open(os.path.join(ROOT, "include", "vtm.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(vtm_\w+)\s*\(", hdr, re.M))
+    assert {"vtm_partition_evs", "vtm_setup", "vtm_iterate", "vtm_solve"} <= declared
+    lib = vtmlib._lib
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert vtmlib.version() == 1
+
+
+def _local_dense(piece):
+    v, s, (rp, col, val) = piece
+    m = len(v)
+    return v, s, sp.csr_matrix((val, col, rp), shape=(m, m)).toarray()
+
+
+def _compare_split(part, osplit, atol=0.0):
+    info = part.info()
+    assert info.npieces == len(osplit.subgraphs)
+    for j, g in enumerate(osplit.subgraphs):
+        v, s, Aj = _local_dense(part.piece(j))
+        assert np.array_equal(v, g.vertices)
+        assert np.array_equal(s, g.share)
+        ref = g.A.toarray()
+        assert np.max(np.abs(Aj - ref)) <= atol * max(1.0, np.abs(ref).max()), j
+    lines = {tuple(q) for q in part.lines()}
+    olines = {tuple(int(x) for x in q) for q in osplit.vtl}
+    assert lines == olines
+
+
+def test_grid_config1_partition_matches_oracle(vtmlib):
+    A = inputs.grid_poisson((32, 32))
+    part = vtmlib.partition_evs(A, "grid", dims=(32, 32), block=(16, 16))
+    info = part.info()
+    assert (info.npieces, info.ncopies, info.nlines) == (4, 1089, 66)
+    _compare_split(part, evs.split_grid(A, (32, 32), (16, 16)), atol=0.0)
+
+
+@pytest.mark.parametrize("dims,block,sigma", [((9, 7, 6), (4, 3, 5), 0.7), ((10, 9, 9), (4, 4, 4), 1.5),
+                                               ((17, 5), (4, 2), 1.0), ((5, 5, 5), (2, 2, 2), 0.0)])
+def test_grid_partition_matches_oracle(vtmlib, dims, block, sigma):
+    A = inputs.grid_poisson(dims, sigma=sigma, seed=11)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    _compare_split(part, evs.split_grid(A, dims, block), atol=1e-15)
+
+
+def test_owner_partition_matches_oracle(vtmlib):
+    A = inputs.random_dd_spd(60, avg_degree=4, excess=0.2, seed=2)
+    rng = np.random.default_rng(2)
+    As = A.to_scipy()
+    home = rng.integers(0, 4, A.n)
+    home[:4] = np.arange(4)
+    owners = [tuple(sorted({int(home[i])} | {int(h) for h in home[As.indices[As.indptr[i]:As.indptr[i + 1]]]}))
+              for i in range(A.n)]
+    lines = [(i, p, q) for i, o in enumerate(owners) for a, p in enumerate(o) for q in o[a + 1:]]
+    part = vtmlib.partition_evs(A, "owners", owners=owners, lines=lines)
+    _compare_split(part, evs.split_by_owners(As, owners, lines), atol=1e-15)
+
+
+def example_explicit(golden):
+    g = golden("example_4_1.json")
+    gb = golden("example_3_1.json")
+    A = inputs.csr_from_dense(np.array(gb["A"], float))
+    b = np.array(gb["b"], float)
+    A1, A2 = sp.csr_matrix(np.array(g["A1"], float)), sp.csr_matrix(np.array(g["A2"], float))
+    blk = sp.block_diag([A1, A2]).tocsr()
+    # local columns: the block-diagonal column minus the piece's first copy
+    cols = blk.indices.copy()
+    cols[blk.indptr[4]:] -= 4
+    verts = np.array(g["vertices_1"] + g["vertices_2"])
+    share = np.concatenate([np.array(g["b1"]), np.array(g["b2"])]) / b[verts]
+    la = [4 * l[0] + l[1] for l in g["lines"]]
+    lb = [4 * l[2] + l[3] for l in g["lines"]]
+    spec = dict(piece_ptr=[0, 4, 8], copy_vertex=verts, copy_share=share, local_rowptr=blk.indptr,
+                local_col=cols, local_val=blk.data, line_copy_a=la, line_copy_b=lb)
+    return A, b, spec
+
+
+def test_explicit_partition_example_4_1(vtmlib, golden):
+    A, b, spec = example_explicit(golden)
+    part = vtmlib.partition_evs(A, "explicit", explicit=spec)
+    info = part.info()
+    assert (info.npieces, info.ncopies, info.nlines, info.nboundary) == (2, 8, 2, 2)
+    g = golden("example_4_1.json")
+    assert np.array_equal(_local_dense(part.piece(0))[2], np.array(g["A1"]))
+    assert np.array_equal(_local_dense(part.piece(1))[2], np.array(g["A2"]))
+
+
+def test_errors_are_reported(vtmlib):
+    A = inputs.grid_poisson((6, 6))
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(A, "grid", dims=(6, 5), block=(3, 3))
+    assert e.value.code == 1
+    # not symmetric
+    bad = inputs.CSR(n=A.n, rowptr=A.rowptr, col=A.col, val=A.val.copy())
+    bad.val[1] *= 2
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(bad, "grid", dims=(6, 6), block=(3, 3))
+    assert e.value.code == 2
+    # not conformal at a boundary vertex
+    D = np.array([[1.0, -2.0, 0], [-2.0, 5.0, -1.0], [0, -1.0, 2.0]])
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(inputs.csr_from_dense(D), "owners", owners=[(0, 1), (1,), (1,)], lines=[(0, 0, 1)])
+    assert e.value.code == 3
