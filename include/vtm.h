@@ -225,6 +225,31 @@ int vtm_get_state(vtm_solver* s, double* waves);
 int vtm_set_state(vtm_solver* s, const double* waves);
 int vtm_get_copies(vtm_solver* s, double* copies);
 
+/* ----------------------------------------------------------------------------------------------
+ * Allocation-free residual (the paper has no counterpart: this is a service for callers)
+ * --------------------------------------------------------------------------------------------*/
+
+/* Largest nrhs accepted by vtm_relative_residual_noalloc. */
+#define VTM_NOALLOC_MAX_RHS 8
+
+/* rel[r] = ||b_r - A x_r||_2 / ||b_r||_2 (||b_r - A x_r||_2 when b_r = 0) in FP64, for callers
+ * that must not allocate device memory when they call it — e.g. a monitoring thread in a process
+ * whose device memory is reserved up front by a framework's caching allocator, or a loop that
+ * cannot afford cudaMalloc/cudaFree synchronising the device.  It calls no allocating routine:
+ * its only scratch is a 128-byte file-scope device array (2 * VTM_NOALLOC_MAX_RHS doubles) that
+ * every device which loads the library holds until the process exits.
+ *   n, rowptr (n+1 int64), col (int32), val (double): A in full CSR, DEVICE memory.
+ *   b, x: DEVICE, column-major n x nrhs with leading dimensions ldb, ldx >= n.
+ *   rel: DEVICE, nrhs doubles (output).  nrhs in [1, VTM_NOALLOC_MAX_RHS], else VTM_ERR_INVALID.
+ * Asynchronous on cuda_stream.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call reuses the same array (cleared at the start of each call), so calls that
+ * overlap on the GPU — from two streams or two host threads — race and return wrong values:
+ * serialise them. */
+int vtm_relative_residual_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                                  int32_t nrhs, const double* b, int64_t ldb, const double* x, int64_t ldx,
+                                  double* rel, void* cuda_stream);
+
 const char* vtm_last_error(void);
 int vtm_version(void);
 

@@ -92,6 +92,7 @@ def _load():
         "vtm_get_state": (C.c_int, [vp, vp]),
         "vtm_set_state": (C.c_int, [vp, vp]),
         "vtm_get_copies": (C.c_int, [vp, vp]),
+        "vtm_relative_residual_noalloc": (C.c_int, [i64, vp, vp, vp, i32, vp, i64, vp, i64, vp, vp]),
         "vtm_last_error": (C.c_char_p, []),
         "vtm_version": (C.c_int, []),
     }
@@ -310,6 +311,21 @@ class Solver:
         x = np.empty((self.nrhs, nc), np.float64)
         _check(_lib.vtm_get_copies(self._h, _ptr(x)))
         return x
+
+
+def relative_residual_noalloc(rowptr, col, val, b, x, rel, stream=None):
+    """vtm_relative_residual_noalloc on device tensors: rel[r] = ||b_r - A x_r|| / ||b_r||.
+
+    For callers that must not allocate device memory at call time; the library uses a fixed
+    128-byte device array as its only scratch.  rowptr (int64), col (int32), val, b, x (float64,
+    shape (nrhs, n)) and rel (float64, nrhs) are CUDA tensors.  Asynchronous on ``stream``.
+    """
+    n = int(rowptr.numel()) - 1
+    nrhs = int(b.shape[0]) if b.dim() == 2 else 1
+    _check(_lib.vtm_relative_residual_noalloc(n, C.c_void_p(rowptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                              C.c_void_p(val.data_ptr()), nrhs, C.c_void_p(b.data_ptr()), n,
+                                              C.c_void_p(x.data_ptr()), n, C.c_void_p(rel.data_ptr()),
+                                              _stream_handle(stream)))
 
 
 def version() -> int:
