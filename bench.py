@@ -34,6 +34,8 @@ WORKLOADS = {
     # name: dims, block, sigma, rtol
     "poisson3d-128": dict(dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0, rtol=1e-8),
     "laplace2d-32": dict(dims=(32, 32), block=(16, 16), sigma=0.0, rtol=1e-8),
+    # small case of the same subgraph shape (64 subgraphs, 0.37 GB factor > L2) for ncu captures
+    "poisson3d-64": dict(dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, rtol=1e-8),
 }
 METRIC = "time to rel. residual 1e-8 (learned-Z batched vs plain VTM) on 1 GB300; HBM GB/s"
 
@@ -359,7 +361,8 @@ def run_vtm(args):
                    "l2": "inputs larger than L2 (FP32 factor %.2f GB)" % (sinfo.factor_bytes / 1e9),
                    "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,
                    "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
-                   "partition_ms": round(t_part * 1e3, 1), "plain": plain},
+                   "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
+                   "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain},
         "roofline": {"bound": "hbm", "kernel": "k_sweep<float,1>", "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "peak_source": pk["source"], "unit": "GB/s",
                      "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,

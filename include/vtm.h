@@ -177,6 +177,9 @@ typedef struct vtm_solver_info {
   int64_t max_halfband;        /* max_j w_j                                                   */
   double setup_ms;             /* wall time of vtm_setup                                      */
   double factor_ms;            /* device time of the factorisation kernels                    */
+  int32_t sweep_stages;        /* staged slabs per CTA chosen by the setup-time autotuner     */
+  int32_t sweep_ctas_per_sm;   /* resident sweep CTAs per SM at that staging depth            */
+  double sweep_ms;             /* autotuner's device time of one sweep (all subgraphs)        */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

@@ -35,6 +35,8 @@ size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_e
 template <typename T>
 cudaError_t sweep_configure(int R, size_t smem);
 template <typename T>
+cudaError_t sweep_occupancy(int R, size_t smem, int* ctas_per_sm);
+template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
 
 // Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T into the (zeroed) band storage (eq. 5.8).

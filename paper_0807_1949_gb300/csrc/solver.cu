@@ -100,6 +100,7 @@ struct vtm_solver {
   size_t sweep_smem = 0;
   int slot_elems = 0, ys_elems = 0, win_elems = 0;
   long wait_limit = 1L << 22;
+  std::vector<int> stage_cands;
   vtm_solver_info info{};
 
   ~vtm_solver() {
@@ -118,6 +119,10 @@ static void check_status(vtm_solver* s) {
   if (st == kStatusNotSpd) fail(VTM_ERR_NOT_SPD, "a local matrix K_j had a non-positive Cholesky pivot");
   if (st != 0) fail(VTM_ERR_INVALID, "device status " + std::to_string(st));
 }
+
+template <typename T>
+static void autotune_sweep(vtm_solver* s);
+void reset_waves(vtm_solver* s);
 
 template <typename T>
 static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s) {
@@ -229,19 +234,27 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     max_ends = std::max(max_ends, pd[j].nends);
   }
 
-  // ---- sweep shared-memory plan
+  // ---- sweep shared-memory plan: every staging depth that fits is a tuning candidate
   const int R = s->R;
   s->slot_elems = kNB * max_Wp;
   s->ys_elems = (max_Wp - 1 + max_pad) * R;
   s->win_elems = std::max(1, max_ends) * R;
   const size_t kSmemMax = 227 * 1024;
-  int stages = 4;
-  while (stages >= 2 && sweep_smem_bytes(sizeof(T), R, stages, s->slot_elems, s->ys_elems, s->win_elems) > kSmemMax) --stages;
-  if (stages < 2)
+  std::vector<int> stage_cands;
+  size_t smem_cap = 0;
+  for (int st2 = 2; st2 <= 4; ++st2) {
+    const size_t b = sweep_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->ys_elems, s->win_elems);
+    if (b <= kSmemMax) {
+      stage_cands.push_back(st2);
+      smem_cap = std::max(smem_cap, b);
+    }
+  }
+  if (stage_cands.empty())
     fail(VTM_ERR_INVALID, "a subgraph is too large for the shared-memory sweep (n_j, bandwidth or nrhs too big)");
-  s->stages = stages;
-  s->sweep_smem = sweep_smem_bytes(sizeof(T), R, stages, s->slot_elems, s->ys_elems, s->win_elems);
-  VTM_CUDA(sweep_configure<T>(R, s->sweep_smem));
+  s->stages = stage_cands.back();
+  s->sweep_smem = sweep_smem_bytes(sizeof(T), R, s->stages, s->slot_elems, s->ys_elems, s->win_elems);
+  VTM_CUDA(sweep_configure<T>(R, smem_cap));
+  s->stage_cands = stage_cands;
 
   // ---- vertex -> copies (for assembly)
   std::vector<int64_t> vc_ptr(p->n + 1, 0), vc_copy(C);
@@ -322,6 +335,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaMallocHost(&s->h_norms, 4 * 8 * sizeof(double)));
   VTM_CUDA(cudaStreamSynchronize(st));
 
+  autotune_sweep<T>(s);
+
   s->info.npieces = np;
   s->info.ncopies = C;
   s->info.nends = s->E;
@@ -366,6 +381,45 @@ static void sweeps_typed(vtm_solver* s, int k) {
     s->launches++;
   }
   if (k > 0) s->have_copies = true;
+}
+
+// Setup-time autotuner: time each staging depth that fits (fewer stages leave room for more
+// resident CTAs per SM) on the solver's own subgraphs and keep the fastest.
+template <typename T>
+static void autotune_sweep(vtm_solver* s) {
+  cudaEvent_t e0, e1;
+  VTM_CUDA(cudaEventCreate(&e0));
+  VTM_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_st = s->stage_cands.back();
+  for (int st2 : s->stage_cands) {
+    s->stages = st2;
+    s->sweep_smem = sweep_smem_bytes(sizeof(T), s->R, st2, s->slot_elems, s->ys_elems, s->win_elems);
+    sweeps_typed<T>(s, 1);
+    VTM_CUDA(cudaEventRecord(e0, s->stream));
+    sweeps_typed<T>(s, 3);
+    VTM_CUDA(cudaEventRecord(e1, s->stream));
+    VTM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    VTM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3;
+    if (ms < best) {
+      best = ms;
+      best_st = st2;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->stages = best_st;
+  s->sweep_smem = sweep_smem_bytes(sizeof(T), s->R, best_st, s->slot_elems, s->ys_elems, s->win_elems);
+  int occ = 0;
+  VTM_CUDA(sweep_occupancy<T>(s->R, s->sweep_smem, &occ));
+  s->info.sweep_stages = best_st;
+  s->info.sweep_ctas_per_sm = occ;
+  s->info.sweep_ms = best;
+  s->launches = 0;
+  check_status(s);
+  reset_waves(s);
 }
 
 void run_sweeps(vtm_solver* s, int k) {

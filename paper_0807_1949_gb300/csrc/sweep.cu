@@ -15,7 +15,7 @@
 namespace vtm {
 
 template <typename T, int R>
-__global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
   const int tid = threadIdx.x;
@@ -87,17 +87,34 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
     const T* L = ring + (size_t)slot * a.slot_elems;
     if (s < nblk) {
       const int k0 = s * kNB;
-      // t_r = r_r - sum_{col < k0} L[r][col] y_col
+      // t_r = r_r - sum_{col < k0} L[r][col] y_col   (positions p < off - r of row r)
       const T* Lr = L + rg * Wp;
       const int pend = off - rg;
       const T* yb = ys + (size_t)(k0 + rg) * R;
       T acc[R];
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
-      for (int p = g; p < pend; p += 8) {
-        const T l = Lr[p];
+      if constexpr (sizeof(T) == 4 && R == 1) {
+        // 16-byte loads of the factor row; four independent FMA chains
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float4* L4 = reinterpret_cast<const float4*>(Lr);
+        const int nchunk = (pend + 3) >> 2;
+        for (int q = g; q < nchunk; q += 8) {
+          const float4 l = L4[q];
+          const int p = q << 2;
+          const float* y = reinterpret_cast<const float*>(yb) + p;
+          a0 = fmaf(l.x, y[0], a0);
+          if (p + 1 < pend) a1 = fmaf(l.y, y[1], a1);
+          if (p + 2 < pend) a2 = fmaf(l.z, y[2], a2);
+          if (p + 3 < pend) a3 = fmaf(l.w, y[3], a3);
+        }
+        acc[0] = (a0 + a1) + (a2 + a3);
+      } else {
+        for (int p = g; p < pend; p += 8) {
+          const T l = Lr[p];
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) acc[rr] += l * yb[(size_t)p * R + rr];
+          for (int rr = 0; rr < R; ++rr) acc[rr] += l * yb[(size_t)p * R + rr];
+        }
       }
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) acc[rr] = warp_sum_g8(acc[rr]);
@@ -141,17 +158,32 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + tid + off) * R + rr] = tb[tid * R + rr];
       // y_col -= sum_r L[k0 + r][col] x_r for the Wp-1 columns left of the block
       for (int co = tid; co < off; co += kSweepThreads) {
-        T acc3[R];
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) acc3[rr] = T(0);
         const int rmax = co < kNB - 1 ? co : kNB - 1;
-        for (int r = 0; r <= rmax; ++r) {
-          const T l = L[r * Wp + co - r];
+        if constexpr (R == 1) {
+          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+          const T* Lc = L + co;  // entry (r, co - r) is at Lc[r * (Wp - 1)]
+          const int step = Wp - 1;
+          int r = 0;
+          for (; r + 3 <= rmax; r += 4) {
+            a0 += Lc[(r + 0) * step] * tb[r + 0];
+            a1 += Lc[(r + 1) * step] * tb[r + 1];
+            a2 += Lc[(r + 2) * step] * tb[r + 2];
+            a3 += Lc[(r + 3) * step] * tb[r + 3];
+          }
+          for (; r <= rmax; ++r) a0 += Lc[r * step] * tb[r];
+          ys[k0 + co] -= (a0 + a1) + (a2 + a3);
+        } else {
+          T acc3[R];
 #pragma unroll
-          for (int rr = 0; rr < R; ++rr) acc3[rr] += l * tb[r * R + rr];
+          for (int rr = 0; rr < R; ++rr) acc3[rr] = T(0);
+          for (int r = 0; r <= rmax; ++r) {
+            const T l = L[r * Wp + co - r];
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) acc3[rr] += l * tb[r * R + rr];
+          }
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + co) * R + rr] -= acc3[rr];
         }
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + co) * R + rr] -= acc3[rr];
       }
     }
     __syncthreads();
@@ -205,6 +237,22 @@ cudaError_t sweep_configure(int R, size_t smem) {
   }
 }
 
+template <typename T, int R>
+static cudaError_t occupancy_one(size_t smem, int* n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_sweep<T, R>, kSweepThreads, smem);
+}
+
+template <typename T>
+cudaError_t sweep_occupancy(int R, size_t smem, int* n) {
+  switch (R) {
+    case 1: return occupancy_one<T, 1>(smem, n);
+    case 2: return occupancy_one<T, 2>(smem, n);
+    case 4: return occupancy_one<T, 4>(smem, n);
+    case 8: return occupancy_one<T, 8>(smem, n);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
   dim3 grid(npieces), block(kSweepThreads);
@@ -220,6 +268,8 @@ cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem,
 
 template cudaError_t sweep_configure<float>(int, size_t);
 template cudaError_t sweep_configure<double>(int, size_t);
+template cudaError_t sweep_occupancy<float>(int, size_t, int*);
+template cudaError_t sweep_occupancy<double>(int, size_t, int*);
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, size_t, cudaStream_t);
 

@@ -58,7 +58,8 @@ class SolverInfo(C.Structure):
     _fields_ = [("npieces", C.c_int32), ("ncopies", C.c_int64), ("nends", C.c_int64), ("nrhs", C.c_int32),
                 ("precision", C.c_int32), ("block_rows", C.c_int32), ("factor_entries", C.c_int64),
                 ("band_entries", C.c_int64), ("factor_bytes", C.c_int64), ("max_halfband", C.c_int64),
-                ("setup_ms", C.c_double), ("factor_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("factor_ms", C.c_double), ("sweep_stages", C.c_int32),
+                ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double)]
 
 
 class Stats(C.Structure):
