@@ -142,7 +142,13 @@ void vtm_partition_destroy(vtm_partition* p);
 
 enum vtm_z_mode {
   VTM_Z_UNIFORM = 0,   /* every line has impedance z_uniform (Example 5.1 style)            */
-  VTM_Z_EXPLICIT = 1   /* z_lines[t] per line, in the order of vtm_partition_get_lines      */
+  VTM_Z_EXPLICIT = 1,  /* z_lines[t] per line, in the order of vtm_partition_get_lines      */
+  VTM_Z_MATCHED = 2,   /* impedance matching (§7.1): start from z_uniform on every line,
+                          compute each end's input impedance (Def. 7.1 with the other lines
+                          terminated), set Z_t = sqrt(r_in(a) r_in(b)) and refactor          */
+  VTM_Z_LEARNED = 3    /* learned impedances: opts.model maps the 8 features of each line end
+                          (vtm_line_features) to log Z_e; both ends agree on
+                          Z_t = exp((log Z_a + log Z_b) / 2) (Table 1 step 1)               */
 };
 
 enum vtm_precision {
@@ -150,6 +156,8 @@ enum vtm_precision {
   VTM_FP32 = 1         /* factor, substitution and waves in FP32; FP64 residual and defect
                           correction around the sweeps (outer refinement)                     */
 };
+
+typedef struct vtm_mlp vtm_mlp;
 
 typedef struct vtm_setup_opts {
   int32_t z_mode;          /* vtm_z_mode                                                     */
@@ -160,6 +168,7 @@ typedef struct vtm_setup_opts {
   int32_t check_every;     /* sweeps between residual checks in vtm_solve (0 = 10)           */
   double inner_reduction;  /* FP32: restart the defect correction once the inner residual has
                               dropped by this factor (0 = 1e-4); ignored for FP64            */
+  const vtm_mlp* model;    /* LEARNED: impedance model (not retained after vtm_setup)        */
 } vtm_setup_opts;
 
 typedef struct vtm_solver vtm_solver;
@@ -220,6 +229,16 @@ typedef struct vtm_stats {
 int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int32_t maxit,
               vtm_stats* st);
 
+/* Input impedance of every line end (Def. 7.1): with all sources zero, a unit inflow current at
+ * the end's port and its own line open (every other line of the subgraph terminated by its
+ * impedance), the port potential.  Computed on the device from the stored factors with unit
+ * right-hand sides: g_c = (K_j^{-1})_{cc}, r_in(e) = g_c / (1 - g_c / Z_e).
+ * r_in: host, nends doubles in end order (2t = side a, 2t+1 = side b of line t).  Resets waves. */
+int vtm_input_impedances(vtm_solver* s, double* r_in);
+/* The line impedances the solver was set up with (after matching or the learned model), host,
+ * nlines doubles in vtm_partition_get_lines order. */
+int vtm_solver_get_impedances(const vtm_solver* s, double* z_lines);
+
 /* Checkpoint / inspection.  Waves: outgoing waves of the last sweep, host, nends x nrhs
  * column-major (end order of vtm_partition_get_lines: end 2t = side a of line t, 2t+1 = side b).
  * Copies: the last local solutions, host, ncopies x nrhs column-major, copies numbered piece by
@@ -227,6 +246,40 @@ int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol
 int vtm_get_state(vtm_solver* s, double* waves);
 int vtm_set_state(vtm_solver* s, const double* waves);
 int vtm_get_copies(vtm_solver* s, double* copies);
+
+/* ----------------------------------------------------------------------------------------------
+ * Learned impedance model (§7: the choice of Z is the preconditioner; §7.1 matching is the
+ * paper's rule, the model is trained on impedances that the method finds by search)
+ * --------------------------------------------------------------------------------------------*/
+
+#define VTM_MLP_IN 8
+#define VTM_MLP_HIDDEN 64
+#define VTM_MLP_PARAMS 4801  /* W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3 (FP32 master) */
+
+/* 8 features of every line end (its port copy c of vertex i in subgraph j), host float array of
+ * nends x 8 (row e = end e in vtm_partition_get_lines order: 2t = side a, 2t+1 = side b):
+ *   0 log a_ii            1 log a_ii^(c) (split weight of the copy, §4 step 3)
+ *   2 log |O(i)| (copies)  3 lines at the copy (Fig. 7: 1, 2 or 3)
+ *   4 log sum_{j in piece} |a_ij^(c)|   5 log a_ii^(twin copy)
+ *   6 log(max_j |a_ij| / min_j |a_ij|) over the neighbours of i in A
+ *   7 log(n / n_j) (how many subgraphs of this size the problem holds)                        */
+int vtm_line_features(const vtm_partition* p, float* feats);
+
+/* Model: 8 -> 64 -> 64 -> 1 perceptron, ReLU, BF16 weights with FP32 accumulation, output log Z.
+ * Created with He-uniform weights from a SplitMix64 counter stream of `seed`; device memory owned
+ * by the handle.  Parameters are exchanged as FP32 host arrays of VTM_MLP_PARAMS. */
+int vtm_mlp_create(uint64_t seed, vtm_mlp** out);
+void vtm_mlp_destroy(vtm_mlp* m);
+int vtm_mlp_get_params(const vtm_mlp* m, float* params);
+int vtm_mlp_set_params(vtm_mlp* m, const float* params);   /* also resets the Adam moments */
+/* y[i] = model(X[i, :]); X: device n x 8 row-major float, y: device n floats. */
+int vtm_mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, void* cuda_stream);
+/* loss = mean_i (model(X_i) - target_i)^2 (returned on the host) and its gradient w.r.t. the BF16
+ * weights, stored in the model (vtm_mlp_get_grads).  X, target: device. Synchronises the stream. */
+int vtm_mlp_loss_grad(vtm_mlp* m, const float* X, const float* target, int64_t n, float* loss, void* cuda_stream);
+int vtm_mlp_get_grads(const vtm_mlp* m, float* grads);
+/* One Adam step on the FP32 master weights with the stored gradient; refreshes the BF16 copy. */
+int vtm_mlp_adam_step(vtm_mlp* m, float lr, float beta1, float beta2, float eps, void* cuda_stream);
 
 /* ----------------------------------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a service for callers)

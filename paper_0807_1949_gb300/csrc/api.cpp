@@ -3,6 +3,8 @@
 #include <cstring>
 #include <new>
 
+#include <cuda_runtime.h>
+
 #include "internal.h"
 
 namespace vtm {
@@ -16,6 +18,17 @@ void solver_get_state(vtm_solver* s, double* waves);
 void solver_set_state(vtm_solver* s, const double* waves);
 void solver_get_copies(vtm_solver* s, double* out);
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info);
+void solver_input_impedances(vtm_solver* s, double* r);
+void line_features(const vtm_partition* p, float* out);
+void solver_get_impedances(const vtm_solver* s, double* z);
+vtm_mlp* mlp_create(uint64_t seed);
+void mlp_set_params(vtm_mlp* m, const float* host);
+void mlp_get_params(const vtm_mlp* m, float* host);
+void mlp_get_grads(const vtm_mlp* m, float* host);
+void mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, cudaStream_t st);
+float mlp_loss_grad(vtm_mlp* m, const float* X, const float* t, int64_t n, cudaStream_t st);
+void mlp_adam(vtm_mlp* m, float lr, float b1, float b2, float eps, cudaStream_t st);
+void mlp_destroy(vtm_mlp* m);
 void solver_destroy(vtm_solver* s);
 
 static thread_local std::string g_last_error;
@@ -168,6 +181,22 @@ int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol
   });
 }
 
+int vtm_input_impedances(vtm_solver* s, double* r_in) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_input_impedances(s, r_in);
+    return VTM_OK;
+  });
+}
+
+int vtm_solver_get_impedances(const vtm_solver* s, double* z_lines) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_get_impedances(s, z_lines);
+    return VTM_OK;
+  });
+}
+
 int vtm_get_state(vtm_solver* s, double* waves) {
   return guarded([&] {
     if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
@@ -188,6 +217,77 @@ int vtm_get_copies(vtm_solver* s, double* copies) {
   return guarded([&] {
     if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
     vtm::solver_get_copies(s, copies);
+    return VTM_OK;
+  });
+}
+
+int vtm_line_features(const vtm_partition* p, float* feats) {
+  return guarded([&] {
+    if (!p || !feats) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::line_features(p, feats);
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_create(uint64_t seed, vtm_mlp** out) {
+  return guarded([&] {
+    if (!out) vtm::fail(VTM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    *out = vtm::mlp_create(seed);
+    return VTM_OK;
+  });
+}
+
+void vtm_mlp_destroy(vtm_mlp* m) {
+  if (m) vtm::mlp_destroy(m);
+}
+
+int vtm_mlp_get_params(const vtm_mlp* m, float* params) {
+  return guarded([&] {
+    if (!m || !params) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::mlp_get_params(m, params);
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_set_params(vtm_mlp* m, const float* params) {
+  return guarded([&] {
+    if (!m || !params) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::mlp_set_params(m, params);
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_get_grads(const vtm_mlp* m, float* grads) {
+  return guarded([&] {
+    if (!m || !grads) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::mlp_get_grads(m, grads);
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, void* cuda_stream) {
+  return guarded([&] {
+    if (!m || (n > 0 && (!X || !y)) || n < 0) vtm::fail(VTM_ERR_INVALID, "bad argument");
+    vtm::mlp_forward(m, X, y, n, static_cast<cudaStream_t>(cuda_stream));
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_loss_grad(vtm_mlp* m, const float* X, const float* target, int64_t n, float* loss, void* cuda_stream) {
+  return guarded([&] {
+    if (!m || !X || !target || n <= 0) vtm::fail(VTM_ERR_INVALID, "bad argument");
+    const float l = vtm::mlp_loss_grad(m, X, target, n, static_cast<cudaStream_t>(cuda_stream));
+    if (loss) *loss = l;
+    return VTM_OK;
+  });
+}
+
+int vtm_mlp_adam_step(vtm_mlp* m, float lr, float beta1, float beta2, float eps, void* cuda_stream) {
+  return guarded([&] {
+    if (!m || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+      vtm::fail(VTM_ERR_INVALID, "bad Adam hyper-parameters");
+    vtm::mlp_adam(m, lr, beta1, beta2, eps, static_cast<cudaStream_t>(cuda_stream));
     return VTM_OK;
   });
 }

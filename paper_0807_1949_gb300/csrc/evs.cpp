@@ -403,3 +403,57 @@ void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_parti
     if (p->piece_ptr[q + 1] == p->piece_ptr[q]) fail(VTM_ERR_INVALID, "a subgraph is empty");
 }
 }  // namespace vtm
+
+namespace vtm {
+
+// Eight local features of every line end (see vtm_line_features in vtm.h), in API end order.
+void line_features(const vtm_partition* p, float* out) {
+  const int64_t C = p->piece_ptr[p->npieces];
+  const int64_t nl = (int64_t)p->line_a.size();
+  std::vector<int32_t> ncopies(p->n, 0), nlines(C, 0), piece(C, 0);
+  for (int64_t c = 0; c < C; ++c) ncopies[p->copy_vertex[c]]++;
+  for (int64_t t = 0; t < nl; ++t) {
+    nlines[p->line_a[t]]++;
+    nlines[p->line_b[t]]++;
+  }
+  for (int32_t j = 0; j < p->npieces; ++j)
+    for (int64_t c = p->piece_ptr[j]; c < p->piece_ptr[j + 1]; ++c) piece[c] = j;
+  auto safe_log = [](double v) { return std::log(std::max(v, 1e-300)); };
+  auto copy_diag_and_off = [&](int64_t c, double* d, double* off) {
+    const int64_t l = c - p->piece_ptr[piece[c]];
+    *d = 0;
+    *off = 0;
+    for (int64_t k = p->l_rowptr[c]; k < p->l_rowptr[c + 1]; ++k) {
+      if (p->l_col[k] == l) *d += p->l_val[k];
+      else *off += std::fabs(p->l_val[k]);
+    }
+  };
+  for (int64_t e = 0; e < 2 * nl; ++e) {
+    const int64_t c = (e & 1) ? p->line_b[e >> 1] : p->line_a[e >> 1];
+    const int64_t tw = (e & 1) ? p->line_a[e >> 1] : p->line_b[e >> 1];
+    const int64_t i = p->copy_vertex[c];
+    double aii = 0, amax = 0, amin = INFINITY;
+    for (int64_t k = p->a_rowptr[i]; k < p->a_rowptr[i + 1]; ++k) {
+      if (p->a_col[k] == i) aii = p->a_val[k];
+      else {
+        amax = std::max(amax, std::fabs(p->a_val[k]));
+        amin = std::min(amin, std::fabs(p->a_val[k]));
+      }
+    }
+    double dc, offc, dt, offt;
+    copy_diag_and_off(c, &dc, &offc);
+    copy_diag_and_off(tw, &dt, &offt);
+    const int64_t nj = p->piece_ptr[piece[c] + 1] - p->piece_ptr[piece[c]];
+    float* f = out + e * VTM_MLP_IN;
+    f[0] = (float)safe_log(aii);
+    f[1] = (float)safe_log(dc);
+    f[2] = (float)std::log((double)ncopies[i]);
+    f[3] = (float)nlines[c];
+    f[4] = (float)safe_log(offc);
+    f[5] = (float)safe_log(dt);
+    f[6] = (amax > 0 && std::isfinite(amin) && amin > 0) ? (float)std::log(amax / amin) : 0.f;
+    f[7] = (float)std::log((double)p->n / (double)nj);
+  }
+}
+
+}  // namespace vtm

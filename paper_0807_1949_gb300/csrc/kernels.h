@@ -49,6 +49,14 @@ cudaError_t launch_build_band(int64_t ncopies, const int32_t* copy_piece, const 
 template <typename T>
 cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, cudaStream_t st);
 
+// Unit right-hand sides for batch b of every subgraph's ports (b̃ of port b*R + r = e_c in column r).
+template <typename T>
+cudaError_t launch_unit_rhs(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, int b, T* bt,
+                            cudaStream_t st);
+// g[port] = x_c of column r for the ports of batch b (diagonal of K_j^{-1}).
+template <typename T>
+cudaError_t launch_gather_diag(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, int b,
+                               const T* xc, double* g, cudaStream_t st);
 // b̃_c = share_c * src[vertex(c)]  (§4 step 3), into T precision, R contiguous.
 template <typename T>
 cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, const double* share,

@@ -106,6 +106,31 @@ __global__ void k_copy2d(int64_t n, int R, const double* __restrict__ src, int64
   for (int r = 0; r < R; ++r) dst[i + r * ldd] = src[i + r * lds];
 }
 
+template <typename T>
+__global__ void k_unit_rhs(const PieceDesc* __restrict__ pieces, const int32_t* __restrict__ port_local, int R, int b,
+                           T* __restrict__ bt) {
+  const PieceDesc pd = pieces[blockIdx.x];
+  T* p = bt + (size_t)pd.copy_off * R;
+  for (int i = threadIdx.x; i < pd.n * R; i += blockDim.x) p[i] = T(0);
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < R) {
+    const int q = b * R + r;
+    if (q < pd.nports) p[(size_t)port_local[pd.port_off + q] * R + r] = T(1);
+  }
+}
+
+template <typename T>
+__global__ void k_gather_diag(const PieceDesc* __restrict__ pieces, const int32_t* __restrict__ port_local, int R,
+                              int b, const T* __restrict__ xc, double* __restrict__ g) {
+  const PieceDesc pd = pieces[blockIdx.x];
+  const int r = threadIdx.x;
+  if (r < R) {
+    const int q = b * R + r;
+    if (q < pd.nports) g[pd.port_off + q] = (double)xc[((size_t)pd.copy_off + port_local[pd.port_off + q]) * R + r];
+  }
+}
+
 static unsigned nblocks(int64_t n) { return (unsigned)((n + kBS - 1) / kBS); }
 
 template <typename T>
@@ -141,6 +166,26 @@ cudaError_t launch_copy2d(int64_t n, int R, const double* src, int64_t lds, doub
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_unit_rhs(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, int b, T* bt,
+                            cudaStream_t st) {
+  k_unit_rhs<T><<<npieces, 256, 0, st>>>(pieces, port_local, R, b, bt);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_diag(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, int b,
+                               const T* xc, double* g, cudaStream_t st) {
+  k_gather_diag<T><<<npieces, 32, 0, st>>>(pieces, port_local, R, b, xc, g);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_unit_rhs<float>(const PieceDesc*, int, const int32_t*, int, int, float*, cudaStream_t);
+template cudaError_t launch_unit_rhs<double>(const PieceDesc*, int, const int32_t*, int, int, double*, cudaStream_t);
+template cudaError_t launch_gather_diag<float>(const PieceDesc*, int, const int32_t*, int, int, const float*, double*,
+                                               cudaStream_t);
+template cudaError_t launch_gather_diag<double>(const PieceDesc*, int, const int32_t*, int, int, const double*,
+                                                double*, cudaStream_t);
 template cudaError_t launch_split<float>(int64_t, int, const int64_t*, const double*, const double*, int64_t, float*,
                                          cudaStream_t);
 template cudaError_t launch_split<double>(int64_t, int, const int64_t*, const double*, const double*, int64_t, double*,

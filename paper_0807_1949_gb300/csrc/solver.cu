@@ -101,6 +101,12 @@ struct vtm_solver {
   int slot_elems = 0, ys_elems = 0, win_elems = 0;
   long wait_limit = 1L << 22;
   std::vector<int> stage_cands;
+  // kept for re-assembly with new impedances (eq. 5.8 depends on Z)
+  DevBuf d_copy_piece, d_lrowptr, d_lcol, d_lval, d_port_of_copy, d_invz64;
+  std::vector<double> Z;             // per line, API order
+  std::vector<int32_t> end_api;      // internal end -> API end (2t + side)
+  std::vector<int32_t> end_port;     // internal end -> port
+  int max_w = 0, max_pad = 0, max_ports = 0;
   vtm_solver_info info{};
 
   ~vtm_solver() {
@@ -123,6 +129,47 @@ static void check_status(vtm_solver* s) {
 template <typename T>
 static void autotune_sweep(vtm_solver* s);
 void reset_waves(vtm_solver* s);
+void line_features(const vtm_partition* p, float* out);
+void mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, cudaStream_t st);
+
+// Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T for the solver's current line impedances and factor
+// every K_j on the device (eq. 5.8, once per choice of Z).
+template <typename T>
+static void factor_typed(vtm_solver* s) {
+  cudaStream_t st = s->stream;
+  std::vector<double> invz(s->E);
+  for (int64_t k = 0; k < s->E; ++k) invz[k] = 1.0 / s->Z[s->end_api[k] >> 1];
+  upload(s->d_invz64, invz, st);
+  {
+    std::vector<T> iz(invz.begin(), invz.end());
+    upload(s->invz_t, iz, st);
+  }
+  VTM_CUDA(cudaMemsetAsync(s->factor.p, 0, s->factor.bytes, st));
+  VTM_CUDA(launch_build_band<T>(s->C, s->d_copy_piece.as<int32_t>(), s->pieces.as<PieceDesc>(),
+                                s->d_lrowptr.as<int64_t>(), s->d_lcol.as<int32_t>(), s->d_lval.as<double>(),
+                                s->d_port_of_copy.as<int32_t>(), s->port_end_ptr.as<int32_t>(),
+                                s->d_invz64.as<double>(), s->npieces, s->max_pad, s->factor.as<T>(),
+                                s->status.as<int>(), st));
+  cudaEvent_t e0, e1;
+  VTM_CUDA(cudaEventCreate(&e0));
+  VTM_CUDA(cudaEventCreate(&e1));
+  VTM_CUDA(cudaEventRecord(e0, st));
+  cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), s->npieces, s->max_w, s->factor.as<T>(),
+                                    s->status.as<int>(), st);
+  VTM_CUDA(cudaEventRecord(e1, st));
+  VTM_CUDA(cudaStreamSynchronize(st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (fe == cudaErrorInvalidValue) fail(VTM_ERR_INVALID, "bandwidth too large for the factorisation kernel");
+  VTM_CUDA(fe);
+  s->info.factor_ms += ms;
+  check_status(s);
+}
+
+template <typename T>
+static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api);
 
 template <typename T>
 static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s) {
@@ -139,9 +186,27 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   // ---- impedances per line
   std::vector<double> Z(nl);
   for (int64_t t = 0; t < nl; ++t) {
-    double z = (o->z_mode == VTM_Z_EXPLICIT) ? o->z_lines[t] : o->z_uniform;
+    double z = (o->z_mode == VTM_Z_EXPLICIT) ? o->z_lines[t] : o->z_uniform;  // MATCHED starts from z_uniform
+    if (o->z_mode == VTM_Z_LEARNED) z = 1.0;
     if (!(z > 0) || !std::isfinite(z)) fail(VTM_ERR_INVALID, "line impedances must be positive and finite");
     Z[t] = z;
+  }
+  if (o->z_mode == VTM_Z_LEARNED && nl > 0) {
+    // the model proposes log Z for each end; both ends agree on the geometric mean (Table 1 step 1)
+    std::vector<float> feats((size_t)2 * nl * VTM_MLP_IN), y(2 * nl);
+    line_features(p, feats.data());
+    DevBuf dX, dy;
+    upload(dX, feats, st);
+    dy.alloc(y.size() * sizeof(float));
+    mlp_forward(o->model, dX.as<float>(), dy.as<float>(), 2 * nl, st);
+    VTM_CUDA(cudaMemcpyAsync(y.data(), dy.p, y.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    VTM_CUDA(cudaStreamSynchronize(st));
+    for (int64_t t = 0; t < nl; ++t) {
+      double lz = 0.5 * ((double)y[2 * t] + (double)y[2 * t + 1]);
+      if (!std::isfinite(lz)) fail(VTM_ERR_INVALID, "learned impedance is not finite");
+      lz = std::min(30.0, std::max(-30.0, lz));
+      Z[t] = std::exp(lz);
+    }
   }
 
   // ---- ends sorted by (copy, line, side); copies are grouped by subgraph in local order
@@ -270,10 +335,6 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   upload(s->port_local, port_local, st);
   upload(s->port_end_ptr, port_end_ptr, st);
   upload(s->twin, twin, st);
-  {
-    std::vector<T> iz(invz.begin(), invz.end());
-    upload(s->invz_t, iz, st);
-  }
   upload(s->a_rowptr, p->a_rowptr, st);
   upload(s->a_col, p->a_col, st);
   upload(s->a_val, p->a_val, st);
@@ -285,36 +346,21 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
 
   // local matrices and factor
-  {
-    DevBuf d_piece, d_rowptr, d_col, d_val, d_poc, d_invz;
-    upload(d_piece, copy_piece, st);
-    upload(d_rowptr, p->l_rowptr, st);
-    upload(d_col, p->l_col, st);
-    upload(d_val, p->l_val, st);
-    upload(d_poc, port_of_copy, st);
-    upload(d_invz, invz, st);
-    s->factor.alloc((size_t)foff * sizeof(T));
-    VTM_CUDA(cudaMemsetAsync(s->factor.p, 0, (size_t)foff * sizeof(T), st));
-    VTM_CUDA(launch_build_band<T>(C, d_piece.as<int32_t>(), s->pieces.as<PieceDesc>(), d_rowptr.as<int64_t>(),
-                                  d_col.as<int32_t>(), d_val.as<double>(), d_poc.as<int32_t>(),
-                                  s->port_end_ptr.as<int32_t>(), d_invz.as<double>(), np, max_pad,
-                                  s->factor.as<T>(), s->status.as<int>(), st));
-    cudaEvent_t e0, e1;
-    VTM_CUDA(cudaEventCreate(&e0));
-    VTM_CUDA(cudaEventCreate(&e1));
-    VTM_CUDA(cudaEventRecord(e0, st));
-    cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), np, max_w, s->factor.as<T>(), s->status.as<int>(), st);
-    VTM_CUDA(cudaEventRecord(e1, st));
-    VTM_CUDA(cudaStreamSynchronize(st));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (fe == cudaErrorInvalidValue) fail(VTM_ERR_INVALID, "bandwidth too large for the factorisation kernel");
-    VTM_CUDA(fe);
-    s->info.factor_ms = ms;
-    check_status(s);
-  }
+  upload(s->d_copy_piece, copy_piece, st);
+  upload(s->d_lrowptr, p->l_rowptr, st);
+  upload(s->d_lcol, p->l_col, st);
+  upload(s->d_lval, p->l_val, st);
+  upload(s->d_port_of_copy, port_of_copy, st);
+  s->factor.alloc((size_t)foff * sizeof(T));
+  s->max_w = max_w;
+  s->max_pad = max_pad;
+  s->Z = Z;
+  s->end_api = order;
+  s->end_port.assign(2 * nl, 0);
+  for (size_t q = 0; q + 1 < port_end_ptr.size(); ++q)
+    for (int32_t e = port_end_ptr[q]; e < port_end_ptr[q + 1]; ++e) s->end_port[e] = (int32_t)q;
+  for (int32_t j = 0; j < np; ++j) s->max_ports = std::max(s->max_ports, pd[j].nports);
+  factor_typed<T>(s);
 
   // vectors
   s->bt.alloc((size_t)C * R * sizeof(T));
@@ -336,6 +382,16 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaStreamSynchronize(st));
 
   autotune_sweep<T>(s);
+
+  if (o->z_mode == VTM_Z_MATCHED) {
+    // §7.1 impedance matching: every line takes the geometric mean of its two ends' input
+    // impedances (Def. 7.1, other lines terminated with the initial Z), then K_j is refactored.
+    std::vector<double> r;
+    input_impedances_typed<T>(s, r);
+    for (int64_t t = 0; t < nl; ++t) s->Z[t] = std::sqrt(r[2 * t] * r[2 * t + 1]);
+    factor_typed<T>(s);
+    reset_waves(s);
+  }
 
   s->info.npieces = np;
   s->info.ncopies = C;
@@ -422,6 +478,45 @@ static void autotune_sweep(vtm_solver* s) {
   reset_waves(s);
 }
 
+// Def. 7.1 on the device: g_c = (K_j^{-1})_{cc} for every port copy, nrhs unit right-hand sides
+// per subgraph per sweep with zero incident waves (no exchange); the input impedance seen by end e
+// (its own line open, every other line terminated) is g_c / (1 - g_c / Z_e) (rank-one downdate).
+template <typename T>
+static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api) {
+  DevBuf g;
+  g.alloc((size_t)std::max(1, s->nports) * sizeof(double));
+  const int R = s->R;
+  const int nb = (s->max_ports + R - 1) / R;
+  for (int b = 0; b < nb; ++b) {
+    VTM_CUDA(launch_unit_rhs<T>(s->pieces.as<PieceDesc>(), s->npieces, s->port_local.as<int32_t>(), R, b,
+                                s->bt.as<T>(), s->stream));
+    reset_waves(s);
+    sweeps_typed<T>(s, 1);
+    VTM_CUDA(launch_gather_diag<T>(s->pieces.as<PieceDesc>(), s->npieces, s->port_local.as<int32_t>(), R, b,
+                                   s->xc.as<T>(), g.as<double>(), s->stream));
+  }
+  std::vector<double> gh(std::max(1, s->nports));
+  VTM_CUDA(cudaMemcpyAsync(gh.data(), g.p, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+  check_status(s);
+  r_api.assign(s->E, 0.0);
+  for (int64_t k = 0; k < s->E; ++k) {
+    const double gc = gh[s->end_port[k]];
+    const double z = s->Z[s->end_api[k] >> 1];
+    r_api[s->end_api[k]] = gc / (1.0 - gc / z);
+  }
+  VTM_CUDA(cudaMemsetAsync(s->bt.p, 0, s->bt.bytes, s->stream));
+  reset_waves(s);
+}
+
+void solver_input_impedances(vtm_solver* s, double* r) {
+  if (!r) fail(VTM_ERR_INVALID, "null output");
+  std::vector<double> v;
+  if (s->precision == VTM_FP32) input_impedances_typed<float>(s, v);
+  else input_impedances_typed<double>(s, v);
+  std::copy(v.begin(), v.end(), r);
+}
+
 void run_sweeps(vtm_solver* s, int k) {
   if (s->precision == VTM_FP32) sweeps_typed<float>(s, k);
   else sweeps_typed<double>(s, k);
@@ -458,7 +553,10 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   if (!p || !o) fail(VTM_ERR_INVALID, "null partition or options");
   if (o->precision != VTM_FP32 && o->precision != VTM_FP64) fail(VTM_ERR_INVALID, "unknown precision");
   if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8)) fail(VTM_ERR_INVALID, "nrhs must be 1, 2, 4 or 8");
-  if (o->z_mode != VTM_Z_UNIFORM && o->z_mode != VTM_Z_EXPLICIT) fail(VTM_ERR_INVALID, "unknown z_mode");
+  if (o->z_mode != VTM_Z_UNIFORM && o->z_mode != VTM_Z_EXPLICIT && o->z_mode != VTM_Z_MATCHED &&
+      o->z_mode != VTM_Z_LEARNED)
+    fail(VTM_ERR_INVALID, "unknown z_mode");
+  if (o->z_mode == VTM_Z_LEARNED && !o->model) fail(VTM_ERR_INVALID, "LEARNED z_mode needs a model");
   if (o->z_mode == VTM_Z_EXPLICIT && !o->z_lines && !p->line_a.empty()) fail(VTM_ERR_INVALID, "z_lines is NULL");
   std::unique_ptr<vtm_solver> s(new vtm_solver());
   s->precision = o->precision;
@@ -660,6 +758,10 @@ void solver_get_copies(vtm_solver* s, double* out) {
   else get_copies_typed<double>(s, out);
 }
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info) { *info = s->info; }
+void solver_get_impedances(const vtm_solver* s, double* z) {
+  if (!z) fail(VTM_ERR_INVALID, "null output");
+  std::copy(s->Z.begin(), s->Z.end(), z);
+}
 void solver_destroy(vtm_solver* s) { delete s; }
 
 }  // namespace vtm

@@ -1,0 +1,231 @@
+"""Learned line impedances: search, training and evaluation (orchestration only).
+
+§7 makes the line impedances VTM's preconditioner and §7.1 proposes matching them to the ports'
+input impedances.  Here the method itself finds good impedances by search on generated problems,
+and a small perceptron (the library's vtm_mlp_* kernels, BF16 weights, FP32 accumulation) learns to
+predict them from 8 local features of every line end (vtm_line_features).  Every solve, forward and
+backward pass runs in the library; this module only drives them.
+
+Search family (per problem): log Z_t = th0 + th1 (g_t - median g) + th2 (m_t - 1), where g_t is the
+mean over the line's two ends of log a_ii^(c) (feature 1) and m_t the mean number of lines at the
+two copies (feature 3).  The search minimises the relative residual after a fixed number of sweeps
+(a smooth stand-in for sweeps-to-tolerance), coarse-to-fine in th0, then th1 and th2.  The searched
+impedance of every line is the training target of both its ends.
+
+Families:
+  poisson2d-256  2D 5-point, 256 x 256, sigma ~ U[0.5, 2] per seed, blocks of 32 (64 subgraphs)
+  poisson3d      3D 7-point, 64^3 / 96^3 / 128^3, sigma ~ U[0.75, 1.25], blocks of 16
+
+Run:  python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --train 200 --test 60
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import inputs, vtm
+
+MODELS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models")
+
+
+def problem(family: str, seed: int):
+    """(A, dims, block, sigma, b) of the seeded problem of a family."""
+    rng = np.random.default_rng(10_000 + seed)
+    if family == "poisson2d-256":
+        sigma = float(rng.uniform(0.5, 2.0))
+        dims, block = (256, 256), (32, 32)
+    elif family == "poisson3d":
+        sigma = float(rng.uniform(0.75, 1.25))
+        m = int(rng.choice([64, 96, 128]))
+        dims, block = (m, m, m), (16, 16, 16)
+    elif family == "poisson3d-128":
+        sigma = 1.0
+        dims, block = (128, 128, 128), (16, 16, 16)
+    else:
+        raise ValueError(family)
+    A = inputs.grid_poisson(dims, sigma=sigma, seed=seed)
+    b = inputs.rhs_uniform(A.n, 1, seed=seed)
+    return A, dims, block, sigma, b
+
+
+def family_z(feats: np.ndarray, theta) -> np.ndarray:
+    """Line impedances of the search family from the end features (ends 2t, 2t+1 of line t)."""
+    g = 0.5 * (feats[0::2, 1] + feats[1::2, 1]).astype(np.float64)
+    mm = 0.5 * (feats[0::2, 3] + feats[1::2, 3]).astype(np.float64)
+    th0, th1, th2 = theta
+    return np.exp(th0 + th1 * (g - np.median(g)) + th2 * (mm - 1.0))
+
+
+class Evaluator:
+    """Solves one problem on the GPU for candidate impedances."""
+
+    def __init__(self, A, dims, block, b, precision="fp32"):
+        import torch
+
+        self.part = vtm.partition_evs(A, "grid", dims=dims, block=block)
+        self.feats = self.part.line_features()
+        self.precision = precision
+        self.b = torch.tensor(b, device="cuda")
+        self.x = torch.zeros_like(self.b)
+
+    def residual_after(self, z, sweeps: int) -> float:
+        s = vtm.Solver(self.part, z=z, precision=self.precision, check_every=10)
+        st = s.solve(self.b, self.x, rtol=1e-15, maxit=sweeps, raise_on_fail=False)
+        r = st.rel_residual
+        return r if math.isfinite(r) else 1e30
+
+    def to_tolerance(self, z, rtol=1e-8, maxit=40000):
+        s = vtm.Solver(self.part, z=z, precision=self.precision, check_every=10)
+        st = s.solve(self.b, self.x, rtol=rtol, maxit=maxit, raise_on_fail=False)
+        return dict(sweeps=st.sweeps, solve_ms=st.solve_ms, converged=st.status == 0, rel=st.rel_residual)
+
+
+def search(ev: Evaluator, sweeps: int) -> tuple[tuple, list]:
+    """Coarse-to-fine coordinate search of the family parameters (th0, th1, th2)."""
+    log = []
+    cache = {}
+
+    def f(theta):
+        key = tuple(round(v, 6) for v in theta)
+        if key not in cache:
+            r = ev.residual_after(family_z(ev.feats, theta), sweeps)
+            cache[key] = r
+            log.append((list(theta), r))
+        return cache[key]
+
+    best, bth = math.inf, None
+    for z0 in (0.5, 1, 2, 4, 8, 16, 32):
+        th = (math.log(z0), 0.0, 0.0)
+        r = f(th)
+        if r < best:
+            best, bth = r, th
+
+    def refine0(step, rounds):
+        nonlocal best, bth
+        for _ in range(rounds):
+            for d in (-step, step):
+                th = (bth[0] + d, bth[1], bth[2])
+                r = f(th)
+                if r < best:
+                    best, bth = r, th
+            step /= 2
+
+    refine0(math.log(2.0) / 2, 3)
+    for k in (1, 2):
+        for direction in (-0.5, 0.5):
+            for _ in range(3):                     # walk while it keeps improving
+                th = list(bth)
+                th[k] = round(th[k] + direction, 6)
+                r = f(tuple(th))
+                if r < best:
+                    best, bth = r, tuple(th)
+                else:
+                    break
+    refine0(math.log(2.0) / 4, 1)
+    return bth, log
+
+
+def train(model: vtm.MLP, X: np.ndarray, y: np.ndarray, epochs: int = 40, batch: int = 16384, lr: float = 3e-3,
+          seed: int = 0) -> list:
+    """Adam on mini-batches of (features, target log Z) pairs; all passes in the library kernels."""
+    import torch
+
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    hist = []
+    n = len(X)
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).cuda()
+        tot = 0.0
+        lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))
+        for i in range(0, n, batch):
+            idx = perm[i:i + batch]
+            xb = Xd[idx].contiguous()
+            yb = yd[idx].contiguous()
+            tot += model.loss_grad(xb, yb) * len(idx)
+            model.adam_step(lr=max(lr_ep, 1e-5))
+        hist.append(tot / n)
+    return hist
+
+
+def build_dataset(family: str, seeds, sweeps: int, verbose=True):
+    X, y, meta = [], [], []
+    for sd in seeds:
+        t0 = time.time()
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        th, log = search(ev, sweeps)
+        zl = family_z(ev.feats, th)
+        X.append(ev.feats)
+        y.append(np.repeat(np.log(zl), 2).astype(np.float32))
+        meta.append(dict(seed=sd, sigma=sigma, dims=dims, theta=th, evals=len(log), seconds=round(time.time() - t0, 2)))
+        if verbose:
+            print(f"search seed {sd} sigma {sigma:.2f} dims {dims}: theta {np.round(th, 3).tolist()} "
+                  f"({time.time() - t0:.1f}s)", flush=True)
+    return np.concatenate(X), np.concatenate(y), meta
+
+
+def evaluate(model: vtm.MLP, family: str, seeds, rtol=1e-8, matched=True, verbose=True):
+    rows = []
+    for sd in seeds:
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        row = dict(seed=sd, sigma=sigma, dims=dims)
+        row["z1"] = ev.to_tolerance(1.0, rtol)
+        row["learned"] = ev.to_tolerance(model, rtol)
+        if matched:
+            row["matched"] = ev.to_tolerance("matched", rtol)
+        rows.append(row)
+        if verbose:
+            print(f"eval seed {sd}: Z=1 {row['z1']['sweeps']}  learned {row['learned']['sweeps']}"
+                  + (f"  matched {row['matched']['sweeps']}" if matched else ""), flush=True)
+    return rows
+
+
+def save(model: vtm.MLP, path: str, **meta):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(dict(params=[float(v) for v in model.get_params()], **meta), f)
+
+
+def load(path: str) -> vtm.MLP:
+    with open(path) as f:
+        d = json.load(f)
+    m = vtm.MLP(seed=0)
+    m.set_params(np.asarray(d["params"], np.float32))
+    return m
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--family", default="poisson2d-256")
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=60)
+    ap.add_argument("--sweeps", type=int, default=300)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    t0 = time.time()
+    X, y, meta = build_dataset(a.family, range(a.train), a.sweeps)
+    t_search = time.time() - t0
+    model = vtm.MLP(seed=1)
+    hist = train(model, X, y, epochs=a.epochs)
+    print(f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}", flush=True)
+    rows = evaluate(model, a.family, range(100_000, 100_000 + a.test))
+    summ = {k: float(np.median([r[k]["sweeps"] for r in rows])) for k in ("z1", "learned", "matched")}
+    print("median sweeps to 1e-8 on held-out seeds:", summ, flush=True)
+    out = a.out or os.path.join(MODELS, f"z_{a.family}.json")
+    save(model, out, family=a.family, train_seeds=a.train, test_seeds=a.test, search_sweeps=a.sweeps,
+         search_seconds=round(t_search, 1), loss=hist, search=meta, eval=rows, median_sweeps=summ,
+         features="vtm_line_features (8 per end)", target="log Z of the searched family, both ends")
+
+
+if __name__ == "__main__":
+    main()

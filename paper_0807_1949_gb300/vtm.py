@@ -21,7 +21,8 @@ VTM_OK = 0
 STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SYMMETRIC", 3: "NOT_CONFORMAL", 4: "NOT_SPD", 5: "NOT_CONVERGED",
           6: "DIVERGED", 7: "TIMEOUT", 8: "CUDA", 9: "OOM"}
 PART_GRID, PART_OWNERS, PART_EXPLICIT = 1, 2, 3
-Z_UNIFORM, Z_EXPLICIT = 0, 1
+Z_UNIFORM, Z_EXPLICIT, Z_MATCHED, Z_LEARNED = 0, 1, 2, 3
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 FP64, FP32 = 0, 1
 
 
@@ -51,7 +52,8 @@ class PartitionInfo(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("z_mode", C.c_int32), ("z_uniform", C.c_double), ("z_lines", C.c_void_p), ("precision", C.c_int32),
-                ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double)]
+                ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double),
+                ("model", C.c_void_p)]
 
 
 class SolverInfo(C.Structure):
@@ -91,6 +93,17 @@ def _load():
         "vtm_iterate": (C.c_int, [vp, i32]),
         "vtm_solve": (C.c_int, [vp, vp, vp, i64, dbl, i32, vp]),
         "vtm_get_state": (C.c_int, [vp, vp]),
+        "vtm_input_impedances": (C.c_int, [vp, vp]),
+        "vtm_solver_get_impedances": (C.c_int, [vp, vp]),
+        "vtm_line_features": (C.c_int, [vp, vp]),
+        "vtm_mlp_create": (C.c_int, [C.c_uint64, vp]),
+        "vtm_mlp_destroy": (None, [vp]),
+        "vtm_mlp_get_params": (C.c_int, [vp, vp]),
+        "vtm_mlp_set_params": (C.c_int, [vp, vp]),
+        "vtm_mlp_get_grads": (C.c_int, [vp, vp]),
+        "vtm_mlp_forward": (C.c_int, [vp, vp, vp, i64, vp]),
+        "vtm_mlp_loss_grad": (C.c_int, [vp, vp, vp, i64, vp, vp]),
+        "vtm_mlp_adam_step": (C.c_int, [vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]),
         "vtm_set_state": (C.c_int, [vp, vp]),
         "vtm_get_copies": (C.c_int, [vp, vp]),
         "vtm_relative_residual_noalloc": (C.c_int, [i64, vp, vp, vp, i32, vp, i64, vp, i64, vp, vp]),
@@ -162,6 +175,12 @@ class Partition:
         q = np.empty((self.info().nlines, 4), np.int64)
         _check(_lib.vtm_partition_get_lines(self._h, _ptr(q)))
         return q
+
+    def line_features(self) -> np.ndarray:
+        """(nends, 8) float32 features of every line end (vtm_line_features)."""
+        f = np.empty((2 * self.info().nlines, MLP_IN), np.float32)
+        _check(_lib.vtm_line_features(self._h, _ptr(f)))
+        return f
 
 
 def _csr_struct(A):
@@ -240,16 +259,23 @@ def _data_ptr(x):
 class Solver:
     """vtm_setup / vtm_iterate / vtm_solve on one partition.
 
-    z: scalar (uniform) or per-line array (order of Partition.lines()).
+    z: scalar (uniform), per-line array (order of Partition.lines()), "matched" (§7.1 rule,
+       starting from z_init on every line), or an ``MLP`` (learned impedances).
     precision: "fp64" or "fp32".  nrhs: 1, 2, 4 or 8.
     Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
     """
 
     def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
-                 check_every: int = 10, inner_reduction: float = 0.0):
+                 check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0):
         o = _Opts()
         zarr = None
-        if np.ndim(z) == 0:
+        if isinstance(z, MLP):
+            o.z_mode, o.model = Z_LEARNED, z.handle.value
+        elif isinstance(z, str):
+            if z != "matched":
+                raise ValueError(z)
+            o.z_mode, o.z_uniform = Z_MATCHED, float(z_init)
+        elif np.ndim(z) == 0:
             o.z_mode, o.z_uniform = Z_UNIFORM, float(z)
         else:
             zarr = _arr(z, np.float64)
@@ -295,6 +321,18 @@ class Solver:
         st.status = code
         return st
 
+    def impedances(self) -> np.ndarray:
+        """Line impedances in use, (nlines,)."""
+        z = np.empty(self.info().nends // 2, np.float64)
+        _check(_lib.vtm_solver_get_impedances(self._h, _ptr(z)))
+        return z
+
+    def input_impedances(self) -> np.ndarray:
+        """Input impedance of every line end (Def. 7.1, other lines terminated), (nends,)."""
+        r = np.empty(self.info().nends, np.float64)
+        _check(_lib.vtm_input_impedances(self._h, _ptr(r)))
+        return r
+
     def get_state(self) -> np.ndarray:
         """Outgoing waves of the last sweep, (nrhs, nends), end 2t / 2t+1 = sides a / b of line t."""
         ne = self.info().nends
@@ -312,6 +350,53 @@ class Solver:
         x = np.empty((self.nrhs, nc), np.float64)
         _check(_lib.vtm_get_copies(self._h, _ptr(x)))
         return x
+
+
+class MLP:
+    """Learned impedance model (vtm_mlp_*): 8 -> 64 -> 64 -> 1, BF16 weights, FP32 accumulate."""
+
+    def __init__(self, seed: int = 0):
+        h = C.c_void_p()
+        _check(_lib.vtm_mlp_create(C.c_uint64(seed), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.vtm_mlp_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(MLP_PARAMS, np.float32)
+        _check(_lib.vtm_mlp_get_params(self._h, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        a = _arr(p, np.float32)
+        assert a.size == MLP_PARAMS
+        _check(_lib.vtm_mlp_set_params(self._h, _ptr(a)))
+
+    def get_grads(self) -> np.ndarray:
+        g = np.empty(MLP_PARAMS, np.float32)
+        _check(_lib.vtm_mlp_get_grads(self._h, _ptr(g)))
+        return g
+
+    def forward(self, X, y, stream=None):
+        """X: CUDA float32 (n, 8); y: CUDA float32 (n,)."""
+        _check(_lib.vtm_mlp_forward(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(y.data_ptr()), int(X.shape[0]),
+                                    _stream_handle(stream)))
+
+    def loss_grad(self, X, t, stream=None) -> float:
+        l = C.c_float()
+        _check(_lib.vtm_mlp_loss_grad(self._h, C.c_void_p(X.data_ptr()), C.c_void_p(t.data_ptr()), int(X.shape[0]),
+                                      C.byref(l), _stream_handle(stream)))
+        return l.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(_lib.vtm_mlp_adam_step(self._h, lr, beta1, beta2, eps, _stream_handle(stream)))
 
 
 def relative_residual_noalloc(rowptr, col, val, b, x, rel, stream=None):

@@ -119,3 +119,19 @@ def test_errors_are_reported(vtmlib):
     with pytest.raises(vtmlib.VTMError) as e:
         vtmlib.partition_evs(inputs.csr_from_dense(D), "owners", owners=[(0, 1), (1,), (1,)], lines=[(0, 0, 1)])
     assert e.value.code == 3
+
+
+@pytest.mark.parametrize("dims,block,sigma", [((9, 7, 6), (4, 3, 5), 0.7), ((17, 12), (8, 5), 1.3)])
+def test_line_features_match_oracle(vtmlib, dims, block, sigma):
+    from oracle import features
+    A = inputs.grid_poisson(dims, sigma=sigma, seed=3)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    got = part.line_features()
+    ref = features.line_features(osplit, A)
+    idx = {tuple(int(x) for x in q): t for t, q in enumerate(osplit.vtl)}
+    order = []
+    for q in part.lines():
+        t = idx[tuple(int(x) for x in q)]
+        order += [2 * t, 2 * t + 1]
+    assert np.allclose(got, ref[order], rtol=1e-6, atol=1e-6)
