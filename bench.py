@@ -31,11 +31,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: dims, block, sigma, rtol
-    "poisson3d-128": dict(dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0, rtol=1e-8),
-    "laplace2d-32": dict(dims=(32, 32), block=(16, 16), sigma=0.0, rtol=1e-8),
-    # small case of the same subgraph shape (64 subgraphs, 0.37 GB factor > L2) for ncu captures
-    "poisson3d-64": dict(dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, rtol=1e-8),
+    # the benchmarked configuration: 3D 128^3, sigma = 1, 512 subgraphs, one right-hand side
+    "poisson3d-128": dict(kind="grid", dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0, nrhs=1,
+                          z="learned:poisson3d", rtol=1e-8),
+    # large multi-RHS run: 256^3, sigma = 1.5, 4096 subgraphs, 32 right-hand sides per sweep
+    "poisson3d-256-r32": dict(kind="grid", dims=(256, 256, 256), block=(16, 16, 16), sigma=1.5, nrhs=32,
+                              z="learned:poisson3d", rtol=1e-8),
+    # uneven batching: P1 FEM on the Delaunay triangulation of 1M points, 2000 RCB subgraphs, 16 RHS
+    "fem2d-1m-r16": dict(kind="fem", npoints=1_000_000, pieces=2000, nrhs=16, z="matched", z_init=1e-2,
+                         rtol=1e-8),
+    # learned-impedance family: 2D 256^2, 64 subgraphs
+    "poisson2d-256": dict(kind="grid", dims=(256, 256), block=(32, 32), sigma=1.25, nrhs=1,
+                          z="learned:poisson2d-256", rtol=1e-8),
+    "laplace2d-32": dict(kind="grid", dims=(32, 32), block=(16, 16), sigma=0.0, nrhs=1, z=1.0, rtol=1e-8),
+    # small case of the 3D subgraph shape (64 subgraphs, 0.37 GB factor > L2) for ncu captures
+    "poisson3d-64": dict(kind="grid", dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, nrhs=1, z=1.0, rtol=1e-8),
 }
 METRIC = "time to rel. residual 1e-8 (learned-Z batched vs plain VTM) on 1 GB300; HBM GB/s"
 
@@ -250,6 +260,34 @@ def reference_sweeps(workload: str) -> int:
         return -1
 
 
+def build_problem(w, vtm, inputs):
+    """(A, partition, b) of a workload; b has shape (nrhs, n)."""
+    if w["kind"] == "grid":
+        A = inputs.grid_poisson(w["dims"], sigma=w["sigma"], seed=0)
+        t0 = time.perf_counter()
+        part = vtm.partition_evs(A, "grid", dims=w["dims"], block=w["block"])
+    else:
+        fem = inputs.fem_delaunay(w["npoints"], seed=0)
+        A = fem.A
+        t0 = time.perf_counter()
+        part = vtm.partition_evs(A, "elements", elements=dict(elem_nodes=fem.elem_nodes, elem_mats=fem.elem_mats,
+                                                            node_unknown=fem.node_unknown,
+                                                            elem_coords=fem.centroids), npieces=w["pieces"])
+    t_part = time.perf_counter() - t0
+    b = inputs.rhs_uniform(A.n, w["nrhs"], seed=0)
+    return A, part, b, t_part
+
+
+def impedance_arg(w, vtm):
+    z = w["z"]
+    if isinstance(z, str) and z.startswith("learned:"):
+        from paper_0807_1949_gb300 import learned_z
+
+        path = os.path.join(learned_z.MODELS, "z_" + z.split(":", 1)[1] + ".json")
+        return learned_z.load(path), z
+    return z, z
+
+
 def run_vtm(args):
     import numpy as np
     import torch
@@ -259,15 +297,12 @@ def run_vtm(args):
     from paper_0807_1949_gb300 import inputs, vtm
 
     w = WORKLOADS[args.workload]
-    t0 = time.perf_counter()
-    A = inputs.grid_poisson(w["dims"], sigma=w["sigma"], seed=0)
-    b = inputs.rhs_uniform(A.n, 1, seed=0)
-    t_gen = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    part = vtm.partition_evs(A, "grid", dims=w["dims"], block=w["block"])
-    t_part = time.perf_counter() - t0
+    A, part, b, t_part = build_problem(w, vtm, inputs)
+    R = w["nrhs"]
     stream = torch.cuda.Stream()
-    solver = vtm.Solver(part, z=1.0, precision="fp32", nrhs=1, stream=stream, check_every=10)
+    zarg, zdesc = impedance_arg(w, vtm)
+    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=10,
+                        z_init=w.get("z_init", 1.0))
     sinfo = solver.info()
     bd = torch.tensor(b, device="cuda")
     xd = torch.zeros_like(bd)
@@ -293,9 +328,10 @@ def run_vtm(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = max_over_ranks(ws, ms)
     x = xd.cpu().numpy()
-    rel = float(np.linalg.norm(b[0] - A.to_scipy() @ x[0]) / np.linalg.norm(b[0]))
+    As = A.to_scipy()
+    rel = float(np.max(np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)))
     sweeps = stats[-1].sweeps
-    launches = sum(s.launches for s in stats)
+    launches = sum(s_.launches for s_ in stats)
 
     # ---- dominant kernel: one sweep launch, CUDA events around back-to-back sweeps
     solver.set_rhs(bd)
@@ -310,11 +346,14 @@ def run_vtm(args):
     torch.cuda.synchronize()
     sweep_ms = k0.elapsed_time(k1) / nsw
     elem = 4
-    alg_bytes = (2 * sinfo.band_entries * elem + sinfo.ncopies * elem + 2 * sinfo.nends * elem
-                 + sinfo.nends * 8)
+    vec_passes = 4 if R >= 16 else 1   # wide kernel: b̃ read, y written and read back, x written
+    alg_bytes = (2 * sinfo.band_entries * elem + vec_passes * sinfo.ncopies * R * elem
+                 + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
     pk = peaks()
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc", "sweep.cu"), args.workload)
+    kname = ("k_sweep_wide<float,%d>" % R) if R >= 16 else ("k_sweep<float,%d>" % R)
+    traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc",
+                                          "sweep_wide.cu" if R >= 16 else "sweep.cu"), args.workload)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.tensor(b).pin_memory()
@@ -327,49 +366,56 @@ def run_vtm(args):
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = max_over_ranks(ws, statistics.median(e2e))
 
-    # ---- plain method (FP64 factors, no correction), same workload
+    # ---- plain method (FP64 factors, Z = 1, no correction), same workload, one right-hand side
     plain = None
     if not args.no_plain:
         del solver
         torch.cuda.empty_cache()
         ps = vtm.Solver(part, z=1.0, precision="fp64", nrhs=1, stream=stream, check_every=10)
-        ps.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+        b1, x1 = bd[:1].contiguous(), torch.zeros_like(bd[:1])
+        ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
         torch.cuda.synchronize()
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        pst = ps.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+        pst = ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
         p1.record(stream)
         torch.cuda.synchronize()
-        plain = {"ms": round(p0.elapsed_time(p1), 3), "sweeps": pst.sweeps, "setup_ms": round(ps.info().setup_ms, 1),
-                 "precision": "fp64", "z": 1.0}
+        plain = {"ms": round(p0.elapsed_time(p1), 3), "nrhs": 1, "sweeps": pst.sweeps, "converged": pst.status == 0,
+                 "setup_ms": round(ps.info().setup_ms, 1), "precision": "fp64", "z": 1.0}
+        if R > 1:
+            plain["ms_for_all_rhs"] = round(plain["ms"] * R, 3)
         del ps
 
     if rank != 0:
         return 0
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and w["kind"] == "grid":
         ks = plain["sweeps"] if plain else sweeps
         cpu = cpu_baseline(args.workload, ks)
+        if cpu.get("value") is not None and R > 1:
+            cpu["value"] = round(cpu["value"] * R, 3)
+            cpu["sample"] += f"; times {R} right-hand sides"
+    cfg = {"workload": args.workload, "nrhs": R, "rtol": w["rtol"], "z": zdesc, "pieces": sinfo.npieces,
+           "parallelism": "replicas" if ws > 1 else "single",
+           "l2": "inputs larger than L2 (FP32 factor %.2f GB)" % (sinfo.factor_bytes / 1e9),
+           "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,
+           "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
+           "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
+           "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain}
+    cfg.update({k: w[k] for k in ("dims", "block", "sigma", "npoints") if k in w})
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (f64 residual + defect correction)", "data": "synthetic",
-        "config": {"workload": args.workload, "dims": w["dims"], "block": w["block"], "sigma": w["sigma"],
-                   "rtol": w["rtol"], "z": 1.0, "pieces": sinfo.npieces, "nrhs": 1,
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (FP32 factor %.2f GB)" % (sinfo.factor_bytes / 1e9),
-                   "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,
-                   "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
-                   "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
-                   "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep<float,1>", "achieved": round(achieved, 1),
+        "config": cfg,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "peak_source": pk["source"], "unit": "GB/s",
                      "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
                      "alg_bytes_per_launch": int(alg_bytes), "launch_ms": round(sweep_ms, 4)},
         "cpu_baseline": cpu,
-        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(A.n * 8),
-                "d2h_bytes_per_step": int(A.n * 8)},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(A.n * 8 * R),
+                "d2h_bytes_per_step": int(A.n * 8 * R)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

@@ -76,7 +76,18 @@ enum vtm_partition_kind {
   VTM_PART_OWNERS = 2,
   /* A complete split given explicitly: copies, local matrices Ã_j, source shares and lines
    * (any conformal scheme, e.g. the uneven shares of Example 4.1). */
-  VTM_PART_EXPLICIT = 3
+  VTM_PART_EXPLICIT = 3,
+  /* Finite elements split by elements (§4: "do the partitioning on the physical level"): every
+   * element belongs to one subgraph, Ã_j is the sum of its elements' matrices (each SPSD, so every
+   * piece is SNND, Cor. 4.1, and the pieces sum to A exactly up to rounding); b_i is shared as
+   * b_i/|O(i)|.  Elements go to subgraphs by elem_piece, or, when elem_piece is NULL, by recursive
+   * coordinate bisection of elem_coords into npieces parts (split the element set at position
+   * floor(|E| * floor(p/2) / p) of its order by (coordinate, element id) along the axis of largest
+   * extent; the first part recursively gets ids base..base+floor(p/2)-1).  Copies inside a
+   * subgraph are in reverse Cuthill-McKee order (start: a minimum-degree node, smallest id on ties;
+   * neighbours by increasing degree, then id).  Lines: the copies of vertex i in subgraphs p and q
+   * are joined when an element edge through i has elements of both p and q around it. */
+  VTM_PART_ELEMENTS = 4
 };
 
 /* Split rule of GRID and OWNERS (§4 step 3; the paper leaves the shares open, this is the
@@ -108,6 +119,16 @@ typedef struct vtm_partition_spec {
   int64_t ncopy_lines;        /* EXPLICIT: lines as pairs of copy ids                            */
   const int64_t* line_copy_a;
   const int64_t* line_copy_b;
+  /* ELEMENTS */
+  int64_t nelem;              /* number of elements                                              */
+  int32_t nodes_per_elem;     /* k (3 for triangles)                                              */
+  int64_t nnodes;             /* nodes of the mesh (including eliminated ones)                    */
+  const int64_t* elem_nodes;  /* host, nelem x k mesh node ids                                    */
+  const double* elem_mats;    /* host, nelem x k x k element matrices (row-major)                 */
+  const int64_t* node_unknown;/* host, nnodes: row of A of each node, -1 if eliminated            */
+  const int32_t* elem_piece;  /* host, nelem subgraph ids, or NULL for RCB                        */
+  const double* elem_coords;  /* host, nelem x coord_dim (RCB)                                    */
+  int32_t coord_dim;
 } vtm_partition_spec;
 
 typedef struct vtm_partition vtm_partition;
@@ -126,6 +147,9 @@ typedef struct vtm_partition_info {
  * that do not exist), VTM_ERR_NOT_SYMMETRIC, VTM_ERR_NOT_CONFORMAL. */
 int vtm_partition_evs(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition** out);
 int vtm_partition_get_info(const vtm_partition* p, vtm_partition_info* info);
+/* Recursive coordinate bisection used by VTM_PART_ELEMENTS (rule in its comment): coords host
+ * n x dim (dim 1..3), out host n subgraph ids in [0, nparts).  Host only. */
+int vtm_rcb(const double* coords, int64_t n, int32_t dim, int32_t nparts, int32_t* out);
 /* Subgraph j (eq. 4.4): copies' parent vertices (host, n_j int64), shares (host, n_j double) and
  * Ã_j in local CSR (rowptr n_j+1 int64, col int32, val double).  Any output may be NULL; call
  * first with NULL arrays to read *n_j and *nnz_j. */

@@ -288,3 +288,78 @@ def grid_piece_line_count(dims, block, piece: int) -> np.ndarray:
     for a, coord in enumerate((xx.ravel(), yy.ravel(), zz.ravel())):
         cnt += np.array([len(per_axis[a][c]) == 2 for c in coord], dtype=np.int64)
     return cnt
+
+
+def rcb(coords: np.ndarray, nparts: int) -> np.ndarray:
+    """Recursive coordinate bisection: split at position floor(|E| floor(p/2) / p) of the order by
+    (coordinate, id) along the axis of largest extent; the first part gets the lower ids."""
+    coords = np.asarray(coords, dtype=np.float64)
+    piece = np.zeros(len(coords), dtype=np.int64)
+
+    def rec(ids, p, base):
+        if p <= 1:
+            piece[ids] = base
+            return
+        pl = p // 2
+        ext = coords[ids].max(axis=0) - coords[ids].min(axis=0)
+        axis = int(np.argmax(ext))
+        order = ids[np.lexsort((ids, coords[ids, axis]))]
+        m = (len(ids) * pl) // p
+        rec(order[:m], pl, base)
+        rec(order[m:], p - pl, base + pl)
+
+    rec(np.arange(len(coords)), nparts, 0)
+    return piece
+
+
+def split_by_elements(A, elem_nodes, elem_mats, node_unknown, elem_piece) -> SplitGraph:
+    """EVS on the physical level (§4): each element goes to one subgraph, Ã_j = sum of its elements'
+    matrices (SPSD each, so every piece is SNND, Cor. 4.1), b_i shared as b_i / |O(i)|.  Lines join
+    the copies of vertex i in p and q when an element edge through i has elements of p and q around
+    it.  Local order: ascending vertex.  Line order: sorted (vertex, p, q)."""
+    A = _as_csr(A)
+    n = A.shape[0]
+    elem_nodes = np.asarray(elem_nodes)
+    k = elem_nodes.shape[1]
+    npieces = int(np.max(elem_piece)) + 1
+    U = np.asarray(node_unknown)[elem_nodes]
+    subs, local = [], []
+    ncop = np.zeros(n, dtype=np.int64)
+    for j in range(npieces):
+        es = np.nonzero(elem_piece == j)[0]
+        verts = np.unique(U[es][U[es] >= 0])
+        ncop[verts] += 1
+        local.append({int(v): c for c, v in enumerate(verts)})
+        subs.append((es, verts))
+    out = []
+    for j, (es, verts) in enumerate(subs):
+        rows, cols, vals = [], [], []
+        for e in es:
+            for a in range(k):
+                for b in range(k):
+                    ua, ub = U[e, a], U[e, b]
+                    if ua >= 0 and ub >= 0:
+                        rows.append(local[j][int(ua)]); cols.append(local[j][int(ub)]); vals.append(elem_mats[e][a][b])
+        m = len(verts)
+        Aj = sp.coo_matrix((vals, (rows, cols)), shape=(m, m)).tocsr()
+        out.append(Subgraph(vertices=verts.astype(np.int64), A=Aj, share=1.0 / ncop[verts]))
+    edge_pieces = {}
+    for e in range(len(elem_nodes)):
+        for a in range(k):
+            for b in range(a + 1, k):
+                u, v = sorted((int(elem_nodes[e, a]), int(elem_nodes[e, b])))
+                edge_pieces.setdefault((u, v), set()).add(int(elem_piece[e]))
+    trip = set()
+    for (u, v), ps in edge_pieces.items():
+        if len(ps) < 2:
+            continue
+        ps = sorted(ps)
+        for node in (u, v):
+            x = int(node_unknown[node])
+            if x < 0:
+                continue
+            for i1 in range(len(ps)):
+                for i2 in range(i1 + 1, len(ps)):
+                    trip.add((x, ps[i1], ps[i2]))
+    vtl = np.array([(p, local[p][x], q, local[q][x]) for (x, p, q) in sorted(trip)], dtype=np.int64).reshape(-1, 4)
+    return SplitGraph(n=n, subgraphs=out, vtl=vtl)

@@ -20,6 +20,7 @@ void solver_get_copies(vtm_solver* s, double* out);
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info);
 void solver_input_impedances(vtm_solver* s, double* r);
 void line_features(const vtm_partition* p, float* out);
+void element_pieces(const vtm_partition_spec* sp, int32_t* out);
 void solver_get_impedances(const vtm_solver* s, double* z);
 vtm_mlp* mlp_create(uint64_t seed);
 void mlp_set_params(vtm_mlp* m, const float* host);
@@ -72,6 +73,20 @@ int vtm_partition_evs(const vtm_csr* A, const vtm_partition_spec* spec, vtm_part
       throw;
     }
     *out = p;
+    return VTM_OK;
+  });
+}
+
+int vtm_rcb(const double* coords, int64_t n, int32_t dim, int32_t nparts, int32_t* out) {
+  return guarded([&] {
+    if (!coords || !out || n < 1 || dim < 1 || dim > 3 || nparts < 1 || nparts > n)
+      vtm::fail(VTM_ERR_INVALID, "vtm_rcb: bad arguments");
+    vtm_partition_spec sp{};
+    sp.nelem = n;
+    sp.elem_coords = coords;
+    sp.coord_dim = dim;
+    sp.npieces = nparts;
+    vtm::element_pieces(&sp, out);
     return VTM_OK;
   });
 }

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <thread>
+#include <tuple>
 
 #include "internal.h"
 
@@ -389,6 +390,7 @@ void build_explicit(const vtm_partition_spec* sp, vtm_partition* p) {
 }  // namespace
 
 namespace vtm {
+void build_elements(const vtm_partition_spec* sp, vtm_partition* p);
 void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition* p) {
   if (!spec) fail(VTM_ERR_INVALID, "null partition spec");
   copy_and_check_matrix(A, p);
@@ -396,6 +398,7 @@ void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_parti
     case VTM_PART_GRID: build_grid(spec, p); break;
     case VTM_PART_OWNERS: build_owners(spec, p); break;
     case VTM_PART_EXPLICIT: build_explicit(spec, p); break;
+    case VTM_PART_ELEMENTS: build_elements(spec, p); break;
     default: fail(VTM_ERR_INVALID, "unknown partition kind");
   }
   // every copy that has a line must sit in a piece; pieces must be non-empty
@@ -454,6 +457,274 @@ void line_features(const vtm_partition* p, float* out) {
     f[6] = (amax > 0 && std::isfinite(amin) && amin > 0) ? (float)std::log(amax / amin) : 0.f;
     f[7] = (float)std::log((double)p->n / (double)nj);
   }
+}
+
+}  // namespace vtm
+
+// ------------------------------------------------------------------------------------------ ELEMENTS
+
+namespace {
+
+using vtm::fail;
+
+void rcb(const double* coords, int dim, std::vector<int64_t>& ids, int64_t lo, int64_t hi, int32_t nparts, int32_t base,
+         std::vector<int32_t>& piece) {
+  if (nparts <= 1) {
+    for (int64_t k = lo; k < hi; ++k) piece[ids[k]] = base;
+    return;
+  }
+  const int32_t pl = nparts / 2;
+  int axis = 0;
+  double best = -1.0;
+  for (int a = 0; a < dim; ++a) {
+    double mn = INFINITY, mx = -INFINITY;
+    for (int64_t k = lo; k < hi; ++k) {
+      const double v = coords[ids[k] * dim + a];
+      mn = std::min(mn, v);
+      mx = std::max(mx, v);
+    }
+    if (mx - mn > best) {
+      best = mx - mn;
+      axis = a;
+    }
+  }
+  std::sort(ids.begin() + lo, ids.begin() + hi, [&](int64_t x, int64_t y) {
+    const double vx = coords[x * dim + axis], vy = coords[y * dim + axis];
+    return vx < vy || (vx == vy && x < y);
+  });
+  const int64_t m = lo + ((hi - lo) * (int64_t)pl) / nparts;
+  rcb(coords, dim, ids, lo, m, pl, base, piece);
+  rcb(coords, dim, ids, m, hi, nparts - pl, base + pl, piece);
+}
+
+// Reverse Cuthill-McKee order of a small graph given as adjacency lists over 0..m-1.
+std::vector<int32_t> rcm_order(const std::vector<std::vector<int32_t>>& adj) {
+  const int32_t m = (int32_t)adj.size();
+  std::vector<int32_t> order;
+  order.reserve(m);
+  std::vector<char> seen(m, 0);
+  auto deg = [&](int32_t v) { return (int32_t)adj[v].size(); };
+  for (;;) {
+    int32_t start = -1;
+    for (int32_t v = 0; v < m; ++v)
+      if (!seen[v] && (start < 0 || deg(v) < deg(start))) start = v;
+    if (start < 0) break;
+    const size_t first = order.size();
+    order.push_back(start);
+    seen[start] = 1;
+    for (size_t h = first; h < order.size(); ++h) {
+      std::vector<int32_t> nb;
+      for (int32_t u : adj[order[h]])
+        if (!seen[u]) {
+          seen[u] = 1;
+          nb.push_back(u);
+        }
+      std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg(a) < deg(b) || (deg(a) == deg(b) && a < b); });
+      for (int32_t u : nb) order.push_back(u);
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+}  // namespace
+
+namespace vtm {
+
+void build_elements(const vtm_partition_spec* sp, vtm_partition* p) {
+  const int64_t ne = sp->nelem;
+  const int k = sp->nodes_per_elem;
+  if (ne < 1 || k < 2 || k > 64 || !sp->elem_nodes || !sp->elem_mats || !sp->node_unknown || sp->nnodes < 1)
+    fail(VTM_ERR_INVALID, "elements: missing arrays");
+  if (sp->npieces < 1) fail(VTM_ERR_INVALID, "elements: npieces must be >= 1");
+  const int32_t np = sp->npieces;
+  p->npieces = np;
+  std::vector<int32_t> epiece(ne);
+  if (sp->elem_piece) {
+    for (int64_t e = 0; e < ne; ++e) {
+      epiece[e] = sp->elem_piece[e];
+      if (epiece[e] < 0 || epiece[e] >= np) fail(VTM_ERR_INVALID, "elements: piece id out of range");
+    }
+  } else {
+    if (!sp->elem_coords || sp->coord_dim < 1 || sp->coord_dim > 3) fail(VTM_ERR_INVALID, "elements: RCB needs coordinates");
+    if (np > ne) fail(VTM_ERR_INVALID, "elements: more pieces than elements");
+    std::vector<int64_t> ids(ne);
+    for (int64_t e = 0; e < ne; ++e) ids[e] = e;
+    rcb(sp->elem_coords, sp->coord_dim, ids, 0, ne, np, 0, epiece);
+  }
+  auto unk = [&](int64_t node) -> int64_t {
+    if (node < 0 || node >= sp->nnodes) fail(VTM_ERR_INVALID, "elements: node id out of range");
+    const int64_t u = sp->node_unknown[node];
+    if (u >= p->n) fail(VTM_ERR_INVALID, "elements: unknown index out of range");
+    return u;
+  };
+  // elements of each piece
+  std::vector<std::vector<int64_t>> pel(np);
+  for (int64_t e = 0; e < ne; ++e) pel[epiece[e]].push_back(e);
+  // per piece: vertices (unknowns), RCM order, local matrix
+  std::vector<std::vector<int64_t>> pverts(np);
+  std::vector<std::vector<int64_t>> prow_cols(np);
+  std::vector<int64_t> ncop(p->n, 0);
+  struct Local {
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+  };
+  std::vector<Local> loc(np);
+  parallel_for(np, [&](int64_t jj) {
+    const int32_t j = (int32_t)jj;
+    std::vector<int64_t> vs;
+    for (int64_t e : pel[j])
+      for (int a = 0; a < k; ++a) {
+        const int64_t u = unk(sp->elem_nodes[e * k + a]);
+        if (u >= 0) vs.push_back(u);
+      }
+    std::sort(vs.begin(), vs.end());
+    vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+    const int32_t m = (int32_t)vs.size();
+    auto lid = [&](int64_t u) { return (int32_t)(std::lower_bound(vs.begin(), vs.end(), u) - vs.begin()); };
+    std::vector<std::vector<int32_t>> adj(m);
+    for (int64_t e : pel[j])
+      for (int a = 0; a < k; ++a) {
+        const int64_t ua = unk(sp->elem_nodes[e * k + a]);
+        if (ua < 0) continue;
+        for (int b = 0; b < k; ++b) {
+          const int64_t ub = unk(sp->elem_nodes[e * k + b]);
+          if (ub < 0 || b == a) continue;
+          adj[lid(ua)].push_back(lid(ub));
+        }
+      }
+    for (auto& l : adj) {
+      std::sort(l.begin(), l.end());
+      l.erase(std::unique(l.begin(), l.end()), l.end());
+    }
+    const std::vector<int32_t> ord = rcm_order(adj);  // ord[new] = old
+    std::vector<int32_t> newid(m);
+    for (int32_t t = 0; t < m; ++t) newid[ord[t]] = t;
+    // local matrix rows in the new order: sum of element contributions, columns merged
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(m);
+    for (int64_t e : pel[j]) {
+      const double* K = sp->elem_mats + e * k * k;
+      for (int a = 0; a < k; ++a) {
+        const int64_t ua = unk(sp->elem_nodes[e * k + a]);
+        if (ua < 0) continue;
+        const int32_t ra = newid[lid(ua)];
+        for (int b = 0; b < k; ++b) {
+          const int64_t ub = unk(sp->elem_nodes[e * k + b]);
+          if (ub < 0) continue;
+          rows[ra].emplace_back(newid[lid(ub)], K[a * k + b]);
+        }
+      }
+    }
+    Local& L = loc[j];
+    L.rowptr.assign(m + 1, 0);
+    for (int32_t r = 0; r < m; ++r) {
+      auto& rr = rows[r];
+      std::stable_sort(rr.begin(), rr.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      for (size_t q = 0; q < rr.size();) {
+        size_t q2 = q;
+        double v = 0.0;
+        while (q2 < rr.size() && rr[q2].first == rr[q].first) v += rr[q2++].second;
+        L.col.push_back(rr[q].first);
+        L.val.push_back(v);
+        q = q2;
+      }
+      L.rowptr[r + 1] = (int64_t)L.col.size();
+    }
+    std::vector<int64_t> vnew(m);
+    for (int32_t t = 0; t < m; ++t) vnew[t] = vs[ord[t]];
+    pverts[j] = std::move(vnew);
+  });
+  p->piece_ptr.assign(np + 1, 0);
+  for (int32_t j = 0; j < np; ++j) {
+    if (pverts[j].empty()) fail(VTM_ERR_INVALID, "elements: a subgraph has no unknowns");
+    p->piece_ptr[j + 1] = p->piece_ptr[j] + (int64_t)pverts[j].size();
+    for (int64_t u : pverts[j]) ncop[u]++;
+  }
+  for (int64_t i = 0; i < p->n; ++i)
+    if (ncop[i] == 0) fail(VTM_ERR_INVALID, "elements: an unknown belongs to no element");
+  const int64_t C = p->piece_ptr[np];
+  p->copy_vertex.resize(C);
+  p->copy_share.resize(C);
+  p->l_rowptr.assign(C + 1, 0);
+  int64_t nb = 0;
+  for (int64_t i = 0; i < p->n; ++i) nb += ncop[i] > 1;
+  p->nboundary = nb;
+  for (int32_t j = 0; j < np; ++j) {
+    const int64_t c0 = p->piece_ptr[j];
+    const Local& L = loc[j];
+    const int64_t k0 = (int64_t)p->l_col.size();
+    for (size_t t = 0; t < pverts[j].size(); ++t) {
+      p->copy_vertex[c0 + t] = pverts[j][t];
+      p->copy_share[c0 + t] = 1.0 / (double)ncop[pverts[j][t]];
+      p->l_rowptr[c0 + t + 1] = k0 + L.rowptr[t + 1];
+    }
+    p->l_col.insert(p->l_col.end(), L.col.begin(), L.col.end());
+    p->l_val.insert(p->l_val.end(), L.val.begin(), L.val.end());
+  }
+  // lines: element edges through a vertex with elements of two subgraphs around them
+  std::vector<std::tuple<int64_t, int64_t, int32_t>> edges;  // (lo node, hi node, piece)
+  edges.reserve((size_t)ne * k * (k - 1) / 2);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b) {
+        const int64_t u = sp->elem_nodes[e * k + a], v = sp->elem_nodes[e * k + b];
+        edges.emplace_back(std::min(u, v), std::max(u, v), epiece[e]);
+      }
+  std::sort(edges.begin(), edges.end());
+  std::vector<std::tuple<int64_t, int32_t, int32_t>> trip;  // (vertex, pa, pb)
+  for (size_t q = 0; q < edges.size();) {
+    size_t q2 = q;
+    std::vector<int32_t> ps;
+    while (q2 < edges.size() && std::get<0>(edges[q2]) == std::get<0>(edges[q]) &&
+           std::get<1>(edges[q2]) == std::get<1>(edges[q])) {
+      ps.push_back(std::get<2>(edges[q2]));
+      ++q2;
+    }
+    std::sort(ps.begin(), ps.end());
+    ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
+    if (ps.size() > 1)
+      for (int64_t node : {std::get<0>(edges[q]), std::get<1>(edges[q])}) {
+        const int64_t u = unk(node);
+        if (u < 0) continue;
+        for (size_t x = 0; x < ps.size(); ++x)
+          for (size_t y = x + 1; y < ps.size(); ++y) trip.emplace_back(u, ps[x], ps[y]);
+      }
+    q = q2;
+  }
+  std::sort(trip.begin(), trip.end());
+  trip.erase(std::unique(trip.begin(), trip.end()), trip.end());
+  auto copy_of = [&](int32_t j, int64_t u) -> int64_t {
+    const auto& vs = pverts[j];
+    for (size_t t = 0; t < vs.size(); ++t)
+      if (vs[t] == u) return p->piece_ptr[j] + (int64_t)t;
+    fail(VTM_ERR_INVALID, "elements: line joins a missing copy");
+  };
+  // vertex -> (piece, copy) lookup through a per-piece hash would be faster; pieces are small
+  std::vector<std::vector<std::pair<int64_t, int32_t>>> pindex(np);
+  for (int32_t j = 0; j < np; ++j) {
+    pindex[j].reserve(pverts[j].size());
+    for (size_t t = 0; t < pverts[j].size(); ++t) pindex[j].emplace_back(pverts[j][t], (int32_t)t);
+    std::sort(pindex[j].begin(), pindex[j].end());
+  }
+  auto copy_fast = [&](int32_t j, int64_t u) -> int64_t {
+    const auto& ix = pindex[j];
+    auto it = std::lower_bound(ix.begin(), ix.end(), std::make_pair(u, (int32_t)-1));
+    if (it == ix.end() || it->first != u) return copy_of(j, u);
+    return p->piece_ptr[j] + it->second;
+  };
+  for (const auto& t : trip) {
+    p->line_a.push_back(copy_fast(std::get<1>(t), std::get<0>(t)));
+    p->line_b.push_back(copy_fast(std::get<2>(t), std::get<0>(t)));
+  }
+}
+
+void element_pieces(const vtm_partition_spec* sp, int32_t* out) {
+  std::vector<int32_t> ep(sp->nelem);
+  std::vector<int64_t> ids(sp->nelem);
+  for (int64_t e = 0; e < sp->nelem; ++e) ids[e] = e;
+  rcb(sp->elem_coords, sp->coord_dim, ids, 0, sp->nelem, sp->npieces, 0, ep);
+  std::copy(ep.begin(), ep.end(), out);
 }
 
 }  // namespace vtm

@@ -29,6 +29,7 @@ struct SweepArgs {
   int ys_elems;                // (max Wp - 1 + max n_pad) * R
   int win_elems;               // (max ends per piece) * R
   long wait_limit;             // bounded mbarrier polls before a timeout is recorded
+  int cap;                     // wide kernel: window rows (power of two >= max Wp - 1 + kNB)
 };
 
 size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
@@ -38,6 +39,15 @@ template <typename T>
 cudaError_t sweep_occupancy(int R, size_t smem, int* ctas_per_sm);
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+
+// Wide variant (R = 16, 32): vectors spill to xc, a circular window of 512 rows stays in shared memory.
+size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap);
+template <typename T>
+cudaError_t sweep_wide_configure(int R, size_t smem);
+template <typename T>
+cudaError_t launch_sweep_wide(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+constexpr int kWideWindow = 512;
+constexpr int kMaxRhs = 32;
 
 // Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T into the (zeroed) band storage (eq. 5.8).
 template <typename T>

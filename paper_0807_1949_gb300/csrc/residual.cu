@@ -6,7 +6,7 @@
 namespace vtm {
 
 namespace {
-constexpr int kMaxR = 8;
+constexpr int kMaxR = kMaxRhs;
 constexpr int kBS = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {

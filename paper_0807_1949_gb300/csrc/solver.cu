@@ -107,6 +107,8 @@ struct vtm_solver {
   std::vector<int32_t> end_api;      // internal end -> API end (2t + side)
   std::vector<int32_t> end_port;     // internal end -> port
   int max_w = 0, max_pad = 0, max_ports = 0;
+  bool wide = false;                 // R >= 16: windowed multi-RHS sweep kernel
+  int cap = 0;                       // its window rows
   vtm_solver_info info{};
 
   ~vtm_solver() {
@@ -129,6 +131,11 @@ static void check_status(vtm_solver* s) {
 template <typename T>
 static void autotune_sweep(vtm_solver* s);
 void reset_waves(vtm_solver* s);
+
+static size_t sweep_smem_for(const vtm_solver* s, size_t elem, int stages) {
+  return s->wide ? sweep_wide_smem_bytes(elem, s->R, stages, s->slot_elems, s->cap)
+                 : sweep_smem_bytes(elem, s->R, stages, s->slot_elems, s->ys_elems, s->win_elems);
+}
 void line_features(const vtm_partition* p, float* out);
 void mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, cudaStream_t st);
 
@@ -301,14 +308,20 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
 
   // ---- sweep shared-memory plan: every staging depth that fits is a tuning candidate
   const int R = s->R;
+  s->wide = R >= 16;
   s->slot_elems = kNB * max_Wp;
   s->ys_elems = (max_Wp - 1 + max_pad) * R;
   s->win_elems = std::max(1, max_ends) * R;
   const size_t kSmemMax = 227 * 1024;
   std::vector<int> stage_cands;
   size_t smem_cap = 0;
+  if (s->wide && max_Wp - 1 + kNB > kWideWindow)
+    fail(VTM_ERR_INVALID, "bandwidth too large for the multi-RHS sweep window");
+  s->cap = 64;
+  while (s->cap < max_Wp - 1 + kNB) s->cap *= 2;
   for (int st2 = 2; st2 <= 4; ++st2) {
-    const size_t b = sweep_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->ys_elems, s->win_elems);
+    const size_t b = s->wide ? sweep_wide_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->cap)
+                             : sweep_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->ys_elems, s->win_elems);
     if (b <= kSmemMax) {
       stage_cands.push_back(st2);
       smem_cap = std::max(smem_cap, b);
@@ -316,10 +329,11 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   }
   if (stage_cands.empty())
     fail(VTM_ERR_INVALID, "a subgraph is too large for the shared-memory sweep (n_j, bandwidth or nrhs too big)");
-  s->stages = stage_cands.back();
-  s->sweep_smem = sweep_smem_bytes(sizeof(T), R, s->stages, s->slot_elems, s->ys_elems, s->win_elems);
-  VTM_CUDA(sweep_configure<T>(R, smem_cap));
   s->stage_cands = stage_cands;
+  s->stages = stage_cands.back();
+  s->sweep_smem = sweep_smem_for(s, sizeof(T), s->stages);
+  if (s->wide) VTM_CUDA(sweep_wide_configure<T>(R, smem_cap));
+  else VTM_CUDA(sweep_configure<T>(R, smem_cap));
 
   // ---- vertex -> copies (for assembly)
   std::vector<int64_t> vc_ptr(p->n + 1, 0), vc_copy(C);
@@ -377,8 +391,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->vxt.alloc(nv);
   s->vr.alloc(nv);
   s->vrt.alloc(nv);
-  s->norms.alloc(4 * 8 * sizeof(double));
-  VTM_CUDA(cudaMallocHost(&s->h_norms, 4 * 8 * sizeof(double)));
+  s->norms.alloc(2 * kMaxRhs * sizeof(double));
+  VTM_CUDA(cudaMallocHost(&s->h_norms, 2 * kMaxRhs * sizeof(double)));
   VTM_CUDA(cudaStreamSynchronize(st));
 
   autotune_sweep<T>(s);
@@ -425,6 +439,7 @@ static SweepArgs<T> sweep_args(vtm_solver* s, int write_x) {
   a.ys_elems = s->ys_elems;
   a.win_elems = s->win_elems;
   a.wait_limit = s->wait_limit;
+  a.cap = s->cap;
   return a;
 }
 
@@ -432,7 +447,8 @@ template <typename T>
 static void sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i < k; ++i) {
     SweepArgs<T> a = sweep_args<T>(s, i == k - 1);
-    VTM_CUDA(launch_sweep<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
+    if (s->wide) VTM_CUDA(launch_sweep_wide<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
+    else VTM_CUDA(launch_sweep<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
     s->cur ^= 1;
     s->launches++;
   }
@@ -450,7 +466,7 @@ static void autotune_sweep(vtm_solver* s) {
   int best_st = s->stage_cands.back();
   for (int st2 : s->stage_cands) {
     s->stages = st2;
-    s->sweep_smem = sweep_smem_bytes(sizeof(T), s->R, st2, s->slot_elems, s->ys_elems, s->win_elems);
+    s->sweep_smem = sweep_smem_for(s, sizeof(T), st2);
     sweeps_typed<T>(s, 1);
     VTM_CUDA(cudaEventRecord(e0, s->stream));
     sweeps_typed<T>(s, 3);
@@ -467,9 +483,9 @@ static void autotune_sweep(vtm_solver* s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s->stages = best_st;
-  s->sweep_smem = sweep_smem_bytes(sizeof(T), s->R, best_st, s->slot_elems, s->ys_elems, s->win_elems);
-  int occ = 0;
-  VTM_CUDA(sweep_occupancy<T>(s->R, s->sweep_smem, &occ));
+  s->sweep_smem = sweep_smem_for(s, sizeof(T), best_st);
+  int occ = 1;
+  if (!s->wide) VTM_CUDA(sweep_occupancy<T>(s->R, s->sweep_smem, &occ));
   s->info.sweep_stages = best_st;
   s->info.sweep_ctas_per_sm = occ;
   s->info.sweep_ms = best;
@@ -552,7 +568,8 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   auto t0 = std::chrono::steady_clock::now();
   if (!p || !o) fail(VTM_ERR_INVALID, "null partition or options");
   if (o->precision != VTM_FP32 && o->precision != VTM_FP64) fail(VTM_ERR_INVALID, "unknown precision");
-  if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8)) fail(VTM_ERR_INVALID, "nrhs must be 1, 2, 4 or 8");
+  if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8 || o->nrhs == 16 || o->nrhs == 32))
+    fail(VTM_ERR_INVALID, "nrhs must be 1, 2, 4, 8, 16 or 32");
   if (o->z_mode != VTM_Z_UNIFORM && o->z_mode != VTM_Z_EXPLICIT && o->z_mode != VTM_Z_MATCHED &&
       o->z_mode != VTM_Z_LEARNED)
     fail(VTM_ERR_INVALID, "unknown z_mode");
@@ -613,14 +630,14 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     for (int r = 0; r < R; ++r)
       VTM_CUDA(cudaMemcpyAsync(db + r * n, b + r * ld, n * sizeof(double), cudaMemcpyHostToDevice, st));
   double* norms = s->norms.as<double>();
-  VTM_CUDA(cudaMemsetAsync(norms, 0, 2 * 8 * sizeof(double), st));
+  VTM_CUDA(cudaMemsetAsync(norms, 0, 2 * kMaxRhs * sizeof(double), st));
   VTM_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
-  VTM_CUDA(launch_sqnorm(n, R, db, n, norms + 8, st));
+  VTM_CUDA(launch_sqnorm(n, R, db, n, norms + kMaxRhs, st));
   VTM_CUDA(launch_copy2d(n, R, db, n, s->vr.as<double>(), n, st));
   s->launches += 2;
-  read_norms(s, 16);
+  read_norms(s, 2 * kMaxRhs);
   std::vector<double> bn(R);
-  for (int r = 0; r < R; ++r) bn[r] = std::sqrt(s->h_norms[8 + r]) > 0 ? std::sqrt(s->h_norms[8 + r]) : 1.0;
+  for (int r = 0; r < R; ++r) bn[r] = s->h_norms[kMaxRhs + r] > 0 ? std::sqrt(s->h_norms[kMaxRhs + r]) : 1.0;
 
   double* xacc = s->vx.as<double>();   // accepted solution
   double* xt = s->vxt.as<double>();    // trial solution
@@ -643,11 +660,11 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     sweeps += k;
     inner_sweeps += k;
     assemble(s, xacc, xt);
-    VTM_CUDA(cudaMemsetAsync(norms, 0, 8 * sizeof(double), st));
+    VTM_CUDA(cudaMemsetAsync(norms, 0, kMaxRhs * sizeof(double), st));
     VTM_CUDA(launch_residual(n, R, s->a_rowptr.as<int64_t>(), s->a_col.as<int32_t>(), s->a_val.as<double>(), db, n,
                              xt, n, rt, n, norms, st));
     s->launches++;
-    read_norms(s, 8);
+    read_norms(s, R);
     ++checks;
     check_status(s);
     rel = 0;

@@ -1,0 +1,270 @@
+// One VTM sweep for many right-hand sides at once (R = 16 or 32): the factor of every subgraph is
+// streamed once per sweep for all R columns (Table 1 steps 3-5, eq. 5.6 / 5.8 per column).
+//
+// The subgraph's vectors no longer fit in shared memory, so the CTA keeps a circular window of
+// the last Wp-1+32 rows x R in shared memory; the forward pass spills each finished block of y to
+// the copies buffer (xc) and the backward pass reads y back and overwrites it with x.  Per 32-row
+// block (the window holds `cap` rows, a power of two >= Wp - 1 + 32) the dot part of the forward pass, t = r - L_off y_window, and the column update of the
+// backward pass, y_window -= L_off^T x_B, are small dense products done with register tiles of
+// 4 rows x 4 columns per thread (the K dimension split across thread groups, partial tiles summed
+// in shared memory).  The factor slabs arrive through the same TMA bulk-copy ring as in sweep.cu.
+#include "kernels.h"
+
+namespace vtm {
+
+namespace {
+
+template <typename T, int R>
+struct WideLayout {
+  static constexpr int kRG = kNB / 4;           // row groups (rows rg, rg+8, rg+16, rg+24)
+  static constexpr int kCG = R / 4;             // column groups of 4
+  static constexpr int kTiles = kRG * kCG;      // thread tiles per block product
+  static constexpr int kKS = kSweepThreads / kTiles;  // K splits
+  static_assert(kKS >= 1 && kSweepThreads % kTiles == 0, "tile mapping");
+};
+
+}  // namespace
+
+size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap) {
+  const int tiles = (kNB / 4) * (R / 4);
+  const int ks = kSweepThreads / tiles;
+  return 128 + elem * ((size_t)stages * slot_elems + (size_t)cap * R + (size_t)ks * kNB * R + 2 * (size_t)kNB * R);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs<T> a) {
+  using LY = WideLayout<T, R>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int abort_flag;
+  __shared__ int pcur;
+  const int tid = threadIdx.x;
+  const PieceDesc pd = a.pieces[blockIdx.x];
+  const int S = a.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  T* ring = reinterpret_cast<T*>(smem + 128);
+  const int kCap = a.cap;
+  T* Yw = ring + (size_t)S * a.slot_elems;  // [cap][R]
+  T* part = Yw + (size_t)kCap * R;          // [kKS][kNB][R]
+  T* TB = part + (size_t)LY::kKS * kNB * R; // [kNB][R]
+  T* XB = TB + (size_t)kNB * R;             // [kNB][R]
+  const int kMask = kCap - 1;
+
+  const int Wp = pd.Wp;
+  const int off = Wp - 1;
+  const int nblk = pd.n_pad / kNB;
+  const int total = 2 * nblk;
+  const uint32_t slab_bytes = (uint32_t)(kNB * Wp * sizeof(T));
+  const T* fbase = a.factor + pd.factor_off;
+  T* xg = a.xc + (size_t)pd.copy_off * R;         // y, then x, of this subgraph (n rows x R)
+  const T* bg = a.bt + (size_t)pd.copy_off * R;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    pcur = 0;
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  auto issue = [&](int s) {
+    const int kb = s < nblk ? s : total - 1 - s;
+    const int slot = s % S;
+    mbar_arrive_expect_tx(&bars[slot], slab_bytes);
+    bulk_copy_g2s(ring + (size_t)slot * a.slot_elems, fbase + (size_t)kb * kNB * Wp, slab_bytes, &bars[slot]);
+  };
+  if (tid == 0)
+    for (int s = 0; s < S && s < total; ++s) issue(s);
+  for (int i = tid; i < kCap * R; i += kSweepThreads) Yw[i] = T(0);
+  __syncthreads();
+
+  // thread tile of the block products
+  const int ks = tid / LY::kTiles;
+  const int tt = tid % LY::kTiles;
+  const int rg = tt / LY::kCG, cg = tt % LY::kCG;
+
+  int s = 0;
+  for (; s < total; ++s) {
+    const bool fwd = s < nblk;
+    const int k0 = (fwd ? s : total - 1 - s) * kNB;
+    if (fwd) {
+      // rows k0..k0+31 enter the window: b̃ plus the incident waves of their ports / Z
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        const int row = k0 + r;
+        Yw[(size_t)(row & kMask) * R + c] = row < pd.n ? bg[(size_t)row * R + c] : T(0);
+      }
+      __syncthreads();
+      {
+        const int p0 = pcur;
+        int p1 = p0;
+        while (p1 < pd.nports && a.port_local[pd.port_off + p1] < k0 + kNB) ++p1;
+        for (int i = tid; i < (p1 - p0) * R; i += kSweepThreads) {
+          const int q = p0 + i / R, c = i % R;
+          const int l = a.port_local[pd.port_off + q];
+          T acc = T(0);
+          for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
+            acc += a.wprev[(size_t)a.twin[e] * R + c] * a.invz[e];
+          Yw[(size_t)(l & kMask) * R + c] += acc;
+        }
+        __syncthreads();
+        if (tid == 0) pcur = p1;
+      }
+    } else if (s > nblk) {
+      // backward: rows k0 - off .. k0 - off + 31 enter the window from the stored y
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        const int row = k0 - off + r;
+        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = xg[(size_t)row * R + c];
+      }
+    }
+    const int slot = s % S;
+    if (!mbar_wait_bounded(&bars[slot], (uint32_t)((s / S) & 1), a.wait_limit)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const T* L = ring + (size_t)slot * a.slot_elems;
+    if (fwd) {
+      // partial t over this thread's K range of window columns q in [0, off): column k0 - off + q
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      const int q0 = (off * ks) / LY::kKS, q1 = (off * (ks + 1)) / LY::kKS;
+      for (int q = q0; q < q1; ++q) {
+        const T* y = Yw + (size_t)((k0 - off + q) & kMask) * R + 4 * cg;
+        T yv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yv[j] = y[j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = rg + 8 * i;
+          const T l = (q >= r) ? L[r * Wp + q - r] : T(0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += l * yv[j];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part[((size_t)ks * kNB + rg + 8 * i) * R + 4 * cg + j] = acc[i][j];
+      __syncthreads();
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        T v = Yw[(size_t)((k0 + r) & kMask) * R + c];
+#pragma unroll
+        for (int k = 0; k < LY::kKS; ++k) v -= part[((size_t)k * kNB + r) * R + c];
+        TB[i] = v;
+      }
+      __syncthreads();
+      // y_B = inv(L_KK) t
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        const T* Lr = L + r * Wp + off - r;
+        T v = T(0);
+        for (int c2 = 0; c2 <= r; ++c2) v += Lr[c2] * TB[c2 * R + c];
+        Yw[(size_t)((k0 + r) & kMask) * R + c] = v;
+        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = v;
+      }
+    } else {
+      // x_B = inv(L_KK)^T y_B
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        T v = T(0);
+        for (int r2 = r; r2 < kNB; ++r2) v += L[r2 * Wp + off - r2 + r] * Yw[(size_t)((k0 + r2) & kMask) * R + c];
+        XB[i] = v;
+      }
+      __syncthreads();
+      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+        const int r = i / R, c = i % R;
+        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = XB[i];
+        Yw[(size_t)((k0 + r) & kMask) * R + c] = XB[i];
+      }
+      // window rows q in [0, off) (column k0 - off + q) -= sum_r L[r][q - r] x_B[r]
+      // tiles of 4 consecutive q x 4 columns, split over the threads
+      constexpr int kQT = 4;
+      const int nq = (off + kQT - 1) / kQT;
+      for (int tile = tid; tile < nq * LY::kCG; tile += kSweepThreads) {
+        const int qb = (tile / LY::kCG) * kQT, cc = (tile % LY::kCG) * 4;
+        T acc[kQT][4];
+#pragma unroll
+        for (int i = 0; i < kQT; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        const int rmax = min(kNB - 1, qb + kQT - 1);
+        for (int r = 0; r <= rmax; ++r) {
+          T xv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] = XB[r * R + cc + j];
+#pragma unroll
+          for (int i = 0; i < kQT; ++i) {
+            const int q = qb + i;
+            const T l = (q >= r && q < off) ? L[r * Wp + q - r] : T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += l * xv[j];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kQT; ++i) {
+          const int q = qb + i;
+          if (q < off && k0 - off + q >= 0)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Yw[(size_t)((k0 - off + q) & kMask) * R + cc + j] -= acc[i][j];
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && s + S < total) {
+      fence_proxy_async_smem();
+      issue(s + S);
+    }
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      atomicExch(a.status, kStatusTimeout);
+      for (int s2 = s; s2 < total && s2 < s + S; ++s2)
+        mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), a.wait_limit);
+    }
+    return;
+  }
+  __syncthreads();
+  // w_out[e] = 2 x_c - w_in[e]
+  for (int i = tid; i < pd.nports * R; i += kSweepThreads) {
+    const int q = i / R, c = i % R;
+    const int l = a.port_local[pd.port_off + q];
+    const T x = xg[(size_t)l * R + c];
+    for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
+      a.wnext[(size_t)e * R + c] = T(2) * x - a.wprev[(size_t)a.twin[e] * R + c];
+  }
+}
+
+template <typename T, int R>
+static cudaError_t wide_configure_one(size_t smem) {
+  return cudaFuncSetAttribute(k_sweep_wide<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T>
+cudaError_t sweep_wide_configure(int R, size_t smem) {
+  switch (R) {
+    case 16: return wide_configure_one<T, 16>(smem);
+    case 32: return wide_configure_one<T, 32>(smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_sweep_wide(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+  dim3 grid(npieces), block(kSweepThreads);
+  switch (R) {
+    case 16: k_sweep_wide<T, 16><<<grid, block, smem, st>>>(a); break;
+    case 32: k_sweep_wide<T, 32><<<grid, block, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t sweep_wide_configure<float>(int, size_t);
+template cudaError_t sweep_wide_configure<double>(int, size_t);
+template cudaError_t launch_sweep_wide<float>(const SweepArgs<float>&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_sweep_wide<double>(const SweepArgs<double>&, int, int, size_t, cudaStream_t);
+
+}  // namespace vtm

@@ -170,3 +170,57 @@ def grid_coordinates(dims) -> np.ndarray:
     nx, ny, nz = dims
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+@dataclass
+class FEMProblem:
+    """P1 finite elements on a Delaunay triangulation (the problem only, no splitting).
+
+    A              assembled stiffness on the interior nodes (hull nodes are Dirichlet, eliminated)
+    elem_nodes     (m, 3) int64 triangle vertices in the original node numbering
+    elem_mats      (m, 3, 3) float64 element stiffness matrices k_e * area * grad(phi_a).grad(phi_b)
+    node_unknown   (N,) int64: unknown index in A of each node, -1 for Dirichlet nodes
+    centroids      (m, 2) float64 triangle centroids
+    coords         (N, 2) float64 node coordinates
+    """
+
+    A: CSR
+    elem_nodes: np.ndarray
+    elem_mats: np.ndarray
+    node_unknown: np.ndarray
+    centroids: np.ndarray
+    coords: np.ndarray
+
+
+def fem_delaunay(npoints: int, pattern: int = 8, k_lo: float = 1e-3, k_hi: float = 1e3, seed: int = 0) -> FEMProblem:
+    """P1 stiffness of -div(k grad u) on the Delaunay triangulation of uniform random points in the
+    unit square, k a checkerboard of k_lo / k_hi on a pattern x pattern grid (by triangle centroid),
+    homogeneous Dirichlet conditions on the convex hull."""
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(0.0, 1.0, size=(npoints, 2))
+    tri = Delaunay(pts)
+    T = tri.simplices.astype(np.int64)
+    P = pts[T]                                             # (m, 3, 2)
+    cen = P.mean(axis=1)
+    cell = np.floor(np.clip(cen, 0, 1 - 1e-12) * pattern).astype(np.int64)
+    k = np.where((cell[:, 0] + cell[:, 1]) % 2 == 0, k_lo, k_hi)
+    # barycentric gradients: grad phi_a = perp(p_c - p_b) / (2 area) for (a, b, c) cyclic
+    d = np.stack([P[:, 2] - P[:, 1], P[:, 0] - P[:, 2], P[:, 1] - P[:, 0]], axis=1)   # (m, 3, 2)
+    area2 = d[:, 1, 0] * d[:, 2, 1] - d[:, 1, 1] * d[:, 2, 0]
+    sign = np.sign(area2)[:, None, None]
+    G = np.stack([-d[..., 1], d[..., 0]], axis=-1) * sign       # gradients times 2*area
+    area = 0.5 * np.abs(area2)
+    Ke = (k / (4.0 * area))[:, None, None] * np.einsum("mad,mbd->mab", G, G)
+    hull = np.unique(tri.convex_hull.ravel())
+    unknown = np.full(npoints, -1, dtype=np.int64)
+    interior = np.setdiff1d(np.arange(npoints), hull)
+    unknown[interior] = np.arange(len(interior))
+    U = unknown[T]                                             # (m, 3)
+    rows = np.repeat(U, 3, axis=1).ravel()
+    cols = np.tile(U, (1, 3)).ravel()
+    vals = Ke.reshape(len(T), 9).ravel()
+    keep = (rows >= 0) & (cols >= 0)
+    A = _csr_from_coo(len(interior), rows[keep], cols[keep], vals[keep])
+    return FEMProblem(A=A, elem_nodes=T, elem_mats=Ke, node_unknown=unknown, centroids=cen, coords=pts)

@@ -43,6 +43,7 @@ def problem(family: str, seed: int):
         sigma = float(rng.uniform(0.75, 1.25))
         m = int(rng.choice([64, 96, 128]))
         dims, block = (m, m, m), (16, 16, 16)
+        seed += 1000   # keep the benchmark's 128^3 / seed 0 problem out of every training set
     elif family == "poisson3d-128":
         sigma = 1.0
         dims, block = (128, 128, 128), (16, 16, 16)
@@ -211,6 +212,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=300)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--no-matched", action="store_true")
     a = ap.parse_args()
     t0 = time.time()
     X, y, meta = build_dataset(a.family, range(a.train), a.sweeps)
@@ -218,8 +220,9 @@ def main():
     model = vtm.MLP(seed=1)
     hist = train(model, X, y, epochs=a.epochs)
     print(f"training loss {hist[0]:.4f} -> {hist[-1]:.4f}", flush=True)
-    rows = evaluate(model, a.family, range(100_000, 100_000 + a.test))
-    summ = {k: float(np.median([r[k]["sweeps"] for r in rows])) for k in ("z1", "learned", "matched")}
+    rows = evaluate(model, a.family, range(100_000, 100_000 + a.test), matched=not a.no_matched)
+    keys = ("z1", "learned") if a.no_matched else ("z1", "learned", "matched")
+    summ = {k: float(np.median([r[k]["sweeps"] for r in rows])) for k in keys}
     print("median sweeps to 1e-8 on held-out seeds:", summ, flush=True)
     out = a.out or os.path.join(MODELS, f"z_{a.family}.json")
     save(model, out, family=a.family, train_seeds=a.train, test_seeds=a.test, search_sweeps=a.sweeps,

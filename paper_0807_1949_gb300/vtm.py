@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 VTM_OK = 0
 STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SYMMETRIC", 3: "NOT_CONFORMAL", 4: "NOT_SPD", 5: "NOT_CONVERGED",
           6: "DIVERGED", 7: "TIMEOUT", 8: "CUDA", 9: "OOM"}
-PART_GRID, PART_OWNERS, PART_EXPLICIT = 1, 2, 3
+PART_GRID, PART_OWNERS, PART_EXPLICIT, PART_ELEMENTS = 1, 2, 3, 4
 Z_UNIFORM, Z_EXPLICIT, Z_MATCHED, Z_LEARNED = 0, 1, 2, 3
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 FP64, FP32 = 0, 1
@@ -42,7 +42,10 @@ class _Spec(C.Structure):
                 ("line_vertex", C.c_void_p), ("line_piece_a", C.c_void_p), ("line_piece_b", C.c_void_p),
                 ("piece_ptr", C.c_void_p), ("copy_vertex", C.c_void_p), ("copy_share", C.c_void_p),
                 ("local_rowptr", C.c_void_p), ("local_col", C.c_void_p), ("local_val", C.c_void_p),
-                ("ncopy_lines", C.c_int64), ("line_copy_a", C.c_void_p), ("line_copy_b", C.c_void_p)]
+                ("ncopy_lines", C.c_int64), ("line_copy_a", C.c_void_p), ("line_copy_b", C.c_void_p),
+                ("nelem", C.c_int64), ("nodes_per_elem", C.c_int32), ("nnodes", C.c_int64),
+                ("elem_nodes", C.c_void_p), ("elem_mats", C.c_void_p), ("node_unknown", C.c_void_p),
+                ("elem_piece", C.c_void_p), ("elem_coords", C.c_void_p), ("coord_dim", C.c_int32)]
 
 
 class PartitionInfo(C.Structure):
@@ -82,6 +85,7 @@ def _load():
     sig = {
         "vtm_partition_evs": (C.c_int, [vp, vp, vp]),
         "vtm_partition_get_info": (C.c_int, [vp, vp]),
+        "vtm_rcb": (C.c_int, [vp, i64, i32, i32, vp]),
         "vtm_partition_get_piece": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "vtm_partition_get_lines": (C.c_int, [vp, vp]),
         "vtm_partition_destroy": (None, [vp]),
@@ -189,13 +193,16 @@ def _csr_struct(A):
     return s, (rowptr, col, val)
 
 
-def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, lines=None, explicit=None) -> Partition:
+def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, lines=None, explicit=None,
+                  elements=None, npieces=None) -> Partition:
     """vtm_partition_evs.  A: object with n, rowptr, col, val (inputs.CSR).
 
     kind="grid":     dims=(nx, ny[, nz]), block=(sx, sy[, sz]).
     kind="owners":   owners=list of sorted piece tuples per vertex, lines=[(vertex, pa, pb), ...].
     kind="explicit": explicit=dict(piece_ptr, copy_vertex, copy_share, local_rowptr, local_col, local_val,
                      line_copy_a, line_copy_b).
+    kind="elements": elements=dict(elem_nodes (m, k), elem_mats (m, k, k), node_unknown, and either
+                     elem_piece (m,) or elem_coords (m, dim) with npieces).
     """
     csr, keep = _csr_struct(A)
     sp = _Spec()
@@ -231,11 +238,38 @@ def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, 
                   "line_copy_a", "line_copy_b"):
             setattr(sp, k, arrs[k].ctypes.data)
         sp.ncopy_lines = len(arrs["line_copy_a"])
+    elif kind == "elements":
+        e = elements
+        en = _arr(e["elem_nodes"], np.int64)
+        em = _arr(e["elem_mats"], np.float64)
+        nu = _arr(e["node_unknown"], np.int64)
+        hold += [en, em, nu]
+        sp.kind = PART_ELEMENTS
+        sp.nelem, sp.nodes_per_elem, sp.nnodes = en.shape[0], en.shape[1], len(nu)
+        sp.elem_nodes, sp.elem_mats, sp.node_unknown = en.ctypes.data, em.ctypes.data, nu.ctypes.data
+        if e.get("elem_piece") is not None:
+            ep = _arr(e["elem_piece"], np.int32)
+            hold.append(ep)
+            sp.elem_piece = ep.ctypes.data
+            sp.npieces = int(npieces or ep.max() + 1)
+        else:
+            ec = _arr(e["elem_coords"], np.float64)
+            hold.append(ec)
+            sp.elem_coords, sp.coord_dim = ec.ctypes.data, ec.shape[1]
+            sp.npieces = int(npieces)
     else:
         raise ValueError(kind)
     h = C.c_void_p()
     _check(_lib.vtm_partition_evs(C.byref(csr), C.byref(sp), C.byref(h)))
     return Partition(h.value)
+
+
+def rcb(coords, nparts: int) -> np.ndarray:
+    """vtm_rcb: recursive coordinate bisection of points (n, dim) into nparts subgraph ids."""
+    c = _arr(coords, np.float64)
+    out = np.empty(len(c), np.int32)
+    _check(_lib.vtm_rcb(_ptr(c), len(c), c.shape[1], int(nparts), _ptr(out)))
+    return out
 
 
 def _stream_handle(stream):

@@ -128,7 +128,7 @@ def test_random_multilevel_fp64(vtmlib, seed):
     assert np.all(np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1) <= 1e-10)
 
 
-@pytest.mark.parametrize("nrhs", [1, 4])
+@pytest.mark.parametrize("nrhs", [1, 4, 16, 32])
 def test_3d_fp32_sweeps_and_refined_solve(vtmlib, nrhs):
     """3D variable-coefficient grid (ragged blocks), FP32 factors: sweeps within the FP32 bound,
     defect-corrected solve to 1e-8 and the direct solution."""
@@ -150,6 +150,22 @@ def test_3d_fp32_sweeps_and_refined_solve(vtmlib, nrhs):
     assert np.all(np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1) <= 1e-8)
     xs = ovtm.direct_solve(A, b)
     assert np.max(np.abs(x - xs)) <= 1e-6 * np.max(np.abs(xs))
+
+
+def test_wide_fp64_matches_oracle(vtmlib):
+    """The windowed multi-RHS kernel in FP64 (16 right-hand sides) against the oracle, 4 sweeps."""
+    dims, block = (23, 17), (8, 6)
+    A = inputs.grid_poisson(dims, sigma=1.2, seed=8)
+    b = inputs.rhs_uniform(A.n, 16, seed=8)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    s = vtmlib.Solver(part, z=0.8, precision="fp64", nrhs=16)
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(4)
+    copies, waves = _oracle_after(osplit, b, 0.8, 4)
+    assert _rel(s.copies(), copies) <= 1e-12
+    assert _rel(s.get_state(), waves[:, _line_map(part, osplit)]) <= 1e-12
 
 
 def test_config2_full_size_sampled(vtmlib):

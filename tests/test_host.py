@@ -135,3 +135,41 @@ def test_line_features_match_oracle(vtmlib, dims, block, sigma):
         t = idx[tuple(int(x) for x in q)]
         order += [2 * t, 2 * t + 1]
     assert np.allclose(got, ref[order], rtol=1e-6, atol=1e-6)
+
+
+def test_rcb_is_identical_to_oracle(vtmlib):
+    rng = np.random.default_rng(0)
+    for dim, n, parts in [(2, 5000, 37), (3, 3000, 64), (2, 999, 2)]:
+        pts = rng.uniform(size=(n, dim))
+        pts[:50] = pts[0]  # ties broken by id
+        assert np.array_equal(vtmlib.rcb(pts, parts), evs.rcb(pts, parts))
+
+
+def test_element_partition_matches_oracle(vtmlib):
+    """P1 FEM split by elements (RCB of centroids): pieces, shares and lines against the oracle;
+    the pieces sum back to A (KCL) and are SNND."""
+    fem = inputs.fem_delaunay(600, seed=3)
+    A = fem.A
+    parts = 9
+    part = vtmlib.partition_evs(A, "elements", elements=dict(elem_nodes=fem.elem_nodes, elem_mats=fem.elem_mats,
+                                                           node_unknown=fem.node_unknown, elem_coords=fem.centroids),
+                                npieces=parts)
+    ep = evs.rcb(fem.centroids, parts)
+    osplit = evs.split_by_elements(A, fem.elem_nodes, fem.elem_mats, fem.node_unknown, ep)
+    info = part.info()
+    assert info.npieces == parts and info.nlines == len(osplit.vtl)
+    assert evs.kcl_residual(osplit, A) <= 1e-12 * np.abs(A.val).max()
+    for j, g in enumerate(osplit.subgraphs):
+        v, s, Aj = _local_dense(part.piece(j))
+        order = np.argsort(v)                       # library order is RCM; compare by vertex
+        assert np.array_equal(v[order], g.vertices)
+        assert np.allclose(s[order], g.share, rtol=0, atol=0)
+        ref = g.A.toarray()
+        assert np.max(np.abs(Aj[np.ix_(order, order)] - ref)) <= 1e-12 * np.abs(ref).max()
+        assert np.linalg.eigvalsh(ref).min() >= -1e-9 * np.abs(ref).max()
+    lines = set()
+    for (pa, la, pb, lb) in part.lines():
+        va = part.piece(int(pa))[0][la]
+        lines.add((int(va), int(pa), int(pb)))
+    olines = {(int(osplit.subgraphs[p].vertices[c]), int(p), int(q)) for (p, c, q, _) in osplit.vtl}
+    assert lines == olines
