@@ -193,6 +193,10 @@ typedef struct vtm_setup_opts {
   double inner_reduction;  /* FP32: restart the defect correction once the inner residual has
                               dropped by this factor (0 = 1e-4); ignored for FP64            */
   const vtm_mlp* model;    /* LEARNED: impedance model (not retained after vtm_setup)        */
+  int64_t wait_polls;      /* polls of a bounded device wait before the sweep gives up and
+                              reports VTM_ERR_TIMEOUT (0 = 4194304)                          */
+  int32_t withhold_slab;   /* testing only: the sweep never issues the copy of this factor slab
+                              of each subgraph, so that wait runs out (0 = off; k>0 = slab k-1) */
 } vtm_setup_opts;
 
 typedef struct vtm_solver vtm_solver;
@@ -213,6 +217,8 @@ typedef struct vtm_solver_info {
   int32_t sweep_stages;        /* staged slabs per CTA chosen by the setup-time autotuner     */
   int32_t sweep_ctas_per_sm;   /* resident sweep CTAs per SM at that staging depth            */
   double sweep_ms;             /* autotuner's device time of one sweep (all subgraphs)        */
+  int32_t flagged_pieces;      /* FP32 solvers: subgraphs refactored and swept in FP64 because
+                                  their FP32 pivots broke down or kept < 1e-4 of the diagonal  */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the
@@ -262,6 +268,9 @@ int vtm_input_impedances(vtm_solver* s, double* r_in);
 /* The line impedances the solver was set up with (after matching or the learned model), host,
  * nlines doubles in vtm_partition_get_lines order. */
 int vtm_solver_get_impedances(const vtm_solver* s, double* z_lines);
+/* Precision of each subgraph's factor and substitution: 32 or 64 (FP32 solvers refactor flagged
+ * subgraphs in FP64), host int32 array of npieces. */
+int vtm_solver_get_piece_precision(const vtm_solver* s, int32_t* bits);
 
 /* Checkpoint / inspection.  Waves: outgoing waves of the last sweep, host, nends x nrhs
  * column-major (end order of vtm_partition_get_lines: end 2t = side a of line t, 2t+1 = side b).

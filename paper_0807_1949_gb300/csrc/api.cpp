@@ -22,6 +22,7 @@ void solver_input_impedances(vtm_solver* s, double* r);
 void line_features(const vtm_partition* p, float* out);
 void element_pieces(const vtm_partition_spec* sp, int32_t* out);
 void solver_get_impedances(const vtm_solver* s, double* z);
+void solver_get_piece_precision(const vtm_solver* s, int32_t* bits);
 vtm_mlp* mlp_create(uint64_t seed);
 void mlp_set_params(vtm_mlp* m, const float* host);
 void mlp_get_params(const vtm_mlp* m, float* host);
@@ -208,6 +209,14 @@ int vtm_solver_get_impedances(const vtm_solver* s, double* z_lines) {
   return guarded([&] {
     if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
     vtm::solver_get_impedances(s, z_lines);
+    return VTM_OK;
+  });
+}
+
+int vtm_solver_get_piece_precision(const vtm_solver* s, int32_t* bits) {
+  return guarded([&] {
+    if (!s) vtm::fail(VTM_ERR_INVALID, "null solver");
+    vtm::solver_get_piece_precision(s, bits);
     return VTM_OK;
   });
 }

@@ -16,9 +16,17 @@ namespace vtm {
 constexpr int kNB = 32;            // rows per block (slab) of the substitution and factorisation
 constexpr int kSweepThreads = 256; // 8 threads per slab row
 
+// Polls allowed when a CTA that gave up drains the bulk copies it has issued (they target valid
+// memory and complete; the limit only keeps the drain bounded).
+constexpr long kDrainPolls = 1L << 26;
+
 // Status word written by kernels (0 = ok); values are vtm_status codes.
 constexpr int kStatusNotSpd = 4;
 constexpr int kStatusTimeout = 7;
+
+// A subgraph whose FP32 Cholesky pivot keeps less than this fraction of its original diagonal
+// (pivot^2 / K_ii < kFlagRatio: the matrix is close to singular for FP32) is refactored in FP64.
+constexpr double kFlagRatio = 1e-5;
 
 struct PieceDesc {
   int64_t factor_off;  // element offset of row 0 of this piece's band
@@ -31,6 +39,7 @@ struct PieceDesc {
   int32_t nports;
   int32_t end_off;     // first (sorted) line end of the piece
   int32_t nends;
+  int64_t row_off;     // first padded row of the piece in per-row arrays (sum of earlier n_pad)
 };
 
 // ------------------------------------------------------------------ PTX wrappers (sm_90+)

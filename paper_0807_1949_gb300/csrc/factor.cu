@@ -18,6 +18,7 @@ __global__ void k_build_band(int64_t ncopies, const int32_t* __restrict__ copy_p
                              int* status) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= ncopies) return;
+  if (copy_piece[c] < 0) return;  // subgraph not part of this band
   const PieceDesc pd = pieces[copy_piece[c]];
   const int64_t l = c - pd.copy_off;
   const int off = pd.Wp - 1;
@@ -50,16 +51,20 @@ __global__ void k_pad_rows(const PieceDesc* __restrict__ pieces, int npieces, in
 
 // One CTA (256 threads) per subgraph.  Shared memory: D (kNB x 33) and the panel P (w x 33).
 template <typename T>
-__global__ void __launch_bounds__(256) k_factor(const PieceDesc* __restrict__ pieces, T* band, int* status) {
+__global__ void __launch_bounds__(256) k_factor(const PieceDesc* __restrict__ pieces, T* band, int* status,
+                                                int* piece_flag, T* diag0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* D = reinterpret_cast<T*>(smem_raw);
   T* P = D + kNB * 33;
-  __shared__ int bad;
+  __shared__ int bad;   // 1: non-positive pivot, 2: pivot^2 < kFlagRatio * original diagonal
   const PieceDesc pd = pieces[blockIdx.x];
   T* B = band + pd.factor_off;
   const int Wp = pd.Wp, off = Wp - 1, w = pd.w, n_pad = pd.n_pad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) bad = 0;
+  // original diagonal of K_j (rows are updated in place by earlier blocks)
+  if (diag0)
+    for (int r = tid; r < n_pad; r += blockDim.x) diag0[pd.row_off + r] = B[(int64_t)r * Wp + off];
   __syncthreads();
   for (int k0 = 0; k0 < n_pad; k0 += kNB) {
     // (a) diagonal block of the updated band
@@ -72,12 +77,16 @@ __global__ void __launch_bounds__(256) k_factor(const PieceDesc* __restrict__ pi
       T row[kNB];
 #pragma unroll
       for (int c = 0; c < kNB; ++c) row[c] = D[lane * 33 + c];
+      const T d0 = diag0 ? diag0[pd.row_off + k0 + lane] : D[lane * 33 + lane];
 #pragma unroll
       for (int j = 0; j < kNB; ++j) {
         T djj = __shfl_sync(0xffffffffu, row[j], j);
+        const T dj0 = __shfl_sync(0xffffffffu, d0, j);
         if (!(djj > T(0))) {
           if (lane == 0) bad = 1;
           djj = T(1);
+        } else if (djj < T(kFlagRatio) * dj0 && lane == 0 && bad == 0) {
+          bad = 2;
         }
         const T d = sqrt(djj);
         const T lj = (lane > j) ? row[j] / d : (lane == j ? d : row[j]);
@@ -155,8 +164,38 @@ __global__ void __launch_bounds__(256) k_factor(const PieceDesc* __restrict__ pi
     }
     __syncthreads();
   }
-  if (tid == 0 && bad) atomicExch(status, kStatusNotSpd);
+  if (tid == 0 && bad) {
+    if (piece_flag) piece_flag[blockIdx.x] = bad;
+    else if (bad == 1) atomicExch(status, kStatusNotSpd);
+  }
 }
+
+// U = L^T in the same band geometry, LEFT-aligned: entry d of row i holds U[i][i+d] = L[i+d][i]
+// (d = 0 is the diagonal).  The diagonal blocks carry the transposed inverses, inv(L_KK)^T =
+// inv(L_KK^T), so the back substitution runs in dot form on contiguous rows of U.
+template <typename T>
+__global__ void k_transpose_band(const PieceDesc* __restrict__ pieces, const T* __restrict__ L, T* __restrict__ U) {
+  const PieceDesc pd = pieces[blockIdx.y];
+  const int Wp = pd.Wp, off = Wp - 1;
+  const int64_t total = (int64_t)pd.n_pad * Wp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / Wp;
+    const int d = (int)(idx % Wp);
+    T v = T(0);
+    if (i + d < pd.n_pad) v = L[pd.factor_off + (i + d) * Wp + off - d];
+    U[pd.factor_off + idx] = v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose_band(const PieceDesc* pieces, int npieces, const T* L, T* U, cudaStream_t st) {
+  dim3 grid(64, npieces);
+  k_transpose_band<T><<<grid, 256, 0, st>>>(pieces, L, U);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_transpose_band<float>(const PieceDesc*, int, const float*, float*, cudaStream_t);
+template cudaError_t launch_transpose_band<double>(const PieceDesc*, int, const double*, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_build_band(int64_t ncopies, const int32_t* copy_piece, const PieceDesc* pieces,
@@ -175,12 +214,13 @@ cudaError_t launch_build_band(int64_t ncopies, const int32_t* copy_piece, const 
 }
 
 template <typename T>
-cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, cudaStream_t st) {
+cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, int* piece_flag,
+                          T* diag0, cudaStream_t st) {
   const size_t smem = sizeof(T) * 33 * (size_t)(kNB + (max_w > kNB ? max_w : kNB));
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<T><<<npieces, 256, smem, st>>>(pieces, band, status);
+  k_factor<T><<<npieces, 256, smem, st>>>(pieces, band, status, piece_flag, diag0);
   return cudaGetLastError();
 }
 
@@ -190,7 +230,7 @@ template cudaError_t launch_build_band<float>(int64_t, const int32_t*, const Pie
 template cudaError_t launch_build_band<double>(int64_t, const int32_t*, const PieceDesc*, const int64_t*, const int32_t*,
                                                const double*, const int32_t*, const int32_t*, const double*, int, int,
                                                double*, int*, cudaStream_t);
-template cudaError_t launch_factor<float>(const PieceDesc*, int, int, float*, int*, cudaStream_t);
-template cudaError_t launch_factor<double>(const PieceDesc*, int, int, double*, int*, cudaStream_t);
+template cudaError_t launch_factor<float>(const PieceDesc*, int, int, float*, int*, int*, float*, cudaStream_t);
+template cudaError_t launch_factor<double>(const PieceDesc*, int, int, double*, int*, int*, double*, cudaStream_t);
 
 }  // namespace vtm

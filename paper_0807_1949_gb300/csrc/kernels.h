@@ -9,43 +9,46 @@
 
 namespace vtm {
 
-// Arguments of one VTM sweep (Table 1 steps 3-5) over all subgraphs.
-template <typename T>
+// Arguments of one VTM sweep (Table 1 steps 3-5) over a set of subgraphs.  TF: factor and
+// substitution type; TV: type of the sources, local solutions, waves and 1/Z in global memory.
+template <typename TF, typename TV = TF>
 struct SweepArgs {
-  const PieceDesc* pieces;
-  const T* factor;             // band factors (see device.cuh)
-  const T* bt;                 // b̃: copies x R, R contiguous
-  T* xc;                       // local solutions: copies x R (written when write_x)
-  const T* wprev;              // outgoing waves of the previous sweep: ends x R
-  T* wnext;                    // outgoing waves of this sweep
+  const PieceDesc* pieces;     // the subgraphs of this launch, one CTA each
+  const TF* factor;            // band factors (see device.cuh)
+  const TF* factor_u;          // transposed band (rows of U = L^T, left-aligned), R <= 8 kernel
+  const TV* bt;                // b̃: copies x R, R contiguous
+  TV* xc;                      // local solutions: copies x R (written when write_x)
+  const TV* wprev;             // outgoing waves of the previous sweep: ends x R
+  TV* wnext;                   // outgoing waves of this sweep
   const int32_t* port_local;   // per port: local row of the port copy
   const int32_t* port_end_ptr; // per port: first (sorted) end; nports_total + 1 entries
   const int32_t* twin;         // per end: the twin end of the same line
-  const T* invz;               // per end: 1 / Z_e
+  const TV* invz;              // per end: 1 / Z_e
   int* status;                 // kernel status word (0 = ok)
   int write_x;
   int stages;                  // staged slabs in flight (>= 2)
   int slot_elems;              // ring slot stride in elements (kNB * max Wp)
-  int ys_elems;                // (max Wp - 1 + max n_pad) * R
+  int ys_elems;                // (2 (max Wp - 1) + max n_pad) * R
   int win_elems;               // (max ends per piece) * R
   long wait_limit;             // bounded mbarrier polls before a timeout is recorded
+  int withhold;                // testing: slab index whose copy is never issued (-1 = none)
   int cap;                     // wide kernel: window rows (power of two >= max Wp - 1 + kNB)
 };
 
 size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_configure(int R, size_t smem);
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_occupancy(int R, size_t smem, int* ctas_per_sm);
-template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+template <typename TF, typename TV>
+cudaError_t launch_sweep(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
 
 // Wide variant (R = 16, 32): vectors spill to xc, a circular window of 512 rows stays in shared memory.
 size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap);
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_wide_configure(int R, size_t smem);
-template <typename T>
-cudaError_t launch_sweep_wide(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+template <typename TF, typename TV>
+cudaError_t launch_sweep_wide(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;
 
@@ -55,9 +58,16 @@ cudaError_t launch_build_band(int64_t ncopies, const int32_t* copy_piece, const 
                               const int64_t* l_rowptr, const int32_t* l_col, const double* l_val,
                               const int32_t* port_of_copy, const int32_t* port_end_ptr, const double* invz,
                               int npieces, int max_pad_rows, T* band, int* status, cudaStream_t st);
-// Banded Cholesky of every K_j in place; each diagonal block replaced by its inverse.
+// U = L^T (left-aligned rows, transposed inverse diagonal blocks) for the dot-form back substitution.
 template <typename T>
-cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, cudaStream_t st);
+cudaError_t launch_transpose_band(const PieceDesc* pieces, int npieces, const T* L, T* U, cudaStream_t st);
+// Banded Cholesky of every K_j in place; each diagonal block replaced by its inverse.
+// piece_flag[j] (may be NULL): 1 = non-positive pivot, 2 = pivot^2 < kFlagRatio K_ii (precision
+// lost); the global status gets kStatusNotSpd only when piece_flag is NULL.  diag0 (may be NULL):
+// per-row scratch (sum of n_pad entries) holding the original diagonal.
+template <typename T>
+cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, int* piece_flag,
+                          T* diag0, cudaStream_t st);
 
 // Unit right-hand sides for batch b of every subgraph's ports (b̃ of port b*R + r = e_c in column r).
 template <typename T>

@@ -87,7 +87,7 @@ struct vtm_solver {
   int32_t npieces = 0, nports = 0;
   size_t elem = 8;
 
-  DevBuf pieces, factor, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status;
+  DevBuf pieces, factor, factor_u, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status;
   DevBuf a_rowptr, a_col, a_val, vc_ptr, vc_copy, copy_vertex, share;
   DevBuf vb, vx, vxt, vr, vrt, norms;
   double* h_norms = nullptr;  // pinned: [R] residual^2, [R] b^2 ... plus status
@@ -100,6 +100,7 @@ struct vtm_solver {
   size_t sweep_smem = 0;
   int slot_elems = 0, ys_elems = 0, win_elems = 0;
   long wait_limit = 1L << 22;
+  int withhold = -1;
   std::vector<int> stage_cands;
   // kept for re-assembly with new impedances (eq. 5.8 depends on Z)
   DevBuf d_copy_piece, d_lrowptr, d_lcol, d_lval, d_port_of_copy, d_invz64;
@@ -109,9 +110,27 @@ struct vtm_solver {
   int max_w = 0, max_pad = 0, max_ports = 0;
   bool wide = false;                 // R >= 16: windowed multi-RHS sweep kernel
   int cap = 0;                       // its window rows
+  std::vector<PieceDesc> pd_host;    // all subgraphs
+  DevBuf pieces_lo;                  // subgraphs of the main launch (all, or the unflagged ones)
+  int np_lo = 0;
+  // FP32 solvers: subgraphs flagged by the FP32 factorisation, refactored and swept in FP64
+  DevBuf hi_pieces, hi_factor, hi_factor_u;
+  int np_hi = 0;
+  int hi_stages = 2, hi_slot = 0, hi_ys = 0, hi_win = 0, hi_cap = 0;
+  std::vector<int32_t> piece_bits;   // 32 or 64 per subgraph
+  size_t hi_smem = 0;
   vtm_solver_info info{};
 
+  // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
+  struct Graph {
+    int k, cur;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  bool use_graphs = true;
+
   ~vtm_solver() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     if (h_norms) cudaFreeHost(h_norms);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -141,9 +160,14 @@ void mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, cudaStre
 
 // Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T for the solver's current line impedances and factor
 // every K_j on the device (eq. 5.8, once per choice of Z).
+// Assemble K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T for the solver's line impedances and factor every
+// K_j on the device once (eq. 5.8).  FP32 solvers flag the subgraphs whose FP32 factorisation broke
+// down or lost most of its digits, and refactor those in FP64 (their own band, swept by an FP64
+// instance of the sweep kernel).
 template <typename T>
 static void factor_typed(vtm_solver* s) {
   cudaStream_t st = s->stream;
+  const int np = s->npieces;
   std::vector<double> invz(s->E);
   for (int64_t k = 0; k < s->E; ++k) invz[k] = 1.0 / s->Z[s->end_api[k] >> 1];
   upload(s->d_invz64, invz, st);
@@ -155,14 +179,21 @@ static void factor_typed(vtm_solver* s) {
   VTM_CUDA(launch_build_band<T>(s->C, s->d_copy_piece.as<int32_t>(), s->pieces.as<PieceDesc>(),
                                 s->d_lrowptr.as<int64_t>(), s->d_lcol.as<int32_t>(), s->d_lval.as<double>(),
                                 s->d_port_of_copy.as<int32_t>(), s->port_end_ptr.as<int32_t>(),
-                                s->d_invz64.as<double>(), s->npieces, s->max_pad, s->factor.as<T>(),
+                                s->d_invz64.as<double>(), np, s->max_pad, s->factor.as<T>(),
                                 s->status.as<int>(), st));
+  const bool flagging = sizeof(T) == 4;
+  DevBuf flags, diag0;
+  if (flagging) {
+    flags.alloc((size_t)np * sizeof(int));
+    VTM_CUDA(cudaMemsetAsync(flags.p, 0, flags.bytes, st));
+    diag0.alloc((size_t)(s->pd_host.back().row_off + s->pd_host.back().n_pad) * sizeof(T));
+  }
   cudaEvent_t e0, e1;
   VTM_CUDA(cudaEventCreate(&e0));
   VTM_CUDA(cudaEventCreate(&e1));
   VTM_CUDA(cudaEventRecord(e0, st));
-  cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), s->npieces, s->max_w, s->factor.as<T>(),
-                                    s->status.as<int>(), st);
+  cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), np, s->max_w, s->factor.as<T>(), s->status.as<int>(),
+                                    flagging ? flags.as<int>() : nullptr, flagging ? diag0.as<T>() : nullptr, st);
   VTM_CUDA(cudaEventRecord(e1, st));
   VTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0;
@@ -173,10 +204,102 @@ static void factor_typed(vtm_solver* s) {
   VTM_CUDA(fe);
   s->info.factor_ms += ms;
   check_status(s);
+  if (!s->wide) {
+    VTM_CUDA(launch_transpose_band<T>(s->pieces.as<PieceDesc>(), np, s->factor.as<T>(), s->factor_u.as<T>(), st));
+    VTM_CUDA(cudaStreamSynchronize(st));
+  }
+  std::vector<int> fl(np, 0);
+  if (flagging) VTM_CUDA(cudaMemcpy(fl.data(), flags.p, np * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<PieceDesc> lo, hi;
+  std::vector<int32_t> hi_of_piece(np, -1);
+  int64_t hoff = 0;
+  int max_w_hi = 0;
+  for (int j = 0; j < np; ++j) {
+    if (!fl[j]) {
+      lo.push_back(s->pd_host[j]);
+      continue;
+    }
+    PieceDesc d = s->pd_host[j];
+    int Wp = std::max(d.w + 1, kNB);
+    while (Wp % 16 != 4) ++Wp;
+    d.Wp = Wp;
+    d.factor_off = hoff;
+    hoff += (int64_t)d.n_pad * Wp;
+    hi_of_piece[j] = (int32_t)hi.size();
+    max_w_hi = std::max(max_w_hi, d.w);
+    hi.push_back(d);
+  }
+  s->np_lo = (int)lo.size();
+  s->np_hi = (int)hi.size();
+  s->piece_bits.assign(np, sizeof(T) == 8 ? 64 : 32);
+  for (int j = 0; j < np; ++j)
+    if (fl[j]) s->piece_bits[j] = 64;
+  s->info.flagged_pieces = s->np_hi;
+  if (!lo.empty()) upload(s->pieces_lo, lo, st);
+  if (hi.empty()) return;
+  // FP64 band of the flagged subgraphs
+  std::vector<int32_t> cp(s->C, -1);
+  for (int j = 0; j < np; ++j)
+    if (hi_of_piece[j] >= 0)
+      for (int64_t c = s->pd_host[j].copy_off; c < s->pd_host[j].copy_off + s->pd_host[j].n; ++c) cp[c] = hi_of_piece[j];
+  DevBuf dcp;
+  upload(dcp, cp, st);
+  upload(s->hi_pieces, hi, st);
+  s->hi_factor.alloc((size_t)hoff * sizeof(double));
+  VTM_CUDA(cudaMemsetAsync(s->hi_factor.p, 0, s->hi_factor.bytes, st));
+  int max_pad_hi = 0;
+  for (const auto& d : hi) max_pad_hi = std::max(max_pad_hi, d.n_pad);
+  VTM_CUDA(launch_build_band<double>(s->C, dcp.as<int32_t>(), s->hi_pieces.as<PieceDesc>(), s->d_lrowptr.as<int64_t>(),
+                                     s->d_lcol.as<int32_t>(), s->d_lval.as<double>(), s->d_port_of_copy.as<int32_t>(),
+                                     s->port_end_ptr.as<int32_t>(), s->d_invz64.as<double>(), s->np_hi, max_pad_hi,
+                                     s->hi_factor.as<double>(), s->status.as<int>(), st));
+  VTM_CUDA(launch_factor<double>(s->hi_pieces.as<PieceDesc>(), s->np_hi, max_w_hi, s->hi_factor.as<double>(),
+                                 s->status.as<int>(), nullptr, nullptr, st));
+  VTM_CUDA(cudaStreamSynchronize(st));
+  check_status(s);
+  if (!s->wide) {
+    s->hi_factor_u.alloc((size_t)hoff * sizeof(double));
+    VTM_CUDA(launch_transpose_band<double>(s->hi_pieces.as<PieceDesc>(), s->np_hi, s->hi_factor.as<double>(),
+                                           s->hi_factor_u.as<double>(), st));
+    VTM_CUDA(cudaStreamSynchronize(st));
+  }
 }
 
 template <typename T>
 static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api);
+
+// Shared-memory plan of the FP64 launch over the flagged subgraphs (FP64 factor, FP32 vectors).
+static void plan_hi(vtm_solver* s) {
+  if (s->np_hi == 0) return;
+  std::vector<PieceDesc> hi(s->np_hi);
+  VTM_CUDA(cudaMemcpy(hi.data(), s->hi_pieces.p, hi.size() * sizeof(PieceDesc), cudaMemcpyDeviceToHost));
+  int mWp = 0, mpad = 0, mends = 0;
+  for (const auto& d : hi) {
+    mWp = std::max(mWp, d.Wp);
+    mpad = std::max(mpad, d.n_pad);
+    mends = std::max(mends, d.nends);
+  }
+  const int R = s->R;
+  s->hi_slot = kNB * mWp;
+  s->hi_ys = (2 * (mWp - 1) + mpad) * R;
+  s->hi_win = std::max(1, mends) * R;
+  s->hi_cap = 64;
+  while (s->hi_cap < mWp - 1 + kNB) s->hi_cap *= 2;
+  if (s->wide && s->hi_cap > kWideWindow) fail(VTM_ERR_INVALID, "flagged subgraph too wide for the multi-RHS window");
+  const size_t kSmemMax = 227 * 1024;
+  s->hi_stages = 0;
+  for (int st2 = 4; st2 >= 2 && !s->hi_stages; --st2) {
+    const size_t b = s->wide ? sweep_wide_smem_bytes(sizeof(double), R, st2, s->hi_slot, s->hi_cap)
+                             : sweep_smem_bytes(sizeof(double), R, st2, s->hi_slot, s->hi_ys, s->hi_win);
+    if (b <= kSmemMax) {
+      s->hi_stages = st2;
+      s->hi_smem = b;
+    }
+  }
+  if (!s->hi_stages) fail(VTM_ERR_INVALID, "a subgraph flagged for FP64 is too large for the FP64 sweep");
+  if (s->wide) VTM_CUDA((sweep_wide_configure<double, float>(R, s->hi_smem)));
+  else VTM_CUDA((sweep_configure<double, float>(R, s->hi_smem)));
+}
 
 template <typename T>
 static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s) {
@@ -189,6 +312,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->E = 2 * nl;
   s->npieces = np;
   s->elem = sizeof(T);
+  s->wide = s->R >= 16;
 
   // ---- impedances per line
   std::vector<double> Z(nl);
@@ -279,7 +403,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
 
   // ---- band layout
   const int wmod = (sizeof(T) == 4) ? 32 : 16, wrem = (sizeof(T) == 4) ? 8 : 4;
-  int64_t foff = 0, band_entries = 0;
+  int64_t foff = 0, band_entries = 0, row_total = 0;
   int max_w = 0, max_Wp = 0, max_pad = 0, max_ends = 0;
   for (int32_t j = 0; j < np; ++j) {
     const int64_t n_j = p->piece_ptr[j + 1] - p->piece_ptr[j];
@@ -293,6 +417,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     while (Wp % wmod != wrem) ++Wp;
     const int n_pad = (int)((n_j + kNB - 1) / kNB) * kNB;
     pd[j].factor_off = foff;
+    pd[j].row_off = row_total;
+    row_total += (int64_t)((n_j + kNB - 1) / kNB) * kNB;
     pd[j].copy_off = p->piece_ptr[j];
     pd[j].n = (int32_t)n_j;
     pd[j].n_pad = n_pad;
@@ -308,9 +434,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
 
   // ---- sweep shared-memory plan: every staging depth that fits is a tuning candidate
   const int R = s->R;
-  s->wide = R >= 16;
   s->slot_elems = kNB * max_Wp;
-  s->ys_elems = (max_Wp - 1 + max_pad) * R;
+  s->ys_elems = (2 * (max_Wp - 1) + max_pad) * R;
   s->win_elems = std::max(1, max_ends) * R;
   const size_t kSmemMax = 227 * 1024;
   std::vector<int> stage_cands;
@@ -332,8 +457,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->stage_cands = stage_cands;
   s->stages = stage_cands.back();
   s->sweep_smem = sweep_smem_for(s, sizeof(T), s->stages);
-  if (s->wide) VTM_CUDA(sweep_wide_configure<T>(R, smem_cap));
-  else VTM_CUDA(sweep_configure<T>(R, smem_cap));
+  if (s->wide) VTM_CUDA((sweep_wide_configure<T, T>(R, smem_cap)));
+  else VTM_CUDA((sweep_configure<T, T>(R, smem_cap)));
 
   // ---- vertex -> copies (for assembly)
   std::vector<int64_t> vc_ptr(p->n + 1, 0), vc_copy(C);
@@ -346,6 +471,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
 
   // ---- device buffers
   upload(s->pieces, pd, st);
+  s->pd_host = pd;
   upload(s->port_local, port_local, st);
   upload(s->port_end_ptr, port_end_ptr, st);
   upload(s->twin, twin, st);
@@ -366,6 +492,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   upload(s->d_lval, p->l_val, st);
   upload(s->d_port_of_copy, port_of_copy, st);
   s->factor.alloc((size_t)foff * sizeof(T));
+  if (!s->wide) s->factor_u.alloc((size_t)foff * sizeof(T));
   s->max_w = max_w;
   s->max_pad = max_pad;
   s->Z = Z;
@@ -375,6 +502,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     for (int32_t e = port_end_ptr[q]; e < port_end_ptr[q + 1]; ++e) s->end_port[e] = (int32_t)q;
   for (int32_t j = 0; j < np; ++j) s->max_ports = std::max(s->max_ports, pd[j].nports);
   factor_typed<T>(s);
+  plan_hi(s);
 
   // vectors
   s->bt.alloc((size_t)C * R * sizeof(T));
@@ -396,16 +524,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaStreamSynchronize(st));
 
   autotune_sweep<T>(s);
-
-  if (o->z_mode == VTM_Z_MATCHED) {
-    // §7.1 impedance matching: every line takes the geometric mean of its two ends' input
-    // impedances (Def. 7.1, other lines terminated with the initial Z), then K_j is refactored.
-    std::vector<double> r;
-    input_impedances_typed<T>(s, r);
-    for (int64_t t = 0; t < nl; ++t) s->Z[t] = std::sqrt(r[2 * t] * r[2 * t + 1]);
-    factor_typed<T>(s);
-    reset_waves(s);
-  }
+  s->withhold = o->withhold_slab > 0 ? o->withhold_slab - 1 : -1;  // after tuning: only real sweeps
 
   s->info.npieces = np;
   s->info.ncopies = C;
@@ -419,38 +538,48 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->info.max_halfband = max_w;
 }
 
-template <typename T>
-static SweepArgs<T> sweep_args(vtm_solver* s, int write_x) {
-  SweepArgs<T> a;
-  a.pieces = s->pieces.as<PieceDesc>();
-  a.factor = s->factor.as<T>();
-  a.bt = s->bt.as<T>();
-  a.xc = s->xc.as<T>();
-  a.wprev = s->w[s->cur].as<T>();
-  a.wnext = s->w[s->cur ^ 1].as<T>();
+template <typename TF, typename TV>
+static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
+  SweepArgs<TF, TV> a;
+  a.pieces = hi ? s->hi_pieces.as<PieceDesc>() : s->pieces_lo.as<PieceDesc>();
+  a.factor = hi ? s->hi_factor.as<TF>() : s->factor.as<TF>();
+  a.factor_u = hi ? s->hi_factor_u.as<TF>() : s->factor_u.as<TF>();
+  a.bt = s->bt.as<TV>();
+  a.xc = s->xc.as<TV>();
+  a.wprev = s->w[s->cur].as<TV>();
+  a.wnext = s->w[s->cur ^ 1].as<TV>();
   a.port_local = s->port_local.as<int32_t>();
   a.port_end_ptr = s->port_end_ptr.as<int32_t>();
   a.twin = s->twin.as<int32_t>();
-  a.invz = s->invz_t.as<T>();
+  a.invz = s->invz_t.as<TV>();
   a.status = s->status.as<int>();
   a.write_x = write_x;
-  a.stages = s->stages;
-  a.slot_elems = s->slot_elems;
-  a.ys_elems = s->ys_elems;
-  a.win_elems = s->win_elems;
+  a.stages = hi ? s->hi_stages : s->stages;
+  a.slot_elems = hi ? s->hi_slot : s->slot_elems;
+  a.ys_elems = hi ? s->hi_ys : s->ys_elems;
+  a.win_elems = hi ? s->hi_win : s->win_elems;
   a.wait_limit = s->wait_limit;
-  a.cap = s->cap;
+  a.withhold = s->withhold;
+  a.cap = hi ? s->hi_cap : s->cap;
   return a;
+}
+
+template <typename TF, typename TV>
+static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t smem) {
+  if (s->wide) VTM_CUDA((launch_sweep_wide<TF, TV>(a, s->R, np, smem, s->stream)));
+  else VTM_CUDA((launch_sweep<TF, TV>(a, s->R, np, smem, s->stream)));
+  s->launches++;
 }
 
 template <typename T>
 static void sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i < k; ++i) {
-    SweepArgs<T> a = sweep_args<T>(s, i == k - 1);
-    if (s->wide) VTM_CUDA(launch_sweep_wide<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
-    else VTM_CUDA(launch_sweep<T>(a, s->R, s->npieces, s->sweep_smem, s->stream));
+    const int wx = i == k - 1;
+    if (s->np_lo > 0) launch_one<T, T>(s, sweep_args<T, T>(s, wx, false), s->np_lo, s->sweep_smem);
+    if constexpr (sizeof(T) == 4) {
+      if (s->np_hi > 0) launch_one<double, float>(s, sweep_args<double, float>(s, wx, true), s->np_hi, s->hi_smem);
+    }
     s->cur ^= 1;
-    s->launches++;
   }
   if (k > 0) s->have_copies = true;
 }
@@ -469,7 +598,7 @@ static void autotune_sweep(vtm_solver* s) {
     s->sweep_smem = sweep_smem_for(s, sizeof(T), st2);
     sweeps_typed<T>(s, 1);
     VTM_CUDA(cudaEventRecord(e0, s->stream));
-    sweeps_typed<T>(s, 3);
+    sweeps_typed<T>(s, 3);  // direct launches: the staging depth is still being chosen
     VTM_CUDA(cudaEventRecord(e1, s->stream));
     VTM_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
@@ -485,7 +614,7 @@ static void autotune_sweep(vtm_solver* s) {
   s->stages = best_st;
   s->sweep_smem = sweep_smem_for(s, sizeof(T), best_st);
   int occ = 1;
-  if (!s->wide) VTM_CUDA(sweep_occupancy<T>(s->R, s->sweep_smem, &occ));
+  if (!s->wide) VTM_CUDA((sweep_occupancy<T, T>(s->R, s->sweep_smem, &occ)));
   s->info.sweep_stages = best_st;
   s->info.sweep_ctas_per_sm = occ;
   s->info.sweep_ms = best;
@@ -519,7 +648,12 @@ static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api) {
   for (int64_t k = 0; k < s->E; ++k) {
     const double gc = gh[s->end_port[k]];
     const double z = s->Z[s->end_api[k] >> 1];
-    r_api[s->end_api[k]] = gc / (1.0 - gc / z);
+    const double den = 1.0 - gc / z;
+    // den > 0 in exact arithmetic (the end's own admittance is part of K_j); a port held almost
+    // entirely by its line is open-circuit-like: its impedance is capped at 1e12 g_c
+    double r = den > 1e-12 ? gc / den : gc * 1e12;
+    if (!(r > 0) || !std::isfinite(r)) r = gc > 0 ? gc : z;
+    r_api[s->end_api[k]] = r;
   }
   VTM_CUDA(cudaMemsetAsync(s->bt.p, 0, s->bt.bytes, s->stream));
   reset_waves(s);
@@ -533,9 +667,56 @@ void solver_input_impedances(vtm_solver* s, double* r) {
   std::copy(v.begin(), v.end(), r);
 }
 
-void run_sweeps(vtm_solver* s, int k) {
+static void run_sweeps_direct(vtm_solver* s, int k) {
   if (s->precision == VTM_FP32) sweeps_typed<float>(s, k);
   else sweeps_typed<double>(s, k);
+}
+
+// k sweeps; batches of two or more sweeps replay a captured CUDA graph (one launch instead of k).
+// The graph bakes in the buffer pointers, which stay fixed for the solver's lifetime; the wave
+// buffer that a batch starts from is part of the key.
+void run_sweeps(vtm_solver* s, int k) {
+  if (k < 2 || !s->use_graphs) {
+    run_sweeps_direct(s, k);
+    return;
+  }
+  for (auto& g : s->graphs)
+    if (g.k == k && g.cur == s->cur) {
+      VTM_CUDA(cudaGraphLaunch(g.exec, s->stream));
+      s->cur = (s->cur + k) & 1;
+      s->launches += (int64_t)k * ((s->np_lo > 0) + (s->np_hi > 0));
+      s->have_copies = true;
+      return;
+    }
+  cudaStreamCaptureStatus cs;
+  VTM_CUDA(cudaStreamIsCapturing(s->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {  // the caller is capturing: just record the launches
+    run_sweeps_direct(s, k);
+    return;
+  }
+  const int cur0 = s->cur;
+  const int64_t l0 = s->launches;
+  cudaGraph_t graph;
+  VTM_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    run_sweeps_direct(s, k);
+  } catch (...) {
+    cudaStreamEndCapture(s->stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  VTM_CUDA(cudaStreamEndCapture(s->stream, &graph));
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  VTM_CUDA(e);
+  s->graphs.push_back({k, cur0, exec});
+  s->launches = l0;  // the captured launches did not run; count the replay
+  s->cur = cur0;
+  VTM_CUDA(cudaGraphLaunch(exec, s->stream));
+  s->cur = (cur0 + k) & 1;
+  s->launches += (int64_t)k * ((s->np_lo > 0) + (s->np_hi > 0));
+  s->have_copies = true;
 }
 
 void reset_waves(vtm_solver* s) {
@@ -575,11 +756,45 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
     fail(VTM_ERR_INVALID, "unknown z_mode");
   if (o->z_mode == VTM_Z_LEARNED && !o->model) fail(VTM_ERR_INVALID, "LEARNED z_mode needs a model");
   if (o->z_mode == VTM_Z_EXPLICIT && !o->z_lines && !p->line_a.empty()) fail(VTM_ERR_INVALID, "z_lines is NULL");
+  if (o->z_mode == VTM_Z_MATCHED) {
+    // §7.1 impedance matching, computed in FP64 (the rank-one downdate of Def. 7.1 cancels badly in
+    // FP32 when a line's admittance dominates its port): an FP64 solver with Z = z_uniform on every
+    // line gives each end's input impedance, every line takes the geometric mean of its two ends,
+    // and the requested solver is built with those impedances.
+    vtm_setup_opts t = *o;
+    t.precision = VTM_FP64;
+    t.z_mode = VTM_Z_UNIFORM;
+    t.withhold_slab = 0;
+    std::unique_ptr<vtm_solver> tmp;
+    for (int r : {8, 4, 2, 1}) {
+      t.nrhs = r;
+      try {
+        tmp.reset(create_solver(p, &t, cuda_stream));
+        break;
+      } catch (const Error& e) {
+        if (e.code != VTM_ERR_INVALID || r == 1) throw;
+      }
+    }
+    std::vector<double> rin;
+    input_impedances_typed<double>(tmp.get(), rin);
+    tmp.reset();
+    const size_t nl = p->line_a.size();
+    std::vector<double> Zm(nl);
+    for (size_t t2 = 0; t2 < nl; ++t2) Zm[t2] = std::sqrt(rin[2 * t2] * rin[2 * t2 + 1]);
+    vtm_setup_opts e = *o;
+    e.z_mode = VTM_Z_EXPLICIT;
+    e.z_lines = Zm.data();
+    vtm_solver* s = create_solver(p, &e, cuda_stream);
+    s->info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+  }
   std::unique_ptr<vtm_solver> s(new vtm_solver());
   s->precision = o->precision;
   s->R = o->nrhs;
   s->check_every = o->check_every > 0 ? o->check_every : 10;
   s->inner_reduction = o->inner_reduction > 0 ? o->inner_reduction : 1e-4;
+  if (o->wait_polls < 0) fail(VTM_ERR_INVALID, "wait_polls must be >= 0");
+  if (o->wait_polls > 0) s->wait_limit = (long)o->wait_polls;
   if (cuda_stream) {
     s->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -775,6 +990,10 @@ void solver_get_copies(vtm_solver* s, double* out) {
   else get_copies_typed<double>(s, out);
 }
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info) { *info = s->info; }
+void solver_get_piece_precision(const vtm_solver* s, int32_t* bits) {
+  if (!bits) fail(VTM_ERR_INVALID, "null output");
+  std::copy(s->piece_bits.begin(), s->piece_bits.end(), bits);
+}
 void solver_get_impedances(const vtm_solver* s, double* z) {
   if (!z) fail(VTM_ERR_INVALID, "null output");
   std::copy(s->Z.begin(), s->Z.end(), z);

@@ -5,17 +5,19 @@
 //      (the N2N exchange), and forms r_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8 right side);
 //   2. streams the band factor of K_j from HBM in kNB-row slabs with the TMA bulk-copy engine
 //      (cp.async.bulk into a ring of shared-memory stages tracked by mbarriers) and runs the
-//      forward substitution L y = r (dot-product form) and the back substitution L^T x = y
-//      (column/axpy form) with the diagonal blocks stored as inverses;
+//      forward substitution L y = r on rows of L and the back substitution L^T x = y on rows of
+//      U = L^T (both in dot form: 16-byte shared loads, independent FMA chains, 8-lane shuffle
+//      reductions) with the diagonal blocks stored as inverses;
 //   3. emits w_out[e] = 2 x_c - w_in[e] for every end (u - Z omega of eq. 5.6, written as the
 //      single wave that the twin receives next sweep).
-// The vector state of the subgraph (y / x, n_pad + Wp - 1 rows x R) stays in shared memory.
+// The vector state of the subgraph (y / x: Wp-1 zero rows, n_pad rows, Wp-1 zero rows, x R) stays in
+// shared memory.
 #include "kernels.h"
 
 namespace vtm {
 
-template <typename T, int R>
-__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a) {
+template <typename T, typename TV, int R>
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T, TV> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
   const int tid = threadIdx.x;
@@ -33,6 +35,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
   const int total = 2 * nblk;
   const uint32_t slab_bytes = (uint32_t)(kNB * Wp * sizeof(T));
   const T* fbase = a.factor + pd.factor_off;
+  const T* ubase = a.factor_u + pd.factor_off;
 
   if (tid == 0) {
     abort_flag = 0;
@@ -42,18 +45,23 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
   }
   __syncthreads();
   auto issue = [&](int s) {
+    if (s == a.withhold) return;  // testing hook: this slab's wait can only run out
     const int kb = s < nblk ? s : total - 1 - s;
     const int slot = s % S;
     mbar_arrive_expect_tx(&bars[slot], slab_bytes);
-    bulk_copy_g2s(ring + (size_t)slot * a.slot_elems, fbase + (size_t)kb * kNB * Wp, slab_bytes, &bars[slot]);
+    bulk_copy_g2s(ring + (size_t)slot * a.slot_elems, (s < nblk ? fbase : ubase) + (size_t)kb * kNB * Wp, slab_bytes,
+                  &bars[slot]);
   };
   if (tid == 0)
     for (int s = 0; s < S && s < total; ++s) issue(s);
 
   // ---- prologue: r_j = b̃_j + sum_e w_in[e] / Z_e at the port rows
-  for (int i = tid; i < off * R; i += kSweepThreads) ys[i] = T(0);
-  const T* btp = a.bt + (size_t)pd.copy_off * R;
-  for (int i = tid; i < pd.n_pad * R; i += kSweepThreads) ys[(size_t)off * R + i] = (i < pd.n * R) ? btp[i] : T(0);
+  for (int i = tid; i < off * R; i += kSweepThreads) {
+    ys[i] = T(0);
+    ys[(size_t)(off + pd.n_pad) * R + i] = T(0);
+  }
+  const TV* btp = a.bt + (size_t)pd.copy_off * R;
+  for (int i = tid; i < pd.n_pad * R; i += kSweepThreads) ys[(size_t)off * R + i] = (i < pd.n * R) ? (T)btp[i] : T(0);
   __syncthreads();
   for (int q = tid; q < pd.nports; q += kSweepThreads) {
     const int l = a.port_local[pd.port_off + q];
@@ -63,10 +71,10 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
     for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
     for (int e = e0; e < e1; ++e) {
       const int tw = a.twin[e];
-      const T iz = a.invz[e];
+      const T iz = (T)a.invz[e];
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
-        const T w = a.wprev[(size_t)tw * R + rr];
+        const T w = (T)a.wprev[(size_t)tw * R + rr];
         win[(e - pd.end_off) * R + rr] = w;
         acc[rr] += w * iz;
       }
@@ -138,53 +146,54 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
         for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + rg + off) * R + rr] = acc2[rr];
     } else {
       const int k0 = (total - 1 - s) * kNB;
-      // x_B = inv(L_KK)^T y_B      (thread (rg = column c, g))
+      // rows of U = L^T: t_r = y_r - sum_{col > k0+31} U[r][col] x_col  (positions p >= 32 - r)
+      const T* Ur = L + rg * Wp;
+      const int pbeg = kNB - rg;
+      const T* xb = ys + (size_t)(k0 + rg + off) * R;
       T acc[R];
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
-      for (int r = rg + g; r < kNB; r += 8) {
-        const T l = L[r * Wp + off - r + rg];
+      if constexpr (sizeof(T) == 4 && R == 1) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const float4* U4 = reinterpret_cast<const float4*>(Ur);
+        const int nchunk = Wp >> 2;
+        for (int q = (pbeg >> 2) + g; q < nchunk; q += 8) {
+          const float4 u = U4[q];
+          const int p = q << 2;
+          const float* x = reinterpret_cast<const float*>(xb) + p;
+          if (p >= pbeg) a0 = fmaf(u.x, x[0], a0);
+          if (p + 1 >= pbeg) a1 = fmaf(u.y, x[1], a1);
+          if (p + 2 >= pbeg) a2 = fmaf(u.z, x[2], a2);
+          a3 = fmaf(u.w, x[3], a3);  // p + 3 >= pbeg always holds for chunks at or after pbeg / 4
+        }
+        acc[0] = (a0 + a1) + (a2 + a3);
+      } else {
+        for (int p = pbeg + g; p < Wp; p += 8) {
+          const T u = Ur[p];
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) acc[rr] += l * ys[(size_t)(k0 + r + off) * R + rr];
+          for (int rr = 0; rr < R; ++rr) acc[rr] += u * xb[(size_t)p * R + rr];
+        }
       }
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) acc[rr] = warp_sum_g8(acc[rr]);
       if (g == 0)
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) tb[rg * R + rr] = acc[rr];
+        for (int rr = 0; rr < R; ++rr) tb[rg * R + rr] = xb[rr] - acc[rr];
       __syncthreads();
-      if (tid < kNB)
+      // x_B = inv(U_KK) t: x_r = sum_{c >= r} inv(U_KK)[r][c] t_c at positions c - r
+      T acc2[R];
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + tid + off) * R + rr] = tb[tid * R + rr];
-      // y_col -= sum_r L[k0 + r][col] x_r for the Wp-1 columns left of the block
-      for (int co = tid; co < off; co += kSweepThreads) {
-        const int rmax = co < kNB - 1 ? co : kNB - 1;
-        if constexpr (R == 1) {
-          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-          const T* Lc = L + co;  // entry (r, co - r) is at Lc[r * (Wp - 1)]
-          const int step = Wp - 1;
-          int r = 0;
-          for (; r + 3 <= rmax; r += 4) {
-            a0 += Lc[(r + 0) * step] * tb[r + 0];
-            a1 += Lc[(r + 1) * step] * tb[r + 1];
-            a2 += Lc[(r + 2) * step] * tb[r + 2];
-            a3 += Lc[(r + 3) * step] * tb[r + 3];
-          }
-          for (; r <= rmax; ++r) a0 += Lc[r * step] * tb[r];
-          ys[k0 + co] -= (a0 + a1) + (a2 + a3);
-        } else {
-          T acc3[R];
+      for (int rr = 0; rr < R; ++rr) acc2[rr] = T(0);
+      for (int c = rg + g; c < kNB; c += 8) {
+        const T u = Ur[c - rg];
 #pragma unroll
-          for (int rr = 0; rr < R; ++rr) acc3[rr] = T(0);
-          for (int r = 0; r <= rmax; ++r) {
-            const T l = L[r * Wp + co - r];
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr) acc3[rr] += l * tb[r * R + rr];
-          }
-#pragma unroll
-          for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + co) * R + rr] -= acc3[rr];
-        }
+        for (int rr = 0; rr < R; ++rr) acc2[rr] += u * tb[c * R + rr];
       }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc2[rr] = warp_sum_g8(acc2[rr]);
+      if (g == 0)
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) ys[(size_t)(k0 + rg + off) * R + rr] = acc2[rr];
     }
     __syncthreads();
     if (tid == 0 && s + S < total) {
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
       atomicExch(a.status, kStatusTimeout);
       // drain the copies still in flight (bounded) before the CTA leaves
       for (int s2 = s; s2 < total && s2 < s + S; ++s2)
-        mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), a.wait_limit);
+        if (s2 != a.withhold) mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), kDrainPolls);
     }
     return;
   }
@@ -209,11 +218,11 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T> a
     for (int e = e0; e < e1; ++e)
 #pragma unroll
       for (int rr = 0; rr < R; ++rr)
-        a.wnext[(size_t)e * R + rr] = T(2) * ys[(size_t)(off + l) * R + rr] - win[(e - pd.end_off) * R + rr];
+        a.wnext[(size_t)e * R + rr] = (TV)(T(2) * ys[(size_t)(off + l) * R + rr] - win[(e - pd.end_off) * R + rr]);
   }
   if (a.write_x) {
-    T* xp = a.xc + (size_t)pd.copy_off * R;
-    for (int i = tid; i < pd.n * R; i += kSweepThreads) xp[i] = ys[(size_t)off * R + i];
+    TV* xp = a.xc + (size_t)pd.copy_off * R;
+    for (int i = tid; i < pd.n * R; i += kSweepThreads) xp[i] = (TV)ys[(size_t)off * R + i];
   }
 }
 
@@ -221,56 +230,58 @@ size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_e
   return 128 + elem * ((size_t)stages * slot_elems + ys_elems + win_elems + (size_t)kNB * R);
 }
 
-template <typename T, int R>
+template <typename TF, typename TV, int R>
 static cudaError_t configure_one(size_t smem) {
-  return cudaFuncSetAttribute(k_sweep<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_sweep<TF, TV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_configure(int R, size_t smem) {
   switch (R) {
-    case 1: return configure_one<T, 1>(smem);
-    case 2: return configure_one<T, 2>(smem);
-    case 4: return configure_one<T, 4>(smem);
-    case 8: return configure_one<T, 8>(smem);
+    case 1: return configure_one<TF, TV, 1>(smem);
+    case 2: return configure_one<TF, TV, 2>(smem);
+    case 4: return configure_one<TF, TV, 4>(smem);
+    case 8: return configure_one<TF, TV, 8>(smem);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, int R>
+template <typename TF, typename TV, int R>
 static cudaError_t occupancy_one(size_t smem, int* n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_sweep<T, R>, kSweepThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_sweep<TF, TV, R>, kSweepThreads, smem);
 }
 
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_occupancy(int R, size_t smem, int* n) {
   switch (R) {
-    case 1: return occupancy_one<T, 1>(smem, n);
-    case 2: return occupancy_one<T, 2>(smem, n);
-    case 4: return occupancy_one<T, 4>(smem, n);
-    case 8: return occupancy_one<T, 8>(smem, n);
+    case 1: return occupancy_one<TF, TV, 1>(smem, n);
+    case 2: return occupancy_one<TF, TV, 2>(smem, n);
+    case 4: return occupancy_one<TF, TV, 4>(smem, n);
+    case 8: return occupancy_one<TF, TV, 8>(smem, n);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+template <typename TF, typename TV>
+cudaError_t launch_sweep(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
   dim3 grid(npieces), block(kSweepThreads);
   switch (R) {
-    case 1: k_sweep<T, 1><<<grid, block, smem, st>>>(a); break;
-    case 2: k_sweep<T, 2><<<grid, block, smem, st>>>(a); break;
-    case 4: k_sweep<T, 4><<<grid, block, smem, st>>>(a); break;
-    case 8: k_sweep<T, 8><<<grid, block, smem, st>>>(a); break;
+    case 1: k_sweep<TF, TV, 1><<<grid, block, smem, st>>>(a); break;
+    case 2: k_sweep<TF, TV, 2><<<grid, block, smem, st>>>(a); break;
+    case 4: k_sweep<TF, TV, 4><<<grid, block, smem, st>>>(a); break;
+    case 8: k_sweep<TF, TV, 8><<<grid, block, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template cudaError_t sweep_configure<float>(int, size_t);
-template cudaError_t sweep_configure<double>(int, size_t);
-template cudaError_t sweep_occupancy<float>(int, size_t, int*);
-template cudaError_t sweep_occupancy<double>(int, size_t, int*);
-template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, size_t, cudaStream_t);
-template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, size_t, cudaStream_t);
+#define VTM_SWEEP_INST(TF, TV)                                                                    \
+  template cudaError_t sweep_configure<TF, TV>(int, size_t);                                       \
+  template cudaError_t sweep_occupancy<TF, TV>(int, size_t, int*);                                 \
+  template cudaError_t launch_sweep<TF, TV>(const SweepArgs<TF, TV>&, int, int, size_t, cudaStream_t);
+VTM_SWEEP_INST(float, float)
+VTM_SWEEP_INST(double, double)
+VTM_SWEEP_INST(double, float)
 
 }  // namespace vtm

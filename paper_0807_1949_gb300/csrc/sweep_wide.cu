@@ -31,8 +31,8 @@ size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int
   return 128 + elem * ((size_t)stages * slot_elems + (size_t)cap * R + (size_t)ks * kNB * R + 2 * (size_t)kNB * R);
 }
 
-template <typename T, int R>
-__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs<T> a) {
+template <typename T, typename TV, int R>
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs<T, TV> a) {
   using LY = WideLayout<T, R>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   const int total = 2 * nblk;
   const uint32_t slab_bytes = (uint32_t)(kNB * Wp * sizeof(T));
   const T* fbase = a.factor + pd.factor_off;
-  T* xg = a.xc + (size_t)pd.copy_off * R;         // y, then x, of this subgraph (n rows x R)
-  const T* bg = a.bt + (size_t)pd.copy_off * R;
+  TV* xg = a.xc + (size_t)pd.copy_off * R;        // y, then x, of this subgraph (n rows x R)
+  const TV* bg = a.bt + (size_t)pd.copy_off * R;
 
   if (tid == 0) {
     abort_flag = 0;
@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   }
   __syncthreads();
   auto issue = [&](int s) {
+    if (s == a.withhold) return;  // testing hook: this slab's wait can only run out
     const int kb = s < nblk ? s : total - 1 - s;
     const int slot = s % S;
     mbar_arrive_expect_tx(&bars[slot], slab_bytes);
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       for (int i = tid; i < kNB * R; i += kSweepThreads) {
         const int r = i / R, c = i % R;
         const int row = k0 + r;
-        Yw[(size_t)(row & kMask) * R + c] = row < pd.n ? bg[(size_t)row * R + c] : T(0);
+        Yw[(size_t)(row & kMask) * R + c] = row < pd.n ? (T)bg[(size_t)row * R + c] : T(0);
       }
       __syncthreads();
       {
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
           const int l = a.port_local[pd.port_off + q];
           T acc = T(0);
           for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
-            acc += a.wprev[(size_t)a.twin[e] * R + c] * a.invz[e];
+            acc += (T)a.wprev[(size_t)a.twin[e] * R + c] * (T)a.invz[e];
           Yw[(size_t)(l & kMask) * R + c] += acc;
         }
         __syncthreads();
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       for (int i = tid; i < kNB * R; i += kSweepThreads) {
         const int r = i / R, c = i % R;
         const int row = k0 - off + r;
-        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = xg[(size_t)row * R + c];
+        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = (T)xg[(size_t)row * R + c];
       }
     }
     const int slot = s % S;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
         T v = T(0);
         for (int c2 = 0; c2 <= r; ++c2) v += Lr[c2] * TB[c2 * R + c];
         Yw[(size_t)((k0 + r) & kMask) * R + c] = v;
-        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = v;
+        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = (TV)v;
       }
     } else {
       // x_B = inv(L_KK)^T y_B
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       __syncthreads();
       for (int i = tid; i < kNB * R; i += kSweepThreads) {
         const int r = i / R, c = i % R;
-        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = XB[i];
+        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = (TV)XB[i];
         Yw[(size_t)((k0 + r) & kMask) * R + c] = XB[i];
       }
       // window rows q in [0, off) (column k0 - off + q) -= sum_r L[r][q - r] x_B[r]
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
     if (tid == 0) {
       atomicExch(a.status, kStatusTimeout);
       for (int s2 = s; s2 < total && s2 < s + S; ++s2)
-        mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), a.wait_limit);
+        if (s2 != a.withhold) mbar_wait_bounded(&bars[s2 % S], (uint32_t)((s2 / S) & 1), kDrainPolls);
     }
     return;
   }
@@ -231,40 +232,43 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   for (int i = tid; i < pd.nports * R; i += kSweepThreads) {
     const int q = i / R, c = i % R;
     const int l = a.port_local[pd.port_off + q];
-    const T x = xg[(size_t)l * R + c];
+    const T x = (T)xg[(size_t)l * R + c];
     for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
-      a.wnext[(size_t)e * R + c] = T(2) * x - a.wprev[(size_t)a.twin[e] * R + c];
+      a.wnext[(size_t)e * R + c] = (TV)(T(2) * x - (T)a.wprev[(size_t)a.twin[e] * R + c]);
   }
 }
 
-template <typename T, int R>
+template <typename TF, typename TV, int R>
 static cudaError_t wide_configure_one(size_t smem) {
-  return cudaFuncSetAttribute(k_sweep_wide<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_sweep_wide<TF, TV, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T>
+template <typename TF, typename TV>
 cudaError_t sweep_wide_configure(int R, size_t smem) {
   switch (R) {
-    case 16: return wide_configure_one<T, 16>(smem);
-    case 32: return wide_configure_one<T, 32>(smem);
+    case 16: return wide_configure_one<TF, TV, 16>(smem);
+    case 32: return wide_configure_one<TF, TV, 32>(smem);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T>
-cudaError_t launch_sweep_wide(const SweepArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+template <typename TF, typename TV>
+cudaError_t launch_sweep_wide(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
   dim3 grid(npieces), block(kSweepThreads);
   switch (R) {
-    case 16: k_sweep_wide<T, 16><<<grid, block, smem, st>>>(a); break;
-    case 32: k_sweep_wide<T, 32><<<grid, block, smem, st>>>(a); break;
+    case 16: k_sweep_wide<TF, TV, 16><<<grid, block, smem, st>>>(a); break;
+    case 32: k_sweep_wide<TF, TV, 32><<<grid, block, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template cudaError_t sweep_wide_configure<float>(int, size_t);
-template cudaError_t sweep_wide_configure<double>(int, size_t);
-template cudaError_t launch_sweep_wide<float>(const SweepArgs<float>&, int, int, size_t, cudaStream_t);
-template cudaError_t launch_sweep_wide<double>(const SweepArgs<double>&, int, int, size_t, cudaStream_t);
+#define VTM_WIDE_INST(TF, TV)                                  \
+  template cudaError_t sweep_wide_configure<TF, TV>(int, size_t); \
+  template cudaError_t launch_sweep_wide<TF, TV>(const SweepArgs<TF, TV>&, int, int, size_t, cudaStream_t);
+VTM_WIDE_INST(float, float)
+VTM_WIDE_INST(double, double)
+VTM_WIDE_INST(double, float)
 
 }  // namespace vtm

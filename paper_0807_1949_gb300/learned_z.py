@@ -6,15 +6,18 @@ and a small perceptron (the library's vtm_mlp_* kernels, BF16 weights, FP32 accu
 predict them from 8 local features of every line end (vtm_line_features).  Every solve, forward and
 backward pass runs in the library; this module only drives them.
 
-Search family (per problem): log Z_t = th0 + th1 (g_t - median g) + th2 (m_t - 1), where g_t is the
-mean over the line's two ends of log a_ii^(c) (feature 1) and m_t the mean number of lines at the
-two copies (feature 3).  The search minimises the relative residual after a fixed number of sweeps
+Search family (per problem): log Z_t = th0 + th1 (g_t - median g) + th2 (m_t - 1) + th3 (h_t - median h),
+where g_t is the mean over the line's two ends of log a_ii^(c) (feature 1), m_t the mean number of
+lines at the two copies (feature 3) and h_t the log of the arithmetic mean of the two split weights
+(across a coefficient jump the stiffer side must set the impedance).  The search minimises the relative residual after a fixed number of sweeps
 (a smooth stand-in for sweeps-to-tolerance), coarse-to-fine in th0, then th1 and th2.  The searched
 impedance of every line is the training target of both its ends.
 
 Families:
   poisson2d-256  2D 5-point, 256 x 256, sigma ~ U[0.5, 2] per seed, blocks of 32 (64 subgraphs)
   poisson3d      3D 7-point, 64^3 / 96^3 / 128^3, sigma ~ U[0.75, 1.25], blocks of 16
+  fem2d          P1 FEM on Delaunay triangulations of 50k-200k points, checkerboard 1e-3/1e3 on 8x8,
+                 RCB into ~500-copy subgraphs (the local shape of the 1M-point, 2000-subgraph run)
 
 Run:  python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --train 200 --test 60
 """
@@ -34,8 +37,14 @@ MODELS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models")
 
 
 def problem(family: str, seed: int):
-    """(A, dims, block, sigma, b) of the seeded problem of a family."""
+    """(A, dims, block, sigma, b) of the seeded problem of a family (FEM: dims = FEMProblem,
+    block = number of subgraphs)."""
     rng = np.random.default_rng(10_000 + seed)
+    if family == "fem2d":
+        npts = int(rng.choice([50_000, 100_000, 200_000]))
+        fem = inputs.fem_delaunay(npts, seed=20_000 + seed)
+        b = inputs.rhs_uniform(fem.A.n, 1, seed=seed)
+        return fem.A, fem, npts // 500, 0.0, b
     if family == "poisson2d-256":
         sigma = float(rng.uniform(0.5, 2.0))
         dims, block = (256, 256), (32, 32)
@@ -56,10 +65,12 @@ def problem(family: str, seed: int):
 
 def family_z(feats: np.ndarray, theta) -> np.ndarray:
     """Line impedances of the search family from the end features (ends 2t, 2t+1 of line t)."""
-    g = 0.5 * (feats[0::2, 1] + feats[1::2, 1]).astype(np.float64)
+    f1a, f1b = feats[0::2, 1].astype(np.float64), feats[1::2, 1].astype(np.float64)
+    g = 0.5 * (f1a + f1b)
+    h = np.logaddexp(f1a, f1b) - np.log(2.0)
     mm = 0.5 * (feats[0::2, 3] + feats[1::2, 3]).astype(np.float64)
-    th0, th1, th2 = theta
-    return np.exp(th0 + th1 * (g - np.median(g)) + th2 * (mm - 1.0))
+    th = tuple(theta) + (0.0,) * (4 - len(theta))
+    return np.exp(th[0] + th[1] * (g - np.median(g)) + th[2] * (mm - 1.0) + th[3] * (h - np.median(h)))
 
 
 class Evaluator:
@@ -68,7 +79,13 @@ class Evaluator:
     def __init__(self, A, dims, block, b, precision="fp32"):
         import torch
 
-        self.part = vtm.partition_evs(A, "grid", dims=dims, block=block)
+        if isinstance(dims, inputs.FEMProblem):
+            f = dims
+            self.part = vtm.partition_evs(A, "elements", elements=dict(
+                elem_nodes=f.elem_nodes, elem_mats=f.elem_mats, node_unknown=f.node_unknown,
+                elem_coords=f.centroids), npieces=block)
+        else:
+            self.part = vtm.partition_evs(A, "grid", dims=dims, block=block)
         self.feats = self.part.line_features()
         self.precision = precision
         self.b = torch.tensor(b, device="cuda")
@@ -86,8 +103,9 @@ class Evaluator:
         return dict(sweeps=st.sweeps, solve_ms=st.solve_ms, converged=st.status == 0, rel=st.rel_residual)
 
 
-def search(ev: Evaluator, sweeps: int) -> tuple[tuple, list]:
-    """Coarse-to-fine coordinate search of the family parameters (th0, th1, th2)."""
+def search(ev: Evaluator, sweeps: int, wide_scan: bool = False) -> tuple[tuple, list]:
+    """Coarse-to-fine coordinate search of the family parameters (th0, th1, th2, th3); the wide scan
+    also tries th3 = -1 over six decades of th0 (problems with large coefficient jumps)."""
     log = []
     cache = {}
 
@@ -100,8 +118,10 @@ def search(ev: Evaluator, sweeps: int) -> tuple[tuple, list]:
         return cache[key]
 
     best, bth = math.inf, None
-    for z0 in (0.5, 1, 2, 4, 8, 16, 32):
-        th = (math.log(z0), 0.0, 0.0)
+    coarse = [(math.log(z0), 0.0, 0.0, 0.0) for z0 in (0.5, 1, 2, 4, 8, 16, 32)]
+    if wide_scan:
+        coarse += [(math.log(z0), 0.0, 0.0, -1.0) for z0 in (1e-3, 1e-2, 0.1, 0.3, 1, 3, 10, 30, 100, 1e3)]
+    for th in coarse:
         r = f(th)
         if r < best:
             best, bth = r, th
@@ -110,14 +130,14 @@ def search(ev: Evaluator, sweeps: int) -> tuple[tuple, list]:
         nonlocal best, bth
         for _ in range(rounds):
             for d in (-step, step):
-                th = (bth[0] + d, bth[1], bth[2])
+                th = (bth[0] + d,) + tuple(bth[1:])
                 r = f(th)
                 if r < best:
                     best, bth = r, th
             step /= 2
 
     refine0(math.log(2.0) / 2, 3)
-    for k in (1, 2):
+    for k in ((1, 2, 3) if wide_scan else (1, 2)):
         for direction in (-0.5, 0.5):
             for _ in range(3):                     # walk while it keeps improving
                 th = list(bth)
@@ -162,13 +182,18 @@ def build_dataset(family: str, seeds, sweeps: int, verbose=True):
         t0 = time.time()
         A, dims, block, sigma, b = problem(family, sd)
         ev = Evaluator(A, dims, block, b)
-        th, log = search(ev, sweeps)
+        # objective horizon: about half the sweeps Z = 1 needs (fast families reach the FP32 floor
+        # of the defect correction early, where the residual no longer ranks the candidates)
+        k1 = ev.to_tolerance(1.0)["sweeps"]
+        horizon = int(min(sweeps, max(40, 10 * round(0.05 * k1))))
+        th, log = search(ev, horizon, wide_scan=family.startswith("fem"))
         zl = family_z(ev.feats, th)
         X.append(ev.feats)
         y.append(np.repeat(np.log(zl), 2).astype(np.float32))
-        meta.append(dict(seed=sd, sigma=sigma, dims=dims, theta=th, evals=len(log), seconds=round(time.time() - t0, 2)))
+        meta.append(dict(seed=sd, sigma=sigma, dims=str(dims) if not isinstance(dims, tuple) else dims, theta=th,
+                         horizon=horizon, evals=len(log), seconds=round(time.time() - t0, 2)))
         if verbose:
-            print(f"search seed {sd} sigma {sigma:.2f} dims {dims}: theta {np.round(th, 3).tolist()} "
+            print(f"search seed {sd} sigma {sigma:.2f}: theta {np.round(th, 3).tolist()} "
                   f"({time.time() - t0:.1f}s)", flush=True)
     return np.concatenate(X), np.concatenate(y), meta
 
@@ -178,7 +203,7 @@ def evaluate(model: vtm.MLP, family: str, seeds, rtol=1e-8, matched=True, verbos
     for sd in seeds:
         A, dims, block, sigma, b = problem(family, sd)
         ev = Evaluator(A, dims, block, b)
-        row = dict(seed=sd, sigma=sigma, dims=dims)
+        row = dict(seed=sd, sigma=sigma, dims=dims if isinstance(dims, tuple) else "fem")
         row["z1"] = ev.to_tolerance(1.0, rtol)
         row["learned"] = ev.to_tolerance(model, rtol)
         if matched:

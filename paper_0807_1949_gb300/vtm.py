@@ -56,7 +56,7 @@ class PartitionInfo(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("z_mode", C.c_int32), ("z_uniform", C.c_double), ("z_lines", C.c_void_p), ("precision", C.c_int32),
                 ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double),
-                ("model", C.c_void_p)]
+                ("model", C.c_void_p), ("wait_polls", C.c_int64), ("withhold_slab", C.c_int32)]
 
 
 class SolverInfo(C.Structure):
@@ -64,7 +64,7 @@ class SolverInfo(C.Structure):
                 ("precision", C.c_int32), ("block_rows", C.c_int32), ("factor_entries", C.c_int64),
                 ("band_entries", C.c_int64), ("factor_bytes", C.c_int64), ("max_halfband", C.c_int64),
                 ("setup_ms", C.c_double), ("factor_ms", C.c_double), ("sweep_stages", C.c_int32),
-                ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double)]
+                ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -99,6 +99,7 @@ def _load():
         "vtm_get_state": (C.c_int, [vp, vp]),
         "vtm_input_impedances": (C.c_int, [vp, vp]),
         "vtm_solver_get_impedances": (C.c_int, [vp, vp]),
+        "vtm_solver_get_piece_precision": (C.c_int, [vp, vp]),
         "vtm_line_features": (C.c_int, [vp, vp]),
         "vtm_mlp_create": (C.c_int, [C.c_uint64, vp]),
         "vtm_mlp_destroy": (None, [vp]),
@@ -300,7 +301,8 @@ class Solver:
     """
 
     def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
-                 check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0):
+                 check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0,
+                 wait_polls: int = 0, withhold_slab: int = -1):
         o = _Opts()
         zarr = None
         if isinstance(z, MLP):
@@ -318,6 +320,8 @@ class Solver:
         o.nrhs = nrhs
         o.check_every = check_every
         o.inner_reduction = inner_reduction
+        o.wait_polls = int(wait_polls)
+        o.withhold_slab = int(withhold_slab) + 1 if withhold_slab >= 0 else 0
         self.nrhs = nrhs
         self.n = part.info().n
         h = C.c_void_p()
@@ -360,6 +364,12 @@ class Solver:
         z = np.empty(self.info().nends // 2, np.float64)
         _check(_lib.vtm_solver_get_impedances(self._h, _ptr(z)))
         return z
+
+    def piece_precision(self) -> np.ndarray:
+        """32 or 64 per subgraph (FP32 solvers refactor flagged subgraphs in FP64)."""
+        b = np.empty(self.info().npieces, np.int32)
+        _check(_lib.vtm_solver_get_piece_precision(self._h, _ptr(b)))
+        return b
 
     def input_impedances(self) -> np.ndarray:
         """Input impedance of every line end (Def. 7.1, other lines terminated), (nends,)."""

@@ -173,3 +173,16 @@ def test_element_partition_matches_oracle(vtmlib):
         lines.add((int(va), int(pa), int(pb)))
     olines = {(int(osplit.subgraphs[p].vertices[c]), int(p), int(q)) for (p, c, q, _) in osplit.vtl}
     assert lines == olines
+
+
+def test_committed_models_are_well_formed():
+    import json
+    import os
+    from paper_0807_1949_gb300 import learned_z
+    for name in ("z_poisson2d-256.json", "z_poisson3d.json"):
+        with open(os.path.join(learned_z.MODELS, name)) as f:
+            d = json.load(f)
+        p = np.asarray(d["params"])
+        assert p.shape == (4801,) and np.all(np.isfinite(p))
+        ms = d["median_sweeps"]
+        assert ms["learned"] < ms["z1"] and ms["learned"] < ms["matched"]
