@@ -15,6 +15,7 @@ namespace vtm {
 
 constexpr int kNB = 32;            // rows per block (slab) of the substitution and factorisation
 constexpr int kSweepThreads = 256; // 8 threads per slab row
+constexpr int kMaxStages = 16;     // slab ring depth limit (the 128-byte mbarrier area holds 16)
 
 // Polls allowed when a CTA that gave up drains the bulk copies it has issued (they target valid
 // memory and complete; the limit only keeps the drain bounded).

@@ -288,7 +288,8 @@ static void plan_hi(vtm_solver* s) {
   if (s->wide && s->hi_cap > kWideWindow) fail(VTM_ERR_INVALID, "flagged subgraph too wide for the multi-RHS window");
   const size_t kSmemMax = 227 * 1024;
   s->hi_stages = 0;
-  for (int st2 = 4; st2 >= 2 && !s->hi_stages; --st2) {
+  for (int st2 : {8, 6, 4, 3, 2}) {
+    if (s->hi_stages) break;
     const size_t b = s->wide ? sweep_wide_smem_bytes(sizeof(double), R, st2, s->hi_slot, s->hi_cap)
                              : sweep_smem_bytes(sizeof(double), R, st2, s->hi_slot, s->hi_ys, s->hi_win);
     if (b <= kSmemMax) {
@@ -444,7 +445,9 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     fail(VTM_ERR_INVALID, "bandwidth too large for the multi-RHS sweep window");
   s->cap = 64;
   while (s->cap < max_Wp - 1 + kNB) s->cap *= 2;
-  for (int st2 = 2; st2 <= 4; ++st2) {
+  // deeper rings for thin bands: a slab of a 2D subgraph is a few KB, and hiding DRAM latency takes
+  // several of them in flight (the mbarrier area holds up to kMaxStages)
+  for (int st2 : {2, 3, 4, 6, 8, 12, kMaxStages}) {
     const size_t b = s->wide ? sweep_wide_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->cap)
                              : sweep_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->ys_elems, s->win_elems);
     if (b <= kSmemMax) {
