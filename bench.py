@@ -168,8 +168,9 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def kernel_traffic(kernel_src: str, workload: str):
-    """Measured DRAM bytes per sweep launch from a committed ncu summary, if it is current."""
+def kernel_traffic(kernel_src: str, workload: str, kname: str):
+    """Measured DRAM bytes per sweep launch from a committed ncu summary, if it is current (same
+    kernel source, same kernel variant)."""
     path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     try:
         with open(path) as f:
@@ -177,7 +178,7 @@ def kernel_traffic(kernel_src: str, workload: str):
         with open(kernel_src, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
         e = d.get(workload)
-        if e and e.get("kernel_sha") == h:
+        if e and e.get("kernel_sha") == h and e.get("kernel", kname) == kname:
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -353,9 +354,14 @@ def run_vtm(args):
                  + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
     pk = peaks()
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    kname = ("k_sweep_wide<float,%d>" % R) if R >= 16 else ("k_sweep<float,%d>" % R)
+    if R >= 16:
+        kname = "k_sweep_wide<float,float,%d>" % R
+    elif sinfo.sweep_variant == 1:
+        kname = "k_sweep_pipe<float,float,%d>" % R
+    else:
+        kname = "k_sweep<float,float,%d>" % R
     traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc",
-                                          "sweep_wide.cu" if R >= 16 else "sweep.cu"), args.workload)
+                                          "sweep_wide.cu" if R >= 16 else "sweep.cu"), args.workload, kname)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.tensor(b).pin_memory()
@@ -404,6 +410,7 @@ def run_vtm(args):
            "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,
            "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
            "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
+           "sweep_variant": "pipelined" if sinfo.sweep_variant == 1 else "single-block",
            "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain}
     cfg.update({k: w[k] for k in ("dims", "block", "sigma", "npoints") if k in w})
     line = {

@@ -188,7 +188,7 @@ typedef struct vtm_setup_opts {
   double z_uniform;        /* UNIFORM: impedance (> 0)                                       */
   const double* z_lines;   /* EXPLICIT: host, nlines values (> 0)                            */
   int32_t precision;       /* vtm_precision                                                  */
-  int32_t nrhs;            /* right-hand sides solved together (1..8)                        */
+  int32_t nrhs;            /* right-hand sides solved together: 1, 2, 4, 8, 16 or 32         */
   int32_t check_every;     /* sweeps between residual checks in vtm_solve (0 = 10)           */
   double inner_reduction;  /* FP32: restart the defect correction once the inner residual has
                               dropped by this factor (0 = 1e-4); ignored for FP64            */
@@ -197,6 +197,8 @@ typedef struct vtm_setup_opts {
                               reports VTM_ERR_TIMEOUT (0 = 4194304)                          */
   int32_t withhold_slab;   /* testing only: the sweep never issues the copy of this factor slab
                               of each subgraph, so that wait runs out (0 = off; k>0 = slab k-1) */
+  int32_t sweep_variant;   /* 0: the autotuner picks; 1: single-block sweep only; 2: pipelined
+                              sweep only (nrhs <= 2; VTM_ERR_INVALID if no staging depth fits) */
 } vtm_setup_opts;
 
 typedef struct vtm_solver vtm_solver;
@@ -218,7 +220,9 @@ typedef struct vtm_solver_info {
   int32_t sweep_ctas_per_sm;   /* resident sweep CTAs per SM at that staging depth            */
   double sweep_ms;             /* autotuner's device time of one sweep (all subgraphs)        */
   int32_t flagged_pieces;      /* FP32 solvers: subgraphs refactored and swept in FP64 because
-                                  their FP32 pivots broke down or kept < 1e-4 of the diagonal  */
+                                  their FP32 pivots broke down or kept < 1e-5 of the diagonal  */
+  int32_t sweep_variant;       /* 0: one CTA works each block step in turn; 1: pipelined (warp 0
+                                  finishes block k while the others prepare block k+1)        */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

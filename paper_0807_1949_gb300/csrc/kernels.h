@@ -33,6 +33,8 @@ struct SweepArgs {
   long wait_limit;             // bounded mbarrier polls before a timeout is recorded
   int withhold;                // testing: slab index whose copy is never issued (-1 = none)
   int cap;                     // wide kernel: window rows (power of two >= max Wp - 1 + kNB)
+  TF* yspill;                  // wide kernel: forward result y in factor precision, n_pad x R per
+                               // piece at row_off (nullptr: y goes through xc, TF == TV)
 };
 
 size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
@@ -42,6 +44,15 @@ template <typename TF, typename TV>
 cudaError_t sweep_occupancy(int R, size_t smem, int* ctas_per_sm);
 template <typename TF, typename TV>
 cudaError_t launch_sweep(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
+
+// Pipelined variant (R = 1, 2): warp 0 finishes block k while warps 1-7 prepare block k+1.
+size_t sweep_pipe_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
+template <typename TF, typename TV>
+cudaError_t sweep_pipe_configure(int R, size_t smem);
+template <typename TF, typename TV>
+cudaError_t sweep_pipe_occupancy(int R, size_t smem, int* ctas_per_sm);
+template <typename TF, typename TV>
+cudaError_t launch_sweep_pipe(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
 
 // Wide variant (R = 16, 32): vectors spill to xc, a circular window of 512 rows stays in shared memory.
 size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap);

@@ -109,6 +109,12 @@ struct vtm_solver {
   std::vector<int32_t> end_port;     // internal end -> port
   int max_w = 0, max_pad = 0, max_ports = 0;
   bool wide = false;                 // R >= 16: windowed multi-RHS sweep kernel
+  bool pipe = false;                 // R <= 2: pipelined sweep kernel chosen by the autotuner
+  struct Cand {
+    int stages;
+    bool pipe;
+  };
+  std::vector<Cand> cands;
   int cap = 0;                       // its window rows
   std::vector<PieceDesc> pd_host;    // all subgraphs
   DevBuf pieces_lo;                  // subgraphs of the main launch (all, or the unflagged ones)
@@ -119,6 +125,7 @@ struct vtm_solver {
   int hi_stages = 2, hi_slot = 0, hi_ys = 0, hi_win = 0, hi_cap = 0;
   std::vector<int32_t> piece_bits;   // 32 or 64 per subgraph
   size_t hi_smem = 0;
+  DevBuf hi_yspill;                  // R >= 16: FP64 forward results of the flagged subgraphs
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -151,9 +158,10 @@ template <typename T>
 static void autotune_sweep(vtm_solver* s);
 void reset_waves(vtm_solver* s);
 
-static size_t sweep_smem_for(const vtm_solver* s, size_t elem, int stages) {
-  return s->wide ? sweep_wide_smem_bytes(elem, s->R, stages, s->slot_elems, s->cap)
-                 : sweep_smem_bytes(elem, s->R, stages, s->slot_elems, s->ys_elems, s->win_elems);
+static size_t sweep_smem_for(const vtm_solver* s, size_t elem, int stages, bool pipe = false) {
+  if (s->wide) return sweep_wide_smem_bytes(elem, s->R, stages, s->slot_elems, s->cap);
+  if (pipe) return sweep_pipe_smem_bytes(elem, s->R, stages, s->slot_elems, s->ys_elems, s->win_elems);
+  return sweep_smem_bytes(elem, s->R, stages, s->slot_elems, s->ys_elems, s->win_elems);
 }
 void line_features(const vtm_partition* p, float* out);
 void mlp_forward(const vtm_mlp* m, const float* X, float* y, int64_t n, cudaStream_t st);
@@ -212,7 +220,7 @@ static void factor_typed(vtm_solver* s) {
   if (flagging) VTM_CUDA(cudaMemcpy(fl.data(), flags.p, np * sizeof(int), cudaMemcpyDeviceToHost));
   std::vector<PieceDesc> lo, hi;
   std::vector<int32_t> hi_of_piece(np, -1);
-  int64_t hoff = 0;
+  int64_t hoff = 0, hrows = 0;
   int max_w_hi = 0;
   for (int j = 0; j < np; ++j) {
     if (!fl[j]) {
@@ -224,6 +232,8 @@ static void factor_typed(vtm_solver* s) {
     while (Wp % 16 != 4) ++Wp;
     d.Wp = Wp;
     d.factor_off = hoff;
+    d.row_off = hrows;  // rows of this piece in the FP64 spill buffer of the multi-RHS sweep
+    hrows += d.n_pad;
     hoff += (int64_t)d.n_pad * Wp;
     hi_of_piece[j] = (int32_t)hi.size();
     max_w_hi = std::max(max_w_hi, d.w);
@@ -246,6 +256,7 @@ static void factor_typed(vtm_solver* s) {
   upload(dcp, cp, st);
   upload(s->hi_pieces, hi, st);
   s->hi_factor.alloc((size_t)hoff * sizeof(double));
+  if (s->wide) s->hi_yspill.alloc((size_t)hrows * s->R * sizeof(double));
   VTM_CUDA(cudaMemsetAsync(s->hi_factor.p, 0, s->hi_factor.bytes, st));
   int max_pad_hi = 0;
   for (const auto& d : hi) max_pad_hi = std::max(max_pad_hi, d.n_pad);
@@ -447,21 +458,32 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   while (s->cap < max_Wp - 1 + kNB) s->cap *= 2;
   // deeper rings for thin bands: a slab of a 2D subgraph is a few KB, and hiding DRAM latency takes
   // several of them in flight (the mbarrier area holds up to kMaxStages)
+  size_t pipe_cap = 0;
   for (int st2 : {2, 3, 4, 6, 8, 12, kMaxStages}) {
-    const size_t b = s->wide ? sweep_wide_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->cap)
-                             : sweep_smem_bytes(sizeof(T), R, st2, s->slot_elems, s->ys_elems, s->win_elems);
+    const size_t b = sweep_smem_for(s, sizeof(T), st2, false);
     if (b <= kSmemMax) {
       stage_cands.push_back(st2);
+      if (o->sweep_variant != 2) s->cands.push_back({st2, false});
       smem_cap = std::max(smem_cap, b);
+    }
+    if (!s->wide && R <= 2 && st2 >= 3 && o->sweep_variant != 1) {
+      const size_t bp = sweep_smem_for(s, sizeof(T), st2, true);
+      if (bp <= kSmemMax) {
+        s->cands.push_back({st2, true});
+        pipe_cap = std::max(pipe_cap, bp);
+      }
     }
   }
   if (stage_cands.empty())
     fail(VTM_ERR_INVALID, "a subgraph is too large for the shared-memory sweep (n_j, bandwidth or nrhs too big)");
+  if (s->cands.empty())
+    fail(VTM_ERR_INVALID, "the requested sweep variant is not available for this nrhs and subgraph size");
   s->stage_cands = stage_cands;
   s->stages = stage_cands.back();
   s->sweep_smem = sweep_smem_for(s, sizeof(T), s->stages);
   if (s->wide) VTM_CUDA((sweep_wide_configure<T, T>(R, smem_cap)));
   else VTM_CUDA((sweep_configure<T, T>(R, smem_cap)));
+  if (pipe_cap > 0) VTM_CUDA((sweep_pipe_configure<T, T>(R, pipe_cap)));
 
   // ---- vertex -> copies (for assembly)
   std::vector<int64_t> vc_ptr(p->n + 1, 0), vc_copy(C);
@@ -564,12 +586,14 @@ static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
   a.wait_limit = s->wait_limit;
   a.withhold = s->withhold;
   a.cap = hi ? s->hi_cap : s->cap;
+  a.yspill = (hi && s->wide) ? s->hi_yspill.as<TF>() : nullptr;
   return a;
 }
 
 template <typename TF, typename TV>
-static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t smem) {
+static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t smem, bool pipe) {
   if (s->wide) VTM_CUDA((launch_sweep_wide<TF, TV>(a, s->R, np, smem, s->stream)));
+  else if (pipe) VTM_CUDA((launch_sweep_pipe<TF, TV>(a, s->R, np, smem, s->stream)));
   else VTM_CUDA((launch_sweep<TF, TV>(a, s->R, np, smem, s->stream)));
   s->launches++;
 }
@@ -578,9 +602,10 @@ template <typename T>
 static void sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i < k; ++i) {
     const int wx = i == k - 1;
-    if (s->np_lo > 0) launch_one<T, T>(s, sweep_args<T, T>(s, wx, false), s->np_lo, s->sweep_smem);
+    if (s->np_lo > 0) launch_one<T, T>(s, sweep_args<T, T>(s, wx, false), s->np_lo, s->sweep_smem, s->pipe);
     if constexpr (sizeof(T) == 4) {
-      if (s->np_hi > 0) launch_one<double, float>(s, sweep_args<double, float>(s, wx, true), s->np_hi, s->hi_smem);
+      if (s->np_hi > 0)
+        launch_one<double, float>(s, sweep_args<double, float>(s, wx, true), s->np_hi, s->hi_smem, false);
     }
     s->cur ^= 1;
   }
@@ -596,12 +621,14 @@ static void autotune_sweep(vtm_solver* s) {
   VTM_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_st = s->stage_cands.back();
-  for (int st2 : s->stage_cands) {
-    s->stages = st2;
-    s->sweep_smem = sweep_smem_for(s, sizeof(T), st2);
+  bool best_pipe = false;
+  for (const auto& c : s->cands) {
+    s->stages = c.stages;
+    s->pipe = c.pipe;
+    s->sweep_smem = sweep_smem_for(s, sizeof(T), c.stages, c.pipe);
     sweeps_typed<T>(s, 1);
     VTM_CUDA(cudaEventRecord(e0, s->stream));
-    sweeps_typed<T>(s, 3);  // direct launches: the staging depth is still being chosen
+    sweeps_typed<T>(s, 3);  // direct launches: the configuration is still being chosen
     VTM_CUDA(cudaEventRecord(e1, s->stream));
     VTM_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
@@ -609,15 +636,19 @@ static void autotune_sweep(vtm_solver* s) {
     ms /= 3;
     if (ms < best) {
       best = ms;
-      best_st = st2;
+      best_st = c.stages;
+      best_pipe = c.pipe;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s->stages = best_st;
-  s->sweep_smem = sweep_smem_for(s, sizeof(T), best_st);
+  s->pipe = best_pipe;
+  s->sweep_smem = sweep_smem_for(s, sizeof(T), best_st, best_pipe);
+  s->info.sweep_variant = best_pipe ? 1 : 0;
   int occ = 1;
-  if (!s->wide) VTM_CUDA((sweep_occupancy<T, T>(s->R, s->sweep_smem, &occ)));
+  if (!s->wide && !s->pipe) VTM_CUDA((sweep_occupancy<T, T>(s->R, s->sweep_smem, &occ)));
+  if (s->pipe) VTM_CUDA((sweep_pipe_occupancy<T, T>(s->R, s->sweep_smem, &occ)));
   s->info.sweep_stages = best_st;
   s->info.sweep_ctas_per_sm = occ;
   s->info.sweep_ms = best;
@@ -768,6 +799,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
     t.precision = VTM_FP64;
     t.z_mode = VTM_Z_UNIFORM;
     t.withhold_slab = 0;
+    t.sweep_variant = 0;
     std::unique_ptr<vtm_solver> tmp;
     for (int r : {8, 4, 2, 1}) {
       t.nrhs = r;
@@ -797,6 +829,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   s->check_every = o->check_every > 0 ? o->check_every : 10;
   s->inner_reduction = o->inner_reduction > 0 ? o->inner_reduction : 1e-4;
   if (o->wait_polls < 0) fail(VTM_ERR_INVALID, "wait_polls must be >= 0");
+  if (o->sweep_variant < 0 || o->sweep_variant > 2) fail(VTM_ERR_INVALID, "sweep_variant must be 0, 1 or 2");
   if (o->wait_polls > 0) s->wait_limit = (long)o->wait_polls;
   if (cuda_stream) {
     s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -905,7 +938,8 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       status = VTM_OK;
       break;
     }
-    if (refine && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
+    // accept the trial only when it improves on the residual it started from
+    if (refine && inner < 1.0 && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);
       s->vr.swap(s->vrt);

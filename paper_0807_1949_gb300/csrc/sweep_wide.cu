@@ -3,7 +3,8 @@
 //
 // The subgraph's vectors no longer fit in shared memory, so the CTA keeps a circular window of
 // the last Wp-1+32 rows x R in shared memory; the forward pass spills each finished block of y to
-// the copies buffer (xc) and the backward pass reads y back and overwrites it with x.  Per 32-row
+// the copies buffer (xc; a factor-precision spill buffer when the vectors are narrower than the
+// factor) and the backward pass reads y back and overwrites it with x.  Per 32-row
 // block (the window holds `cap` rows, a power of two >= Wp - 1 + 32) the dot part of the forward pass, t = r - L_off y_window, and the column update of the
 // backward pass, y_window -= L_off^T x_B, are small dense products done with register tiles of
 // 4 rows x 4 columns per thread (the K dimension split across thread groups, partial tiles summed
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   const uint32_t slab_bytes = (uint32_t)(kNB * Wp * sizeof(T));
   const T* fbase = a.factor + pd.factor_off;
   TV* xg = a.xc + (size_t)pd.copy_off * R;        // y, then x, of this subgraph (n rows x R)
+  T* yg = a.yspill ? a.yspill + (size_t)pd.row_off * R : nullptr;  // y in factor precision
   const TV* bg = a.bt + (size_t)pd.copy_off * R;
 
   if (tid == 0) {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       for (int i = tid; i < kNB * R; i += kSweepThreads) {
         const int r = i / R, c = i % R;
         const int row = k0 - off + r;
-        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = (T)xg[(size_t)row * R + c];
+        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = yg ? yg[(size_t)row * R + c] : (T)xg[(size_t)row * R + c];
       }
     }
     const int slot = s % S;
@@ -164,7 +166,10 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
         T v = T(0);
         for (int c2 = 0; c2 <= r; ++c2) v += Lr[c2] * TB[c2 * R + c];
         Yw[(size_t)((k0 + r) & kMask) * R + c] = v;
-        if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = (TV)v;
+        if (k0 + r < pd.n) {
+          if (yg) yg[(size_t)(k0 + r) * R + c] = v;
+          else xg[(size_t)(k0 + r) * R + c] = (TV)v;
+        }
       }
     } else {
       // x_B = inv(L_KK)^T y_B

@@ -56,7 +56,8 @@ class PartitionInfo(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("z_mode", C.c_int32), ("z_uniform", C.c_double), ("z_lines", C.c_void_p), ("precision", C.c_int32),
                 ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double),
-                ("model", C.c_void_p), ("wait_polls", C.c_int64), ("withhold_slab", C.c_int32)]
+                ("model", C.c_void_p), ("wait_polls", C.c_int64), ("withhold_slab", C.c_int32),
+                ("sweep_variant", C.c_int32)]
 
 
 class SolverInfo(C.Structure):
@@ -64,7 +65,8 @@ class SolverInfo(C.Structure):
                 ("precision", C.c_int32), ("block_rows", C.c_int32), ("factor_entries", C.c_int64),
                 ("band_entries", C.c_int64), ("factor_bytes", C.c_int64), ("max_halfband", C.c_int64),
                 ("setup_ms", C.c_double), ("factor_ms", C.c_double), ("sweep_stages", C.c_int32),
-                ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32)]
+                ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32),
+                ("sweep_variant", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -296,14 +298,18 @@ class Solver:
 
     z: scalar (uniform), per-line array (order of Partition.lines()), "matched" (§7.1 rule,
        starting from z_init on every line), or an ``MLP`` (learned impedances).
-    precision: "fp64" or "fp32".  nrhs: 1, 2, 4 or 8.
+    precision: "fp64" or "fp32".  nrhs: 1, 2, 4, 8, 16 or 32.
+    sweep_variant: "auto" (the setup-time autotuner picks), "single" (one CTA works each block step
+    in turn) or "pipelined" (warp 0 finishes block k while the other warps prepare block k+1;
+    nrhs <= 2).
     Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
     """
 
     def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
                  check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0,
-                 wait_polls: int = 0, withhold_slab: int = -1):
+                 wait_polls: int = 0, withhold_slab: int = -1, sweep_variant: str = "auto"):
         o = _Opts()
+        o.sweep_variant = {"auto": 0, "single": 1, "pipelined": 2}[sweep_variant]
         zarr = None
         if isinstance(z, MLP):
             o.z_mode, o.model = Z_LEARNED, z.handle.value

@@ -81,15 +81,17 @@ def test_fem_scaled_impedance_solve(vtmlib, nrhs):
     assert np.all(rel <= 1e-8), (rel, st.sweeps, s.info().flagged_pieces)
 
 
-def test_fem_flagged_subgraphs_match_fp64(vtmlib):
+@pytest.mark.parametrize("nrhs", [1, 16])
+def test_fem_flagged_subgraphs_match_fp64(vtmlib, nrhs):
     """Nearly floating subgraphs (Z = 1e4: 1/Z is 1e-7 of the stiff coefficient) lose their FP32
-    digits; the factorisation flags them and they are factored and swept in FP64.  After one sweep
-    from zero waves (subgraphs independent) the flagged subgraphs agree with the FP64 solver to the
-    FP32 rounding of their sources and outputs."""
+    digits; the factorisation flags them and they are factored and swept in FP64 (for 16 right-hand
+    sides the forward result of those subgraphs is kept in FP64 between the two passes).  After one
+    sweep from zero waves (subgraphs independent) the flagged subgraphs agree with the FP64 solver
+    to the FP32 rounding of their sources and outputs."""
     fem, part, osplit = _setup(vtmlib, 6000, 24, seed=9)
-    b = inputs.rhs_uniform(fem.A.n, 1, seed=9)
-    s32 = vtmlib.Solver(part, z=1e4, precision="fp32")
-    s64 = vtmlib.Solver(part, z=1e4, precision="fp64")
+    b = inputs.rhs_uniform(fem.A.n, nrhs, seed=9)
+    s32 = vtmlib.Solver(part, z=1e4, precision="fp32", nrhs=nrhs)
+    s64 = vtmlib.Solver(part, z=1e4, precision="fp64", nrhs=nrhs)
     for s in (s32, s64):
         s.set_rhs(b)
         s.reset()
@@ -97,8 +99,8 @@ def test_fem_flagged_subgraphs_match_fp64(vtmlib):
     bits = s32.piece_precision()
     assert s32.info().flagged_pieces == int(np.sum(bits == 64)) >= 1
     assert np.all(s64.piece_precision() == 64)
-    x32, x64 = s32.copies()[0], s64.copies()[0]
+    x32, x64 = s32.copies(), s64.copies()
     offs = np.cumsum([0] + [part.piece(j)[0].size for j in range(part.info().npieces)])
     for j in np.nonzero(bits == 64)[0]:
-        a, c = x32[offs[j]:offs[j + 1]], x64[offs[j]:offs[j + 1]]
+        a, c = x32[:, offs[j]:offs[j + 1]], x64[:, offs[j]:offs[j + 1]]
         assert np.max(np.abs(a - c)) <= 1e-5 * np.max(np.abs(c)), j

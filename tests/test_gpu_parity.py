@@ -152,6 +152,37 @@ def test_3d_fp32_sweeps_and_refined_solve(vtmlib, nrhs):
     assert np.max(np.abs(x - xs)) <= 1e-6 * np.max(np.abs(xs))
 
 
+@pytest.mark.parametrize("variant", ["single", "pipelined"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-4)])
+@pytest.mark.parametrize("nrhs", [1, 2])
+@pytest.mark.parametrize("dims,block", [((21, 19, 18), (8, 8, 8)), ((23, 17), (6, 5)), ((70, 9), (70, 9))])
+def test_sweep_variants_match_oracle(vtmlib, variant, precision, tol, nrhs, dims, block):
+    """Both substitution schedules of the sweep (one block step at a time; chain warp plus
+    look-ahead warps) against the oracle after 5 sweeps: ragged 3D blocks (several 32-row blocks per
+    subgraph), 2D blocks of 30 unknowns (one block: the forward/backward turn is the only step) and
+    one subgraph of half-bandwidth 70 (20 blocks, a non-empty far part in every row, no lines)."""
+    A = inputs.grid_poisson(dims, sigma=0.7, seed=11)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=11)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    s = vtmlib.Solver(part, z=0.9, precision=precision, nrhs=nrhs, sweep_variant=variant)
+    assert s.info().sweep_variant == (1 if variant == "pipelined" else 0)
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(5)
+    copies, waves = _oracle_after(osplit, b, 0.9, 5)
+    assert _rel(s.copies(), copies) <= tol
+    if len(osplit.vtl):
+        assert _rel(s.get_state(), waves[:, _line_map(part, osplit)]) <= tol
+
+
+def test_pipelined_variant_needs_nrhs_le_2(vtmlib):
+    A = inputs.grid_poisson((16, 16))
+    part = vtmlib.partition_evs(A, "grid", dims=(16, 16), block=(8, 8))
+    with pytest.raises(vtmlib.VTMError):
+        vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=4, sweep_variant="pipelined")
+
+
 def test_wide_fp64_matches_oracle(vtmlib):
     """The windowed multi-RHS kernel in FP64 (16 right-hand sides) against the oracle, 4 sweeps."""
     dims, block = (23, 17), (8, 6)
