@@ -281,8 +281,16 @@ def build_problem(w, vtm, inputs):
     return A, part, b, t_part
 
 
-def impedance_arg(w, vtm):
-    z = w["z"]
+def impedance_arg(z, vtm, part):
+    """Solver impedance argument and its description for a workload's impedance rule:
+    a number (uniform), "learned:<family>" (a trained model) or "scaled:<c>" (fixed per-line rule
+    Z_t = c / (d_a + d_b), d the split diagonal weights of the line's two copies)."""
+    if isinstance(z, str) and z.startswith("scaled:"):
+        import numpy as np
+
+        f = part.line_features()
+        d = np.exp(f[:, 1].astype(np.float64))
+        return float(z.split(":", 1)[1]) / (d[0::2] + d[1::2]), z
     if isinstance(z, str) and z.startswith("learned:"):
         from paper_0807_1949_gb300 import learned_z
 
@@ -303,7 +311,7 @@ def run_vtm(args):
     A, part, b, t_part = build_problem(w, vtm, inputs)
     R = w["nrhs"]
     stream = torch.cuda.Stream()
-    zarg, zdesc = impedance_arg(w, vtm)
+    zarg, zdesc = impedance_arg(w["z"], vtm, part)
     solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=10,
                         z_init=w.get("z_init", 1.0))
     sinfo = solver.info()
@@ -374,12 +382,13 @@ def run_vtm(args):
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = max_over_ranks(ws, statistics.median(e2e))
 
-    # ---- plain method (FP64 factors, Z = 1, no correction), same workload, one right-hand side
+    # ---- plain method (FP64 factors, fixed impedance, no correction), same workload, one RHS
     plain = None
     if not args.no_plain:
         del solver
         torch.cuda.empty_cache()
-        ps = vtm.Solver(part, z=1.0, precision="fp64", nrhs=1, stream=stream, check_every=10)
+        pz, pzdesc = impedance_arg(w.get("plain_z", 1.0), vtm, part)
+        ps = vtm.Solver(part, z=pz, precision="fp64", nrhs=1, stream=stream, check_every=10)
         b1, x1 = bd[:1].contiguous(), torch.zeros_like(bd[:1])
         ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
         torch.cuda.synchronize()
@@ -390,7 +399,7 @@ def run_vtm(args):
         p1.record(stream)
         torch.cuda.synchronize()
         plain = {"ms": round(p0.elapsed_time(p1), 3), "nrhs": 1, "sweeps": pst.sweeps, "converged": pst.status == 0,
-                 "setup_ms": round(ps.info().setup_ms, 1), "precision": "fp64", "z": 1.0}
+                 "setup_ms": round(ps.info().setup_ms, 1), "precision": "fp64", "z": pzdesc}
         if R > 1:
             plain["ms_for_all_rhs"] = round(plain["ms"] * R, 3)
         del ps

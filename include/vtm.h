@@ -197,8 +197,10 @@ typedef struct vtm_setup_opts {
                               reports VTM_ERR_TIMEOUT (0 = 4194304)                          */
   int32_t withhold_slab;   /* testing only: the sweep never issues the copy of this factor slab
                               of each subgraph, so that wait runs out (0 = off; k>0 = slab k-1) */
-  int32_t sweep_variant;   /* 0: the autotuner picks; 1: single-block sweep only; 2: pipelined
-                              sweep only (nrhs <= 2; VTM_ERR_INVALID if no staging depth fits) */
+  int32_t sweep_variant;   /* 0 or 1: single-block sweep (the autotuner picks the staging depth);
+                              2: pipelined sweep (nrhs <= 2; VTM_ERR_INVALID if no staging depth
+                              fits).  The pipelined schedule is never chosen automatically: it
+                              measured slower on every workload tried                          */
 } vtm_setup_opts;
 
 typedef struct vtm_solver vtm_solver;

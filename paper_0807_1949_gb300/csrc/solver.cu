@@ -466,7 +466,9 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
       if (o->sweep_variant != 2) s->cands.push_back({st2, false});
       smem_cap = std::max(smem_cap, b);
     }
-    if (!s->wide && R <= 2 && st2 >= 3 && o->sweep_variant != 1) {
+    // the pipelined schedule measured slower than the single-block one on every workload tried, so
+    // the autotuner only considers it when it is asked for explicitly
+    if (!s->wide && R <= 2 && st2 >= 3 && o->sweep_variant == 2) {
       const size_t bp = sweep_smem_for(s, sizeof(T), st2, true);
       if (bp <= kSmemMax) {
         s->cands.push_back({st2, true});

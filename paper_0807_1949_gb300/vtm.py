@@ -299,9 +299,9 @@ class Solver:
     z: scalar (uniform), per-line array (order of Partition.lines()), "matched" (§7.1 rule,
        starting from z_init on every line), or an ``MLP`` (learned impedances).
     precision: "fp64" or "fp32".  nrhs: 1, 2, 4, 8, 16 or 32.
-    sweep_variant: "auto" (the setup-time autotuner picks), "single" (one CTA works each block step
-    in turn) or "pipelined" (warp 0 finishes block k while the other warps prepare block k+1;
-    nrhs <= 2).
+    sweep_variant: "auto" or "single" (one CTA works each block step in turn; the setup-time
+    autotuner picks the staging depth) or "pipelined" (warp 0 finishes block k while the other
+    warps prepare block k+1; nrhs <= 2; opt-in only, it measured slower everywhere).
     Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
     """
 
