@@ -201,7 +201,20 @@ typedef struct vtm_setup_opts {
                               2: pipelined sweep (nrhs <= 2; VTM_ERR_INVALID if no staging depth
                               fits).  The pipelined schedule is never chosen automatically: it
                               measured slower on every workload tried                          */
+  int32_t sweep_form;      /* how a sweep obtains the port values u = P^T x_j (VTM_FORM_*):
+                              BAND substitutes through the banded factor of K_j every sweep;
+                              PORT precomputes the port response S_j = P^T K_j^{-1} P at setup
+                              and updates the ports only (u = u_base + S_j s), running the band
+                              substitution once per batch of sweeps to refresh the interior
+                              unknowns; AUTO (0) takes PORT where it moves fewer bytes per sweep,
+                              fits in shared memory (nrhs <= 8) and in device memory            */
 } vtm_setup_opts;
+
+enum {
+  VTM_FORM_AUTO = 0,
+  VTM_FORM_BAND = 1,
+  VTM_FORM_PORT = 2
+};
 
 typedef struct vtm_solver vtm_solver;
 
@@ -225,6 +238,10 @@ typedef struct vtm_solver_info {
                                   their FP32 pivots broke down or kept < 1e-5 of the diagonal  */
   int32_t sweep_variant;       /* 0: one CTA works each block step in turn; 1: pipelined (warp 0
                                   finishes block k while the others prepare block k+1)        */
+  int32_t sweep_form;          /* VTM_FORM_BAND or VTM_FORM_PORT (after AUTO was resolved)    */
+  int64_t port_bytes;          /* PORT: bytes of the stored port responses S_j                */
+  double port_setup_ms;        /* PORT: device time of computing S_j (unit-source solves)     */
+  double port_sweep_ms;        /* PORT: device time of one port-form sweep                    */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the
@@ -246,7 +263,9 @@ int vtm_reset(vtm_solver* s);
 /* Run `sweeps` synchronous sweeps on the solver's stream (asynchronous): each sweep gathers the
  * incident wave of every line end from its twin (w_in[e] = w_out_prev[twin(e)]), solves every
  * K_j x_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8) with the stored factor, and emits
- * w_out[e] = 2 u_e - w_in[e] (the left side u - Z omega of eq. 5.6 seen from the twin). */
+ * w_out[e] = 2 u_e - w_in[e] (the left side u - Z omega of eq. 5.6 seen from the twin).
+ * PORT form: the first sweeps - 1 sweeps update the ports only; the last one is a band sweep, so
+ * the local solutions x_j (vtm_get_copies) always belong to the last sweep. */
 int vtm_iterate(vtm_solver* s, int32_t sweeps);
 
 /* Solve A x = b to max_r ||b_r - A x_r||_2 / ||b_r||_2 <= rtol (FP64 residual on the device,

@@ -60,6 +60,32 @@ template <typename TF, typename TV>
 cudaError_t sweep_wide_configure(int R, size_t smem);
 template <typename TF, typename TV>
 cudaError_t launch_sweep_wide(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
+// Arguments of one sweep in port-response form (port.cu): u = u_base + S_j s per subgraph.
+template <typename T>
+struct PortArgs {
+  const PieceDesc* pieces;     // all subgraphs, one CTA each
+  const T* S;                  // port responses, lower block triangle of 32 x 32 tiles
+  const T* ubase;              // P^T K_j^{-1} b̃_j: ports x R
+  const T* wprev;              // outgoing waves of the previous sweep: ends x R
+  T* wnext;                    // outgoing waves of this sweep
+  const int32_t* port_end_ptr;
+  const int32_t* twin;
+  const T* invz;
+};
+
+__host__ __device__ int64_t port_tiles(int nports);
+size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports);
+template <typename T>
+cudaError_t port_sweep_configure(int R, size_t smem);
+template <typename T>
+cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather_port_response(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs, int b,
+                                        const T* xc, T* S, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather_ports(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, const T* xc,
+                                T* ubase, cudaStream_t st);
+
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;
 

@@ -126,6 +126,12 @@ struct vtm_solver {
   std::vector<int32_t> piece_bits;   // 32 or 64 per subgraph
   size_t hi_smem = 0;
   DevBuf hi_yspill;                  // R >= 16: FP64 forward results of the flagged subgraphs
+  int64_t hi_rows = 0;               // sum of the flagged subgraphs' n_pad
+  // port-response form (port.cu): S_j per subgraph, u_base per port, zero / scratch wave buffers
+  bool port_form = false;
+  DevBuf S, ubase, wzero, wscr;
+  bool ubase_ok = false;
+  size_t port_smem = 0;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -156,6 +162,8 @@ static void check_status(vtm_solver* s) {
 
 template <typename T>
 static void autotune_sweep(vtm_solver* s);
+template <typename T>
+static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles, int64_t band_elems);
 void reset_waves(vtm_solver* s);
 
 static size_t sweep_smem_for(const vtm_solver* s, size_t elem, int stages, bool pipe = false) {
@@ -256,6 +264,7 @@ static void factor_typed(vtm_solver* s) {
   upload(dcp, cp, st);
   upload(s->hi_pieces, hi, st);
   s->hi_factor.alloc((size_t)hoff * sizeof(double));
+  s->hi_rows = hrows;
   if (s->wide) s->hi_yspill.alloc((size_t)hrows * s->R * sizeof(double));
   VTM_CUDA(cudaMemsetAsync(s->hi_factor.p, 0, s->hi_factor.bytes, st));
   int max_pad_hi = 0;
@@ -415,7 +424,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
 
   // ---- band layout
   const int wmod = (sizeof(T) == 4) ? 32 : 16, wrem = (sizeof(T) == 4) ? 8 : 4;
-  int64_t foff = 0, band_entries = 0, row_total = 0;
+  int64_t foff = 0, band_entries = 0, row_total = 0, soff = 0;
   int max_w = 0, max_Wp = 0, max_pad = 0, max_ends = 0;
   for (int32_t j = 0; j < np; ++j) {
     const int64_t n_j = p->piece_ptr[j + 1] - p->piece_ptr[j];
@@ -437,6 +446,8 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     pd[j].Wp = Wp;
     pd[j].w = w;
     foff += (int64_t)n_pad * Wp;
+    pd[j].s_off = soff;
+    soff += port_tiles(pd[j].nports);
     band_entries += n_j * (w + 1) - (int64_t)w * (w + 1) / 2;
     max_w = std::max(max_w, w);
     max_Wp = std::max(max_Wp, Wp);
@@ -551,6 +562,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaStreamSynchronize(st));
 
   autotune_sweep<T>(s);
+  choose_form<T>(s, o, soff, foff);
   s->withhold = o->withhold_slab > 0 ? o->withhold_slab - 1 : -1;  // after tuning: only real sweeps
 
   s->info.npieces = np;
@@ -659,6 +671,204 @@ static void autotune_sweep(vtm_solver* s) {
   reset_waves(s);
 }
 
+// ---------------------------------------------------------------- port-response form (port.cu)
+
+// S_j = P^T K_j^{-1} P from unit sources at the ports with zero incident waves: 32 port columns
+// per launch of the multi-RHS band sweep where it fits in shared memory, else the solver's own
+// sweep with its R columns.  Only the subgraphs of the main launch get an S_j: subgraphs flagged
+// ill-conditioned keep their FP64 band sweep every sweep (S_j in FP32 would carry the same
+// cancellation that made their FP32 factor fail).
+template <typename T>
+static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
+  cudaStream_t st = s->stream;
+  const int np = s->npieces;
+  s->S.alloc((size_t)s_tiles * kNB * kNB * sizeof(T));
+  VTM_CUDA(cudaMemsetAsync(s->S.p, 0, s->S.bytes, st));
+  const size_t kSmemMax = 227 * 1024;
+  int st_lo = 0;
+  size_t sm_lo = 0;
+  if (!s->wide && s->cap <= kWideWindow)
+    for (int k : {8, 6, 4, 3, 2}) {
+      const size_t b = sweep_wide_smem_bytes(sizeof(T), 32, k, s->slot_elems, s->cap);
+      if (!st_lo && b <= kSmemMax) st_lo = k, sm_lo = b;
+    }
+  cudaEvent_t e0, e1;
+  VTM_CUDA(cudaEventCreate(&e0));
+  VTM_CUDA(cudaEventCreate(&e1));
+  VTM_CUDA(cudaEventRecord(e0, st));
+  if (st_lo) {
+    constexpr int Rs = 32;
+    DevBuf bt32, xc32, w0, wsc;
+    bt32.alloc((size_t)s->C * Rs * sizeof(T));
+    xc32.alloc((size_t)s->C * Rs * sizeof(T));
+    w0.alloc((size_t)std::max<int64_t>(1, s->E) * Rs * sizeof(T));
+    wsc.alloc(w0.bytes);
+    VTM_CUDA(cudaMemsetAsync(w0.p, 0, w0.bytes, st));
+    VTM_CUDA((sweep_wide_configure<T, T>(Rs, sm_lo)));
+    const int nb = (s->max_ports + Rs - 1) / Rs;
+    for (int b = 0; b < nb; ++b) {
+      VTM_CUDA(launch_unit_rhs<T>(s->pieces.as<PieceDesc>(), np, s->port_local.as<int32_t>(), Rs, b, bt32.as<T>(), st));
+      if (s->np_lo > 0) {
+        SweepArgs<T, T> a = sweep_args<T, T>(s, 1, false);
+        a.bt = bt32.as<T>();
+        a.xc = xc32.as<T>();
+        a.wprev = w0.as<T>();
+        a.wnext = wsc.as<T>();
+        a.stages = st_lo;
+        a.withhold = -1;
+        a.yspill = nullptr;
+        VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
+      }
+      VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
+                                              Rs, b, xc32.as<T>(), s->S.as<T>(), st));
+    }
+    VTM_CUDA(cudaStreamSynchronize(st));
+  } else {
+    const int R = s->R;
+    const int nb = (s->max_ports + R - 1) / R;
+    for (int b = 0; b < nb; ++b) {
+      VTM_CUDA(launch_unit_rhs<T>(s->pieces.as<PieceDesc>(), np, s->port_local.as<int32_t>(), R, b, s->bt.as<T>(), st));
+      reset_waves(s);
+      sweeps_typed<T>(s, 1);
+      VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
+                                              R, b, s->xc.as<T>(), s->S.as<T>(), st));
+    }
+    VTM_CUDA(cudaMemsetAsync(s->bt.p, 0, s->bt.bytes, st));
+    reset_waves(s);
+  }
+  VTM_CUDA(cudaEventRecord(e1, st));
+  VTM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  VTM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->info.port_setup_ms = ms;
+  check_status(s);
+}
+
+// u_base = P^T K_j^{-1} b̃_j: one band sweep with zero incident waves (its waves go to scratch).
+template <typename T>
+static void ubase_typed(vtm_solver* s) {
+  if (s->np_lo > 0) {
+    SweepArgs<T, T> a = sweep_args<T, T>(s, 1, false);
+    a.wprev = s->wzero.as<T>();
+    a.wnext = s->wscr.as<T>();
+    launch_one<T, T>(s, a, s->np_lo, s->sweep_smem, s->pipe);
+  }
+  VTM_CUDA(launch_gather_ports<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(), s->R,
+                                  s->xc.as<T>(), s->ubase.as<T>(), s->stream));
+  s->launches++;
+  s->ubase_ok = true;
+}
+
+static void ensure_ubase(vtm_solver* s) {
+  if (!s->port_form || s->ubase_ok) return;
+  if (s->precision == VTM_FP32) ubase_typed<float>(s);
+  else ubase_typed<double>(s);
+}
+
+template <typename T>
+static void launch_port(vtm_solver* s) {
+  PortArgs<T> a;
+  a.pieces = s->pieces_lo.as<PieceDesc>();
+  a.S = s->S.as<T>();
+  a.ubase = s->ubase.as<T>();
+  a.wprev = s->w[s->cur].as<T>();
+  a.wnext = s->w[s->cur ^ 1].as<T>();
+  a.port_end_ptr = s->port_end_ptr.as<int32_t>();
+  a.twin = s->twin.as<int32_t>();
+  a.invz = s->invz_t.as<T>();
+  VTM_CUDA(launch_port_sweep<T>(a, s->R, s->np_lo, s->port_smem, s->stream));
+  s->launches++;
+}
+
+// k sweeps in port form: k - 1 port-only sweeps, then one band sweep that also writes x_j.  The
+// flagged subgraphs (FP32 solvers) take their FP64 band sweep in every sweep.
+template <typename T>
+static void port_sweeps_typed(vtm_solver* s, int k) {
+  for (int i = 0; i + 1 < k; ++i) {
+    if (s->np_lo > 0) launch_port<T>(s);
+    if constexpr (sizeof(T) == 4) {
+      if (s->np_hi > 0)
+        launch_one<double, float>(s, sweep_args<double, float>(s, 0, true), s->np_hi, s->hi_smem, false);
+    }
+    s->cur ^= 1;
+  }
+  if (k > 0) sweeps_typed<T>(s, 1);
+}
+
+static int64_t launches_per_batch(const vtm_solver* s, int k) {
+  const int64_t band = (s->np_lo > 0) + (s->np_hi > 0);
+  return s->port_form && k >= 2 ? (int64_t)(k - 1) * band + band : (int64_t)k * band;
+}
+
+template <typename T>
+static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles, int64_t band_elems) {
+  s->info.sweep_form = VTM_FORM_BAND;
+  if (o->sweep_form == VTM_FORM_BAND || s->E == 0) {
+    if (o->sweep_form == VTM_FORM_PORT) fail(VTM_ERR_INVALID, "the port form needs at least one line");
+    return;
+  }
+  const size_t kSmemMax = 227 * 1024;
+  // S_j only for the subgraphs of the main launch (flagged ones keep their FP64 band sweep)
+  std::vector<PieceDesc> lo;
+  lo.reserve(s->np_lo);
+  s_tiles = 0;
+  int max_ports_lo = 0;
+  for (size_t j = 0; j < s->pd_host.size(); ++j) {
+    if (s->piece_bits[j] == 64 && sizeof(T) == 4) continue;
+    PieceDesc d = s->pd_host[j];
+    d.s_off = s_tiles;
+    s_tiles += port_tiles(d.nports);
+    max_ports_lo = std::max(max_ports_lo, d.nports);
+    lo.push_back(d);
+  }
+  const size_t smem = port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
+  const double s_bytes = (double)s_tiles * kNB * kNB * sizeof(T);
+  const double band_bytes = 2.0 * (double)band_elems * sizeof(T);
+  size_t free_b = 0, total_b = 0;
+  VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const bool fits = !s->wide && s->np_lo > 0 && smem <= kSmemMax && s_bytes < 0.5 * (double)free_b;
+  if (o->sweep_form == VTM_FORM_PORT && !fits)
+    fail(VTM_ERR_INVALID, "the port form needs nrhs <= 8, port counts whose response vectors fit in shared "
+                          "memory and room for the port responses in device memory");
+  // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form
+  const double m = std::max(2, s->check_every);
+  if (o->sweep_form == VTM_FORM_AUTO && !(fits && (m - 1) * s_bytes + band_bytes < m * band_bytes)) return;
+  s->port_form = true;
+  s->info.sweep_form = VTM_FORM_PORT;
+  upload(s->pieces_lo, lo, s->stream);
+  s->port_smem = smem;
+  VTM_CUDA(port_sweep_configure<T>(s->R, smem));
+  s->ubase.alloc((size_t)std::max(1, s->nports) * s->R * sizeof(T));
+  s->wzero.alloc((size_t)s->E * s->R * sizeof(T));
+  s->wscr.alloc(s->wzero.bytes);
+  VTM_CUDA(cudaMemsetAsync(s->wzero.p, 0, s->wzero.bytes, s->stream));
+  compute_port_response<T>(s, s_tiles);
+  s->info.port_bytes = (int64_t)s_bytes;
+  // one port sweep, timed
+  ensure_ubase(s);
+  cudaEvent_t e0, e1;
+  VTM_CUDA(cudaEventCreate(&e0));
+  VTM_CUDA(cudaEventCreate(&e1));
+  port_sweeps_typed<T>(s, 2);
+  VTM_CUDA(cudaEventRecord(e0, s->stream));
+  for (int i = 0; i < 3; ++i) {
+    if (s->np_lo > 0) launch_port<T>(s);
+    s->cur ^= 1;
+  }
+  VTM_CUDA(cudaEventRecord(e1, s->stream));
+  VTM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  VTM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->info.port_sweep_ms = ms / 3;
+  s->launches = 0;
+  check_status(s);
+  reset_waves(s);
+}
+
 // Def. 7.1 on the device: g_c = (K_j^{-1})_{cc} for every port copy, nrhs unit right-hand sides
 // per subgraph per sweep with zero incident waves (no exchange); the input impedance seen by end e
 // (its own line open, every other line terminated) is g_c / (1 - g_c / Z_e) (rank-one downdate).
@@ -692,6 +902,7 @@ static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api) {
     r_api[s->end_api[k]] = r;
   }
   VTM_CUDA(cudaMemsetAsync(s->bt.p, 0, s->bt.bytes, s->stream));
+  s->ubase_ok = false;
   reset_waves(s);
 }
 
@@ -704,6 +915,11 @@ void solver_input_impedances(vtm_solver* s, double* r) {
 }
 
 static void run_sweeps_direct(vtm_solver* s, int k) {
+  if (s->port_form && k >= 2) {
+    if (s->precision == VTM_FP32) port_sweeps_typed<float>(s, k);
+    else port_sweeps_typed<double>(s, k);
+    return;
+  }
   if (s->precision == VTM_FP32) sweeps_typed<float>(s, k);
   else sweeps_typed<double>(s, k);
 }
@@ -712,6 +928,7 @@ static void run_sweeps_direct(vtm_solver* s, int k) {
 // The graph bakes in the buffer pointers, which stay fixed for the solver's lifetime; the wave
 // buffer that a batch starts from is part of the key.
 void run_sweeps(vtm_solver* s, int k) {
+  ensure_ubase(s);
   if (k < 2 || !s->use_graphs) {
     run_sweeps_direct(s, k);
     return;
@@ -720,7 +937,7 @@ void run_sweeps(vtm_solver* s, int k) {
     if (g.k == k && g.cur == s->cur) {
       VTM_CUDA(cudaGraphLaunch(g.exec, s->stream));
       s->cur = (s->cur + k) & 1;
-      s->launches += (int64_t)k * ((s->np_lo > 0) + (s->np_hi > 0));
+      s->launches += launches_per_batch(s, k);
       s->have_copies = true;
       return;
     }
@@ -751,7 +968,7 @@ void run_sweeps(vtm_solver* s, int k) {
   s->cur = cur0;
   VTM_CUDA(cudaGraphLaunch(exec, s->stream));
   s->cur = (cur0 + k) & 1;
-  s->launches += (int64_t)k * ((s->np_lo > 0) + (s->np_hi > 0));
+  s->launches += launches_per_batch(s, k);
   s->have_copies = true;
 }
 
@@ -763,6 +980,7 @@ void reset_waves(vtm_solver* s) {
 
 static void split_rhs(vtm_solver* s, const double* src, int64_t ld) {
   s->launches++;
+  s->ubase_ok = false;
   if (s->precision == VTM_FP32)
     VTM_CUDA(launch_split<float>(s->C, s->R, s->copy_vertex.as<int64_t>(), s->share.as<double>(), src, ld,
                                  s->bt.as<float>(), s->stream));
@@ -802,6 +1020,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
     t.z_mode = VTM_Z_UNIFORM;
     t.withhold_slab = 0;
     t.sweep_variant = 0;
+    t.sweep_form = VTM_FORM_BAND;
     std::unique_ptr<vtm_solver> tmp;
     for (int r : {8, 4, 2, 1}) {
       t.nrhs = r;
@@ -832,6 +1051,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   s->inner_reduction = o->inner_reduction > 0 ? o->inner_reduction : 1e-4;
   if (o->wait_polls < 0) fail(VTM_ERR_INVALID, "wait_polls must be >= 0");
   if (o->sweep_variant < 0 || o->sweep_variant > 2) fail(VTM_ERR_INVALID, "sweep_variant must be 0, 1 or 2");
+  if (o->sweep_form < 0 || o->sweep_form > 2) fail(VTM_ERR_INVALID, "sweep_form must be 0, 1 or 2");
   if (o->wait_polls > 0) s->wait_limit = (long)o->wait_polls;
   if (cuda_stream) {
     s->stream = static_cast<cudaStream_t>(cuda_stream);
