@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
     p.add_argument("--workload", default="poisson3d-128", choices=list(WORKLOADS))
+    p.add_argument("--check-every", type=int, default=20,
+                   help="sweeps between FP64 residual checks (a port-form batch ends with one band sweep)")
+    p.add_argument("--form", default="auto", choices=["auto", "band", "port"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -312,7 +315,7 @@ def run_vtm(args):
     R = w["nrhs"]
     stream = torch.cuda.Stream()
     zarg, zdesc = impedance_arg(w["z"], vtm, part)
-    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=10,
+    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every, form=args.form,
                         z_init=w.get("z_init", 1.0))
     sinfo = solver.info()
     bd = torch.tensor(b, device="cuda")
@@ -344,32 +347,52 @@ def run_vtm(args):
     sweeps = stats[-1].sweeps
     launches = sum(s_.launches for s_ in stats)
 
-    # ---- dominant kernel: one sweep launch, CUDA events around back-to-back sweeps
+    # ---- dominant kernel, timed with CUDA events on the solver's stream.  Band form: back-to-back
+    # band sweeps.  Port form: a batch of k sweeps is k - 1 port sweeps and one band sweep, so the
+    # port sweep is (t(k batch) - t(one band sweep)) / (k - 1).
     solver.set_rhs(bd)
     solver.reset()
-    nsw = 40
+    solver.iterate(1)          # computes u_base (port form) outside the timed region
     torch.cuda.synchronize()
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    solver.iterate(nsw)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    sweep_ms = k0.elapsed_time(k1) / nsw
+
+    def timed(k, reps):
+        k0.record(stream)
+        for _ in range(reps):
+            solver.iterate(k)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / reps
+
     elem = 4
+    port = sinfo.sweep_form == 2
+    band_ms = timed(1, 20)
     vec_passes = 4 if R >= 16 else 1   # wide kernel: b̃ read, y written and read back, x written
-    alg_bytes = (2 * sinfo.band_entries * elem + vec_passes * sinfo.ncopies * R * elem
-                 + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
+    band_bytes = (2 * sinfo.band_entries * elem + vec_passes * sinfo.ncopies * R * elem
+                  + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
+    if port:
+        nsw = 41
+        sweep_ms = (timed(nsw, 3) - band_ms) / (nsw - 1)
+        # S_j once; waves in (through twin) and out; twin and 1/Z per end; u_base and the end
+        # pointers per port
+        alg_bytes = (sinfo.port_bytes + 2 * sinfo.nends * R * elem + sinfo.nends * 8
+                     + sinfo.nports * (R * elem + 4))
+        kname = "k_port_sweep<float,%d>" % R
+        ksrc = "port.cu"
+    else:
+        sweep_ms = band_ms
+        alg_bytes = band_bytes
+        if R >= 16:
+            kname = "k_sweep_wide<float,float,%d>" % R
+        elif sinfo.sweep_variant == 1:
+            kname = "k_sweep_pipe<float,float,%d>" % R
+        else:
+            kname = "k_sweep<float,float,%d>" % R
+        ksrc = "sweep_wide.cu" if R >= 16 else "sweep.cu"
     pk = peaks()
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    if R >= 16:
-        kname = "k_sweep_wide<float,float,%d>" % R
-    elif sinfo.sweep_variant == 1:
-        kname = "k_sweep_pipe<float,float,%d>" % R
-    else:
-        kname = "k_sweep<float,float,%d>" % R
-    traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc",
-                                          "sweep_wide.cu" if R >= 16 else "sweep.cu"), args.workload, kname)
+    traffic = kernel_traffic(os.path.join(ROOT, "paper_0807_1949_gb300", "csrc", ksrc), args.workload, kname)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.tensor(b).pin_memory()
@@ -388,7 +411,7 @@ def run_vtm(args):
         del solver
         torch.cuda.empty_cache()
         pz, pzdesc = impedance_arg(w.get("plain_z", 1.0), vtm, part)
-        ps = vtm.Solver(part, z=pz, precision="fp64", nrhs=1, stream=stream, check_every=10)
+        ps = vtm.Solver(part, z=pz, precision="fp64", nrhs=1, stream=stream, check_every=10, form="band")
         b1, x1 = bd[:1].contiguous(), torch.zeros_like(bd[:1])
         ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
         torch.cuda.synchronize()
@@ -420,6 +443,10 @@ def run_vtm(args):
            "setup_ms": round(sinfo.setup_ms, 1), "factor_ms": round(sinfo.factor_ms, 1),
            "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
            "sweep_variant": "pipelined" if sinfo.sweep_variant == 1 else "single-block",
+           "form": "port" if port else "band", "check_every": args.check_every,
+           "band_sweep_ms": round(band_ms, 4), "port_sweep_ms": round(sweep_ms, 4) if port else None,
+           "port_setup_ms": round(sinfo.port_setup_ms, 1) if port else None,
+           "port_bytes": int(sinfo.port_bytes) if port else None,
            "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain}
     cfg.update({k: w[k] for k in ("dims", "block", "sigma", "npoints") if k in w})
     line = {

@@ -242,6 +242,7 @@ typedef struct vtm_solver_info {
   int64_t port_bytes;          /* PORT: bytes of the stored port responses S_j                */
   double port_setup_ms;        /* PORT: device time of computing S_j (unit-source solves)     */
   double port_sweep_ms;        /* PORT: device time of one port-form sweep                    */
+  int64_t nports;              /* port copies (copies with at least one line end)             */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

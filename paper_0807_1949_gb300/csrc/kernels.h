@@ -86,6 +86,30 @@ template <typename T>
 cudaError_t launch_gather_ports(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, const T* xc,
                                 T* ubase, cudaStream_t st);
 
+// Tensor-core port-response sweep for 16 / 32 right-hand sides (port_tc.cu), FP32 solvers.
+struct PortTCArgs {
+  const PieceDesc* pieces;
+  const float* S;              // 128 x 32 chunks of S_j (whole matrix), tensor-core layout
+  float* sglob;                // port-vector scratch: s^T in 32 x 32 chunks
+  const float* ubase;          // ports x R
+  const float* wprev;          // ends x R
+  float* wnext;
+  const int32_t* port_end_ptr;
+  const int32_t* twin;
+  const float* invz;
+  int* status;
+  long wait_limit;
+  int tmem_cols;               // tensor-memory columns per CTA (power of two >= 32 * super-rows)
+};
+
+int64_t port_blocks_tc(int nports);       // 128 x 32 S chunks of one subgraph
+int64_t port_vec_chunks_tc(int nports);   // 32 x 32 s^T chunks of one subgraph
+size_t port_tc_smem_bytes();
+cudaError_t port_tc_configure(int R);
+cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, cudaStream_t st);
+cudaError_t launch_gather_port_response_tc(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs,
+                                           int b, const float* xc, float* S, cudaStream_t st);
+
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;
 

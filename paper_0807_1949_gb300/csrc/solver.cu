@@ -129,9 +129,11 @@ struct vtm_solver {
   int64_t hi_rows = 0;               // sum of the flagged subgraphs' n_pad
   // port-response form (port.cu): S_j per subgraph, u_base per port, zero / scratch wave buffers
   bool port_form = false;
-  DevBuf S, ubase, wzero, wscr;
+  bool port_tc = false;              // R >= 16, FP32: tensor-core port sweep (port_tc.cu)
+  DevBuf S, ubase, wzero, wscr, sglob;
   bool ubase_ok = false;
   size_t port_smem = 0;
+  int tmem_cols = 0;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -568,6 +570,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->info.npieces = np;
   s->info.ncopies = C;
   s->info.nends = s->E;
+  s->info.nports = s->nports;
   s->info.nrhs = R;
   s->info.precision = s->precision;
   s->info.block_rows = kNB;
@@ -730,6 +733,13 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
       VTM_CUDA(launch_unit_rhs<T>(s->pieces.as<PieceDesc>(), np, s->port_local.as<int32_t>(), R, b, s->bt.as<T>(), st));
       reset_waves(s);
       sweeps_typed<T>(s, 1);
+      if constexpr (sizeof(T) == 4) {
+        if (s->port_tc) {
+          VTM_CUDA(launch_gather_port_response_tc(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
+                                                  R, b, s->xc.as<float>(), s->S.as<float>(), st));
+          continue;
+        }
+      }
       VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
                                               R, b, s->xc.as<T>(), s->S.as<T>(), st));
     }
@@ -769,6 +779,26 @@ static void ensure_ubase(vtm_solver* s) {
 
 template <typename T>
 static void launch_port(vtm_solver* s) {
+  if constexpr (sizeof(T) == 4) {
+    if (s->port_tc) {
+      PortTCArgs t;
+      t.pieces = s->pieces_lo.as<PieceDesc>();
+      t.S = s->S.as<float>();
+      t.sglob = s->sglob.as<float>();
+      t.ubase = s->ubase.as<float>();
+      t.wprev = s->w[s->cur].as<float>();
+      t.wnext = s->w[s->cur ^ 1].as<float>();
+      t.port_end_ptr = s->port_end_ptr.as<int32_t>();
+      t.twin = s->twin.as<int32_t>();
+      t.invz = s->invz_t.as<float>();
+      t.status = s->status.as<int>();
+      t.wait_limit = s->wait_limit;
+      t.tmem_cols = s->tmem_cols;
+      VTM_CUDA(launch_port_sweep_tc(t, s->R, s->np_lo, s->stream));
+      s->launches++;
+      return;
+    }
+  }
   PortArgs<T> a;
   a.pieces = s->pieces_lo.as<PieceDesc>();
   a.S = s->S.as<T>();
@@ -813,38 +843,56 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   // S_j only for the subgraphs of the main launch (flagged ones keep their FP64 band sweep)
   std::vector<PieceDesc> lo;
   lo.reserve(s->np_lo);
+  // R >= 16 (FP32): tensor-core sweep over 128 x 128 super-blocks; R <= 8: SIMT sweep over tiles
+  const bool tc = s->wide && sizeof(T) == 4;
   s_tiles = 0;
+  int64_t v_blocks = 0;
   int max_ports_lo = 0;
   for (size_t j = 0; j < s->pd_host.size(); ++j) {
     if (s->piece_bits[j] == 64 && sizeof(T) == 4) continue;
     PieceDesc d = s->pd_host[j];
     d.s_off = s_tiles;
-    s_tiles += port_tiles(d.nports);
+    d.v_off = v_blocks;
+    s_tiles += tc ? port_blocks_tc(d.nports) : port_tiles(d.nports);
+    v_blocks += port_vec_chunks_tc(d.nports);
     max_ports_lo = std::max(max_ports_lo, d.nports);
     lo.push_back(d);
   }
-  const size_t smem = port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
-  const double s_bytes = (double)s_tiles * kNB * kNB * sizeof(T);
+  const size_t smem = tc ? port_tc_smem_bytes() : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
+  const double s_bytes = (double)s_tiles * (tc ? 128.0 * 32.0 : (double)kNB * kNB) * sizeof(T);
   const double band_bytes = 2.0 * (double)band_elems * sizeof(T);
   size_t free_b = 0, total_b = 0;
   VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const bool fits = !s->wide && s->np_lo > 0 && smem <= kSmemMax && s_bytes < 0.5 * (double)free_b;
+  const bool shape_ok = tc ? (max_ports_lo <= 2048) : !s->wide;
+  const bool fits = shape_ok && s->np_lo > 0 && smem <= kSmemMax && s_bytes < 0.5 * (double)free_b;
   if (o->sweep_form == VTM_FORM_PORT && !fits)
-    fail(VTM_ERR_INVALID, "the port form needs nrhs <= 8, port counts whose response vectors fit in shared "
-                          "memory and room for the port responses in device memory");
-  // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form
+    fail(VTM_ERR_INVALID, "the port form needs FP32 or nrhs <= 8, port counts whose response vectors fit in "
+                          "shared (nrhs <= 8) or tensor memory (<= 2048 ports, nrhs 16/32) and room for the port "
+                          "responses in device memory");
+  // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form.  The
+  // tensor-core form (TF32 products) is taken only on request: its rounding stalls the defect
+  // correction on slowly converging problems
   const double m = std::max(2, s->check_every);
-  if (o->sweep_form == VTM_FORM_AUTO && !(fits && (m - 1) * s_bytes + band_bytes < m * band_bytes)) return;
+  if (o->sweep_form == VTM_FORM_AUTO && (tc || !(fits && (m - 1) * s_bytes + band_bytes < m * band_bytes))) return;
   s->port_form = true;
+  s->port_tc = tc;
   s->info.sweep_form = VTM_FORM_PORT;
   upload(s->pieces_lo, lo, s->stream);
   s->port_smem = smem;
-  VTM_CUDA(port_sweep_configure<T>(s->R, smem));
+  if (tc) {
+    int n4max = (max_ports_lo + 127) / 128;
+    s->tmem_cols = 32;
+    while (s->tmem_cols < 32 * n4max) s->tmem_cols *= 2;
+    s->sglob.alloc((size_t)std::max<int64_t>(1, v_blocks) * 32 * 32 * sizeof(float));
+    VTM_CUDA(port_tc_configure(s->R));
+  } else {
+    VTM_CUDA(port_sweep_configure<T>(s->R, smem));
+  }
   s->ubase.alloc((size_t)std::max(1, s->nports) * s->R * sizeof(T));
   s->wzero.alloc((size_t)s->E * s->R * sizeof(T));
   s->wscr.alloc(s->wzero.bytes);
   VTM_CUDA(cudaMemsetAsync(s->wzero.p, 0, s->wzero.bytes, s->stream));
-  compute_port_response<T>(s, s_tiles);
+  compute_port_response<T>(s, s_tiles * (tc ? 128 * 32 / (kNB * kNB) : 1));
   s->info.port_bytes = (int64_t)s_bytes;
   // one port sweep, timed
   ensure_ubase(s);

@@ -67,7 +67,8 @@ class SolverInfo(C.Structure):
                 ("setup_ms", C.c_double), ("factor_ms", C.c_double), ("sweep_stages", C.c_int32),
                 ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32),
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32), ("port_bytes", C.c_int64),
-                ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double)]
+                ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double),
+                ("nports", C.c_int64)]
 
 
 class Stats(C.Structure):

@@ -47,7 +47,7 @@ def test_fem_sweeps_match_oracle(vtmlib, precision, nrhs, tol):
     fem, part, osplit = _setup(vtmlib, 3000, 12, seed=5)
     b = inputs.rhs_uniform(fem.A.n, nrhs, seed=5)
     Z = 1e-2
-    s = vtmlib.Solver(part, z=Z, precision=precision, nrhs=nrhs)
+    s = vtmlib.Solver(part, z=Z, precision=precision, nrhs=nrhs, form="band")
     s.set_rhs(b)
     s.reset()
     s.iterate(3)

@@ -137,7 +137,7 @@ def test_3d_fp32_sweeps_and_refined_solve(vtmlib, nrhs):
     b = inputs.rhs_uniform(A.n, nrhs, seed=4)
     part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
     osplit = evs.split_grid(A, dims, block)
-    s = vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=nrhs)
+    s = vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=nrhs, form="band")
     s.set_rhs(b)
     s.reset()
     s.iterate(3)

@@ -89,15 +89,61 @@ def test_port_form_solve(vtmlib, precision, rtol):
 
 
 def test_port_form_auto_choice(vtmlib):
-    """AUTO takes the port form where S_j is smaller than the band traffic of a batch (3D cubes),
-    and the band form where the port form is unavailable (16 right-hand sides)."""
+    """AUTO takes the port form where S_j is smaller than the band traffic of a batch (3D cubes), the
+    band form for 16 right-hand sides (the tensor-core port form is taken on request only); FP64
+    with 16 right-hand sides has no port form."""
     dims, block = (33, 33, 33), (16, 16, 16)
     A = inputs.grid_poisson(dims, sigma=1.0, seed=23)
     part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
     assert vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=1).info().sweep_form == 2
     assert vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=16).info().sweep_form == 1
+    assert vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=16, form="port").info().sweep_form == 2
+    dims2, block2 = (40, 33), (13, 11)
+    A2 = inputs.grid_poisson(dims2, sigma=1.0, seed=23)
+    part2 = vtmlib.partition_evs(A2, "grid", dims=dims2, block=block2)
+    assert vtmlib.Solver(part2, z=1.0, precision="fp64", nrhs=16).info().sweep_form == 1
     with pytest.raises(vtmlib.VTMError):
-        vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=16, form="port")
+        vtmlib.Solver(part2, z=1.0, precision="fp64", nrhs=16, form="port")
+
+
+# Tensor-core form (R = 16 / 32): S_j and s enter the products rounded to TF32 (unit roundoff
+# 2^-11), accumulated in FP32.  After k sweeps the copies and waves carry about k such roundings
+# relative to |S||s|: tolerance 5e-3 of the max norm after 7 sweeps; the solve with FP64 defect
+# correction must still reach 1e-8.
+@pytest.mark.parametrize("nrhs", [16, 32])
+@pytest.mark.parametrize("dims,block", [((21, 19, 18), (8, 8, 8)), ((34, 34, 34), (16, 16, 16)),
+                                        ((40, 33), (13, 11))])
+def test_port_tc_sweeps_match_oracle(vtmlib, nrhs, dims, block):
+    """One to seven 128-port super-rows per subgraph (34^3 in 16^3 blocks: up to 817 ports), so the
+    transposed products of the off-diagonal super-blocks and the zero padding are all exercised."""
+    A = inputs.grid_poisson(dims, sigma=0.8, seed=24)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=24)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    s = vtmlib.Solver(part, z=0.7, precision="fp32", nrhs=nrhs, form="port")
+    assert s.info().sweep_form == 2
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(7)
+    copies, waves = _oracle_after(osplit, b, 0.7, 7)
+    assert _rel(s.copies(), copies) <= 5e-3
+    assert _rel(s.get_state(), waves[:, _line_map(part, osplit)]) <= 5e-3
+
+
+@pytest.mark.parametrize("nrhs", [16, 32])
+def test_port_tc_solve(vtmlib, nrhs):
+    dims, block = (34, 30, 33), (16, 16, 16)
+    A = inputs.grid_poisson(dims, sigma=1.0, seed=25)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=25)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    s = vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=nrhs, form="port")
+    x = np.zeros_like(b)
+    st = s.solve(b, x, rtol=1e-8, maxit=20000)
+    As = A.to_scipy()
+    rel = np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)
+    assert np.all(rel <= 1e-8) and st.rel_residual <= 1e-8
+    xs = ovtm.direct_solve(A, b)
+    assert np.max(np.abs(x - xs)) <= 1e-5 * np.max(np.abs(xs))
 
 
 def _fem(vtmlib, npts, parts, seed):
@@ -136,6 +182,31 @@ def test_port_form_fem_matches_oracle(vtmlib, precision, tol):
     ref_c = np.concatenate([st.x_local[j] for j in range(len(osplit.subgraphs))], axis=1)
     assert _rel(s.copies(), ref_c[:, cmap]) <= tol
     assert _rel(s.get_state(), m.waves_out(st)[:, emap]) <= tol
+
+
+def test_port_tc_fem_matches_oracle(vtmlib):
+    """Uneven FEM subgraphs (one partial super-row each) with 16 right-hand sides on the tensor
+    cores, stiffness-scaled impedances, 7 sweeps against the oracle."""
+    from test_gpu_fem import _maps
+    fem, part, osplit = _fem(vtmlib, 5000, 20, seed=13)
+    f = part.line_features()
+    d = np.exp(f[:, 1].astype(np.float64))
+    Z = 2.0 / (d[0::2] + d[1::2])
+    b = inputs.rhs_uniform(fem.A.n, 16, seed=13)
+    s = vtmlib.Solver(part, z=Z, precision="fp32", nrhs=16, form="port")
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(7)
+    cmap, emap = _maps(part, osplit)
+    zl = np.empty(len(osplit.vtl))
+    zl[emap[0::2] // 2] = Z
+    m = ovtm.VTM(osplit, zl)
+    st = m.initial_state(16)
+    for _ in range(7):
+        st = m.sweep(st, b)
+    ref_c = np.concatenate([st.x_local[j] for j in range(len(osplit.subgraphs))], axis=1)
+    assert _rel(s.copies(), ref_c[:, cmap]) <= 5e-3
+    assert _rel(s.get_state(), m.waves_out(st)[:, emap]) <= 5e-3
 
 
 def test_port_form_skips_flagged_subgraphs(vtmlib):
