@@ -37,9 +37,11 @@ WORKLOADS = {
     # large multi-RHS run: 256^3, sigma = 1.5, 4096 subgraphs, 32 right-hand sides per sweep
     "poisson3d-256-r32": dict(kind="grid", dims=(256, 256, 256), block=(16, 16, 16), sigma=1.5, nrhs=32,
                               z="learned:poisson3d", rtol=1e-8),
-    # uneven batching: P1 FEM on the Delaunay triangulation of 1M points, 2000 RCB subgraphs, 16 RHS
-    # (impedance search on this family found nothing better than Z = 1 at the horizons tried)
-    "fem2d-1m-r16": dict(kind="fem", npoints=1_000_000, pieces=2000, nrhs=16, z=1.0, rtol=1e-8),
+    # uneven batching: P1 FEM on the Delaunay triangulation of 1M points, 2000 RCB subgraphs, 16 RHS.
+    # The one-level method does not reach 1e-8 here in any practical number of sweeps (contrast 1e6),
+    # so a step is a fixed number of sweeps and the line reports the residual it reaches.
+    "fem2d-1m-r16": dict(kind="fem", npoints=1_000_000, pieces=2000, nrhs=16, z="scaled:2", plain_z="scaled:2",
+                         rtol=1e-8, sweeps=1000),
     # learned-impedance family: 2D 256^2, 64 subgraphs
     "poisson2d-256": dict(kind="grid", dims=(256, 256), block=(32, 32), sigma=1.25, nrhs=1,
                           z="learned:poisson2d-256", rtol=1e-8),
@@ -323,8 +325,10 @@ def run_vtm(args):
     torch.cuda.synchronize()
 
     # ---- warm-up and timed steps (device timing on the solver's stream)
+    maxit = w.get("sweeps", 100000)
+    fixed = "sweeps" in w
     for _ in range(args.warmup):
-        solver.solve(bd, xd, rtol=w["rtol"], maxit=100000)
+        solver.solve(bd, xd, rtol=w["rtol"], maxit=maxit, raise_on_fail=not fixed)
     torch.cuda.synchronize()
     barrier(ws)
     clk = Clocks(local)
@@ -334,7 +338,7 @@ def run_vtm(args):
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
-        stats.append(solver.solve(bd, xd, rtol=w["rtol"], maxit=100000))
+        stats.append(solver.solve(bd, xd, rtol=w["rtol"], maxit=maxit, raise_on_fail=not fixed))
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -401,7 +405,7 @@ def run_vtm(args):
     for _ in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        solver.solve(bh, xh, rtol=w["rtol"], maxit=100000)
+        solver.solve(bh, xh, rtol=w["rtol"], maxit=maxit, raise_on_fail=not fixed)
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = max_over_ranks(ws, statistics.median(e2e))
 
@@ -413,12 +417,12 @@ def run_vtm(args):
         pz, pzdesc = impedance_arg(w.get("plain_z", 1.0), vtm, part)
         ps = vtm.Solver(part, z=pz, precision="fp64", nrhs=1, stream=stream, check_every=10, form="band")
         b1, x1 = bd[:1].contiguous(), torch.zeros_like(bd[:1])
-        ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
+        ps.solve(b1, x1, rtol=w["rtol"], maxit=maxit, raise_on_fail=False)
         torch.cuda.synchronize()
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        pst = ps.solve(b1, x1, rtol=w["rtol"], maxit=100000, raise_on_fail=False)
+        pst = ps.solve(b1, x1, rtol=w["rtol"], maxit=maxit, raise_on_fail=False)
         p1.record(stream)
         torch.cuda.synchronize()
         plain = {"ms": round(p0.elapsed_time(p1), 3), "nrhs": 1, "sweeps": pst.sweeps, "converged": pst.status == 0,
@@ -450,7 +454,9 @@ def run_vtm(args):
            "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "plain": plain}
     cfg.update({k: w[k] for k in ("dims", "block", "sigma", "npoints") if k in w})
     line = {
-        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC if not fixed else ("time for %d VTM sweeps x %d right-hand sides on 1 GB300 "
+                                            "(relative residual reached: config.final_rel_residual)" % (maxit, R)),
+        "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (f64 residual + defect correction)", "data": "synthetic",
         "config": cfg,

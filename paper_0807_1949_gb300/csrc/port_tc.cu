@@ -4,20 +4,28 @@
 // the method).  With R = 16/32 columns this is a dense matrix product, so it runs as tcgen05.mma
 // (kind::tf32, FP32 accumulation in tensor memory), both operands K-major:
 //
-//  * S_j is stored whole (both triangles) as 128 x 32 chunks (I, c): ports 128 I .. 128 I + 127
-//    by ports 32 c .. 32 c + 31, in the 128-byte-swizzled K-major layout the tensor core reads
+//  * S_j is stored whole (both triangles, FP32) as 128 x 32 chunks (I, c): ports 128 I .. 128 I +
+//    127 by ports 32 c .. 32 c + 31, in the 128-byte-swizzled K-major layout the tensor core reads
 //    (rows of 128 bytes, 16-byte units XOR-ed with the row index mod 8, 8-row groups 1024 bytes
-//    apart), chunks of a row of super-blocks contiguous.  A symmetric half would need the transposed
-//    operand (MN-major), which this build does not use for TF32.
-//  * s^T (32 columns x ports, zero beyond R and beyond the port count) is written by the CTA to a
-//    global scratch in the same layout, 4 KB per 32 ports (B operand, K-major).
-//  * Chunk (I, c) adds S_Ic s_c to y_I: four MMAs of K = 8.  y lives in tensor memory: 128 lanes
-//    (one port each) x 32 columns per super-row, up to 16 super-rows (2048 ports) in 512 columns.
+//    apart), the chunks of a row of super-blocks contiguous.  A symmetric half would need the
+//    transposed operand (MN-major), which this build does not use for TF32.
+//  * Three TF32 products keep FP32 accuracy (the split of Ootomo and Yokota, "Recovering single
+//    precision accuracy from Tensor Cores while surpassing the FP32 theoretical peak performance",
+//    2022): with hi(x) the TF32 truncation of x and lo(x) = x - hi(x) (exact in FP32),
+//    S s ~ hi(S) hi(s) + hi(S) lo(s) + lo(S) hi(s).  hi(S) is what the tensor core reads from the
+//    FP32 chunk itself; lo(S) is formed in shared memory by six converter warps; hi(s) and lo(s)
+//    are written by the CTA to a global scratch (sᵀ: 32 columns x ports, zero padding), 2 x 4 KB
+//    per 32 ports.  The dropped lo(S) lo(s) term and the TF32 truncation of the lo parts are
+//    below 2^-21 relative to |S||s|.
+//  * Chunk (I, c) adds S_Ic s_c to y_I: 3 x 4 MMAs of M = 128, N = 32, K = 8.  y lives in tensor
+//    memory: 128 lanes (one port each) x 32 columns per super-row, up to 16 super-rows (2048
+//    ports) in 512 columns.
 //
-// One CTA per subgraph, 256 threads.  Thread 0 issues the bulk copies of a stage ring (S chunk +
-// s chunk = 20 KB per stage, mbarrier complete_tx) and the MMAs; tcgen05.commit frees a stage once
-// its MMAs have read it.  Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets
-// its copies and MMAs finish, frees its tensor memory and returns.
+// One CTA per subgraph, 256 threads, warp-specialised over a 5-stage ring (40 KB per stage: the
+// S chunk, its lo part, hi(s) and lo(s)): warp 0 issues the bulk copies (mbarrier complete_tx),
+// warps 2-7 form lo(S), warp 1 issues the MMAs and releases each stage with tcgen05.commit.  Every
+// wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its copies and MMAs finish,
+// frees its tensor memory and returns.
 #include "kernels.h"
 
 namespace vtm {
@@ -29,9 +37,12 @@ constexpr int kTN = 32;                         // accumulator columns per super
 constexpr int kKC = 32;                         // ports per K chunk
 constexpr uint32_t kChunkBytes = kTB * kKC * 4; // S chunk: 128 x 32 FP32
 constexpr uint32_t kVecBytes = kTN * kKC * 4;   // s chunk: 32 columns x 32 ports
-constexpr uint32_t kStageBytes = kChunkBytes + kVecBytes;
-constexpr int kTcStages = 6;
+// stage: S chunk | lo(S) | hi(s) | lo(s)
+constexpr uint32_t kStageBytes = 2 * kChunkBytes + 2 * kVecBytes;
+constexpr int kTcStages = 5;
 constexpr int kTcThreads = 256;
+constexpr int kConvWarps = 6;                   // warps 2..7
+constexpr uint32_t kHiMask = 0xFFFFE000u;       // TF32: sign, exponent, 10 mantissa bits
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -82,12 +93,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// FP32 -> TF32 with round-to-nearest (ties away), kept in a 32-bit container; the tensor core
-// ignores the low 13 mantissa bits, so rounding here halves the operand error of truncation.
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & kHiMask); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Byte offset of (row, 4-byte column) inside a 128-byte-swizzled block of 128-byte rows.
@@ -102,7 +111,7 @@ int64_t port_blocks_tc(int nports) {
   return n4 * nkc;
 }
 
-int64_t port_vec_chunks_tc(int nports) { return (nports + kKC - 1) / kKC; }
+int64_t port_vec_chunks_tc(int nports) { return 2 * ((nports + kKC - 1) / kKC); }
 
 size_t port_tc_smem_bytes() { return 1024 + 1024 + (size_t)kTcStages * kStageBytes; }
 
@@ -117,22 +126,25 @@ __global__ void k_gather_port_response_tc(const PieceDesc* __restrict__ pieces, 
     if (cc >= pd.nports) continue;
     const int64_t chunk = pd.s_off + (int64_t)(q / kTB) * nkc + cc / kKC;
     S[chunk * (kChunkBytes / 4) + swz(q % kTB, cc % kKC) / 4] =
-        to_tf32(xc[((size_t)pd.copy_off + port_local[pd.port_off + q]) * Rs + r]);
+        xc[((size_t)pd.copy_off + port_local[pd.port_off + q]) * Rs + r];
   }
 }
 
 template <int R>
 __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int abort_flag;
+  __shared__ volatile int abort_flag;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [kTcStages]
-  uint64_t* empty = full + kTcStages;                // [kTcStages]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [kTcStages] bulk copies landed
+  uint64_t* conv = full + kTcStages;                 // [kTcStages] lo(S) written
+  uint64_t* empty = conv + kTcStages;                // [kTcStages] MMAs done reading
   uint64_t* done = empty + kTcStages;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* vready = done + 1;                       // port vectors written (7 warps arrive)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(vready + 1);
   const uint32_t stage0 = base + 1024;
+  unsigned char* stage0_ptr = sm + 1024;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const PieceDesc pd = a.pieces[blockIdx.x];
@@ -146,9 +158,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     abort_flag = 0;
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&full[s], 1);
+      mbar_init(&conv[s], kConvWarps);
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
+    mbar_init(vready, 7);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -157,72 +171,153 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-
-  // s^T: sum_e w_in[e] / Z_e per port and column, rounded to TF32, zero padding; row = column r
-  // of the right-hand side, 128 bytes = 32 ports per chunk
-  float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
-  for (int i = tid; i < nkc * kKC * kTN; i += kTcThreads) {
-    const int r = i / (nkc * kKC), p = i % (nkc * kKC);
-    float v = 0.f;
-    if (p < np && r < R) {
-      const int e0 = a.port_end_ptr[pd.port_off + p], e1 = a.port_end_ptr[pd.port_off + p + 1];
-      for (int e = e0; e < e1; ++e) v += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
-    }
-    sg[(p / kKC) * (kVecBytes / 4) + swz(r, p % kKC) / 4] = to_tf32(v);
-  }
-  asm volatile("fence.proxy.async;" ::: "memory");  // generic-proxy writes -> bulk-copy reads
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
 
-  if (tid == 0) {
-    const float* Sp = a.S + pd.s_off * (kChunkBytes / 4);
-    int issued = 0;
-    auto load = [&](int st) {
-      const uint32_t sb = stage0 + st * kStageBytes;
-      mbar_arrive_expect_tx(&full[st], kStageBytes);
-      bulk_g2s(sb, Sp + (int64_t)issued * (kChunkBytes / 4), kChunkBytes, &full[st]);
-      bulk_g2s(sb + kChunkBytes, sg + (issued % nkc) * (kVecBytes / 4), kVecBytes, &full[st]);
-      ++issued;
-    };
-    for (int st = 0; st < kTcStages && st < nchunk; ++st) load(st);
-    constexpr uint32_t kId = idesc_tf32(false, false);  // A = S chunk, B = s^T chunk, both K-major
-    int b = 0;
-    for (; b < nchunk; ++b) {
+  if (warp != 0) {
+    // s = sum_e w_in[e] / Z_e per port and column, while warp 0 already streams S: hi(s) and lo(s)
+    // as sᵀ chunks (row = column r of the right-hand side, 128 bytes = 32 ports), zero padding.
+    // Lanes take the columns of one port; each warp keeps kU ports' wave loads in flight.
+    constexpr int kLanesPerPort = R;               // 16 or 32
+    constexpr int kPortsPerWarp = 32 / kLanesPerPort;
+    constexpr int kU = 8;
+    const int r = lane % kLanesPerPort;
+    const int sub = lane / kLanesPerPort;
+    const int step = 7 * kPortsPerWarp;
+    for (int p0 = (warp - 1) * kPortsPerWarp + sub; p0 < nkc * kKC; p0 += step * kU) {
+      // three rounds of independent loads (end range, twin and 1/Z, wave) for kU ports, then the
+      // rare extra ends of corner and edge ports
+      int e0[kU], e1[kU], tw[kU];
+      float iz[kU], v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int p = p0 + u * step;
+        e0[u] = 0;
+        e1[u] = 0;
+        if (p < np) {
+          e0[u] = a.port_end_ptr[pd.port_off + p];
+          e1[u] = a.port_end_ptr[pd.port_off + p + 1];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        tw[u] = 0;
+        iz[u] = 0.f;
+        if (e1[u] > e0[u]) {
+          tw[u] = a.twin[e0[u]];
+          iz[u] = a.invz[e0[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) v[u] = (e1[u] > e0[u]) ? a.wprev[(size_t)tw[u] * R + r] * iz[u] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        for (int e = e0[u] + 1; e < e1[u]; ++e) v[u] += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int p = p0 + u * step;
+        if (p < nkc * kKC) {
+          const size_t o = (size_t)(2 * (p / kKC)) * (kVecBytes / 4);
+          const float hi = tf32_hi(v[u]);
+          sg[o + swz(r, p % kKC) / 4] = hi;
+          sg[o + kVecBytes / 4 + swz(r, p % kKC) / 4] = v[u] - hi;
+          if (R == 16) {  // columns 16..31 of the chunk are zero
+            sg[o + swz(r + 16, p % kKC) / 4] = 0.f;
+            sg[o + kVecBytes / 4 + swz(r + 16, p % kKC) / 4] = 0.f;
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async;" ::: "memory");  // generic-proxy writes -> bulk-copy reads
+    __syncwarp();
+    if (lane == 0) mbar_arrive(vready);
+  }
+
+  if (warp == 0) {
+    // ---- producer: the S chunks of the first stages go out at once; their port-vector chunks, and
+    // every later stage, once the port vectors are written
+    if (lane == 0) {
+      const float* Sp = a.S + pd.s_off * (kChunkBytes / 4);
+      const int pre = nchunk < kTcStages ? nchunk : kTcStages;
+      for (int b = 0; b < pre; ++b) {
+        mbar_arrive_expect_tx(&full[b], kChunkBytes + 2 * kVecBytes);
+        bulk_g2s(stage0 + b * kStageBytes, Sp + (int64_t)b * (kChunkBytes / 4), kChunkBytes, &full[b]);
+      }
+      // (the other warps only compute, so this wait ends; the copies go out even if it ran out, so
+      // that every stage's expected bytes arrive)
+      const bool vok = mbar_wait_bounded(vready, 0, kDrainPolls);
+      for (int b2 = 0; b2 < pre; ++b2)
+        bulk_g2s(stage0 + b2 * kStageBytes + 2 * kChunkBytes, sg + (size_t)(2 * (b2 % nkc)) * (kVecBytes / 4),
+                 2 * kVecBytes, &full[b2]);
+      if (!vok) abort_flag = 1;
+      int b = pre;
+      for (; b < nchunk && !abort_flag; ++b) {
+        const int st = b % kTcStages;
+        if (!mbar_wait_bounded(&empty[st], (uint32_t)(((b / kTcStages) - 1) & 1), a.wait_limit)) {
+          abort_flag = 1;
+          break;
+        }
+        const uint32_t sb = stage0 + st * kStageBytes;
+        mbar_arrive_expect_tx(&full[st], kChunkBytes + 2 * kVecBytes);
+        bulk_g2s(sb, Sp + (int64_t)b * (kChunkBytes / 4), kChunkBytes, &full[st]);
+        bulk_g2s(sb + 2 * kChunkBytes, sg + (size_t)(2 * (b % nkc)) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
+      }
+      // the copies of the last stages must land before the shared memory can go away
+      for (int b2 = (b > kTcStages ? b - kTcStages : 0); b2 < b; ++b2)
+        mbar_wait_bounded(&full[b2 % kTcStages], (uint32_t)((b2 / kTcStages) & 1), kDrainPolls);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t kId = idesc_tf32(false, false);  // both operands K-major
+      for (int b = 0; b < nchunk; ++b) {
+        const int st = b % kTcStages;
+        if (abort_flag || !mbar_wait_bounded(&conv[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit)) {
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const int I = b / nkc, c = b % nkc;
+        const uint32_t sb = stage0 + st * kStageBytes;
+        const uint32_t sS = sb, sL = sb + kChunkBytes, vH = sb + 2 * kChunkBytes, vL = vH + kVecBytes;
+#pragma unroll
+        for (int kk = 0; kk < kKC / 8; ++kk) {
+          const uint64_t aH = sdesc(sS + kk * 32, 16, 1024), aL = sdesc(sL + kk * 32, 16, 1024);
+          const uint64_t bH = sdesc(vH + kk * 32, 16, 1024), bL = sdesc(vL + kk * 32, 16, 1024);
+          mma_tf32(tmem + I * kTN, aH, bH, kId, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem + I * kTN, aH, bL, kId, 1u);
+          mma_tf32(tmem + I * kTN, aL, bH, kId, 1u);
+        }
+        mma_commit(&empty[st]);
+      }
+      mma_commit(done);  // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---- converters: lo(S) = S - hi(S) next to the staged chunk
+    const int ct = tid - 64;
+    for (int b = 0; b < nchunk; ++b) {
       const int st = b % kTcStages;
-      const uint32_t ph = (uint32_t)((b / kTcStages) & 1);
-      if (!mbar_wait_bounded(&full[st], ph, a.wait_limit)) {
+      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit)) {
         abort_flag = 1;
         break;
       }
-      tc_fence_after();
-      const int I = b / nkc, c = b % nkc;
-      const uint32_t sb = stage0 + st * kStageBytes;
-#pragma unroll
-      for (int kk = 0; kk < kKC / 8; ++kk)
-        mma_tf32(tmem + I * kTN, sdesc(sb + kk * 32, 16, 1024), sdesc(sb + kChunkBytes + kk * 32, 16, 1024), kId,
-                 (c > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[st]);
-      if (issued < nchunk) {
-        if (!mbar_wait_bounded(&empty[st], ph, a.wait_limit)) {
-          abort_flag = 1;
-          ++b;
-          break;
-        }
-        load(st);
+      const float4* src = reinterpret_cast<const float4*>(stage0_ptr + st * kStageBytes);
+      float4* dst = reinterpret_cast<float4*>(stage0_ptr + st * kStageBytes + kChunkBytes);
+      for (int i = ct; i < (int)(kChunkBytes / 16); i += 32 * kConvWarps) {
+        const float4 x = src[i];
+        dst[i] = make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
       }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[st]);
     }
-    if (abort_flag) {
-      // let the copies already issued land before the shared memory goes away
-      for (int b2 = b; b2 < issued; ++b2)
-        mbar_wait_bounded(&full[b2 % kTcStages], (uint32_t)((b2 / kTcStages) & 1), kDrainPolls);
-      atomicExch(a.status, kStatusTimeout);
-    }
-    mma_commit(done);  // arrives once every MMA issued above has completed
   }
   __syncthreads();
   const bool ok = mbar_wait_bounded(done, 0, kDrainPolls) && !abort_flag;
+  if (abort_flag && tid == 0) atomicExch(a.status, kStatusTimeout);
   tc_fence_after();
 
   if (ok) {

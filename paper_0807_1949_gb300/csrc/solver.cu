@@ -869,11 +869,10 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     fail(VTM_ERR_INVALID, "the port form needs FP32 or nrhs <= 8, port counts whose response vectors fit in "
                           "shared (nrhs <= 8) or tensor memory (<= 2048 ports, nrhs 16/32) and room for the port "
                           "responses in device memory");
-  // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form.  The
-  // tensor-core form (TF32 products) is taken only on request: its rounding stalls the defect
-  // correction on slowly converging problems
+  // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form (the
+  // multi-RHS band sweep is bound by FP32 arithmetic, so there the tensor-core form always wins)
   const double m = std::max(2, s->check_every);
-  if (o->sweep_form == VTM_FORM_AUTO && (tc || !(fits && (m - 1) * s_bytes + band_bytes < m * band_bytes))) return;
+  if (o->sweep_form == VTM_FORM_AUTO && !(fits && (tc || (m - 1) * s_bytes + band_bytes < m * band_bytes))) return;
   s->port_form = true;
   s->port_tc = tc;
   s->info.sweep_form = VTM_FORM_PORT;
