@@ -37,9 +37,10 @@ constexpr int kTN = 32;                         // accumulator columns per super
 constexpr int kKC = 32;                         // ports per K chunk
 constexpr uint32_t kChunkBytes = kTB * kKC * 4; // S chunk: 128 x 32 FP32
 constexpr uint32_t kVecBytes = kTN * kKC * 4;   // s chunk: 32 columns x 32 ports
-// stage: S chunk | lo(S) | hi(s) | lo(s)
-constexpr uint32_t kStageBytes = 2 * kChunkBytes + 2 * kVecBytes;
-constexpr int kTcStages = 5;
+// bulk-copy stage: S chunk | hi(s) | lo(s); lo(S) goes to a separate ring of kLoBufs buffers
+constexpr uint32_t kStageBytes = kChunkBytes + 2 * kVecBytes;
+constexpr int kTcStages = 7;
+constexpr int kLoBufs = 3;
 constexpr int kTcThreads = 256;
 constexpr int kConvWarps = 6;                   // warps 2..7
 constexpr uint32_t kHiMask = 0xFFFFE000u;       // TF32: sign, exponent, 10 mantissa bits
@@ -113,7 +114,7 @@ int64_t port_blocks_tc(int nports) {
 
 int64_t port_vec_chunks_tc(int nports) { return 2 * ((nports + kKC - 1) / kKC); }
 
-size_t port_tc_smem_bytes() { return 1024 + 1024 + (size_t)kTcStages * kStageBytes; }
+size_t port_tc_smem_bytes() { return 1024 + 1024 + (size_t)kTcStages * kStageBytes + (size_t)kLoBufs * kChunkBytes; }
 
 // S_j columns cc = b * Rs + r from unit-source solves into the chunk layout (whole matrix).
 __global__ void k_gather_port_response_tc(const PieceDesc* __restrict__ pieces, const int32_t* __restrict__ port_local,
@@ -138,12 +139,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [kTcStages] bulk copies landed
-  uint64_t* conv = full + kTcStages;                 // [kTcStages] lo(S) written
-  uint64_t* empty = conv + kTcStages;                // [kTcStages] MMAs done reading
-  uint64_t* done = empty + kTcStages;
+  uint64_t* empty = full + kTcStages;                // [kTcStages] MMAs done reading the stage
+  uint64_t* conv = empty + kTcStages;                // [kLoBufs] lo(S) written
+  uint64_t* lofree = conv + kLoBufs;                 // [kLoBufs] MMAs done reading lo(S)
+  uint64_t* done = lofree + kLoBufs;
   uint64_t* vready = done + 1;                       // port vectors written (7 warps arrive)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(vready + 1);
   const uint32_t stage0 = base + 1024;
+  const uint32_t lo0 = stage0 + kTcStages * kStageBytes;
+  unsigned char* lo0_ptr = sm + 1024 + kTcStages * kStageBytes;
   unsigned char* stage0_ptr = sm + 1024;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,8 +162,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     abort_flag = 0;
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], kConvWarps);
       mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < kLoBufs; ++s) {
+      mbar_init(&conv[s], kConvWarps);
+      mbar_init(&lofree[s], 1);
     }
     mbar_init(done, 1);
     mbar_init(vready, 7);
@@ -180,55 +187,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   if (warp != 0) {
     // s = sum_e w_in[e] / Z_e per port and column, while warp 0 already streams S: hi(s) and lo(s)
     // as sᵀ chunks (row = column r of the right-hand side, 128 bytes = 32 ports), zero padding.
-    // Lanes take the columns of one port; each warp keeps kU ports' wave loads in flight.
-    constexpr int kLanesPerPort = R;               // 16 or 32
-    constexpr int kPortsPerWarp = 32 / kLanesPerPort;
-    constexpr int kU = 8;
-    const int r = lane % kLanesPerPort;
-    const int sub = lane / kLanesPerPort;
-    const int step = 7 * kPortsPerWarp;
-    for (int p0 = (warp - 1) * kPortsPerWarp + sub; p0 < nkc * kKC; p0 += step * kU) {
-      // three rounds of independent loads (end range, twin and 1/Z, wave) for kU ports, then the
-      // rare extra ends of corner and edge ports
-      int e0[kU], e1[kU], tw[kU];
-      float iz[kU], v[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int p = p0 + u * step;
-        e0[u] = 0;
-        e1[u] = 0;
-        if (p < np) {
-          e0[u] = a.port_end_ptr[pd.port_off + p];
-          e1[u] = a.port_end_ptr[pd.port_off + p + 1];
-        }
+    // Warp w takes chunks w - 1, w + 6, ...; lane = port of the chunk, so each store of a column
+    // writes one 128-byte row, and the 32 wave loads of a lane are independent.
+    for (int c = warp - 1; c < nkc; c += 7) {
+      const int p = c * kKC + lane;
+      int e0 = 0, e1 = 0, tw = 0;
+      float iz = 0.f;
+      if (p < np) {
+        e0 = a.port_end_ptr[pd.port_off + p];
+        e1 = a.port_end_ptr[pd.port_off + p + 1];
+        tw = a.twin[e0];
+        iz = a.invz[e0];
       }
+      float v[kTN];
+      const float* w0 = a.wprev + (size_t)tw * R;
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        tw[u] = 0;
-        iz[u] = 0.f;
-        if (e1[u] > e0[u]) {
-          tw[u] = a.twin[e0[u]];
-          iz[u] = a.invz[e0[u]];
-        }
+      for (int r = 0; r < kTN; ++r) v[r] = (r < R && e1 > e0) ? w0[r] * iz : 0.f;
+      for (int e = e0 + 1; e < e1; ++e) {
+        const float* we = a.wprev + (size_t)a.twin[e] * R;
+        const float ize = a.invz[e];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
       }
+      float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
+      float* lo_c = hi_c + kVecBytes / 4;
 #pragma unroll
-      for (int u = 0; u < kU; ++u) v[u] = (e1[u] > e0[u]) ? a.wprev[(size_t)tw[u] * R + r] * iz[u] : 0.f;
-#pragma unroll
-      for (int u = 0; u < kU; ++u)
-        for (int e = e0[u] + 1; e < e1[u]; ++e) v[u] += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int p = p0 + u * step;
-        if (p < nkc * kKC) {
-          const size_t o = (size_t)(2 * (p / kKC)) * (kVecBytes / 4);
-          const float hi = tf32_hi(v[u]);
-          sg[o + swz(r, p % kKC) / 4] = hi;
-          sg[o + kVecBytes / 4 + swz(r, p % kKC) / 4] = v[u] - hi;
-          if (R == 16) {  // columns 16..31 of the chunk are zero
-            sg[o + swz(r + 16, p % kKC) / 4] = 0.f;
-            sg[o + kVecBytes / 4 + swz(r + 16, p % kKC) / 4] = 0.f;
-          }
-        }
+      for (int r = 0; r < kTN; ++r) {
+        const float hi = tf32_hi(v[r]);
+        hi_c[swz(r, lane) / 4] = hi;
+        lo_c[swz(r, lane) / 4] = v[r] - hi;
       }
     }
     asm volatile("fence.proxy.async;" ::: "memory");  // generic-proxy writes -> bulk-copy reads
@@ -250,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       // that every stage's expected bytes arrive)
       const bool vok = mbar_wait_bounded(vready, 0, kDrainPolls);
       for (int b2 = 0; b2 < pre; ++b2)
-        bulk_g2s(stage0 + b2 * kStageBytes + 2 * kChunkBytes, sg + (size_t)(2 * (b2 % nkc)) * (kVecBytes / 4),
+        bulk_g2s(stage0 + b2 * kStageBytes + kChunkBytes, sg + (size_t)(2 * (b2 % nkc)) * (kVecBytes / 4),
                  2 * kVecBytes, &full[b2]);
       if (!vok) abort_flag = 1;
       int b = pre;
@@ -263,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         const uint32_t sb = stage0 + st * kStageBytes;
         mbar_arrive_expect_tx(&full[st], kChunkBytes + 2 * kVecBytes);
         bulk_g2s(sb, Sp + (int64_t)b * (kChunkBytes / 4), kChunkBytes, &full[st]);
-        bulk_g2s(sb + 2 * kChunkBytes, sg + (size_t)(2 * (b % nkc)) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
+        bulk_g2s(sb + kChunkBytes, sg + (size_t)(2 * (b % nkc)) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
       }
       // the copies of the last stages must land before the shared memory can go away
       for (int b2 = (b > kTcStages ? b - kTcStages : 0); b2 < b; ++b2)
@@ -274,15 +261,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     if (lane == 0) {
       constexpr uint32_t kId = idesc_tf32(false, false);  // both operands K-major
       for (int b = 0; b < nchunk; ++b) {
-        const int st = b % kTcStages;
-        if (abort_flag || !mbar_wait_bounded(&conv[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit)) {
+        const int st = b % kTcStages, lb = b % kLoBufs;
+        // conv[lb] for chunk b implies full[st] (the converters waited for it)
+        if (abort_flag || !mbar_wait_bounded(&conv[lb], (uint32_t)((b / kLoBufs) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
         }
         tc_fence_after();
         const int I = b / nkc, c = b % nkc;
         const uint32_t sb = stage0 + st * kStageBytes;
-        const uint32_t sS = sb, sL = sb + kChunkBytes, vH = sb + 2 * kChunkBytes, vL = vH + kVecBytes;
+        const uint32_t sS = sb, sL = lo0 + lb * kChunkBytes, vH = sb + kChunkBytes, vL = vH + kVecBytes;
 #pragma unroll
         for (int kk = 0; kk < kKC / 8; ++kk) {
           const uint64_t aH = sdesc(sS + kk * 32, 16, 1024), aL = sdesc(sL + kk * 32, 16, 1024);
@@ -292,6 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
           mma_tf32(tmem + I * kTN, aL, bH, kId, 1u);
         }
         mma_commit(&empty[st]);
+        mma_commit(&lofree[lb]);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
     }
@@ -299,20 +288,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     // ---- converters: lo(S) = S - hi(S) next to the staged chunk
     const int ct = tid - 64;
     for (int b = 0; b < nchunk; ++b) {
-      const int st = b % kTcStages;
-      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit)) {
+      const int st = b % kTcStages, lb = b % kLoBufs;
+      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit) ||
+          (b >= kLoBufs &&
+           !mbar_wait_bounded(&lofree[lb], (uint32_t)(((b / kLoBufs) - 1) & 1), a.wait_limit))) {
         abort_flag = 1;
         break;
       }
       const float4* src = reinterpret_cast<const float4*>(stage0_ptr + st * kStageBytes);
-      float4* dst = reinterpret_cast<float4*>(stage0_ptr + st * kStageBytes + kChunkBytes);
+      float4* dst = reinterpret_cast<float4*>(lo0_ptr + lb * kChunkBytes);
       for (int i = ct; i < (int)(kChunkBytes / 16); i += 32 * kConvWarps) {
         const float4 x = src[i];
         dst[i] = make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[st]);
+      if (lane == 0) mbar_arrive(&conv[lb]);
     }
   }
   __syncthreads();
@@ -322,20 +313,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
 
   if (ok) {
     // u = u_base + y; w_out[e] = 2 u - w_in[e].  Warp w reads lanes 32 (w % 4) .. + 31 of every
-    // other super-row.
+    // other super-row: one port per lane, its R columns in registers; u_base, the incident waves
+    // and the outgoing waves move as 16-byte vectors (rows of R floats).
     const int q = warp & 3;
     for (int bb = warp >> 2; bb < n4; bb += 2) {
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(bb * kTN), v);
       const int p = bb * kTB + q * 32 + lane;
       if (p < np) {
-        const float* ub = a.ubase + (size_t)(pd.port_off + p) * R;
+        const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)(pd.port_off + p) * R);
         const int e0 = a.port_end_ptr[pd.port_off + p], e1 = a.port_end_ptr[pd.port_off + p + 1];
-        for (int e = e0; e < e1; ++e) {
-          const float* wi = a.wprev + (size_t)a.twin[e] * R;
-          float* wo = a.wnext + (size_t)e * R;
+        float4 u[R / 4];
 #pragma unroll
-          for (int r = 0; r < R; ++r) wo[r] = 2.f * (ub[r] + __uint_as_float(v[r])) - wi[r];
+        for (int k = 0; k < R / 4; ++k) {
+          const float4 b4 = ub[k];
+          u[k] = make_float4(b4.x + __uint_as_float(v[4 * k]), b4.y + __uint_as_float(v[4 * k + 1]),
+                             b4.z + __uint_as_float(v[4 * k + 2]), b4.w + __uint_as_float(v[4 * k + 3]));
+        }
+        for (int e = e0; e < e1; ++e) {
+          const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+          float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
+          float4 w[R / 4];
+#pragma unroll
+          for (int k = 0; k < R / 4; ++k) w[k] = wi[k];
+#pragma unroll
+          for (int k = 0; k < R / 4; ++k)
+            wo[k] = make_float4(2.f * u[k].x - w[k].x, 2.f * u[k].y - w[k].y, 2.f * u[k].z - w[k].z,
+                                2.f * u[k].w - w[k].w);
         }
       }
     }
