@@ -99,14 +99,15 @@ struct PortTCArgs {
   const float* invz;
   int* status;
   long wait_limit;
-  int tmem_cols;               // tensor-memory columns per CTA (power of two >= 32 * super-rows)
+  const int2* items;           // (subgraph, 128-port super-row) per CTA of the product kernel
 };
 
 int64_t port_blocks_tc(int nports);       // 128 x 32 S chunks of one subgraph
 int64_t port_vec_chunks_tc(int nports);   // 32 x 32 s^T chunks of one subgraph
 size_t port_tc_smem_bytes();
 cudaError_t port_tc_configure(int R);
-cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, cudaStream_t st);
+// Two launches: the port vectors (one CTA per subgraph), then the product (one CTA per item).
+cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, int nitems, cudaStream_t st);
 cudaError_t launch_gather_port_response_tc(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs,
                                            int b, const float* xc, float* S, cudaStream_t st);
 

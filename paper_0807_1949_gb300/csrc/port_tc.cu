@@ -21,11 +21,14 @@
 //    memory: 128 lanes (one port each) x 32 columns per super-row, up to 16 super-rows (2048
 //    ports) in 512 columns.
 //
-// One CTA per subgraph, 256 threads, warp-specialised over a 5-stage ring (40 KB per stage: the
-// S chunk, its lo part, hi(s) and lo(s)): warp 0 issues the bulk copies (mbarrier complete_tx),
-// warps 2-7 form lo(S), warp 1 issues the MMAs and releases each stage with tcgen05.commit.  Every
-// wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its copies and MMAs finish,
-// frees its tensor memory and returns.
+// Two launches per sweep.  k_port_vec_tc (one CTA per subgraph) writes hi(s) and lo(s).  Then
+// k_port_sweep_tc works on items (subgraph, 128-port super-row I), 256 threads, two CTAs per SM,
+// warp-specialised over a 3-stage bulk-copy ring (S chunk + hi(s) + lo(s) = 24 KB) and a 2-buffer
+// lo(S) ring: warp 0 issues the bulk copies (mbarrier complete_tx), warps 2-7 form lo(S), warp 1
+// issues the MMAs into 32 tensor-memory columns and releases stages and lo buffers with
+// tcgen05.commit; then every warp reads its quarter of the 128 lanes and half of the columns and
+// writes the waves.  Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its
+// copies and MMAs finish, frees its tensor memory and returns.
 #include "kernels.h"
 
 namespace vtm {
@@ -39,8 +42,9 @@ constexpr uint32_t kChunkBytes = kTB * kKC * 4; // S chunk: 128 x 32 FP32
 constexpr uint32_t kVecBytes = kTN * kKC * 4;   // s chunk: 32 columns x 32 ports
 // bulk-copy stage: S chunk | hi(s) | lo(s); lo(S) goes to a separate ring of kLoBufs buffers
 constexpr uint32_t kStageBytes = kChunkBytes + 2 * kVecBytes;
-constexpr int kTcStages = 7;
-constexpr int kLoBufs = 3;
+constexpr int kTcStages = 3;
+constexpr int kLoBufs = 2;
+constexpr uint32_t kTmemCols = 32;              // one super-row of accumulators per CTA
 constexpr int kTcThreads = 256;
 constexpr int kConvWarps = 6;                   // warps 2..7
 constexpr uint32_t kHiMask = 0xFFFFE000u;       // TF32: sign, exponent, 10 mantissa bits
@@ -131,8 +135,58 @@ __global__ void k_gather_port_response_tc(const PieceDesc* __restrict__ pieces, 
   }
 }
 
+// hi(s), lo(s) per subgraph: s = sum_e w_in[e] / Z_e per port and column as sᵀ chunks (row =
+// column r of the right-hand side, 128 bytes = 32 ports), zero padding.  Warp w takes chunks w,
+// w + 8, ...; lane = port of the chunk, so each store of a column writes one 128-byte row and
+// the R wave loads of a lane are independent.
 template <int R>
-__global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArgs a) {
+__global__ void __launch_bounds__(kTcThreads) k_port_vec_tc(const PortTCArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const PieceDesc pd = a.pieces[blockIdx.x];
+  const int np = pd.nports;
+  const int nkc = (np + kKC - 1) / kKC;
+  float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
+  for (int c = warp; c < nkc; c += kTcThreads / 32) {
+    const int p = c * kKC + lane;
+    int e0 = 0, e1 = 0, tw = 0;
+    float iz = 0.f;
+    if (p < np) {
+      e0 = a.port_end_ptr[pd.port_off + p];
+      e1 = a.port_end_ptr[pd.port_off + p + 1];
+      tw = a.twin[e0];
+      iz = a.invz[e0];
+    }
+    float v[kTN];
+    const float4* w0 = reinterpret_cast<const float4*>(a.wprev + (size_t)tw * R);
+#pragma unroll
+    for (int k = 0; k < R / 4; ++k) {
+      const float4 x = (e1 > e0) ? w0[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[4 * k] = x.x * iz;
+      v[4 * k + 1] = x.y * iz;
+      v[4 * k + 2] = x.z * iz;
+      v[4 * k + 3] = x.w * iz;
+    }
+#pragma unroll
+    for (int r = R; r < kTN; ++r) v[r] = 0.f;
+    for (int e = e0 + 1; e < e1; ++e) {
+      const float* we = a.wprev + (size_t)a.twin[e] * R;
+      const float ize = a.invz[e];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
+    }
+    float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
+    float* lo_c = hi_c + kVecBytes / 4;
+#pragma unroll
+    for (int r = 0; r < kTN; ++r) {
+      const float hi = tf32_hi(v[r]);
+      hi_c[swz(r, lane) / 4] = hi;
+      lo_c[swz(r, lane) / 4] = v[r] - hi;
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kTcThreads, 2) k_port_sweep_tc(const PortTCArgs a) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ volatile int abort_flag;
   const uint32_t raw = smem_u32(smem_raw);
@@ -143,20 +197,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   uint64_t* conv = empty + kTcStages;                // [kLoBufs] lo(S) written
   uint64_t* lofree = conv + kLoBufs;                 // [kLoBufs] MMAs done reading lo(S)
   uint64_t* done = lofree + kLoBufs;
-  uint64_t* vready = done + 1;                       // port vectors written (7 warps arrive)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(vready + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   const uint32_t stage0 = base + 1024;
   const uint32_t lo0 = stage0 + kTcStages * kStageBytes;
-  unsigned char* lo0_ptr = sm + 1024 + kTcStages * kStageBytes;
   unsigned char* stage0_ptr = sm + 1024;
+  unsigned char* lo0_ptr = stage0_ptr + kTcStages * kStageBytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const PieceDesc pd = a.pieces[blockIdx.x];
+  const int2 item = a.items[blockIdx.x];
+  const PieceDesc pd = a.pieces[item.x];
+  const int I = item.y;
   const int np = pd.nports;
-  if (np == 0) return;
-  const int n4 = (np + kTB - 1) / kTB;
   const int nkc = (np + kKC - 1) / kKC;
-  const int nchunk = n4 * nkc;
 
   if (tid == 0) {
     abort_flag = 0;
@@ -169,12 +221,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       mbar_init(&lofree[s], 1);
     }
     mbar_init(done, 1);
-    mbar_init(vready, 7);
     fence_mbar_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"((uint32_t)a.tmem_cols)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -182,102 +233,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
-
-  if (warp != 0) {
-    // s = sum_e w_in[e] / Z_e per port and column, while warp 0 already streams S: hi(s) and lo(s)
-    // as sᵀ chunks (row = column r of the right-hand side, 128 bytes = 32 ports), zero padding.
-    // Warp w takes chunks w - 1, w + 6, ...; lane = port of the chunk, so each store of a column
-    // writes one 128-byte row, and the 32 wave loads of a lane are independent.
-    for (int c = warp - 1; c < nkc; c += 7) {
-      const int p = c * kKC + lane;
-      int e0 = 0, e1 = 0, tw = 0;
-      float iz = 0.f;
-      if (p < np) {
-        e0 = a.port_end_ptr[pd.port_off + p];
-        e1 = a.port_end_ptr[pd.port_off + p + 1];
-        tw = a.twin[e0];
-        iz = a.invz[e0];
-      }
-      float v[kTN];
-      const float* w0 = a.wprev + (size_t)tw * R;
-#pragma unroll
-      for (int r = 0; r < kTN; ++r) v[r] = (r < R && e1 > e0) ? w0[r] * iz : 0.f;
-      for (int e = e0 + 1; e < e1; ++e) {
-        const float* we = a.wprev + (size_t)a.twin[e] * R;
-        const float ize = a.invz[e];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
-      }
-      float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
-      float* lo_c = hi_c + kVecBytes / 4;
-#pragma unroll
-      for (int r = 0; r < kTN; ++r) {
-        const float hi = tf32_hi(v[r]);
-        hi_c[swz(r, lane) / 4] = hi;
-        lo_c[swz(r, lane) / 4] = v[r] - hi;
-      }
-    }
-    asm volatile("fence.proxy.async;" ::: "memory");  // generic-proxy writes -> bulk-copy reads
-    __syncwarp();
-    if (lane == 0) mbar_arrive(vready);
-  }
+  const float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
 
   if (warp == 0) {
-    // ---- producer: the S chunks of the first stages go out at once; their port-vector chunks, and
-    // every later stage, once the port vectors are written
+    // ---- producer: chunk c of super-row I and its port-vector chunk c
     if (lane == 0) {
-      const float* Sp = a.S + pd.s_off * (kChunkBytes / 4);
-      const int pre = nchunk < kTcStages ? nchunk : kTcStages;
-      for (int b = 0; b < pre; ++b) {
-        mbar_arrive_expect_tx(&full[b], kChunkBytes + 2 * kVecBytes);
-        bulk_g2s(stage0 + b * kStageBytes, Sp + (int64_t)b * (kChunkBytes / 4), kChunkBytes, &full[b]);
-      }
-      // (the other warps only compute, so this wait ends; the copies go out even if it ran out, so
-      // that every stage's expected bytes arrive)
-      const bool vok = mbar_wait_bounded(vready, 0, kDrainPolls);
-      for (int b2 = 0; b2 < pre; ++b2)
-        bulk_g2s(stage0 + b2 * kStageBytes + kChunkBytes, sg + (size_t)(2 * (b2 % nkc)) * (kVecBytes / 4),
-                 2 * kVecBytes, &full[b2]);
-      if (!vok) abort_flag = 1;
-      int b = pre;
-      for (; b < nchunk && !abort_flag; ++b) {
-        const int st = b % kTcStages;
-        if (!mbar_wait_bounded(&empty[st], (uint32_t)(((b / kTcStages) - 1) & 1), a.wait_limit)) {
+      const float* Sp = a.S + (pd.s_off + (int64_t)I * nkc) * (kChunkBytes / 4);
+      int c = 0;
+      for (; c < nkc && !abort_flag; ++c) {
+        const int st = c % kTcStages;
+        if (c >= kTcStages &&
+            !mbar_wait_bounded(&empty[st], (uint32_t)(((c / kTcStages) - 1) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
         }
         const uint32_t sb = stage0 + st * kStageBytes;
-        mbar_arrive_expect_tx(&full[st], kChunkBytes + 2 * kVecBytes);
-        bulk_g2s(sb, Sp + (int64_t)b * (kChunkBytes / 4), kChunkBytes, &full[st]);
-        bulk_g2s(sb + kChunkBytes, sg + (size_t)(2 * (b % nkc)) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
+        mbar_arrive_expect_tx(&full[st], kStageBytes);
+        bulk_g2s(sb, Sp + (int64_t)c * (kChunkBytes / 4), kChunkBytes, &full[st]);
+        bulk_g2s(sb + kChunkBytes, sg + (size_t)(2 * c) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
       }
       // the copies of the last stages must land before the shared memory can go away
-      for (int b2 = (b > kTcStages ? b - kTcStages : 0); b2 < b; ++b2)
-        mbar_wait_bounded(&full[b2 % kTcStages], (uint32_t)((b2 / kTcStages) & 1), kDrainPolls);
+      for (int c2 = (c > kTcStages ? c - kTcStages : 0); c2 < c; ++c2)
+        mbar_wait_bounded(&full[c2 % kTcStages], (uint32_t)((c2 / kTcStages) & 1), kDrainPolls);
     }
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
       constexpr uint32_t kId = idesc_tf32(false, false);  // both operands K-major
-      for (int b = 0; b < nchunk; ++b) {
-        const int st = b % kTcStages, lb = b % kLoBufs;
-        // conv[lb] for chunk b implies full[st] (the converters waited for it)
-        if (abort_flag || !mbar_wait_bounded(&conv[lb], (uint32_t)((b / kLoBufs) & 1), a.wait_limit)) {
+      for (int c = 0; c < nkc; ++c) {
+        const int st = c % kTcStages, lb = c % kLoBufs;
+        // conv[lb] for chunk c implies full[st] (the converters waited for it)
+        if (abort_flag || !mbar_wait_bounded(&conv[lb], (uint32_t)((c / kLoBufs) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const int I = b / nkc, c = b % nkc;
         const uint32_t sb = stage0 + st * kStageBytes;
         const uint32_t sS = sb, sL = lo0 + lb * kChunkBytes, vH = sb + kChunkBytes, vL = vH + kVecBytes;
 #pragma unroll
         for (int kk = 0; kk < kKC / 8; ++kk) {
           const uint64_t aH = sdesc(sS + kk * 32, 16, 1024), aL = sdesc(sL + kk * 32, 16, 1024);
           const uint64_t bH = sdesc(vH + kk * 32, 16, 1024), bL = sdesc(vL + kk * 32, 16, 1024);
-          mma_tf32(tmem + I * kTN, aH, bH, kId, (c > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem + I * kTN, aH, bL, kId, 1u);
-          mma_tf32(tmem + I * kTN, aL, bH, kId, 1u);
+          mma_tf32(tmem, aH, bH, kId, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, aH, bL, kId, 1u);
+          mma_tf32(tmem, aL, bH, kId, 1u);
         }
         mma_commit(&empty[st]);
         mma_commit(&lofree[lb]);
@@ -285,13 +284,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       mma_commit(done);  // arrives once every MMA issued above has completed
     }
   } else {
-    // ---- converters: lo(S) = S - hi(S) next to the staged chunk
+    // ---- converters: lo(S) = S - hi(S) into the lo ring
     const int ct = tid - 64;
-    for (int b = 0; b < nchunk; ++b) {
-      const int st = b % kTcStages, lb = b % kLoBufs;
-      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((b / kTcStages) & 1), a.wait_limit) ||
-          (b >= kLoBufs &&
-           !mbar_wait_bounded(&lofree[lb], (uint32_t)(((b / kLoBufs) - 1) & 1), a.wait_limit))) {
+    for (int c = 0; c < nkc; ++c) {
+      const int st = c % kTcStages, lb = c % kLoBufs;
+      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((c / kTcStages) & 1), a.wait_limit) ||
+          (c >= kLoBufs &&
+           !mbar_wait_bounded(&lofree[lb], (uint32_t)(((c / kLoBufs) - 1) & 1), a.wait_limit))) {
         abort_flag = 1;
         break;
       }
@@ -312,32 +311,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   tc_fence_after();
 
   if (ok) {
-    // u = u_base + y; w_out[e] = 2 u - w_in[e].  Warp w reads lanes 32 (w % 4) .. + 31 of every
-    // other super-row: one port per lane, its R columns in registers; u_base, the incident waves
-    // and the outgoing waves move as 16-byte vectors (rows of R floats).
-    const int q = warp & 3;
-    for (int bb = warp >> 2; bb < n4; bb += 2) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(bb * kTN), v);
-      const int p = bb * kTB + q * 32 + lane;
+    // u = u_base + y; w_out[e] = 2 u - w_in[e].  Warp w reads lanes 32 (w % 4) .. + 31 (one port
+    // per lane) and the 16 columns 16 (w / 4) .. + 15; rows move as 16-byte vectors.
+    const int q = warp & 3, h = warp >> 2;
+    if (16 * h < R) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * h))
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int p = I * kTB + q * 32 + lane;
       if (p < np) {
-        const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)(pd.port_off + p) * R);
+        const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)(pd.port_off + p) * R + 16 * h);
         const int e0 = a.port_end_ptr[pd.port_off + p], e1 = a.port_end_ptr[pd.port_off + p + 1];
-        float4 u[R / 4];
+        float4 u[4];
 #pragma unroll
-        for (int k = 0; k < R / 4; ++k) {
+        for (int k = 0; k < 4; ++k) {
           const float4 b4 = ub[k];
           u[k] = make_float4(b4.x + __uint_as_float(v[4 * k]), b4.y + __uint_as_float(v[4 * k + 1]),
                              b4.z + __uint_as_float(v[4 * k + 2]), b4.w + __uint_as_float(v[4 * k + 3]));
         }
         for (int e = e0; e < e1; ++e) {
-          const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
-          float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
-          float4 w[R / 4];
+          const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R + 16 * h);
+          float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R + 16 * h);
+          float4 w[4];
 #pragma unroll
-          for (int k = 0; k < R / 4; ++k) w[k] = wi[k];
+          for (int k = 0; k < 4; ++k) w[k] = wi[k];
 #pragma unroll
-          for (int k = 0; k < R / 4; ++k)
+          for (int k = 0; k < 4; ++k)
             wo[k] = make_float4(2.f * u[k].x - w[k].x, 2.f * u[k].y - w[k].y, 2.f * u[k].z - w[k].z,
                                 2.f * u[k].w - w[k].w);
         }
@@ -348,8 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -362,12 +366,18 @@ cudaError_t port_tc_configure(int R) {
   }
 }
 
-cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, cudaStream_t st) {
-  if (npieces <= 0) return cudaSuccess;
+cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, int nitems, cudaStream_t st) {
+  if (npieces <= 0 || nitems <= 0) return cudaSuccess;
   const size_t smem = port_tc_smem_bytes();
   switch (R) {
-    case 16: k_port_sweep_tc<16><<<npieces, kTcThreads, smem, st>>>(a); break;
-    case 32: k_port_sweep_tc<32><<<npieces, kTcThreads, smem, st>>>(a); break;
+    case 16:
+      k_port_vec_tc<16><<<npieces, kTcThreads, 0, st>>>(a);
+      k_port_sweep_tc<16><<<nitems, kTcThreads, smem, st>>>(a);
+      break;
+    case 32:
+      k_port_vec_tc<32><<<npieces, kTcThreads, 0, st>>>(a);
+      k_port_sweep_tc<32><<<nitems, kTcThreads, smem, st>>>(a);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

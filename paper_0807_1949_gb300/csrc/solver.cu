@@ -133,7 +133,8 @@ struct vtm_solver {
   DevBuf S, ubase, wzero, wscr, sglob;
   bool ubase_ok = false;
   size_t port_smem = 0;
-  int tmem_cols = 0;
+  DevBuf tc_items;                   // (subgraph of the main launch, 128-port super-row)
+  int n_items = 0;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -793,9 +794,9 @@ static void launch_port(vtm_solver* s) {
       t.invz = s->invz_t.as<float>();
       t.status = s->status.as<int>();
       t.wait_limit = s->wait_limit;
-      t.tmem_cols = s->tmem_cols;
-      VTM_CUDA(launch_port_sweep_tc(t, s->R, s->np_lo, s->stream));
-      s->launches++;
+      t.items = s->tc_items.as<int2>();
+      VTM_CUDA(launch_port_sweep_tc(t, s->R, s->np_lo, s->n_items, s->stream));
+      s->launches += 2;
       return;
     }
   }
@@ -829,7 +830,9 @@ static void port_sweeps_typed(vtm_solver* s, int k) {
 
 static int64_t launches_per_batch(const vtm_solver* s, int k) {
   const int64_t band = (s->np_lo > 0) + (s->np_hi > 0);
-  return s->port_form && k >= 2 ? (int64_t)(k - 1) * band + band : (int64_t)k * band;
+  if (!s->port_form || k < 2) return (int64_t)k * band;
+  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0);
+  return (int64_t)(k - 1) * port + band;
 }
 
 template <typename T>
@@ -863,12 +866,11 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   const double band_bytes = 2.0 * (double)band_elems * sizeof(T);
   size_t free_b = 0, total_b = 0;
   VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const bool shape_ok = tc ? (max_ports_lo <= 2048) : !s->wide;
+  const bool shape_ok = tc || !s->wide;
   const bool fits = shape_ok && s->np_lo > 0 && smem <= kSmemMax && s_bytes < 0.5 * (double)free_b;
   if (o->sweep_form == VTM_FORM_PORT && !fits)
     fail(VTM_ERR_INVALID, "the port form needs FP32 or nrhs <= 8, port counts whose response vectors fit in "
-                          "shared (nrhs <= 8) or tensor memory (<= 2048 ports, nrhs 16/32) and room for the port "
-                          "responses in device memory");
+                          "shared memory (nrhs <= 8) and room for the port responses in device memory");
   // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form (the
   // multi-RHS band sweep is bound by FP32 arithmetic, so there the tensor-core form always wins)
   const double m = std::max(2, s->check_every);
@@ -879,9 +881,11 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   upload(s->pieces_lo, lo, s->stream);
   s->port_smem = smem;
   if (tc) {
-    int n4max = (max_ports_lo + 127) / 128;
-    s->tmem_cols = 32;
-    while (s->tmem_cols < 32 * n4max) s->tmem_cols *= 2;
+    std::vector<int2> items;
+    for (size_t j = 0; j < lo.size(); ++j)
+      for (int I = 0; I < (lo[j].nports + 127) / 128; ++I) items.push_back(make_int2((int)j, I));
+    s->n_items = (int)items.size();
+    upload(s->tc_items, items, s->stream);
     s->sglob.alloc((size_t)std::max<int64_t>(1, v_blocks) * 32 * 32 * sizeof(float));
     VTM_CUDA(port_tc_configure(s->R));
   } else {
