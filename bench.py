@@ -48,6 +48,9 @@ WORKLOADS = {
     "laplace2d-32": dict(kind="grid", dims=(32, 32), block=(16, 16), sigma=0.0, nrhs=1, z=1.0, rtol=1e-8),
     # small case of the 3D subgraph shape (64 subgraphs, 0.37 GB factor > L2) for ncu captures
     "poisson3d-64": dict(kind="grid", dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, nrhs=1, z=1.0, rtol=1e-8),
+    # the same with 32 right-hand sides (tensor-core port form; 0.5 GB of port responses > L2)
+    "poisson3d-64-r32": dict(kind="grid", dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, nrhs=32, z=1.0,
+                             rtol=1e-8),
 }
 METRIC = "time to rel. residual 1e-8 (learned-Z batched vs plain VTM) on 1 GB300; HBM GB/s"
 

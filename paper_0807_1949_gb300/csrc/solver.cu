@@ -1178,8 +1178,14 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   double prev_inner = INFINITY, rel = INFINITY;
   int status = VTM_ERR_NOT_CONVERGED;
   bool trial_fresh = false;  // xt holds the assembled iterate of the last check
+  // Port form: a batch's last sweep is a band sweep, which costs several port sweeps, so after two
+  // checks of the same inner solve the next batch is sized from the observed rate to end near the
+  // next event (rtol, or the restart threshold of the defect correction), between m and 8 m sweeps.
+  int next_k = m;
+  double last_inner = -1.0;
+  int last_inner_sweeps = 0;
   while (sweeps < maxit) {
-    const int k = std::min(m, maxit - sweeps);
+    const int k = std::min(next_k, maxit - sweeps);
     run_sweeps(s, k);
     sweeps += k;
     inner_sweeps += k;
@@ -1211,6 +1217,18 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       status = VTM_OK;
       break;
     }
+    next_k = m;
+    if (s->port_form && last_inner > 0 && inner > 0 && inner < last_inner && inner_sweeps > last_inner_sweeps) {
+      const double rate = std::pow(inner / last_inner, 1.0 / (inner_sweeps - last_inner_sweeps));
+      double need = rtol / rel;                                   // reduction to reach rtol
+      if (refine) need = std::max(need, s->inner_reduction / inner);  // or the restart threshold
+      if (rate < 1.0 && need < 1.0) {
+        const double kk = std::ceil(1.05 * std::log(need) / std::log(rate));
+        next_k = (int)std::min<double>(8.0 * m, std::max<double>(m, kk));
+      }
+    }
+    last_inner = inner;
+    last_inner_sweeps = inner_sweeps;
     // accept the trial only when it improves on the residual it started from
     if (refine && inner < 1.0 && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
@@ -1226,6 +1244,8 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       ++restarts;
       inner_sweeps = 0;
       prev_inner = INFINITY;
+      last_inner = -1.0;
+      next_k = m;
       trial_fresh = false;
       continue;
     }

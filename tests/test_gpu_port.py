@@ -81,11 +81,12 @@ def test_port_form_solve(vtmlib, precision, rtol):
     assert np.all(rel <= rtol) and st.rel_residual <= rtol
     xs = ovtm.direct_solve(A, b)
     assert np.max(np.abs(x - xs)) <= 1e3 * rtol * np.max(np.abs(xs))
-    # same number of sweeps as the band form up to the check granularity
+    # the same iteration as the band form: as many sweeps up to the check granularity, which the
+    # port form stretches (batches sized from the observed rate, at most 8 check intervals)
     sb = vtmlib.Solver(part, z=1.0, precision=precision, nrhs=2, form="band")
     xb = np.zeros_like(b)
     stb = sb.solve(b, xb, rtol=rtol, maxit=20000)
-    assert abs(st.sweeps - stb.sweeps) <= 20
+    assert stb.sweeps - 20 <= st.sweeps <= 1.2 * stb.sweeps + 80
 
 
 def test_port_form_auto_choice(vtmlib):
