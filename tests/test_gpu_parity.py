@@ -225,3 +225,22 @@ def test_config2_full_size_sampled(vtmlib):
     st = s.solve(b, x, rtol=1e-8, maxit=20000)
     r = np.linalg.norm(b[0] - A.to_scipy() @ x[0]) / np.linalg.norm(b[0])
     assert r <= 1e-8, (r, st.sweeps)
+
+
+@pytest.mark.parametrize("dims,block,sigma", [((32, 32), (16, 16), 0.0), ((21, 19, 18), (8, 8, 8), 1.0)])
+def test_fp32_solve_matches_mixed_oracle(vtmlib, dims, block, sigma):
+    """The library's FP32 sweeps inside FP64 defect correction against the mixed-precision oracle
+    (factors rounded to FP32, FP32 substitution, the same restart rule): both reach 1e-8 with about
+    the same sweeps and restarts; the factors differ only in rounding (the GPU factors in FP32)."""
+    from oracle import mixed
+    A = inputs.grid_poisson(dims, sigma=sigma, seed=3)
+    b = inputs.rhs_uniform(A.n, 1, seed=3)
+    osplit = evs.split_grid(A, dims, block)
+    ref = mixed.solve_refined(osplit, A, b, 1.0, kind="fp32", rtol=1e-8, maxit=20000, check_every=10)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    s = vtmlib.Solver(part, z=1.0, precision="fp32", check_every=10, form="band")
+    x = np.zeros_like(b)
+    st = s.solve(b, x, rtol=1e-8, maxit=20000)
+    assert ref.history[-1][1] <= 1e-8 and st.rel_residual <= 1e-8
+    assert abs(st.sweeps - ref.sweeps) <= max(20, 0.1 * ref.sweeps)
+    assert abs(st.restarts - ref.restarts) <= 1
