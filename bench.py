@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--check-every", type=int, default=20,
                    help="sweeps between FP64 residual checks (a port-form batch ends with one band sweep)")
     p.add_argument("--form", default="auto", choices=["auto", "band", "port"])
+    p.add_argument("--port-storage", default="fp16-auto", choices=["native", "fp16", "fp16-auto"],
+                   help="port form, nrhs <= 8: storage of the port responses")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -320,7 +322,7 @@ def run_vtm(args):
     R = w["nrhs"]
     stream = torch.cuda.Stream()
     zarg, zdesc = impedance_arg(w["z"], vtm, part)
-    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every, form=args.form,
+    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every, form=args.form, port_storage=args.port_storage,
                         z_init=w.get("z_init", 1.0))
     sinfo = solver.info()
     bd = torch.tensor(b, device="cuda")
@@ -353,6 +355,9 @@ def run_vtm(args):
     rel = float(np.max(np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)))
     sweeps = stats[-1].sweeps
     launches = sum(s_.launches for s_ in stats)
+    bits_now = solver.info().port_storage_bits
+    dtype_desc = ("f32 (f16-stored port responses, f64 residual + defect correction)"
+                  if sinfo.sweep_form == 2 and bits_now == 16 else "f32 (f64 residual + defect correction)")
 
     # ---- dominant kernel, timed with CUDA events on the solver's stream.  Band form: back-to-back
     # band sweeps.  Port form: a batch of k sweeps is k - 1 port sweeps and one band sweep, so the
@@ -451,6 +456,7 @@ def run_vtm(args):
            "partition_ms": round(t_part * 1e3, 1), "sweep_stages": sinfo.sweep_stages,
            "sweep_variant": "pipelined" if sinfo.sweep_variant == 1 else "single-block",
            "form": "port" if port else "band", "check_every": args.check_every,
+           "port_storage_bits": int(bits_now) if port else None,
            "band_sweep_ms": round(band_ms, 4), "port_sweep_ms": round(sweep_ms, 4) if port else None,
            "port_setup_ms": round(sinfo.port_setup_ms, 1) if port else None,
            "port_bytes": int(sinfo.port_bytes) if port else None,
@@ -461,7 +467,7 @@ def run_vtm(args):
                                             "(relative residual reached: config.final_rel_residual)" % (maxit, R)),
         "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (f64 residual + defect correction)", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype_desc, "data": "synthetic",
         "config": cfg,
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "peak_source": pk["source"], "unit": "GB/s",

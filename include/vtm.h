@@ -208,7 +208,21 @@ typedef struct vtm_setup_opts {
                               substitution once per batch of sweeps to refresh the interior
                               unknowns; AUTO (0) takes PORT where it moves fewer bytes per sweep,
                               fits in shared memory (nrhs <= 8) and in device memory            */
+  int32_t port_storage;    /* PORT form, FP32 solvers, nrhs <= 8: storage of S_j (VTM_STORE_*):
+                              NATIVE (0) the solver precision; FP16 halves the bytes of a sweep
+                              (each S_j scaled by its largest entry, FP32 arithmetic; the sweeps
+                              then match the FP64 oracle to about 2^-11 per sweep and the FP64
+                              defect correction restores the tolerance); FP16_AUTO takes FP16
+                              when the responses exceed 96 MB (streamed from HBM rather than
+                              held in L2) and returns to FP32 for good once a defect-correction
+                              step gains less than a factor 10                                 */
 } vtm_setup_opts;
+
+enum {
+  VTM_STORE_NATIVE = 0,
+  VTM_STORE_FP16 = 1,
+  VTM_STORE_FP16_AUTO = 2
+};
 
 enum {
   VTM_FORM_AUTO = 0,
@@ -243,6 +257,8 @@ typedef struct vtm_solver_info {
   double port_setup_ms;        /* PORT: device time of computing S_j (unit-source solves)     */
   double port_sweep_ms;        /* PORT: device time of one port-form sweep                    */
   int64_t nports;              /* port copies (copies with at least one line end)             */
+  int32_t port_storage_bits;   /* PORT: bits per stored S_j entry now (16, 32 or 64; FP16_AUTO
+                                  turns 16 into 32 when it falls back)                         */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

@@ -8,9 +8,19 @@
 // the way u is obtained differs.  S_j is symmetric, so only its lower block triangle is stored.
 //
 // Storage of S_j: 32 x 32 tiles (I, J), J <= I, in the order I (I + 1) / 2 + J, from element offset
-// s_off * 1024.  Inside a tile the layout is lane-major: element (row i, column c) sits at
-// ((c / V) * 32 + i) * V + c % V with V = 16 / sizeof(T), so that one 16-byte load per lane gives
-// every lane V consecutive entries of its own row.  Ports beyond n_ports are zero.
+// s_off * 1024.  Inside a tile lane L = 4 a + b of the warp owns the 4 x 8 patch of rows
+// 4a .. 4a+3 and columns 8b .. 8b+7; patch entry p = (i mod 4) * 8 + (c mod 8) of element (i, c)
+// sits at ((p / V) * 32 + L) * V + p mod V with V = 16 / sizeof(entry), so that the k-th 16-byte
+// load of all lanes reads 512 contiguous bytes.  The row part T s_J then sums over 4 lanes and the
+// column part T^T s_I over 8 lanes (short reduce-scatters).  Ports beyond n_ports are zero.
+//
+// FP16 storage (FP32 solvers): the same tiles as IEEE half, V = 8, each subgraph's S_j divided by
+// its largest entry (kept per subgraph in FP32); products and accumulation stay in FP32 and y is
+// scaled back before u = u_base + y.  It halves the bytes of the sweep; its rounding (2^-11 of
+// the largest entry) is absorbed by the FP64 defect correction, and the solver returns to FP32
+// storage if a correction step stops gaining a digit.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace vtm {
@@ -31,6 +41,44 @@ struct Vec16<double> {
   static constexpr int V = 2;
   __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 };
+
+// Position of element (i, c) of a tile in the patch layout, V entries per 16 bytes.
+__host__ __device__ __forceinline__ int patch_pos(int i, int c, int V) {
+  const int L = (i / 4) * 4 + c / 8, p = (i % 4) * 8 + (c % 8);
+  return ((p / V) * kNB + L) * V + p % V;
+}
+
+// The 32 entries of this lane's patch of a stored tile, widened to T.
+template <typename T>
+__device__ __forceinline__ void load_row(const T* tile, int lane, T (&row)[kNB]) {
+  using VT = typename Vec16<T>::type;
+  constexpr int V = Vec16<T>::V;
+  const VT* tp = reinterpret_cast<const VT*>(tile);
+  VT v[kNB / V];
+#pragma unroll
+  for (int k = 0; k < kNB / V; ++k) v[k] = __ldg(tp + k * kNB + lane);
+#pragma unroll
+  for (int k = 0; k < kNB / V; ++k)
+#pragma unroll
+    for (int c = 0; c < V; ++c) row[k * V + c] = Vec16<T>::get(v[k], c);
+}
+
+__device__ __forceinline__ void load_row(const __half* tile, int lane, float (&row)[kNB]) {
+  const uint4* tp = reinterpret_cast<const uint4*>(tile);
+  uint4 v[kNB / 8];
+#pragma unroll
+  for (int k = 0; k < kNB / 8; ++k) v[k] = __ldg(tp + k * kNB + lane);
+#pragma unroll
+  for (int k = 0; k < kNB / 8; ++k) {
+    const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[j]));
+      row[k * 8 + 2 * j] = f.x;
+      row[k * 8 + 2 * j + 1] = f.y;
+    }
+  }
+}
 
 __device__ __forceinline__ void tile_of(int t, int& I, int& J) {
   int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -62,7 +110,7 @@ __global__ void k_gather_port_response(const PieceDesc* __restrict__ pieces, con
     if (I < J) continue;
     const int row = q % kNB, col = cc % kNB;
     const int64_t t = pd.s_off + (int64_t)I * (I + 1) / 2 + J;
-    S[t * kNB * kNB + ((col / V) * kNB + row) * V + col % V] =
+    S[t * kNB * kNB + patch_pos(row, col, V)] =
         xc[((size_t)pd.copy_off + port_local[pd.port_off + q]) * Rs + r];
   }
 }
@@ -80,12 +128,9 @@ __global__ void k_gather_ports(const PieceDesc* __restrict__ pieces, const int32
 
 // One sweep in port-response form, one CTA per subgraph, R right-hand sides.
 // Shared memory: s (n_pad_ports x R) and the accumulator y (same size).
-template <typename T, int R>
+template <typename T, typename TS, int R>
 __global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using VT = typename Vec16<T>::type;
-  constexpr int V = Vec16<T>::V;
-  constexpr int NL = kNB / V;  // 16-byte loads per lane per tile
   const PieceDesc pd = a.pieces[blockIdx.x];
   const int np = pd.nports;
   if (np == 0) return;
@@ -109,56 +154,74 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<
   __syncthreads();
 
   // y = S_j s over the stored lower block triangle: tile (I, J) adds T s_J to y_I and, off the
-  // diagonal, T^T s_I to y_J
+  // diagonal, T^T s_I to y_J.
+  const TS* Sb;
+  if constexpr (sizeof(TS) == 2) Sb = static_cast<const TS*>(a.Sh) + pd.s_off * kNB * kNB;
+  else Sb = reinterpret_cast<const TS*>(a.S) + pd.s_off * kNB * kNB;
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
-  const VT* Sb = reinterpret_cast<const VT*>(a.S + pd.s_off * kNB * kNB);
+  const int pa = lane >> 2, pb = lane & 3;  // patch: rows 4 pa .. +3, columns 8 pb .. +7
   for (int t = warp; t < ntiles; t += kSweepThreads / 32) {
     int I, J;
     tile_of(t, I, J);
-    const VT* tp = Sb + (int64_t)t * (kNB * kNB / V);
-    VT v[NL];
-#pragma unroll
-    for (int k = 0; k < NL; ++k) v[k] = __ldg(tp + k * kNB + lane);
-    const T* sJ = sv + (size_t)J * kNB * R;
-    const T* sI = sv + (size_t)I * kNB * R;
+    T pt[kNB];
+    load_row(Sb + (int64_t)t * kNB * kNB, lane, pt);
+    const T* sJ = sv + ((size_t)J * kNB + 8 * pb) * R;
+    const T* sI = sv + ((size_t)I * kNB + 4 * pa) * R;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      // row part: lane = row of the tile
-      T acc = T(0);
+      // row part: 4 partial row sums over this lane's 8 columns, reduce-scattered over the 4 lanes
+      // of the same row group (xor 2, 1): lane (pa, pb) ends with row 4 pa + pb
+      T rp[4];
 #pragma unroll
-      for (int k = 0; k < NL; ++k)
+      for (int ii = 0; ii < 4; ++ii) {
+        T acc = T(0);
 #pragma unroll
-        for (int c = 0; c < V; ++c) acc += Vec16<T>::get(v[k], c) * sJ[(k * V + c) * R + r];
-      atomicAdd(&yv[((size_t)I * kNB + lane) * R + r], acc);
+        for (int jj = 0; jj < 8; ++jj) acc += pt[ii * 8 + jj] * sJ[jj * R + r];
+        rp[ii] = acc;
+      }
+#pragma unroll
+      for (int h = 2; h >= 1; h >>= 1) {
+        const bool upper = (pb & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+          const T send = upper ? rp[i] : rp[i + h];
+          const T keep = upper ? rp[i + h] : rp[i];
+          rp[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+      }
+      atomicAdd(&yv[((size_t)I * kNB + 4 * pa + pb) * R + r], rp[0]);
       if (I != J) {
-        // column part: p[c] = T[lane][c] s_I[lane], summed over the lanes by a reduce-scatter
-        // (after it, lane c holds column c)
-        const T si = sI[lane * R + r];
-        T p[kNB];
+        // column part: 8 partial column sums over this lane's 4 rows, reduce-scattered over the 8
+        // lanes of the same column group (xor 16, 8, 4): lane (pa, pb) ends with column 8 pb + pa
+        T cp[8];
 #pragma unroll
-        for (int k = 0; k < NL; ++k)
+        for (int jj = 0; jj < 8; ++jj) {
+          T acc = T(0);
 #pragma unroll
-          for (int c = 0; c < V; ++c) p[k * V + c] = Vec16<T>::get(v[k], c) * si;
+          for (int ii = 0; ii < 4; ++ii) acc += pt[ii * 8 + jj] * sI[ii * R + r];
+          cp[jj] = acc;
+        }
 #pragma unroll
-        for (int h = kNB / 2; h >= 1; h >>= 1) {
-          const bool upper = (lane & h) != 0;
+        for (int h = 4; h >= 1; h >>= 1) {
+          const bool upper = (pa & h) != 0;
 #pragma unroll
           for (int i = 0; i < h; ++i) {
-            const T send = upper ? p[i] : p[i + h];
-            const T keep = upper ? p[i + h] : p[i];
-            p[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            const T send = upper ? cp[i] : cp[i + h];
+            const T keep = upper ? cp[i + h] : cp[i];
+            cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4 * h);
           }
         }
-        atomicAdd(&yv[((size_t)J * kNB + lane) * R + r], p[0]);
+        atomicAdd(&yv[((size_t)J * kNB + 8 * pb + pa) * R + r], cp[0]);
       }
     }
   }
   __syncthreads();
 
   // w_out[e] = 2 (u_base + y)_q - w_in[e]
+  const T ys = (sizeof(TS) == 2) ? (T)a.scale[blockIdx.x] : T(1);
   for (int i = tid; i < np * R; i += kSweepThreads) {
     const int q = i / R, r = i % R;
-    const T u = a.ubase[(size_t)(pd.port_off + q) * R + r] + yv[i];
+    const T u = a.ubase[(size_t)(pd.port_off + q) * R + r] + ys * yv[i];
     const int e0 = a.port_end_ptr[pd.port_off + q], e1 = a.port_end_ptr[pd.port_off + q + 1];
     for (int e = e0; e < e1; ++e) a.wnext[(size_t)e * R + r] = T(2) * u - a.wprev[(size_t)a.twin[e] * R + r];
   }
@@ -169,27 +232,80 @@ size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports) {
   return 2 * npad * R * elem;
 }
 
-template <typename T>
-cudaError_t port_sweep_configure(int R, size_t smem) {
+template <typename T, typename TS>
+static cudaError_t port_configure_ts(int R, size_t smem) {
+  const int b = (int)smem;
   switch (R) {
-    case 1: return cudaFuncSetAttribute(k_port_sweep<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    case 2: return cudaFuncSetAttribute(k_port_sweep<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    case 4: return cudaFuncSetAttribute(k_port_sweep<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    case 8: return cudaFuncSetAttribute(k_port_sweep<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    case 1: return cudaFuncSetAttribute(k_port_sweep<T, TS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 2: return cudaFuncSetAttribute(k_port_sweep<T, TS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 4: return cudaFuncSetAttribute(k_port_sweep<T, TS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 8: return cudaFuncSetAttribute(k_port_sweep<T, TS, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
-cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
-  if (npieces <= 0) return cudaSuccess;
+cudaError_t port_sweep_configure(int R, size_t smem) {
+  cudaError_t e = port_configure_ts<T, T>(R, smem);
+  if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = port_configure_ts<T, __half>(R, smem);
+  }
+  return e;
+}
+
+template <typename T, typename TS>
+static cudaError_t port_launch_ts(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
   switch (R) {
-    case 1: k_port_sweep<T, 1><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 2: k_port_sweep<T, 2><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 4: k_port_sweep<T, 4><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 8: k_port_sweep<T, 8><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 1: k_port_sweep<T, TS, 1><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 2: k_port_sweep<T, TS, 2><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 4: k_port_sweep<T, TS, 4><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 8: k_port_sweep<T, TS, 8><<<npieces, kSweepThreads, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (a.Sh) return port_launch_ts<T, __half>(a, R, npieces, smem, st);
+  }
+  return port_launch_ts<T, T>(a, R, npieces, smem, st);
+}
+
+// FP16 copy of the FP32 tiles of one subgraph per CTA: scale = largest |entry| (1 if all zero),
+// tiles re-laid out for 8 halves per 16-byte load.
+__global__ void k_port_to_half(const PieceDesc* __restrict__ pieces, const float* __restrict__ S,
+                               __half* __restrict__ Sh, float* __restrict__ scale) {
+  __shared__ float red[kSweepThreads / 32];
+  const PieceDesc pd = pieces[blockIdx.x];
+  const int64_t n = port_tiles(pd.nports) * kNB * kNB;
+  const float* src = S + pd.s_off * kNB * kNB;
+  __half* dst = Sh + pd.s_off * kNB * kNB;
+  float m = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(src[i]));
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  const float sc = m > 0.f ? m : 1.f;
+  if (threadIdx.x == 0) scale[blockIdx.x] = sc;
+  const float inv = 1.f / sc;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t t = i / (kNB * kNB);
+    const int k = (int)(i % (kNB * kNB));
+    const int L = (k / 4) % kNB, p = (k / 128) * 4 + (k % 4);   // float tile: ((p/4)*32 + L)*4 + p%4
+    dst[t * kNB * kNB + ((p / 8) * kNB + L) * 8 + (p % 8)] = __float2half_rn(src[i] * inv);
+  }
+}
+
+cudaError_t launch_port_to_half(const PieceDesc* pieces, int npieces, const float* S, __half* Sh, float* scale,
+                                cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
+  k_port_to_half<<<npieces, kSweepThreads, 0, st>>>(pieces, S, Sh, scale);
   return cudaGetLastError();
 }
 

@@ -134,6 +134,9 @@ struct vtm_solver {
   bool ubase_ok = false;
   size_t port_smem = 0;
   DevBuf tc_items;                   // (subgraph of the main launch, 128-port super-row)
+  DevBuf Sh, hscale;                 // FP16 copy of S_j and its per-subgraph scale
+  bool port_half = false;            // the port sweep reads the FP16 copy
+  bool port_half_auto = false;       // ... and returns to FP32 when a correction step stalls
   int n_items = 0;
   vtm_solver_info info{};
 
@@ -801,6 +804,8 @@ static void launch_port(vtm_solver* s) {
     }
   }
   PortArgs<T> a;
+  a.Sh = s->port_half ? s->Sh.p : nullptr;
+  a.scale = s->hscale.as<float>();
   a.pieces = s->pieces_lo.as<PieceDesc>();
   a.S = s->S.as<T>();
   a.ubase = s->ubase.as<T>();
@@ -897,6 +902,22 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   VTM_CUDA(cudaMemsetAsync(s->wzero.p, 0, s->wzero.bytes, s->stream));
   compute_port_response<T>(s, s_tiles * (tc ? 128 * 32 / (kNB * kNB) : 1));
   s->info.port_bytes = (int64_t)s_bytes;
+  s->info.port_storage_bits = 8 * (int)sizeof(T);
+  if constexpr (sizeof(T) == 4) {
+    // FP16_AUTO only where the sweep streams S_j from HBM: responses that stay in the 126 MB L2
+    // gain nothing from half the bytes and would pay the extra sweeps of FP16 rounding
+    const bool l2_resident = s_bytes <= 96.0 * (1 << 20);
+    if (!tc && (o->port_storage == VTM_STORE_FP16 || (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident))) {
+      s->Sh.alloc((size_t)s_tiles * kNB * kNB * sizeof(__half));
+      s->hscale.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
+      VTM_CUDA(launch_port_to_half(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(), s->Sh.as<__half>(),
+                                   s->hscale.as<float>(), s->stream));
+      s->port_half = true;
+      s->port_half_auto = (o->port_storage == VTM_STORE_FP16_AUTO);
+      s->info.port_bytes = (int64_t)(s_bytes / 2);
+      s->info.port_storage_bits = 16;
+    }
+  }
   // one port sweep, timed
   ensure_ubase(s);
   cudaEvent_t e0, e1;
@@ -1023,6 +1044,11 @@ void run_sweeps(vtm_solver* s, int k) {
   s->have_copies = true;
 }
 
+static void drop_graphs(vtm_solver* s) {
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
 void reset_waves(vtm_solver* s) {
   for (int b = 0; b < 2; ++b) VTM_CUDA(cudaMemsetAsync(s->w[b].p, 0, s->w[b].bytes, s->stream));
   s->cur = 0;
@@ -1103,6 +1129,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   if (o->wait_polls < 0) fail(VTM_ERR_INVALID, "wait_polls must be >= 0");
   if (o->sweep_variant < 0 || o->sweep_variant > 2) fail(VTM_ERR_INVALID, "sweep_variant must be 0, 1 or 2");
   if (o->sweep_form < 0 || o->sweep_form > 2) fail(VTM_ERR_INVALID, "sweep_form must be 0, 1 or 2");
+  if (o->port_storage < 0 || o->port_storage > 2) fail(VTM_ERR_INVALID, "port_storage must be 0, 1 or 2");
   if (o->wait_polls > 0) s->wait_limit = (long)o->wait_polls;
   if (cuda_stream) {
     s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -1230,6 +1257,15 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     last_inner = inner;
     last_inner_sweeps = inner_sweeps;
     // accept the trial only when it improves on the residual it started from
+    // FP16 port responses: a correction step that gains less than a factor 10, or an inner solve
+    // that has not gained anything after 4 check intervals, means the FP16 rounding is what limits
+    // the sweeps; go back to the FP32 responses for the rest of the solver's life
+    if (s->port_half && s->port_half_auto &&
+        ((inner > 0.1 && inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || (inner >= 1.0 && inner_sweeps >= 4 * m))) {
+      s->port_half = false;
+      s->info.port_storage_bits = 32;
+      drop_graphs(s);
+    }
     if (refine && inner < 1.0 && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);

@@ -57,7 +57,8 @@ class _Opts(C.Structure):
     _fields_ = [("z_mode", C.c_int32), ("z_uniform", C.c_double), ("z_lines", C.c_void_p), ("precision", C.c_int32),
                 ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double),
                 ("model", C.c_void_p), ("wait_polls", C.c_int64), ("withhold_slab", C.c_int32),
-                ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32)]
+                ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32),
+                ("port_storage", C.c_int32)]
 
 
 class SolverInfo(C.Structure):
@@ -68,7 +69,7 @@ class SolverInfo(C.Structure):
                 ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32),
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32), ("port_bytes", C.c_int64),
                 ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double),
-                ("nports", C.c_int64)]
+                ("nports", C.c_int64), ("port_storage_bits", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -310,8 +311,9 @@ class Solver:
     def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
                  check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0,
                  wait_polls: int = 0, withhold_slab: int = -1, sweep_variant: str = "auto",
-                 form: str = "auto"):
+                 form: str = "auto", port_storage: str = "native"):
         o = _Opts()
+        o.port_storage = {"native": 0, "fp16": 1, "fp16-auto": 2}[port_storage]
         o.sweep_variant = {"auto": 0, "single": 1, "pipelined": 2}[sweep_variant]
         o.sweep_form = {"auto": 0, "band": 1, "port": 2}[form]
         zarr = None

@@ -230,3 +230,57 @@ def test_port_form_skips_flagged_subgraphs(vtmlib):
     s.reset()
     s.iterate(5)
     assert np.isfinite(s.copies()).all() and np.isfinite(s.get_state()).all()
+
+
+# FP16 storage of S_j (FP32 solvers): each subgraph's S_j is divided by its largest entry and
+# rounded to half (unit roundoff 2^-11 = 4.9e-4 of that entry); products stay FP32.  After 7 sweeps
+# the copies and waves stay within 7 x 4.9e-4 ~ 3.4e-3 of the oracle: tolerance 5e-3 of the max
+# norm.  The solve with FP64 defect correction must still reach 1e-8.
+@pytest.mark.parametrize("nrhs", [1, 2])
+@pytest.mark.parametrize("dims,block", [((21, 19, 18), (8, 8, 8)), ((40, 33), (13, 11))])
+def test_port_fp16_sweeps_match_oracle(vtmlib, nrhs, dims, block):
+    A = inputs.grid_poisson(dims, sigma=0.8, seed=26)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=26)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    s = vtmlib.Solver(part, z=0.7, precision="fp32", nrhs=nrhs, form="port", port_storage="fp16")
+    assert s.info().port_storage_bits == 16
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(7)
+    copies, waves = _oracle_after(osplit, b, 0.7, 7)
+    assert _rel(s.copies(), copies) <= 5e-3
+    assert _rel(s.get_state(), waves[:, _line_map(part, osplit)]) <= 5e-3
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp16-auto"])
+def test_port_fp16_solve(vtmlib, storage):
+    dims, block = (33, 29, 17), (8, 8, 8)
+    A = inputs.grid_poisson(dims, sigma=1.0, seed=27)
+    b = inputs.rhs_uniform(A.n, 2, seed=27)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    s = vtmlib.Solver(part, z=1.0, precision="fp32", nrhs=2, form="port", port_storage=storage)
+    x = np.zeros_like(b)
+    st = s.solve(b, x, rtol=1e-8, maxit=20000)
+    As = A.to_scipy()
+    rel = np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)
+    assert np.all(rel <= 1e-8)
+    xs = ovtm.direct_solve(A, b)
+    assert np.max(np.abs(x - xs)) <= 1e-5 * np.max(np.abs(xs))
+
+
+def test_port_fp16_auto_on_high_contrast_fem(vtmlib):
+    """The 1e-3/1e3 FEM checkerboard converges slowly; FP16_AUTO must still reach 1e-8 (going back
+    to FP32 responses if a correction step stalls)."""
+    fem, part, osplit = _fem(vtmlib, 4000, 16, seed=6)
+    f = part.line_features()
+    d = np.exp(f[:, 1].astype(np.float64))
+    Z = 6.0 / (d[0::2] + d[1::2])
+    b = inputs.rhs_uniform(fem.A.n, 2, seed=6)
+    s = vtmlib.Solver(part, z=Z, precision="fp32", nrhs=2, form="port", port_storage="fp16-auto")
+    x = np.zeros_like(b)
+    s.solve(b, x, rtol=1e-8, maxit=100000)
+    As = fem.A.to_scipy()
+    rel = np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)
+    assert np.all(rel <= 1e-8)
+    assert s.info().port_storage_bits in (16, 32)
