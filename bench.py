@@ -390,8 +390,11 @@ def run_vtm(args):
         # pointers per port
         alg_bytes = (sinfo.port_bytes + 2 * sinfo.nends * R * elem + sinfo.nends * 8
                      + sinfo.nports * (R * elem + 4))
-        kname = "k_port_sweep<float,%d>" % R
-        ksrc = "port.cu"
+        if R >= 16:
+            kname, ksrc = "k_port_sweep_tc<%d>" % R, "port_tc.cu"
+        else:
+            kname = "k_port_sweep<float,%s,%d>" % ("__half" if sinfo.port_storage_bits == 16 else "float", R)
+            ksrc = "port.cu"
     else:
         sweep_ms = band_ms
         alg_bytes = band_bytes
