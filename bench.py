@@ -187,9 +187,9 @@ def kernel_traffic(kernel_src: str, workload: str, kname: str):
             d = json.load(f)
         with open(kernel_src, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
-        e = d.get(workload)
-        if e and e.get("kernel_sha") == h and e.get("kernel", kname) == kname:
-            return e["dram_bytes_per_launch"]
+        for e in d.get(workload, []):
+            if e.get("kernel_sha") == h and e.get("kernel") == kname:
+                return e["dram_bytes_per_launch"]
     except Exception:
         pass
     return None
@@ -393,7 +393,7 @@ def run_vtm(args):
         if R >= 16:
             kname, ksrc = "k_port_sweep_tc<%d>" % R, "port_tc.cu"
         else:
-            kname = "k_port_sweep<float,%s,%d>" % ("__half" if sinfo.port_storage_bits == 16 else "float", R)
+            kname = "k_port_sweep<float,%s,%d>" % ("__half" if bits_now == 16 else "float", R)
             ksrc = "port.cu"
     else:
         sweep_ms = band_ms
