@@ -48,29 +48,41 @@ __host__ __device__ __forceinline__ int patch_pos(int i, int c, int V) {
   return ((p / V) * kNB + L) * V + p % V;
 }
 
-// The 32 entries of this lane's patch of a stored tile, widened to T.
-template <typename T>
-__device__ __forceinline__ void load_row(const T* tile, int lane, T (&row)[kNB]) {
-  using VT = typename Vec16<T>::type;
-  constexpr int V = Vec16<T>::V;
-  const VT* tp = reinterpret_cast<const VT*>(tile);
-  VT v[kNB / V];
+// The raw 16-byte vectors of this lane's patch (kNB entries of type TS), loaded ahead of use.
+template <typename TS>
+struct RawPatch {
+  uint4 v[kNB * sizeof(TS) / 16];
+};
+
+template <typename TS>
+__device__ __forceinline__ void load_raw(const TS* tile, int lane, RawPatch<TS>& r) {
+  const uint4* tp = reinterpret_cast<const uint4*>(tile);
 #pragma unroll
-  for (int k = 0; k < kNB / V; ++k) v[k] = __ldg(tp + k * kNB + lane);
-#pragma unroll
-  for (int k = 0; k < kNB / V; ++k)
-#pragma unroll
-    for (int c = 0; c < V; ++c) row[k * V + c] = Vec16<T>::get(v[k], c);
+  for (int k = 0; k < (int)(kNB * sizeof(TS) / 16); ++k) r.v[k] = __ldg(tp + k * kNB + lane);
 }
 
-__device__ __forceinline__ void load_row(const __half* tile, int lane, float (&row)[kNB]) {
-  const uint4* tp = reinterpret_cast<const uint4*>(tile);
-  uint4 v[kNB / 8];
+__device__ __forceinline__ void widen(const RawPatch<float>& r, float (&row)[kNB]) {
 #pragma unroll
-  for (int k = 0; k < kNB / 8; ++k) v[k] = __ldg(tp + k * kNB + lane);
+  for (int k = 0; k < kNB / 4; ++k) {
+    row[4 * k] = __uint_as_float(r.v[k].x);
+    row[4 * k + 1] = __uint_as_float(r.v[k].y);
+    row[4 * k + 2] = __uint_as_float(r.v[k].z);
+    row[4 * k + 3] = __uint_as_float(r.v[k].w);
+  }
+}
+
+__device__ __forceinline__ void widen(const RawPatch<double>& r, double (&row)[kNB]) {
+#pragma unroll
+  for (int k = 0; k < kNB / 2; ++k) {
+    row[2 * k] = __hiloint2double((int)r.v[k].y, (int)r.v[k].x);
+    row[2 * k + 1] = __hiloint2double((int)r.v[k].w, (int)r.v[k].z);
+  }
+}
+
+__device__ __forceinline__ void widen(const RawPatch<__half>& r, float (&row)[kNB]) {
 #pragma unroll
   for (int k = 0; k < kNB / 8; ++k) {
-    const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+    const uint32_t w[4] = {r.v[k].x, r.v[k].y, r.v[k].z, r.v[k].w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[j]));
@@ -160,11 +172,17 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<
   else Sb = reinterpret_cast<const TS*>(a.S) + pd.s_off * kNB * kNB;
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int pa = lane >> 2, pb = lane & 3;  // patch: rows 4 pa .. +3, columns 8 pb .. +7
-  for (int t = warp; t < ntiles; t += kSweepThreads / 32) {
+  // each warp keeps the next tile's loads in flight while it works on the current one
+  constexpr int kWarps = kSweepThreads / 32;
+  RawPatch<TS> cur, nxt;
+  if (warp < ntiles) load_raw(Sb + (int64_t)warp * kNB * kNB, lane, cur);
+  for (int t = warp; t < ntiles; t += kWarps) {
+    if (t + kWarps < ntiles) load_raw(Sb + (int64_t)(t + kWarps) * kNB * kNB, lane, nxt);
     int I, J;
     tile_of(t, I, J);
     T pt[kNB];
-    load_row(Sb + (int64_t)t * kNB * kNB, lane, pt);
+    widen(cur, pt);
+    cur = nxt;
     const T* sJ = sv + ((size_t)J * kNB + 8 * pb) * R;
     const T* sI = sv + ((size_t)I * kNB + 4 * pa) * R;
 #pragma unroll
