@@ -152,16 +152,36 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<
   T* yv = sv + (size_t)npad * R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // s_q = sum_e w_in[e] / Z_e, w_in[e] = w_prev[twin[e]]
-  for (int i = tid; i < npad * R; i += kSweepThreads) {
-    const int q = i / R, r = i % R;
-    T acc = T(0);
-    if (q < np) {
-      const int e0 = a.port_end_ptr[pd.port_off + q], e1 = a.port_end_ptr[pd.port_off + q + 1];
-      for (int e = e0; e < e1; ++e) acc += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
+  // s_q = sum_e w_in[e] / Z_e, w_in[e] = w_prev[twin[e]]; kU entries per thread at a time, their
+  // end ranges, twins and waves loaded in three independent rounds
+  constexpr int kU = 4;
+  for (int i0 = tid; i0 < npad * R; i0 += kSweepThreads * kU) {
+    int e0[kU], e1[kU], tw[kU];
+    T iz[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = (i0 + u * kSweepThreads) / R;
+      e0[u] = e1[u] = 0;
+      if (q < np) {
+        e0[u] = a.port_end_ptr[pd.port_off + q];
+        e1[u] = a.port_end_ptr[pd.port_off + q + 1];
+      }
     }
-    sv[i] = acc;
-    yv[i] = T(0);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      tw[u] = (e1[u] > e0[u]) ? a.twin[e0[u]] : 0;
+      iz[u] = (e1[u] > e0[u]) ? a.invz[e0[u]] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * kSweepThreads;
+      if (i >= npad * R) break;
+      const int r = i % R;
+      T acc = (e1[u] > e0[u]) ? a.wprev[(size_t)tw[u] * R + r] * iz[u] : T(0);
+      for (int e = e0[u] + 1; e < e1[u]; ++e) acc += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
+      sv[i] = acc;
+      yv[i] = T(0);
+    }
   }
   __syncthreads();
 
@@ -237,11 +257,32 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<
 
   // w_out[e] = 2 (u_base + y)_q - w_in[e]
   const T ys = (sizeof(TS) == 2) ? (T)a.scale[blockIdx.x] : T(1);
-  for (int i = tid; i < np * R; i += kSweepThreads) {
-    const int q = i / R, r = i % R;
-    const T u = a.ubase[(size_t)(pd.port_off + q) * R + r] + ys * yv[i];
-    const int e0 = a.port_end_ptr[pd.port_off + q], e1 = a.port_end_ptr[pd.port_off + q + 1];
-    for (int e = e0; e < e1; ++e) a.wnext[(size_t)e * R + r] = T(2) * u - a.wprev[(size_t)a.twin[e] * R + r];
+  for (int i0 = tid; i0 < np * R; i0 += kSweepThreads * kU) {
+    int e0[kU], e1[kU], tw[kU];
+    T ub[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * kSweepThreads;
+      e0[u] = e1[u] = 0;
+      ub[u] = T(0);
+      if (i < np * R) {
+        const int q = i / R;
+        e0[u] = a.port_end_ptr[pd.port_off + q];
+        e1[u] = a.port_end_ptr[pd.port_off + q + 1];
+        ub[u] = a.ubase[(size_t)pd.port_off * R + i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) tw[u] = (e1[u] > e0[u]) ? a.twin[e0[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * kSweepThreads;
+      if (i >= np * R) break;
+      const int r = i % R;
+      const T uu = ub[u] + ys * yv[i];
+      a.wnext[(size_t)e0[u] * R + r] = T(2) * uu - a.wprev[(size_t)tw[u] * R + r];
+      for (int e = e0[u] + 1; e < e1[u]; ++e) a.wnext[(size_t)e * R + r] = T(2) * uu - a.wprev[(size_t)a.twin[e] * R + r];
+    }
   }
 }
 

@@ -883,6 +883,9 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   s->port_form = true;
   s->port_tc = tc;
   s->info.sweep_form = VTM_FORM_PORT;
+  // largest subgraphs first: the block scheduler starts CTAs in index order, so the smallest ones
+  // fill the tail of the launch (all launches over pieces_lo write through global indices only)
+  std::stable_sort(lo.begin(), lo.end(), [](const PieceDesc& x, const PieceDesc& y) { return x.nports > y.nports; });
   upload(s->pieces_lo, lo, s->stream);
   s->port_smem = smem;
   if (tc) {
