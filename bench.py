@@ -242,7 +242,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     info = None
     for _ in range(args.steps):
-        info = oracle_sweep_sample(args.workload, 2)
+        info = oracle_sweep_sample(args.workload, 10)
         vals.append(info["sec_per_piece_sweep"] * info["total_pieces"] * ksweeps * 1e3)
     dt = time.perf_counter() - t0
     v = statistics.median(vals)
