@@ -259,6 +259,8 @@ typedef struct vtm_solver_info {
   int64_t nports;              /* port copies (copies with at least one line end)             */
   int32_t port_storage_bits;   /* PORT: bits per stored S_j entry now (16, 32 or 64; FP16_AUTO
                                   turns 16 into 32 when it falls back)                         */
+  int32_t factor_tc;           /* 1: the FP32 factorisation ran its trailing updates on the
+                                  tensor cores (half-bandwidth 64 .. 384)                       */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

@@ -3,7 +3,7 @@
 //
 // K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T is assembled into the right-aligned band storage described
 // in device.cuh, then factored in place by a blocked right-looking band Cholesky (kNB columns per
-// step: factor the diagonal block in registers of one warp, solve the panel below it, update the
+// step: factor the diagonal block with one warp in shared memory, solve the panel below it, update the
 // trailing band).  Every diagonal block is finally replaced by the inverse of its triangular
 // factor so that the substitution needs no sequential triangular solves.
 #include "kernels.h"
@@ -74,31 +74,30 @@ __global__ void __launch_bounds__(256) k_factor(const PieceDesc* __restrict__ pi
     }
     __syncthreads();
     if (warp == 0) {
-      T row[kNB];
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) row[c] = D[lane * 33 + c];
+      // right-looking Cholesky of the block in shared memory, lane i owning row i: at step j lane j
+      // takes the pivot, the lanes below scale their entry of column j and update their row
       const T d0 = diag0 ? diag0[pd.row_off + k0 + lane] : D[lane * 33 + lane];
-#pragma unroll
       for (int j = 0; j < kNB; ++j) {
-        T djj = __shfl_sync(0xffffffffu, row[j], j);
-        const T dj0 = __shfl_sync(0xffffffffu, d0, j);
-        if (!(djj > T(0))) {
-          if (lane == 0) bad = 1;
-          djj = T(1);
-        } else if (djj < T(kFlagRatio) * dj0 && lane == 0 && bad == 0) {
-          bad = 2;
+        if (lane == j) {
+          T djj = D[j * 33 + j];
+          if (!(djj > T(0))) {
+            bad = 1;
+            djj = T(1);
+          } else if (djj < T(kFlagRatio) * d0 && bad == 0) {
+            bad = 2;
+          }
+          D[j * 33 + j] = sqrt(djj);
         }
-        const T d = sqrt(djj);
-        const T lj = (lane > j) ? row[j] / d : (lane == j ? d : row[j]);
-        row[j] = lj;
-#pragma unroll
-        for (int c = j + 1; c < kNB; ++c) {
-          const T lcj = __shfl_sync(0xffffffffu, lj, c);
-          if (lane >= c) row[c] -= lj * lcj;
+        __syncwarp();
+        if (lane > j) D[lane * 33 + j] /= D[j * 33 + j];
+        __syncwarp();
+        if (lane > j) {
+          const T lij = D[lane * 33 + j];
+          for (int c = j + 1; c <= lane; ++c) D[lane * 33 + c] -= lij * D[c * 33 + j];
         }
+        __syncwarp();
       }
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) D[lane * 33 + c] = (c <= lane) ? row[c] : T(0);
+      for (int c = lane + 1; c < kNB; ++c) D[lane * 33 + c] = T(0);
     }
     __syncthreads();
     // (b) panel: rows below the block within the band, L_IK = A_IK L_KK^{-T}

@@ -134,6 +134,10 @@ cudaError_t launch_transpose_band(const PieceDesc* pieces, int npieces, const T*
 // piece_flag[j] (may be NULL): 1 = non-positive pivot, 2 = pivot^2 < kFlagRatio K_ii (precision
 // lost); the global status gets kStatusNotSpd only when piece_flag is NULL.  diag0 (may be NULL):
 // per-row scratch (sum of n_pad entries) holding the original diagonal.
+// FP32 factorisation with the trailing update on the tensor cores (factor_tc.cu), 64 <= max_w <= 384.
+size_t factor_tc_smem_bytes(int max_w);
+cudaError_t launch_factor_tc(const PieceDesc* pieces, int npieces, int max_w, float* band, int* status,
+                             int* piece_flag, float* diag0, long wait_limit, cudaStream_t st);
 template <typename T>
 cudaError_t launch_factor(const PieceDesc* pieces, int npieces, int max_w, T* band, int* status, int* piece_flag,
                           T* diag0, cudaStream_t st);

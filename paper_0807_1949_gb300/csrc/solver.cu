@@ -214,8 +214,19 @@ static void factor_typed(vtm_solver* s) {
   VTM_CUDA(cudaEventCreate(&e0));
   VTM_CUDA(cudaEventCreate(&e1));
   VTM_CUDA(cudaEventRecord(e0, st));
-  cudaError_t fe = launch_factor<T>(s->pieces.as<PieceDesc>(), np, s->max_w, s->factor.as<T>(), s->status.as<int>(),
-                                    flagging ? flags.as<int>() : nullptr, flagging ? diag0.as<T>() : nullptr, st);
+  cudaError_t fe;
+  bool tc_factor = false;
+  if constexpr (sizeof(T) == 4) {
+    // wide bands: the trailing update is a sizeable dense product, run on the tensor cores
+    tc_factor = s->max_w >= 64 && s->max_w <= 384 && factor_tc_smem_bytes(s->max_w) <= 227 * 1024;
+    if (tc_factor)
+      fe = launch_factor_tc(s->pieces.as<PieceDesc>(), np, s->max_w, s->factor.as<float>(), s->status.as<int>(),
+                            flags.as<int>(), diag0.as<float>(), s->wait_limit, st);
+  }
+  if (!tc_factor)
+    fe = launch_factor<T>(s->pieces.as<PieceDesc>(), np, s->max_w, s->factor.as<T>(), s->status.as<int>(),
+                          flagging ? flags.as<int>() : nullptr, flagging ? diag0.as<T>() : nullptr, st);
+  s->info.factor_tc = tc_factor ? 1 : 0;
   VTM_CUDA(cudaEventRecord(e1, st));
   VTM_CUDA(cudaStreamSynchronize(st));
   float ms = 0;

@@ -69,7 +69,7 @@ class SolverInfo(C.Structure):
                 ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32),
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32), ("port_bytes", C.c_int64),
                 ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double),
-                ("nports", C.c_int64), ("port_storage_bits", C.c_int32)]
+                ("nports", C.c_int64), ("port_storage_bits", C.c_int32), ("factor_tc", C.c_int32)]
 
 
 class Stats(C.Structure):
