@@ -141,7 +141,7 @@ __global__ void k_gather_ports(const PieceDesc* __restrict__ pieces, const int32
 // One sweep in port-response form, one CTA per subgraph, R right-hand sides.
 // Shared memory: s (n_pad_ports x R) and the accumulator y (same size).
 template <typename T, typename TS, int R>
-__global__ void __launch_bounds__(kSweepThreads, 2) k_port_sweep(const PortArgs<T> a) {
+__global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port_sweep(const PortArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const PieceDesc pd = a.pieces[blockIdx.x];
   const int np = pd.nports;
