@@ -101,3 +101,33 @@ def test_operator_without_exchange_is_caught(monkeypatch):
 
     monkeypatch.setattr(theory.np, "block", fake_block)
     assert _fails(T.test_a38_operator_reproduces_iteration, 0)
+
+
+# ---------------------------------------------------------------- coupled lines (§7.2)
+import test_oracle_coupled as TC  # noqa: E402
+from oracle import coupled  # noqa: E402
+
+
+def _coupled_pins_fail():
+    return (_fails(TC.test_bundle_reflection_law) and _fails(TC.test_matched_bundle_is_exact_after_three_sweeps)
+            and _fails(TC.test_theorem_7_1_random_spd_bundles_converge, (20, 20), (7, 7), 1.0))
+
+
+def test_coupling_dropped_from_local_matrix_is_caught(monkeypatch):
+    """eq. 5.8 with only the diagonal of Y_j in K_j (the right-hand side still coupled)."""
+    orig = coupled.local_matrix
+    monkeypatch.setattr(coupled, "local_matrix", lambda A, loc, Yj: orig(A, loc, np.diag(np.diag(Yj))))
+    assert _coupled_pins_fail()
+
+
+def test_coupling_dropped_from_inflow_is_caught(monkeypatch):
+    """The incoming waves injected through the diagonal of Y_j only."""
+    orig = coupled.inflow
+    monkeypatch.setattr(coupled, "inflow", lambda u, om, Yj: orig(u, om, np.diag(np.diag(Yj))))
+    assert _coupled_pins_fail()
+
+
+def test_coupled_current_sign_is_caught(monkeypatch):
+    """The twin's current added instead of subtracted in the current update."""
+    monkeypatch.setattr(coupled, "current_update", lambda ut, omt, un, Yj: (ut - un) @ Yj + omt)
+    assert _coupled_pins_fail()
