@@ -158,6 +158,13 @@ int vtm_partition_get_piece(const vtm_partition* p, int32_t j, int64_t* n_j, int
                             double* val);
 /* Lines as (piece_a, local_a, piece_b, local_b) quadruples, host int64 array of 4*nlines. */
 int vtm_partition_get_lines(const vtm_partition* p, int64_t* quads);
+/* Candidate couplings for coupled lines (§7.2): every pair of lines t < t' of one bundle (both
+ * join the same two subgraphs) whose copies are neighbours in both subgraphs, ordered by t, then
+ * by the position of the neighbour in t's local row of its side-a subgraph.  pairs: host,
+ * 2 x count int64 (t, t'); weights: host, count doubles, |a_ik| of the original matrix for the
+ * vertices i, k of the two lines (the coupling rule y_p = gamma |a_ik| follows the local
+ * conductance).  Call with NULL arrays to read *count.  Host only. */
+int vtm_partition_line_pairs(const vtm_partition* p, int64_t* count, int64_t* pairs, double* weights);
 void vtm_partition_destroy(vtm_partition* p);
 
 /* ----------------------------------------------------------------------------------------------
@@ -216,6 +223,19 @@ typedef struct vtm_setup_opts {
                               when the responses exceed 96 MB (streamed from HBM rather than
                               held in L2) and returns to FP32 for good once a defect-correction
                               step gains less than a factor 10                                 */
+  /* Coupled lines (§7.2, Thm 7.1).  Lines that join the same two subgraphs form a bundle; a
+   * conductance y_p >= 0 between two lines t, t' of one bundle makes the bundle's admittance
+   * Y = Z^{-1} = diag(1/Z_t) + sum_p y_p (e_t - e_t')(e_t - e_t')^T, symmetric positive definite,
+   * so Thm 7.1 applies.  Eq. 5.8 becomes K_j = Ã_j + P_j Y_j P_j^T and r_j = b̃_j + P_j Y_j w_in;
+   * the wave update w_out = 2 u - w_in is unchanged.  The two copies that t and t' reach in each of
+   * the two subgraphs must be neighbours there (an off-diagonal entry of Ã_j), so K_j keeps the
+   * band of Ã_j; vtm_partition_line_pairs lists every such pair.  MATCHED impedances are computed
+   * for the uncoupled lines and the couplings added afterwards.  VTM_ERR_INVALID: a line id out of
+   * range, t == t', lines of different bundles, copies that are not neighbours, y < 0 or not
+   * finite, or NULL arrays with ncouplings > 0. */
+  int64_t ncouplings;          /* number of coupled pairs (0 = uncoupled lines)                  */
+  const int64_t* couplings;    /* host, 2 x ncouplings line ids (t, t') per pair                 */
+  const double* coupling_y;    /* host, ncouplings conductances y_p                              */
 } vtm_setup_opts;
 
 enum {
@@ -261,6 +281,7 @@ typedef struct vtm_solver_info {
                                   turns 16 into 32 when it falls back)                         */
   int32_t factor_tc;           /* 1: the FP32 factorisation ran its trailing updates on the
                                   tensor cores (half-bandwidth 64 .. 384)                       */
+  int64_t ncouplings;          /* coupled line pairs with y > 0 (0: uncoupled lines)           */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the
@@ -306,7 +327,8 @@ int vtm_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol
 /* Input impedance of every line end (Def. 7.1): with all sources zero, a unit inflow current at
  * the end's port and its own line open (every other line of the subgraph terminated by its
  * impedance), the port potential.  Computed on the device from the stored factors with unit
- * right-hand sides: g_c = (K_j^{-1})_{cc}, r_in(e) = g_c / (1 - g_c / Z_e).
+ * right-hand sides: g_c = (K_j^{-1})_{cc}, r_in(e) = g_c / (1 - g_c / Z_e).  Uncoupled lines
+ * only (VTM_ERR_INVALID on a solver with couplings).
  * r_in: host, nends doubles in end order (2t = side a, 2t+1 = side b of line t).  Resets waves. */
 int vtm_input_impedances(vtm_solver* s, double* r_in);
 /* The line impedances the solver was set up with (after matching or the learned model), host,

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -20,6 +21,7 @@ void solver_get_copies(vtm_solver* s, double* out);
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info);
 void solver_input_impedances(vtm_solver* s, double* r);
 void line_features(const vtm_partition* p, float* out);
+void line_pairs(const vtm_partition* p, std::vector<int64_t>& pairs, std::vector<double>& wts);
 void element_pieces(const vtm_partition_spec* sp, int32_t* out);
 void solver_get_impedances(const vtm_solver* s, double* z);
 void solver_get_piece_precision(const vtm_solver* s, int32_t* bits);
@@ -139,6 +141,19 @@ int vtm_partition_get_lines(const vtm_partition* p, int64_t* quads) {
       quads[4 * t + 2] = jb;
       quads[4 * t + 3] = b - p->piece_ptr[jb];
     }
+    return VTM_OK;
+  });
+}
+
+int vtm_partition_line_pairs(const vtm_partition* p, int64_t* count, int64_t* pairs, double* weights) {
+  return guarded([&] {
+    if (!p || !count) vtm::fail(VTM_ERR_INVALID, "null argument");
+    std::vector<int64_t> pr;
+    std::vector<double> w;
+    vtm::line_pairs(p, pr, w);
+    *count = (int64_t)w.size();
+    if (pairs) std::copy(pr.begin(), pr.end(), pairs);
+    if (weights) std::copy(w.begin(), w.end(), weights);
     return VTM_OK;
   });
 }

@@ -409,6 +409,63 @@ void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_parti
 
 namespace vtm {
 
+// Candidate couplings of §7.2 (vtm_partition_line_pairs): pairs t < u of lines joining the same
+// two subgraphs whose copies are neighbours on both sides, with |a_ik| of the original matrix.
+void line_pairs(const vtm_partition* p, std::vector<int64_t>& pairs, std::vector<double>& wts) {
+  pairs.clear();
+  wts.clear();
+  const int64_t nl = (int64_t)p->line_a.size();
+  const int64_t C = p->piece_ptr[p->npieces];
+  std::vector<int32_t> piece(C);
+  for (int32_t j = 0; j < p->npieces; ++j)
+    for (int64_t c = p->piece_ptr[j]; c < p->piece_ptr[j + 1]; ++c) piece[c] = j;
+  // lines at each copy
+  std::vector<int64_t> lptr(C + 1, 0), lid(2 * nl);
+  for (int64_t t = 0; t < nl; ++t) {
+    lptr[p->line_a[t] + 1]++;
+    lptr[p->line_b[t] + 1]++;
+  }
+  for (int64_t c = 0; c < C; ++c) lptr[c + 1] += lptr[c];
+  {
+    std::vector<int64_t> fill(lptr.begin(), lptr.end() - 1);
+    for (int64_t t = 0; t < nl; ++t) {
+      lid[fill[p->line_a[t]]++] = t;
+      lid[fill[p->line_b[t]]++] = t;
+    }
+  }
+  auto has_col = [&](int64_t c, int64_t lc) {
+    for (int64_t k = p->l_rowptr[c]; k < p->l_rowptr[c + 1]; ++k)
+      if (p->l_col[k] == lc) return true;
+    return false;
+  };
+  auto a_abs = [&](int64_t i, int64_t k) {
+    for (int64_t q = p->a_rowptr[i]; q < p->a_rowptr[i + 1]; ++q)
+      if (p->a_col[q] == k) return std::fabs(p->a_val[q]);
+    return 0.0;
+  };
+  for (int64_t t = 0; t < nl; ++t) {
+    const int64_t ca = p->line_a[t], cb = p->line_b[t];
+    const int32_t ja = piece[ca], jb = piece[cb];
+    for (int64_t k = p->l_rowptr[ca]; k < p->l_rowptr[ca + 1]; ++k) {
+      const int64_t cn = p->piece_ptr[ja] + p->l_col[k];
+      if (cn == ca) continue;
+      for (int64_t q = lptr[cn]; q < lptr[cn + 1]; ++q) {
+        const int64_t u = lid[q];
+        if (u <= t) continue;
+        const int64_t ua = p->line_a[u], ub = p->line_b[u];
+        int64_t other;  // u's copy in jb
+        if (piece[ua] == ja && piece[ub] == jb) other = ub;
+        else if (piece[ub] == ja && piece[ua] == jb) other = ua;
+        else continue;
+        if (!has_col(cb, other - p->piece_ptr[jb])) continue;
+        pairs.push_back(t);
+        pairs.push_back(u);
+        wts.push_back(a_abs(p->copy_vertex[ca], p->copy_vertex[cn]));
+      }
+    }
+  }
+}
+
 // Eight local features of every line end (see vtm_line_features in vtm.h), in API end order.
 void line_features(const vtm_partition* p, float* out) {
   const int64_t C = p->piece_ptr[p->npieces];

@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
       const int r = i % R;
       T acc = (e1[u] > e0[u]) ? a.wprev[(size_t)tw[u] * R + r] * iz[u] : T(0);
       for (int e = e0[u] + 1; e < e1[u]; ++e) acc += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
+      if (a.cq && i / R < np) acc += a.cq[(size_t)(pd.port_off + i / R) * R + r];
       sv[i] = acc;
       yv[i] = T(0);
     }

@@ -174,6 +174,11 @@ __global__ void __launch_bounds__(kTcThreads) k_port_vec_tc(const PortTCArgs a) 
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
     }
+    if (a.cq && p < np) {
+      const float* cqp = a.cq + (size_t)(pd.port_off + p) * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] += cqp[r];
+    }
     float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
     float* lo_c = hi_c + kVecBytes / 4;
 #pragma unroll

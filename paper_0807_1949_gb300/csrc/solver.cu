@@ -138,6 +138,9 @@ struct vtm_solver {
   bool port_half = false;            // the port sweep reads the FP16 copy
   bool port_half_auto = false;       // ... and returns to FP32 when a correction step stalls
   int n_items = 0;
+  // coupled lines (§7.2): per-port pair lists (couple.cu) and the coupling current of each sweep
+  bool coupled = false;
+  DevBuf cp_ptr, cp_own, cp_oth, cp_y, cq;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -337,6 +340,82 @@ static void plan_hi(vtm_solver* s) {
   if (!s->hi_stages) fail(VTM_ERR_INVALID, "a subgraph flagged for FP64 is too large for the FP64 sweep");
   if (s->wide) VTM_CUDA((sweep_wide_configure<double, float>(R, s->hi_smem)));
   else VTM_CUDA((sweep_configure<double, float>(R, s->hi_smem)));
+}
+
+// Coupled lines (§7.2): check every pair, add y (e_c - e_c')(e_c - e_c')^T to the local matrix values
+// of both subgraphs (K_j = Ã_j + P_j Y_j P_j^T then comes out of the usual assembly with the
+// diagonal 1/Z_t), and list per port the two incoming waves of each coupling for couple.cu.
+template <typename T>
+static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s,
+                         const std::vector<int32_t>& copy_piece, const std::vector<int32_t>& port_end_ptr,
+                         const std::vector<int32_t>& twin, std::vector<double>& lval) {
+  if (!o->couplings || !o->coupling_y) fail(VTM_ERR_INVALID, "couplings or coupling_y is NULL");
+  const int64_t nl = (int64_t)p->line_a.size();
+  std::vector<int32_t> eport(2 * nl, 0);
+  for (size_t q = 0; q + 1 < port_end_ptr.size(); ++q)
+    for (int32_t e = port_end_ptr[q]; e < port_end_ptr[q + 1]; ++e) eport[e] = (int32_t)q;
+  auto find = [&](int64_t c, int64_t lc) -> int64_t {
+    for (int64_t k = p->l_rowptr[c]; k < p->l_rowptr[c + 1]; ++k)
+      if (p->l_col[k] == lc) return k;
+    return -1;
+  };
+  struct Ent {
+    int32_t port, own, oth;
+    double y;
+  };
+  std::vector<Ent> ent;
+  int64_t used = 0;
+  for (int64_t k = 0; k < o->ncouplings; ++k) {
+    const int64_t t = o->couplings[2 * k], u = o->couplings[2 * k + 1];
+    const double y = o->coupling_y[k];
+    if (t < 0 || u < 0 || t >= nl || u >= nl) fail(VTM_ERR_INVALID, "coupled line id out of range");
+    if (t == u) fail(VTM_ERR_INVALID, "a line cannot be coupled with itself");
+    if (!(y >= 0) || !std::isfinite(y)) fail(VTM_ERR_INVALID, "coupling conductances must be >= 0 and finite");
+    const int32_t ja = copy_piece[p->line_a[t]], jb = copy_piece[p->line_b[t]];
+    const int32_t ka = copy_piece[p->line_a[u]], kb = copy_piece[p->line_b[u]];
+    if (!((ja == ka && jb == kb) || (ja == kb && jb == ka)))
+      fail(VTM_ERR_INVALID, "coupled lines must join the same two subgraphs");
+    if (y == 0) continue;
+    ++used;
+    for (int side = 0; side < 2; ++side) {
+      const int32_t j = side ? jb : ja;
+      const int64_t ct = side ? p->line_b[t] : p->line_a[t];
+      const int us = copy_piece[p->line_a[u]] == j ? 0 : 1;
+      const int64_t cu = us ? p->line_b[u] : p->line_a[u];
+      if (ct == cu) fail(VTM_ERR_INVALID, "coupled lines end at the same copy");
+      const int64_t lt = ct - p->piece_ptr[j], lu = cu - p->piece_ptr[j];
+      const int64_t k1 = find(ct, lu), k2 = find(cu, lt), d1 = find(ct, lt), d2 = find(cu, lu);
+      if (k1 < 0 || k2 < 0 || d1 < 0 || d2 < 0)
+        fail(VTM_ERR_INVALID, "coupled lines must join neighbouring copies in both subgraphs");
+      lval[d1] += y;
+      lval[d2] += y;
+      lval[k1] -= y;
+      lval[k2] -= y;
+      const int32_t it = s->api_to_int[2 * t + side], iu = s->api_to_int[2 * u + us];
+      ent.push_back({eport[it], twin[it], twin[iu], y});
+      ent.push_back({eport[iu], twin[iu], twin[it], y});
+    }
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y2) { return x.port < y2.port; });
+  const int nports = (int)port_end_ptr.size() - 1;
+  std::vector<int32_t> ptr(nports + 1, 0), own(ent.size()), oth(ent.size());
+  std::vector<T> yv(ent.size());
+  for (size_t k = 0; k < ent.size(); ++k) {
+    ptr[ent[k].port + 1]++;
+    own[k] = ent[k].own;
+    oth[k] = ent[k].oth;
+    yv[k] = (T)ent[k].y;
+  }
+  for (int q = 0; q < nports; ++q) ptr[q + 1] += ptr[q];
+  s->info.ncouplings = used;
+  if (used == 0) return;
+  s->coupled = true;
+  upload(s->cp_ptr, ptr, s->stream);
+  upload(s->cp_own, own, s->stream);
+  upload(s->cp_oth, oth, s->stream);
+  upload(s->cp_y, yv, s->stream);
+  s->cq.alloc((size_t)std::max(1, nports) * s->R * sizeof(T));
+  VTM_CUDA(cudaMemsetAsync(s->cq.p, 0, s->cq.bytes, s->stream));
 }
 
 template <typename T>
@@ -544,7 +623,14 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   upload(s->d_copy_piece, copy_piece, st);
   upload(s->d_lrowptr, p->l_rowptr, st);
   upload(s->d_lcol, p->l_col, st);
-  upload(s->d_lval, p->l_val, st);
+  if (o->ncouplings > 0) {
+    std::vector<double> lval = p->l_val;
+    couple_setup<T>(p, o, s, copy_piece, port_end_ptr, twin, lval);
+    upload(s->d_lval, lval, st);
+  } else {
+    if (o->ncouplings < 0) fail(VTM_ERR_INVALID, "ncouplings must be >= 0");
+    upload(s->d_lval, p->l_val, st);
+  }
   upload(s->d_port_of_copy, port_of_copy, st);
   s->factor.alloc((size_t)foff * sizeof(T));
   if (!s->wide) s->factor_u.alloc((size_t)foff * sizeof(T));
@@ -619,6 +705,7 @@ static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
   a.withhold = s->withhold;
   a.cap = hi ? s->hi_cap : s->cap;
   a.yspill = (hi && s->wide) ? s->hi_yspill.as<TF>() : nullptr;
+  a.cq = s->coupled ? s->cq.as<TV>() : nullptr;
   return a;
 }
 
@@ -630,10 +717,20 @@ static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t
   s->launches++;
 }
 
+// Coupling current of every port from the waves of the previous sweep (couple.cu).
+template <typename T>
+static void launch_coupling(vtm_solver* s) {
+  if (!s->coupled) return;
+  VTM_CUDA(launch_couple<T>(s->nports, s->R, s->cp_ptr.as<int32_t>(), s->cp_own.as<int32_t>(),
+                            s->cp_oth.as<int32_t>(), s->cp_y.as<T>(), s->w[s->cur].as<T>(), s->cq.as<T>(), s->stream));
+  s->launches++;
+}
+
 template <typename T>
 static void sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i < k; ++i) {
     const int wx = i == k - 1;
+    launch_coupling<T>(s);
     if (s->np_lo > 0) launch_one<T, T>(s, sweep_args<T, T>(s, wx, false), s->np_lo, s->sweep_smem, s->pipe);
     if constexpr (sizeof(T) == 4) {
       if (s->np_hi > 0)
@@ -735,6 +832,7 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
         a.stages = st_lo;
         a.withhold = -1;
         a.yspill = nullptr;
+        a.cq = nullptr;  // unit sources, zero waves: no coupling current
         VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
       }
       VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
@@ -778,6 +876,7 @@ static void ubase_typed(vtm_solver* s) {
     SweepArgs<T, T> a = sweep_args<T, T>(s, 1, false);
     a.wprev = s->wzero.as<T>();
     a.wnext = s->wscr.as<T>();
+    a.cq = nullptr;  // zero waves: no coupling current
     launch_one<T, T>(s, a, s->np_lo, s->sweep_smem, s->pipe);
   }
   VTM_CUDA(launch_gather_ports<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(), s->R,
@@ -806,6 +905,7 @@ static void launch_port(vtm_solver* s) {
       t.port_end_ptr = s->port_end_ptr.as<int32_t>();
       t.twin = s->twin.as<int32_t>();
       t.invz = s->invz_t.as<float>();
+      t.cq = s->coupled ? s->cq.as<float>() : nullptr;
       t.status = s->status.as<int>();
       t.wait_limit = s->wait_limit;
       t.items = s->tc_items.as<int2>();
@@ -825,6 +925,7 @@ static void launch_port(vtm_solver* s) {
   a.port_end_ptr = s->port_end_ptr.as<int32_t>();
   a.twin = s->twin.as<int32_t>();
   a.invz = s->invz_t.as<T>();
+  a.cq = s->coupled ? s->cq.as<T>() : nullptr;
   VTM_CUDA(launch_port_sweep<T>(a, s->R, s->np_lo, s->port_smem, s->stream));
   s->launches++;
 }
@@ -834,6 +935,7 @@ static void launch_port(vtm_solver* s) {
 template <typename T>
 static void port_sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i + 1 < k; ++i) {
+    launch_coupling<T>(s);
     if (s->np_lo > 0) launch_port<T>(s);
     if constexpr (sizeof(T) == 4) {
       if (s->np_hi > 0)
@@ -845,9 +947,9 @@ static void port_sweeps_typed(vtm_solver* s, int k) {
 }
 
 static int64_t launches_per_batch(const vtm_solver* s, int k) {
-  const int64_t band = (s->np_lo > 0) + (s->np_hi > 0);
+  const int64_t band = (s->np_lo > 0) + (s->np_hi > 0) + (s->coupled ? 1 : 0);
   if (!s->port_form || k < 2) return (int64_t)k * band;
-  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0);
+  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0) + (s->coupled ? 1 : 0);
   return (int64_t)(k - 1) * port + band;
 }
 
@@ -994,6 +1096,7 @@ static void input_impedances_typed(vtm_solver* s, std::vector<double>& r_api) {
 
 void solver_input_impedances(vtm_solver* s, double* r) {
   if (!r) fail(VTM_ERR_INVALID, "null output");
+  if (s->coupled) fail(VTM_ERR_INVALID, "input impedances (Def. 7.1) are defined here for uncoupled lines only");
   std::vector<double> v;
   if (s->precision == VTM_FP32) input_impedances_typed<float>(s, v);
   else input_impedances_typed<double>(s, v);
@@ -1112,6 +1215,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
     t.withhold_slab = 0;
     t.sweep_variant = 0;
     t.sweep_form = VTM_FORM_BAND;
+    t.ncouplings = 0;  // matching is done on the uncoupled lines; the couplings are added after
     std::unique_ptr<vtm_solver> tmp;
     for (int r : {8, 4, 2, 1}) {
       t.nrhs = r;

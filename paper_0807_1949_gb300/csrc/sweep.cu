@@ -79,6 +79,11 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T, T
         acc[rr] += w * iz;
       }
     }
+    if (a.cq) {
+      const TV* cqp = a.cq + (size_t)(pd.port_off + q) * R;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] += (T)cqp[rr];
+    }
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) ys[(size_t)(off + l) * R + rr] += acc[rr];
   }
@@ -301,6 +306,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_pipe(const SweepArgs
         win[(e - pd.end_off) * R + rr] = w;
         acc[rr] += w * iz;
       }
+    }
+    if (a.cq) {
+      const TV* cqp = a.cq + (size_t)(pd.port_off + q) * R;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] += (T)cqp[rr];
     }
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) ys[(size_t)(off + l) * R + rr] += acc[rr];

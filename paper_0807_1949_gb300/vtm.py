@@ -58,7 +58,8 @@ class _Opts(C.Structure):
                 ("nrhs", C.c_int32), ("check_every", C.c_int32), ("inner_reduction", C.c_double),
                 ("model", C.c_void_p), ("wait_polls", C.c_int64), ("withhold_slab", C.c_int32),
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32),
-                ("port_storage", C.c_int32)]
+                ("port_storage", C.c_int32), ("ncouplings", C.c_int64), ("couplings", C.c_void_p),
+                ("coupling_y", C.c_void_p)]
 
 
 class SolverInfo(C.Structure):
@@ -69,7 +70,8 @@ class SolverInfo(C.Structure):
                 ("sweep_ctas_per_sm", C.c_int32), ("sweep_ms", C.c_double), ("flagged_pieces", C.c_int32),
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32), ("port_bytes", C.c_int64),
                 ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double),
-                ("nports", C.c_int64), ("port_storage_bits", C.c_int32), ("factor_tc", C.c_int32)]
+                ("nports", C.c_int64), ("port_storage_bits", C.c_int32), ("factor_tc", C.c_int32),
+                ("ncouplings", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -93,6 +95,7 @@ def _load():
         "vtm_rcb": (C.c_int, [vp, i64, i32, i32, vp]),
         "vtm_partition_get_piece": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "vtm_partition_get_lines": (C.c_int, [vp, vp]),
+        "vtm_partition_line_pairs": (C.c_int, [vp, vp, vp, vp]),
         "vtm_partition_destroy": (None, [vp]),
         "vtm_setup": (C.c_int, [vp, vp, vp, vp]),
         "vtm_solver_get_info": (C.c_int, [vp, vp]),
@@ -185,6 +188,16 @@ class Partition:
         q = np.empty((self.info().nlines, 4), np.int64)
         _check(_lib.vtm_partition_get_lines(self._h, _ptr(q)))
         return q
+
+    def line_pairs(self) -> tuple[np.ndarray, np.ndarray]:
+        """Candidate couplings of §7.2 (vtm_partition_line_pairs): (count, 2) int64 line pairs of
+        one bundle whose copies are neighbours in both subgraphs, and |a_ik| of each pair."""
+        cnt = C.c_int64()
+        _check(_lib.vtm_partition_line_pairs(self._h, C.byref(cnt), None, None))
+        pr = np.empty((cnt.value, 2), np.int64)
+        w = np.empty(cnt.value, np.float64)
+        _check(_lib.vtm_partition_line_pairs(self._h, C.byref(cnt), _ptr(pr), _ptr(w)))
+        return pr, w
 
     def line_features(self) -> np.ndarray:
         """(nends, 8) float32 features of every line end (vtm_line_features)."""
@@ -305,14 +318,28 @@ class Solver:
     sweep_variant: "auto" or "single" (one CTA works each block step in turn; the setup-time
     autotuner picks the staging depth) or "pipelined" (warp 0 finishes block k while the other
     warps prepare block k+1; nrhs <= 2; opt-in only, it measured slower everywhere).
+    coupling: coupled lines of §7.2.  None (uncoupled), a number gamma (every candidate pair of
+    Partition.line_pairs() gets the conductance gamma |a_ik|), or (pairs (m, 2), y (m,)).
     Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
     """
 
     def __init__(self, part: Partition, z=1.0, precision: str = "fp64", nrhs: int = 1, stream=None,
                  check_every: int = 10, inner_reduction: float = 0.0, z_init: float = 1.0,
                  wait_polls: int = 0, withhold_slab: int = -1, sweep_variant: str = "auto",
-                 form: str = "auto", port_storage: str = "native"):
+                 form: str = "auto", port_storage: str = "native", coupling=None):
         o = _Opts()
+        ckeep = None
+        if coupling is not None:
+            if np.ndim(coupling) == 0:
+                pairs, w = part.line_pairs()
+                y = float(coupling) * w
+            else:
+                pairs, y = coupling
+            pairs, y = _arr(pairs, np.int64).reshape(-1, 2), _arr(y, np.float64).reshape(-1)
+            if len(pairs) != len(y):
+                raise ValueError("coupling: one conductance per pair")
+            o.ncouplings, o.couplings, o.coupling_y = len(y), pairs.ctypes.data, y.ctypes.data
+            ckeep = (pairs, y)
         o.port_storage = {"native": 0, "fp16": 1, "fp16-auto": 2}[port_storage]
         o.sweep_variant = {"auto": 0, "single": 1, "pipelined": 2}[sweep_variant]
         o.sweep_form = {"auto": 0, "band": 1, "port": 2}[form]
@@ -339,7 +366,7 @@ class Solver:
         h = C.c_void_p()
         _check(_lib.vtm_setup(part.handle, C.byref(o), _stream_handle(stream), C.byref(h)))
         self._h = h
-        self._zkeep = zarr
+        self._zkeep = (zarr, ckeep)
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

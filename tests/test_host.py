@@ -186,3 +186,23 @@ def test_committed_models_are_well_formed():
         assert p.shape == (4801,) and np.all(np.isfinite(p))
         ms = d["median_sweeps"]
         assert ms["learned"] < ms["z1"] and ms["learned"] < ms["matched"]
+
+
+@pytest.mark.parametrize("dims,block,sigma", [((32, 32), (16, 16), 0.0), ((12, 11), (4, 5), 1.0),
+                                               ((9, 8, 7), (4, 4, 3), 0.7)])
+def test_line_pairs_match_oracle(vtmlib, dims, block, sigma):
+    """Candidate couplings of §7.2: the same set of line pairs, with |a_ik|, as the oracle."""
+    from oracle import coupled
+
+    A = inputs.grid_poisson(dims, sigma=sigma, seed=4)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    pr, w = part.line_pairs()
+    opr, ow = coupled.adjacent_line_pairs(evs.split_grid(A, dims, block), A)
+    assert len(pr) == len(opr) > 0
+    # line ids may be numbered differently; a line is identified by its two copies
+    q, oq = part.lines(), evs.split_grid(A, dims, block).vtl
+    got = {frozenset((tuple(q[t]), tuple(q[u]))): x for (t, u), x in zip(pr, w)}
+    ref = {frozenset((tuple(int(v) for v in oq[t]), tuple(int(v) for v in oq[u]))): x for (t, u), x in zip(opr, ow)}
+    assert got.keys() == ref.keys()
+    assert all(got[k] == ref[k] for k in ref)
+    assert np.all(pr[:, 0] < pr[:, 1])
