@@ -16,6 +16,8 @@ impedance of every line is the training target of both its ends.
 Families:
   poisson2d-256  2D 5-point, 256 x 256, sigma ~ U[0.5, 2] per seed, blocks of 32 (64 subgraphs)
   poisson3d      3D 7-point, 64^3 / 96^3 / 128^3, sigma ~ U[0.75, 1.25], blocks of 16
+  poisson3d-wide 3D 7-point, 64^3 / 96^3, sigma ~ U[0.75, 1.75], blocks of 16 (covers the sigma = 1.5
+                 of the 256^3 multi-RHS run)
   fem2d          P1 FEM on Delaunay triangulations of 50k-200k points, checkerboard 1e-3/1e3 on 8x8,
                  RCB into ~500-copy subgraphs (the local shape of the 1M-point, 2000-subgraph run)
 
@@ -53,6 +55,11 @@ def problem(family: str, seed: int):
         m = int(rng.choice([64, 96, 128]))
         dims, block = (m, m, m), (16, 16, 16)
         seed += 1000   # keep the benchmark's 128^3 / seed 0 problem out of every training set
+    elif family == "poisson3d-wide":
+        sigma = float(rng.uniform(0.75, 1.75))
+        m = int(rng.choice([64, 96]))
+        dims, block = (m, m, m), (16, 16, 16)
+        seed += 2000
     elif family == "poisson3d-128":
         sigma = 1.0
         dims, block = (128, 128, 128), (16, 16, 16)
