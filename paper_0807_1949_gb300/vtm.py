@@ -330,7 +330,7 @@ class Solver:
         o = _Opts()
         ckeep = None
         if coupling is not None:
-            if np.ndim(coupling) == 0:
+            if isinstance(coupling, (int, float, np.integer, np.floating)):
                 pairs, w = part.line_pairs()
                 y = float(coupling) * w
             else:
