@@ -69,6 +69,9 @@ def parse():
                    help="port form, nrhs <= 8: storage of the port responses")
     p.add_argument("--z", default=None, help="impedance rule overriding the workload's (a number, "
                    "learned:<family> or scaled:<c>)")
+    p.add_argument("--coupling", default=None,
+                   help="coupled lines (§7.2): 'none', 'model' (the rule stored with the learned model) or a "
+                        "conductance factor gamma (y_p = gamma |a_ik|); default: the workload's")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -313,6 +316,29 @@ def impedance_arg(z, vtm, part):
     return z, z
 
 
+def coupling_arg(rule, z, zarg, zdesc, vtm, part):
+    """(impedance argument, coupling argument, description) for a coupled-line rule: None / "none",
+    "model" (the learned model's stored rule: Z = z_scale Z_model, y_p = gamma |a_ik|) or a number
+    gamma (conductance factor on the workload's own impedances)."""
+    if rule is None or rule == "none":
+        return zarg, None, None
+    if rule == "model":
+        if not (isinstance(z, str) and z.startswith("learned:")):
+            raise SystemExit("--coupling model needs a learned impedance model")
+        import json
+
+        from paper_0807_1949_gb300 import learned_z
+
+        with open(os.path.join(learned_z.MODELS, "z_" + z.split(":", 1)[1] + ".json")) as f:
+            c = json.load(f).get("coupling")
+        if c is None:
+            raise SystemExit("the model file has no coupling rule (learned_z --couple)")
+        zl = vtm.Solver(part, z=zarg, precision="fp32", form="band").impedances()
+        return c["z_scale"] * zl, float(c["gamma"]), {"rule": "model", "z_scale": c["z_scale"], "gamma": c["gamma"]}
+    g = float(rule)
+    return zarg, g, {"rule": "gamma", "gamma": g}
+
+
 def run_vtm(args):
     import numpy as np
     import torch
@@ -325,9 +351,12 @@ def run_vtm(args):
     A, part, b, t_part = build_problem(w, vtm, inputs)
     R = w["nrhs"]
     stream = torch.cuda.Stream()
-    zarg, zdesc = impedance_arg(args.z if args.z is not None else w["z"], vtm, part)
-    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every, form=args.form, port_storage=args.port_storage,
-                        z_init=w.get("z_init", 1.0))
+    zrule = args.z if args.z is not None else w["z"]
+    zarg, zdesc = impedance_arg(zrule, vtm, part)
+    zarg, carg, cdesc = coupling_arg(args.coupling if args.coupling is not None else w.get("coupling"),
+                                     zrule, zarg, zdesc, vtm, part)
+    solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every,
+                        form=args.form, port_storage=args.port_storage, z_init=w.get("z_init", 1.0), coupling=carg)
     sinfo = solver.info()
     bd = torch.tensor(b, device="cuda")
     xd = torch.zeros_like(bd)
@@ -387,6 +416,8 @@ def run_vtm(args):
     vec_passes = 4 if R >= 16 else 1   # wide kernel: b̃ read, y written and read back, x written
     band_bytes = (2 * sinfo.band_entries * elem + vec_passes * sinfo.ncopies * R * elem
                   + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
+    if sinfo.ncouplings:
+        band_bytes += 4 * sinfo.ncouplings * (12 + 2 * R * elem) + sinfo.nports * 4
     if port:
         nsw = 41
         sweep_ms = (timed(nsw, 3) - band_ms) / (nsw - 1)
@@ -394,6 +425,9 @@ def run_vtm(args):
         # pointers per port
         alg_bytes = (sinfo.port_bytes + 2 * sinfo.nends * R * elem + sinfo.nends * 8
                      + sinfo.nports * (R * elem + 4))
+        if sinfo.ncouplings:
+            # per coupling 4 list entries (two ports on each side): indices, y and two waves each
+            alg_bytes += 4 * sinfo.ncouplings * (12 + 2 * R * elem) + sinfo.nports * 4
         if R >= 16:
             kname, ksrc = "k_port_sweep_tc<%d>" % R, "port_tc.cu"
         else:
@@ -455,7 +489,10 @@ def run_vtm(args):
         if cpu.get("value") is not None and R > 1:
             cpu["value"] = round(cpu["value"] * R, 3)
             cpu["sample"] += f"; times {R} right-hand sides"
-    cfg = {"workload": args.workload, "nrhs": R, "rtol": w["rtol"], "z": zdesc, "pieces": sinfo.npieces,
+    if cdesc is not None:
+        cdesc["pairs"] = int(sinfo.ncouplings)
+    cfg = {"workload": args.workload, "nrhs": R, "rtol": w["rtol"], "z": zdesc, "coupling": cdesc,
+           "pieces": sinfo.npieces,
            "parallelism": "replicas" if ws > 1 else "single",
            "l2": "inputs larger than L2 (FP32 factor %.2f GB)" % (sinfo.factor_bytes / 1e9),
            "sweeps": sweeps, "restarts": stats[-1].restarts, "final_rel_residual": rel,

@@ -37,8 +37,7 @@ struct SweepArgs {
   int cap;                     // wide kernel: window rows (power of two >= max Wp - 1 + kNB)
   TF* yspill;                  // wide kernel: forward result y in factor precision, n_pad x R per
                                // piece at row_off (nullptr: y goes through xc, TF == TV)
-  const TV* cq;                // coupled lines: per port, the coupling current (ports x R) added
-                               // to the port row of r_j (nullptr: uncoupled)
+  CoupleRef<TV> cpl;           // coupled lines: per-port coupling lists (cpl.ptr == nullptr: none)
 };
 
 size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
@@ -77,7 +76,7 @@ struct PortArgs {
   const int32_t* port_end_ptr;
   const int32_t* twin;
   const T* invz;
-  const T* cq;                 // coupled lines: per port coupling current, ports x R (or nullptr)
+  CoupleRef<T> cpl;            // coupled lines (cpl.ptr == nullptr: none)
 };
 
 __host__ __device__ int64_t port_tiles(int nports);
@@ -107,7 +106,7 @@ struct PortTCArgs {
   const int32_t* port_end_ptr;
   const int32_t* twin;
   const float* invz;
-  const float* cq;             // coupled lines: per port coupling current, ports x R (or nullptr)
+  CoupleRef<float> cpl;        // coupled lines (cpl.ptr == nullptr: none)
   int* status;
   long wait_limit;
   const int2* items;           // (subgraph, 128-port super-row) per CTA of the product kernel
@@ -121,13 +120,6 @@ cudaError_t port_tc_configure(int R);
 cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, int nitems, cudaStream_t st);
 cudaError_t launch_gather_port_response_tc(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs,
                                            int b, const float* xc, float* S, cudaStream_t st);
-
-// Coupled lines (§7.2): for every port q, cq[q R + r] = sum_k y_k (w[own_k] - w[oth_k]) over
-// k in cp_ptr[q] .. cp_ptr[q+1], where own_k / oth_k index the waves (ends x R) that arrive at
-// the two coupled ends of this subgraph (the twins of those ends).
-template <typename T>
-cudaError_t launch_couple(int nports, int R, const int32_t* cp_ptr, const int32_t* own, const int32_t* oth,
-                          const T* y, const T* w, T* cq, cudaStream_t st);
 
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
       const int r = i % R;
       T acc = (e1[u] > e0[u]) ? a.wprev[(size_t)tw[u] * R + r] * iz[u] : T(0);
       for (int e = e0[u] + 1; e < e1[u]; ++e) acc += a.wprev[(size_t)a.twin[e] * R + r] * a.invz[e];
-      if (a.cq && i / R < np) acc += a.cq[(size_t)(pd.port_off + i / R) * R + r];
+      if (a.cpl.ptr && i / R < np) acc += coupling_current<T, T>(a.cpl, pd.port_off + i / R, r, R, a.wprev);
       sv[i] = acc;
       yv[i] = T(0);
     }

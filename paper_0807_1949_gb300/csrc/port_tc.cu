@@ -174,11 +174,14 @@ __global__ void __launch_bounds__(kTcThreads) k_port_vec_tc(const PortTCArgs a) 
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
     }
-    if (a.cq && p < np) {
-      const float* cqp = a.cq + (size_t)(pd.port_off + p) * R;
+    if (a.cpl.ptr && p < np)
+      for (int k = a.cpl.ptr[pd.port_off + p]; k < a.cpl.ptr[pd.port_off + p + 1]; ++k) {
+        const float yk = a.cpl.y[k];
+        const float* wo = a.wprev + (size_t)a.cpl.own[k] * R;
+        const float* wt = a.wprev + (size_t)a.cpl.oth[k] * R;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] += cqp[r];
-    }
+        for (int r = 0; r < R; ++r) v[r] += yk * (wo[r] - wt[r]);
+      }
     float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
     float* lo_c = hi_c + kVecBytes / 4;
 #pragma unroll

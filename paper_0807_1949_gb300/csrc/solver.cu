@@ -138,9 +138,9 @@ struct vtm_solver {
   bool port_half = false;            // the port sweep reads the FP16 copy
   bool port_half_auto = false;       // ... and returns to FP32 when a correction step stalls
   int n_items = 0;
-  // coupled lines (§7.2): per-port pair lists (couple.cu) and the coupling current of each sweep
+  // coupled lines (§7.2): per-port coupling lists, read by the sweep kernels' port loops
   bool coupled = false;
-  DevBuf cp_ptr, cp_own, cp_oth, cp_y, cq;
+  DevBuf cp_ptr, cp_own, cp_oth, cp_y;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -344,7 +344,7 @@ static void plan_hi(vtm_solver* s) {
 
 // Coupled lines (§7.2): check every pair, add y (e_c - e_c')(e_c - e_c')^T to the local matrix values
 // of both subgraphs (K_j = Ã_j + P_j Y_j P_j^T then comes out of the usual assembly with the
-// diagonal 1/Z_t), and list per port the two incoming waves of each coupling for couple.cu.
+// diagonal 1/Z_t), and list per port the two incoming waves of each coupling (CoupleRef).
 template <typename T>
 static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s,
                          const std::vector<int32_t>& copy_piece, const std::vector<int32_t>& port_end_ptr,
@@ -414,8 +414,6 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
   upload(s->cp_own, own, s->stream);
   upload(s->cp_oth, oth, s->stream);
   upload(s->cp_y, yv, s->stream);
-  s->cq.alloc((size_t)std::max(1, nports) * s->R * sizeof(T));
-  VTM_CUDA(cudaMemsetAsync(s->cq.p, 0, s->cq.bytes, s->stream));
 }
 
 template <typename T>
@@ -681,6 +679,18 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->info.max_halfband = max_w;
 }
 
+template <typename TV>
+static CoupleRef<TV> couple_ref(vtm_solver* s) {
+  CoupleRef<TV> c{};
+  if (s->coupled) {
+    c.ptr = s->cp_ptr.as<int32_t>();
+    c.own = s->cp_own.as<int32_t>();
+    c.oth = s->cp_oth.as<int32_t>();
+    c.y = s->cp_y.as<TV>();
+  }
+  return c;
+}
+
 template <typename TF, typename TV>
 static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
   SweepArgs<TF, TV> a;
@@ -705,7 +715,7 @@ static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
   a.withhold = s->withhold;
   a.cap = hi ? s->hi_cap : s->cap;
   a.yspill = (hi && s->wide) ? s->hi_yspill.as<TF>() : nullptr;
-  a.cq = s->coupled ? s->cq.as<TV>() : nullptr;
+  a.cpl = couple_ref<TV>(s);
   return a;
 }
 
@@ -717,20 +727,10 @@ static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t
   s->launches++;
 }
 
-// Coupling current of every port from the waves of the previous sweep (couple.cu).
-template <typename T>
-static void launch_coupling(vtm_solver* s) {
-  if (!s->coupled) return;
-  VTM_CUDA(launch_couple<T>(s->nports, s->R, s->cp_ptr.as<int32_t>(), s->cp_own.as<int32_t>(),
-                            s->cp_oth.as<int32_t>(), s->cp_y.as<T>(), s->w[s->cur].as<T>(), s->cq.as<T>(), s->stream));
-  s->launches++;
-}
-
 template <typename T>
 static void sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i < k; ++i) {
     const int wx = i == k - 1;
-    launch_coupling<T>(s);
     if (s->np_lo > 0) launch_one<T, T>(s, sweep_args<T, T>(s, wx, false), s->np_lo, s->sweep_smem, s->pipe);
     if constexpr (sizeof(T) == 4) {
       if (s->np_hi > 0)
@@ -832,7 +832,7 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
         a.stages = st_lo;
         a.withhold = -1;
         a.yspill = nullptr;
-        a.cq = nullptr;  // unit sources, zero waves: no coupling current
+        a.cpl.ptr = nullptr;  // unit sources, zero waves: no coupling current
         VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
       }
       VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
@@ -876,7 +876,7 @@ static void ubase_typed(vtm_solver* s) {
     SweepArgs<T, T> a = sweep_args<T, T>(s, 1, false);
     a.wprev = s->wzero.as<T>();
     a.wnext = s->wscr.as<T>();
-    a.cq = nullptr;  // zero waves: no coupling current
+    a.cpl.ptr = nullptr;  // zero waves: no coupling current
     launch_one<T, T>(s, a, s->np_lo, s->sweep_smem, s->pipe);
   }
   VTM_CUDA(launch_gather_ports<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(), s->R,
@@ -905,7 +905,7 @@ static void launch_port(vtm_solver* s) {
       t.port_end_ptr = s->port_end_ptr.as<int32_t>();
       t.twin = s->twin.as<int32_t>();
       t.invz = s->invz_t.as<float>();
-      t.cq = s->coupled ? s->cq.as<float>() : nullptr;
+      t.cpl = couple_ref<float>(s);
       t.status = s->status.as<int>();
       t.wait_limit = s->wait_limit;
       t.items = s->tc_items.as<int2>();
@@ -925,7 +925,7 @@ static void launch_port(vtm_solver* s) {
   a.port_end_ptr = s->port_end_ptr.as<int32_t>();
   a.twin = s->twin.as<int32_t>();
   a.invz = s->invz_t.as<T>();
-  a.cq = s->coupled ? s->cq.as<T>() : nullptr;
+  a.cpl = couple_ref<T>(s);
   VTM_CUDA(launch_port_sweep<T>(a, s->R, s->np_lo, s->port_smem, s->stream));
   s->launches++;
 }
@@ -935,7 +935,6 @@ static void launch_port(vtm_solver* s) {
 template <typename T>
 static void port_sweeps_typed(vtm_solver* s, int k) {
   for (int i = 0; i + 1 < k; ++i) {
-    launch_coupling<T>(s);
     if (s->np_lo > 0) launch_port<T>(s);
     if constexpr (sizeof(T) == 4) {
       if (s->np_hi > 0)
@@ -947,9 +946,9 @@ static void port_sweeps_typed(vtm_solver* s, int k) {
 }
 
 static int64_t launches_per_batch(const vtm_solver* s, int k) {
-  const int64_t band = (s->np_lo > 0) + (s->np_hi > 0) + (s->coupled ? 1 : 0);
+  const int64_t band = (s->np_lo > 0) + (s->np_hi > 0);
   if (!s->port_form || k < 2) return (int64_t)k * band;
-  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0) + (s->coupled ? 1 : 0);
+  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0);
   return (int64_t)(k - 1) * port + band;
 }
 

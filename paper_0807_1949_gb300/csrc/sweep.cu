@@ -79,11 +79,9 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep(const SweepArgs<T, T
         acc[rr] += w * iz;
       }
     }
-    if (a.cq) {
-      const TV* cqp = a.cq + (size_t)(pd.port_off + q) * R;
+    if (a.cpl.ptr)
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) acc[rr] += (T)cqp[rr];
-    }
+      for (int rr = 0; rr < R; ++rr) acc[rr] += coupling_current<T, TV>(a.cpl, pd.port_off + q, rr, R, a.wprev);
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) ys[(size_t)(off + l) * R + rr] += acc[rr];
   }
@@ -307,11 +305,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_pipe(const SweepArgs
         acc[rr] += w * iz;
       }
     }
-    if (a.cq) {
-      const TV* cqp = a.cq + (size_t)(pd.port_off + q) * R;
+    if (a.cpl.ptr)
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) acc[rr] += (T)cqp[rr];
-    }
+      for (int rr = 0; rr < R; ++rr) acc[rr] += coupling_current<T, TV>(a.cpl, pd.port_off + q, rr, R, a.wprev);
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) ys[(size_t)(off + l) * R + rr] += acc[rr];
   }

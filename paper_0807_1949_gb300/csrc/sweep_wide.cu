@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
           T acc = T(0);
           for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
             acc += (T)a.wprev[(size_t)a.twin[e] * R + c] * (T)a.invz[e];
-          if (a.cq) acc += (T)a.cq[(size_t)(pd.port_off + q) * R + c];
+          if (a.cpl.ptr) acc += coupling_current<T, TV>(a.cpl, pd.port_off + q, c, R, a.wprev);
           Yw[(size_t)(l & kMask) * R + c] += acc;
         }
         __syncthreads();

@@ -104,8 +104,8 @@ class Evaluator:
         r = st.rel_residual
         return r if math.isfinite(r) else 1e30
 
-    def to_tolerance(self, z, rtol=1e-8, maxit=40000):
-        s = vtm.Solver(self.part, z=z, precision=self.precision, check_every=10)
+    def to_tolerance(self, z, rtol=1e-8, maxit=40000, coupling=None):
+        s = vtm.Solver(self.part, z=z, precision=self.precision, check_every=10, coupling=coupling)
         st = s.solve(self.b, self.x, rtol=rtol, maxit=maxit, raise_on_fail=False)
         return dict(sweeps=st.sweeps, solve_ms=st.solve_ms, converged=st.status == 0, rel=st.rel_residual)
 
@@ -222,6 +222,48 @@ def evaluate(model: vtm.MLP, family: str, seeds, rtol=1e-8, matched=True, verbos
     return rows
 
 
+def model_impedances(ev: Evaluator, model: vtm.MLP) -> np.ndarray:
+    """Per-line impedances the model gives on an evaluator's partition."""
+    return vtm.Solver(ev.part, z=model, precision=ev.precision, form="band").impedances()
+
+
+def select_coupling(model: vtm.MLP, family: str, seeds, scales, gammas, rtol=1e-8, verbose=True):
+    """Coupled lines (§7.2) on top of the learned impedances: every candidate pair of lines gets the
+    conductance gamma |a_ik| and every line the impedance scale * Z_model (a larger Z damps the
+    smooth interface modes, the coupling keeps the rough ones fast).  Returns the (scale, gamma)
+    with the smallest geometric mean of sweeps to rtol over ``seeds``, and the table."""
+    table = {}
+    for sd in seeds:
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        z = model_impedances(ev, model)
+        for c in scales:
+            for g in gammas:
+                r = ev.to_tolerance(c * z, rtol, coupling=g if g > 0 else None)
+                table.setdefault((c, g), []).append(r["sweeps"] if r["converged"] else 40000)
+        if verbose:
+            print(f"coupling scan seed {sd} sigma {sigma:.2f}: " +
+                  " ".join(f"{c}/{g}:{table[(c, g)][-1]}" for c in scales for g in gammas), flush=True)
+    gm = {k: float(np.exp(np.mean(np.log(v)))) for k, v in table.items()}
+    best = min(gm, key=gm.get)
+    return best, {f"{c}/{g}": v for (c, g), v in gm.items()}
+
+
+def evaluate_coupled(model: vtm.MLP, family: str, seeds, scale: float, gamma: float, rtol=1e-8, verbose=True):
+    rows = []
+    for sd in seeds:
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        z = model_impedances(ev, model)
+        row = dict(seed=sd, sigma=sigma, dims=dims if isinstance(dims, tuple) else "fem",
+                   learned=ev.to_tolerance(z, rtol), coupled=ev.to_tolerance(scale * z, rtol, coupling=gamma))
+        rows.append(row)
+        if verbose:
+            print(f"eval seed {sd}: learned {row['learned']['sweeps']} ({row['learned']['solve_ms']:.1f} ms)  "
+                  f"coupled {row['coupled']['sweeps']} ({row['coupled']['solve_ms']:.1f} ms)", flush=True)
+    return rows
+
+
 def save(model: vtm.MLP, path: str, **meta):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
@@ -245,7 +287,29 @@ def main():
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", default=None)
     ap.add_argument("--no-matched", action="store_true")
+    ap.add_argument("--couple", action="store_true",
+                    help="keep the trained model; select the coupled-line rule (Z scale, gamma) on seeds "
+                         "200000.. and evaluate it on the held-out seeds; stored in the model file")
+    ap.add_argument("--couple-scales", default="2,3,4,5,6")
+    ap.add_argument("--couple-gammas", default="0.5,0.75,1,1.5")
     a = ap.parse_args()
+    if a.couple:
+        path = a.out or os.path.join(MODELS, f"z_{a.family}.json")
+        with open(path) as f:
+            meta = json.load(f)
+        model = load(path)
+        (c, g), scan = select_coupling(model, a.family, range(200_000, 200_000 + 6),
+                                       tuple(float(v) for v in a.couple_scales.split(",")),
+                                       tuple(float(v) for v in a.couple_gammas.split(",")))
+        print(f"selected scale {c} gamma {g}", flush=True)
+        rows = evaluate_coupled(model, a.family, range(100_000, 100_000 + a.test), c, g)
+        med = {k: float(np.median([r[k]["sweeps"] for r in rows])) for k in ("learned", "coupled")}
+        print("median sweeps to 1e-8 on held-out seeds:", med, flush=True)
+        meta["coupling"] = dict(z_scale=c, gamma=g, select_seeds=6, scan_geomean_sweeps=scan, eval=rows,
+                                median_sweeps=med, rule="y_p = gamma |a_ik| on every candidate pair; Z = z_scale Z_model")
+        with open(path, "w") as f:
+            json.dump(meta, f)
+        return
     t0 = time.time()
     X, y, meta = build_dataset(a.family, range(a.train), a.sweeps)
     t_search = time.time() - t0
