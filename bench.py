@@ -4,15 +4,19 @@
 Workload (default "poisson3d-128"): 3D 7-point variable-coefficient Poisson operator on a 128^3
 vertex grid (2,097,152 unknowns), node coefficients log-normal (sigma = 1, seed 0), Dirichlet
 boundary; Electric Vertex Splitting into 8x8x8 = 512 cubic subgraphs (cut planes every 16
-nodes, shared); uniform line impedance Z = 1; b i.i.d. uniform[-1, 1].  The product path uses
-FP32 band factors and FP32 sweeps inside FP64 defect correction (residual b - A x in FP64 on the
-device).  The plain method (FP64 factors and sweeps, no correction) is timed beside it.
+nodes, shared); line impedances from the learned model (models/z_poisson3d.json) with coupled
+lines (§7.2): every line scaled by the model's z_scale and every candidate pair of lines of a
+bundle joined by the conductance gamma |a_ik| (rule selected on held-out seeds, stored with the
+model); b i.i.d. uniform[-1, 1].  The product path uses FP32 factors and FP32 sweeps inside FP64
+defect correction (residual b - A x in FP64 on the device), in port-response form.  The plain
+method (FP64 factors and band sweeps, Z = 1, no coupling, no correction) is timed beside it.
 
 One step = one vtm_solve from zero waves to max relative residual <= 1e-8 (every sweep gathers
-the twins' waves, builds the port right-hand side, runs the forward and back substitution over
-all subgraphs and emits the outgoing waves; the FP64 residual is checked every 10 sweeps).
-The factorisation (vtm_setup) happens once, before the timed region, and is reported as
-setup_ms.  The factor (2.7 GB FP32) is far larger than L2, so no flush is needed between steps.
+the twins' waves, forms the port right-hand sides including the coupling currents, updates the
+ports through the stored responses S_j (the last sweep of each batch through the band factors)
+and emits the outgoing waves; the FP64 residual is checked every 20 sweeps).  vtm_setup
+(factorisation, port responses) happens once, before the timed region, and is reported as
+setup_ms.  The port responses (2 GB FP32) are far larger than L2, so no flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vtm|reference] [--workload W]
 """
@@ -33,10 +37,10 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # the benchmarked configuration: 3D 128^3, sigma = 1, 512 subgraphs, one right-hand side
     "poisson3d-128": dict(kind="grid", dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0, nrhs=1,
-                          z="learned:poisson3d", rtol=1e-8),
+                          z="learned:poisson3d", coupling="model", rtol=1e-8),
     # large multi-RHS run: 256^3, sigma = 1.5, 4096 subgraphs, 32 right-hand sides per sweep
     "poisson3d-256-r32": dict(kind="grid", dims=(256, 256, 256), block=(16, 16, 16), sigma=1.5, nrhs=32,
-                              z="learned:poisson3d-wide", rtol=1e-8),
+                              z="learned:poisson3d-wide", coupling="model", rtol=1e-8),
     # uneven batching: P1 FEM on the Delaunay triangulation of 1M points, 2000 RCB subgraphs, 16 RHS.
     # The one-level method does not reach 1e-8 here in any practical number of sweeps (contrast 1e6),
     # so a step is a fixed number of sweeps and the line reports the residual it reaches.
@@ -44,7 +48,7 @@ WORKLOADS = {
                          rtol=1e-8, sweeps=1000),
     # learned-impedance family: 2D 256^2, 64 subgraphs
     "poisson2d-256": dict(kind="grid", dims=(256, 256), block=(32, 32), sigma=1.25, nrhs=1,
-                          z="learned:poisson2d-256", rtol=1e-8),
+                          z="learned:poisson2d-256", coupling="model", rtol=1e-8),
     "laplace2d-32": dict(kind="grid", dims=(32, 32), block=(16, 16), sigma=0.0, nrhs=1, z=1.0, rtol=1e-8),
     # small case of the 3D subgraph shape (64 subgraphs, 0.37 GB factor > L2) for ncu captures
     "poisson3d-64": dict(kind="grid", dims=(64, 64, 64), block=(16, 16, 16), sigma=1.0, nrhs=1, z=1.0, rtol=1e-8),
@@ -417,7 +421,7 @@ def run_vtm(args):
     band_bytes = (2 * sinfo.band_entries * elem + vec_passes * sinfo.ncopies * R * elem
                   + 2 * sinfo.nends * R * elem + sinfo.nends * 8)
     if sinfo.ncouplings:
-        band_bytes += 4 * sinfo.ncouplings * (12 + 2 * R * elem) + sinfo.nports * 4
+        band_bytes += 4 * sinfo.ncouplings * (8 + R * elem) + sinfo.nports * 4
     if port:
         nsw = 41
         sweep_ms = (timed(nsw, 3) - band_ms) / (nsw - 1)
@@ -426,8 +430,8 @@ def run_vtm(args):
         alg_bytes = (sinfo.port_bytes + 2 * sinfo.nends * R * elem + sinfo.nends * 8
                      + sinfo.nports * (R * elem + 4))
         if sinfo.ncouplings:
-            # per coupling 4 list entries (two ports on each side): indices, y and two waves each
-            alg_bytes += 4 * sinfo.ncouplings * (12 + 2 * R * elem) + sinfo.nports * 4
+            # per coupling 4 list entries (two ports on each side): wave index, -y and one gathered wave
+            alg_bytes += 4 * sinfo.ncouplings * (8 + R * elem) + sinfo.nports * 4
         if R >= 16:
             kname, ksrc = "k_port_sweep_tc<%d>" % R, "port_tc.cu"
         else:

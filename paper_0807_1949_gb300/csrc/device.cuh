@@ -106,14 +106,15 @@ __device__ __forceinline__ T warp_sum_g8(T v) {
   return v;
 }
 
-// Coupled lines (§7.2): the bundle admittance Y = diag(1/Z_t) + sum_p y_p (e_t - e_t')(e_t - e_t')^T
-// adds, at the port of end e of line t, sum over the pairs (t, t') of y (w_in[e] - w_in[e']), e' the
-// end of t' at the same subgraph.  Stored per port (CSR over all ports): for entry k, own[k] and
-// oth[k] index the two incoming waves (the twins of e and e'), y[k] the conductance.
+// Coupled lines (§7.2): the bundle admittance Y = diag(1/Z_t) + sum_p y_p (e_t - e_t')(e_t - e_t')^T.
+// Its diagonal (1/Z_t + sum of the line's y_p) is the per-end 1/Z array that every sweep kernel
+// already applies to the end's own incoming wave; the off-diagonal part adds, at the port of end e
+// of line t, -y_p w_in[e'] for every pair (t, t'), e' the end of t' at the same subgraph.  Stored
+// per port (CSR over all ports): for entry k, oth[k] indexes the incoming wave w_in[e'] (the twin
+// of e') and y[k] = -y_p.
 template <typename TV>
 struct CoupleRef {
   const int32_t* ptr;  // nports_total + 1 entry offsets; nullptr: uncoupled lines
-  const int32_t* own;
   const int32_t* oth;
   const TV* y;
 };
@@ -121,8 +122,7 @@ struct CoupleRef {
 template <typename T, typename TV>
 __device__ __forceinline__ T coupling_current(const CoupleRef<TV>& c, int port, int r, int R, const TV* w) {
   T acc = T(0);
-  for (int k = c.ptr[port]; k < c.ptr[port + 1]; ++k)
-    acc += (T)c.y[k] * ((T)w[(size_t)c.own[k] * R + r] - (T)w[(size_t)c.oth[k] * R + r]);
+  for (int k = c.ptr[port]; k < c.ptr[port + 1]; ++k) acc += (T)c.y[k] * (T)w[(size_t)c.oth[k] * R + r];
   return acc;
 }
 

@@ -177,10 +177,15 @@ __global__ void __launch_bounds__(kTcThreads) k_port_vec_tc(const PortTCArgs a) 
     if (a.cpl.ptr && p < np)
       for (int k = a.cpl.ptr[pd.port_off + p]; k < a.cpl.ptr[pd.port_off + p + 1]; ++k) {
         const float yk = a.cpl.y[k];
-        const float* wo = a.wprev + (size_t)a.cpl.own[k] * R;
-        const float* wt = a.wprev + (size_t)a.cpl.oth[k] * R;
+        const float4* wt = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] += yk * (wo[r] - wt[r]);
+        for (int kk = 0; kk < R / 4; ++kk) {
+          const float4 x = wt[kk];
+          v[4 * kk] += yk * x.x;
+          v[4 * kk + 1] += yk * x.y;
+          v[4 * kk + 2] += yk * x.z;
+          v[4 * kk + 3] += yk * x.w;
+        }
       }
     float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
     float* lo_c = hi_c + kVecBytes / 4;

@@ -140,7 +140,8 @@ struct vtm_solver {
   int n_items = 0;
   // coupled lines (§7.2): per-port coupling lists, read by the sweep kernels' port loops
   bool coupled = false;
-  DevBuf cp_ptr, cp_own, cp_oth, cp_y;
+  DevBuf cp_ptr, cp_oth, cp_y;
+  std::vector<double> ydiag;         // per line: sum of its coupling conductances (diagonal of Y)
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -194,7 +195,10 @@ static void factor_typed(vtm_solver* s) {
   cudaStream_t st = s->stream;
   const int np = s->npieces;
   std::vector<double> invz(s->E);
-  for (int64_t k = 0; k < s->E; ++k) invz[k] = 1.0 / s->Z[s->end_api[k] >> 1];
+  for (int64_t k = 0; k < s->E; ++k) {
+    const int32_t t = s->end_api[k] >> 1;
+    invz[k] = 1.0 / s->Z[t] + (s->ydiag.empty() ? 0.0 : s->ydiag[t]);  // diagonal of Y (§7.2)
+  }
   upload(s->d_invz64, invz, st);
   {
     std::vector<T> iz(invz.begin(), invz.end());
@@ -342,9 +346,10 @@ static void plan_hi(vtm_solver* s) {
   else VTM_CUDA((sweep_configure<double, float>(R, s->hi_smem)));
 }
 
-// Coupled lines (§7.2): check every pair, add y (e_c - e_c')(e_c - e_c')^T to the local matrix values
-// of both subgraphs (K_j = Ã_j + P_j Y_j P_j^T then comes out of the usual assembly with the
-// diagonal 1/Z_t), and list per port the two incoming waves of each coupling (CoupleRef).
+// Coupled lines (§7.2): check every pair; the diagonal of Y (1/Z_t + the line's conductances) goes
+// into the per-end 1/Z array (ydiag), the off-diagonal -y into the local matrix values of both
+// subgraphs, so that K_j = Ã_j + P_j Y_j P_j^T comes out of the usual assembly; list per port the
+// incoming wave and the off-diagonal admittance of each coupling (CoupleRef).
 template <typename T>
 static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s,
                          const std::vector<int32_t>& copy_piece, const std::vector<int32_t>& port_end_ptr,
@@ -360,9 +365,10 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
     return -1;
   };
   struct Ent {
-    int32_t port, own, oth;
+    int32_t port, oth;
     double y;
   };
+  s->ydiag.assign(nl, 0.0);
   std::vector<Ent> ent;
   int64_t used = 0;
   for (int64_t k = 0; k < o->ncouplings; ++k) {
@@ -377,6 +383,8 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
       fail(VTM_ERR_INVALID, "coupled lines must join the same two subgraphs");
     if (y == 0) continue;
     ++used;
+    s->ydiag[t] += y;
+    s->ydiag[u] += y;
     for (int side = 0; side < 2; ++side) {
       const int32_t j = side ? jb : ja;
       const int64_t ct = side ? p->line_b[t] : p->line_a[t];
@@ -384,34 +392,32 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
       const int64_t cu = us ? p->line_b[u] : p->line_a[u];
       if (ct == cu) fail(VTM_ERR_INVALID, "coupled lines end at the same copy");
       const int64_t lt = ct - p->piece_ptr[j], lu = cu - p->piece_ptr[j];
-      const int64_t k1 = find(ct, lu), k2 = find(cu, lt), d1 = find(ct, lt), d2 = find(cu, lu);
-      if (k1 < 0 || k2 < 0 || d1 < 0 || d2 < 0)
-        fail(VTM_ERR_INVALID, "coupled lines must join neighbouring copies in both subgraphs");
-      lval[d1] += y;
-      lval[d2] += y;
+      const int64_t k1 = find(ct, lu), k2 = find(cu, lt);
+      if (k1 < 0 || k2 < 0) fail(VTM_ERR_INVALID, "coupled lines must join neighbouring copies in both subgraphs");
       lval[k1] -= y;
       lval[k2] -= y;
       const int32_t it = s->api_to_int[2 * t + side], iu = s->api_to_int[2 * u + us];
-      ent.push_back({eport[it], twin[it], twin[iu], y});
-      ent.push_back({eport[iu], twin[iu], twin[it], y});
+      ent.push_back({eport[it], twin[iu], -y});
+      ent.push_back({eport[iu], twin[it], -y});
     }
   }
   std::stable_sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y2) { return x.port < y2.port; });
   const int nports = (int)port_end_ptr.size() - 1;
-  std::vector<int32_t> ptr(nports + 1, 0), own(ent.size()), oth(ent.size());
+  std::vector<int32_t> ptr(nports + 1, 0), oth(ent.size());
   std::vector<T> yv(ent.size());
   for (size_t k = 0; k < ent.size(); ++k) {
     ptr[ent[k].port + 1]++;
-    own[k] = ent[k].own;
     oth[k] = ent[k].oth;
     yv[k] = (T)ent[k].y;
   }
   for (int q = 0; q < nports; ++q) ptr[q + 1] += ptr[q];
   s->info.ncouplings = used;
-  if (used == 0) return;
+  if (used == 0) {
+    s->ydiag.clear();
+    return;
+  }
   s->coupled = true;
   upload(s->cp_ptr, ptr, s->stream);
-  upload(s->cp_own, own, s->stream);
   upload(s->cp_oth, oth, s->stream);
   upload(s->cp_y, yv, s->stream);
 }
@@ -684,7 +690,6 @@ static CoupleRef<TV> couple_ref(vtm_solver* s) {
   CoupleRef<TV> c{};
   if (s->coupled) {
     c.ptr = s->cp_ptr.as<int32_t>();
-    c.own = s->cp_own.as<int32_t>();
     c.oth = s->cp_oth.as<int32_t>();
     c.y = s->cp_y.as<TV>();
   }
@@ -1021,8 +1026,11 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   if constexpr (sizeof(T) == 4) {
     // FP16_AUTO only where the sweep streams S_j from HBM: responses that stay in the 126 MB L2
     // gain nothing from half the bytes and would pay the extra sweeps of FP16 rounding
+    // ... and not for coupled lines: their faster contraction meets the FP16 floor sooner, which at
+    // 128^3 cost two to four times the sweeps (and extra restarts) that half the bytes save
     const bool l2_resident = s_bytes <= 96.0 * (1 << 20);
-    if (!tc && (o->port_storage == VTM_STORE_FP16 || (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident))) {
+    if (!tc && (o->port_storage == VTM_STORE_FP16 ||
+                (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident && !s->coupled))) {
       s->Sh.alloc((size_t)s_tiles * kNB * kNB * sizeof(__half));
       s->hscale.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
       VTM_CUDA(launch_port_to_half(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(), s->Sh.as<__half>(),
