@@ -217,8 +217,9 @@ typedef struct vtm_setup_opts {
                               fits in shared memory (nrhs <= 8) and in device memory            */
   int32_t port_storage;    /* PORT form, FP32 solvers, nrhs <= 8: storage of S_j (VTM_STORE_*):
                               NATIVE (0) the solver precision; FP16 halves the bytes of a sweep
-                              (each S_j scaled by its largest entry, FP32 arithmetic; the sweeps
-                              then match the FP64 oracle to about 2^-11 per sweep and the FP64
+                              (each 32 x 32 tile of S_j scaled by its largest entry, FP32
+                              arithmetic; the sweeps then match the FP64 oracle to about 2^-11
+                              per sweep and the FP64
                               defect correction restores the tolerance); FP16_AUTO takes FP16
                               when the responses exceed 96 MB (streamed from HBM rather than
                               held in L2) and the lines are uncoupled, and returns to FP32 for

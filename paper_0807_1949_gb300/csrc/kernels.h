@@ -69,7 +69,7 @@ struct PortArgs {
   const PieceDesc* pieces;     // all subgraphs, one CTA each
   const T* S;                  // port responses, lower block triangle of 32 x 32 tiles
   const void* Sh;              // FP32 solvers: the same tiles in IEEE half (nullptr: use S)
-  const float* scale;          // per subgraph of the launch: the factor the half tiles were divided by
+  const float* scale;          // FP16 storage: per stored tile (global tile index), the factor it was divided by
   const T* ubase;              // P^T K_j^{-1} b̃_j: ports x R
   const T* wprev;              // outgoing waves of the previous sweep: ends x R
   T* wnext;                    // outgoing waves of this sweep
@@ -91,7 +91,7 @@ cudaError_t launch_gather_port_response(const PieceDesc* pieces, int npieces, co
 template <typename T>
 cudaError_t launch_gather_ports(const PieceDesc* pieces, int npieces, const int32_t* port_local, int R, const T* xc,
                                 T* ubase, cudaStream_t st);
-// FP16 copy (and per-subgraph scale) of the FP32 port-response tiles.
+// FP16 copy (and per-tile scale) of the FP32 port-response tiles.
 cudaError_t launch_port_to_half(const PieceDesc* pieces, int npieces, const float* S, __half* Sh, float* scale,
                                 cudaStream_t st);
 

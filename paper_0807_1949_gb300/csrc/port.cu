@@ -14,11 +14,11 @@
 // load of all lanes reads 512 contiguous bytes.  The row part T s_J then sums over 4 lanes and the
 // column part T^T s_I over 8 lanes (short reduce-scatters).  Ports beyond n_ports are zero.
 //
-// FP16 storage (FP32 solvers): the same tiles as IEEE half, V = 8, each subgraph's S_j divided by
-// its largest entry (kept per subgraph in FP32); products and accumulation stay in FP32 and y is
-// scaled back before u = u_base + y.  It halves the bytes of the sweep; its rounding (2^-11 of
-// the largest entry) is absorbed by the FP64 defect correction, and the solver returns to FP32
-// storage if a correction step stops gaining a digit.
+// FP16 storage (FP32 solvers): the same tiles as IEEE half, V = 8, each tile divided by its own
+// largest entry (kept per tile in FP32); products and accumulation stay in FP32 and each tile's two
+// reduced sums are scaled back before they enter y.  It halves the bytes of the sweep; its rounding
+// (2^-11 of each tile's largest entry) is absorbed by the FP64 defect correction, and the solver
+// returns to FP32 storage if a correction step stops gaining a digit.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -196,14 +196,26 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
   // each warp keeps the next tile's loads in flight while it works on the current one
   constexpr int kWarps = kSweepThreads / 32;
   RawPatch<TS> cur, nxt;
-  if (warp < ntiles) load_raw(Sb + (int64_t)warp * kNB * kNB, lane, cur);
+  // FP16 storage: each tile was divided by its own largest |entry|; the two reduced sums of a
+  // tile are multiplied back before they are added to y
+  const float* tsc = (sizeof(TS) == 2) ? a.scale + pd.s_off : nullptr;
+  T sc_cur = T(1), sc_nxt = T(1);
+  if (warp < ntiles) {
+    load_raw(Sb + (int64_t)warp * kNB * kNB, lane, cur);
+    if constexpr (sizeof(TS) == 2) sc_cur = (T)tsc[warp];
+  }
   for (int t = warp; t < ntiles; t += kWarps) {
-    if (t + kWarps < ntiles) load_raw(Sb + (int64_t)(t + kWarps) * kNB * kNB, lane, nxt);
+    if (t + kWarps < ntiles) {
+      load_raw(Sb + (int64_t)(t + kWarps) * kNB * kNB, lane, nxt);
+      if constexpr (sizeof(TS) == 2) sc_nxt = (T)tsc[t + kWarps];
+    }
     int I, J;
     tile_of(t, I, J);
     T pt[kNB];
     widen(cur, pt);
     cur = nxt;
+    const T sc = sc_cur;
+    sc_cur = sc_nxt;
     const T* sJ = sv + ((size_t)J * kNB + 8 * pb) * R;
     const T* sI = sv + ((size_t)I * kNB + 4 * pa) * R;
 #pragma unroll
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
           rp[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
       }
-      atomicAdd(&yv[((size_t)I * kNB + 4 * pa + pb) * R + r], rp[0]);
+      atomicAdd(&yv[((size_t)I * kNB + 4 * pa + pb) * R + r], (sizeof(TS) == 2) ? rp[0] * sc : rp[0]);
       if (I != J) {
         // column part: 8 partial column sums over this lane's 4 rows, reduce-scattered over the 8
         // lanes of the same column group (xor 16, 8, 4): lane (pa, pb) ends with column 8 pb + pa
@@ -250,14 +262,13 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
             cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4 * h);
           }
         }
-        atomicAdd(&yv[((size_t)J * kNB + 8 * pb + pa) * R + r], cp[0]);
+        atomicAdd(&yv[((size_t)J * kNB + 8 * pb + pa) * R + r], (sizeof(TS) == 2) ? cp[0] * sc : cp[0]);
       }
     }
   }
   __syncthreads();
 
   // w_out[e] = 2 (u_base + y)_q - w_in[e]
-  const T ys = (sizeof(TS) == 2) ? (T)a.scale[blockIdx.x] : T(1);
   for (int i0 = tid; i0 < np * R; i0 += kSweepThreads * kU) {
     int e0[kU], e1[kU], tw[kU];
     T ub[kU];
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
       const int i = i0 + u * kSweepThreads;
       if (i >= np * R) break;
       const int r = i % R;
-      const T uu = ub[u] + ys * yv[i];
+      const T uu = ub[u] + yv[i];
       a.wnext[(size_t)e0[u] * R + r] = T(2) * uu - a.wprev[(size_t)tw[u] * R + r];
       for (int e = e0[u] + 1; e < e1[u]; ++e) a.wnext[(size_t)e * R + r] = T(2) * uu - a.wprev[(size_t)a.twin[e] * R + r];
     }
@@ -334,31 +345,29 @@ cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t s
   return port_launch_ts<T, T>(a, R, npieces, smem, st);
 }
 
-// FP16 copy of the FP32 tiles of one subgraph per CTA: scale = largest |entry| (1 if all zero),
-// tiles re-laid out for 8 halves per 16-byte load.
+// FP16 copy of the FP32 tiles of one subgraph per CTA, one warp per tile: each tile is divided by
+// its largest |entry| (1 if all zero), kept per tile in scale[s_off + t], and re-laid out from the
+// float patch layout ((p/4)*32 + L)*4 + p%4 to the half patch layout ((p/8)*32 + L)*8 + p%8.  A scale
+// per tile keeps the small far-field blocks of S_j at full FP16 precision.
 __global__ void k_port_to_half(const PieceDesc* __restrict__ pieces, const float* __restrict__ S,
                                __half* __restrict__ Sh, float* __restrict__ scale) {
-  __shared__ float red[kSweepThreads / 32];
   const PieceDesc pd = pieces[blockIdx.x];
-  const int64_t n = port_tiles(pd.nports) * kNB * kNB;
-  const float* src = S + pd.s_off * kNB * kNB;
-  __half* dst = Sh + pd.s_off * kNB * kNB;
-  float m = 0.f;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(src[i]));
+  const int64_t nt = port_tiles(pd.nports);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = warp; t < nt; t += blockDim.x >> 5) {
+    const float* src = S + (pd.s_off + t) * kNB * kNB;
+    __half* dst = Sh + (pd.s_off + t) * kNB * kNB;
+    float m = 0.f;
+    for (int k = lane; k < kNB * kNB; k += 32) m = fmaxf(m, fabsf(src[k]));
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  m = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
-  const float sc = m > 0.f ? m : 1.f;
-  if (threadIdx.x == 0) scale[blockIdx.x] = sc;
-  const float inv = 1.f / sc;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const int64_t t = i / (kNB * kNB);
-    const int k = (int)(i % (kNB * kNB));
-    const int L = (k / 4) % kNB, p = (k / 128) * 4 + (k % 4);   // float tile: ((p/4)*32 + L)*4 + p%4
-    dst[t * kNB * kNB + ((p / 8) * kNB + L) * 8 + (p % 8)] = __float2half_rn(src[i] * inv);
+    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const float sc = m > 0.f ? m : 1.f;
+    if (lane == 0) scale[pd.s_off + t] = sc;
+    const float inv = 1.f / sc;
+    for (int k = lane; k < kNB * kNB; k += 32) {
+      const int L = (k / 4) % kNB, p = (k / 128) * 4 + (k % 4);
+      dst[((p / 8) * kNB + L) * 8 + (p % 8)] = __float2half_rn(src[k] * inv);
+    }
   }
 }
 

@@ -134,7 +134,7 @@ struct vtm_solver {
   bool ubase_ok = false;
   size_t port_smem = 0;
   DevBuf tc_items;                   // (subgraph of the main launch, 128-port super-row)
-  DevBuf Sh, hscale;                 // FP16 copy of S_j and its per-subgraph scale
+  DevBuf Sh, hscale;                 // FP16 copy of S_j and the scale of each of its tiles
   bool port_half = false;            // the port sweep reads the FP16 copy
   bool port_half_auto = false;       // ... and returns to FP32 when a correction step stalls
   int n_items = 0;
@@ -1032,7 +1032,7 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     if (!tc && (o->port_storage == VTM_STORE_FP16 ||
                 (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident && !s->coupled))) {
       s->Sh.alloc((size_t)s_tiles * kNB * kNB * sizeof(__half));
-      s->hscale.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
+      s->hscale.alloc((size_t)std::max<int64_t>(1, s_tiles) * sizeof(float));  // one scale per tile
       VTM_CUDA(launch_port_to_half(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(), s->Sh.as<__half>(),
                                    s->hscale.as<float>(), s->stream));
       s->port_half = true;
