@@ -220,7 +220,9 @@ typedef struct vtm_setup_opts {
                               (each 32 x 32 tile of S_j scaled by its largest entry, FP32
                               arithmetic; the sweeps then match the FP64 oracle to about 2^-11
                               per sweep and the FP64
-                              defect correction restores the tolerance); FP16_AUTO takes FP16
+                              defect correction restores the tolerance; a phase on FP16
+                              responses restarts once its inner residual is below 4 x 2^-11);
+                              FP16_AUTO takes FP16
                               when the responses exceed 96 MB (streamed from HBM rather than
                               held in L2) and the lines are uncoupled, and returns to FP32 for
                               good once a defect-correction step gains less than a factor 10   */

@@ -170,6 +170,9 @@ static void check_status(vtm_solver* s) {
   if (st != 0) fail(VTM_ERR_INVALID, "device status " + std::to_string(st));
 }
 
+// Restart threshold of a defect-correction phase swept on FP16 port responses: 4 units of 2^-11.
+constexpr double kHalfReduction = 4.0 / 2048.0;
+
 template <typename T>
 static void autotune_sweep(vtm_solver* s);
 template <typename T>
@@ -1370,10 +1373,13 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       break;
     }
     next_k = m;
+    // sweeps on FP16 port responses stall near the FP16 rounding level of the inner solve, so such a
+    // phase restarts once it is within a few units of 2^-11 instead of waiting for the stall
+    const double reduction = s->port_half ? std::max(s->inner_reduction, kHalfReduction) : s->inner_reduction;
     if (s->port_form && last_inner > 0 && inner > 0 && inner < last_inner && inner_sweeps > last_inner_sweeps) {
       const double rate = std::pow(inner / last_inner, 1.0 / (inner_sweeps - last_inner_sweeps));
       double need = rtol / rel;                                   // reduction to reach rtol
-      if (refine) need = std::max(need, s->inner_reduction / inner);  // or the restart threshold
+      if (refine) need = std::max(need, reduction / inner);           // or the restart threshold
       if (rate < 1.0 && need < 1.0) {
         const double kk = std::ceil(1.05 * std::log(need) / std::log(rate));
         next_k = (int)std::min<double>(8.0 * m, std::max<double>(m, kk));
@@ -1391,7 +1397,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       s->info.port_storage_bits = 32;
       drop_graphs(s);
     }
-    if (refine && inner < 1.0 && (inner <= s->inner_reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
+    if (refine && inner < 1.0 && (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);
       s->vr.swap(s->vrt);

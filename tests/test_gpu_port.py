@@ -232,7 +232,7 @@ def test_port_form_skips_flagged_subgraphs(vtmlib):
     assert np.isfinite(s.copies()).all() and np.isfinite(s.get_state()).all()
 
 
-# FP16 storage of S_j (FP32 solvers): each subgraph's S_j is divided by its largest entry and
+# FP16 storage of S_j (FP32 solvers): each 32 x 32 tile of S_j is divided by its largest entry and
 # rounded to half (unit roundoff 2^-11 = 4.9e-4 of that entry); products stay FP32.  After 7 sweeps
 # the copies and waves stay within 7 x 4.9e-4 ~ 3.4e-3 of the oracle: tolerance 5e-3 of the max
 # norm.  The solve with FP64 defect correction must still reach 1e-8.
@@ -270,8 +270,7 @@ def test_port_fp16_solve(vtmlib, storage):
 
 
 def test_port_fp16_auto_on_high_contrast_fem(vtmlib):
-    """The 1e-3/1e3 FEM checkerboard converges slowly; FP16_AUTO must still reach 1e-8 (going back
-    to FP32 responses if a correction step stalls)."""
+    """The 1e-3/1e3 FEM checkerboard converges slowly; FP16_AUTO must still reach 1e-8."""
     fem, part, osplit = _fem(vtmlib, 4000, 16, seed=6)
     f = part.line_features()
     d = np.exp(f[:, 1].astype(np.float64))
@@ -284,3 +283,21 @@ def test_port_fp16_auto_on_high_contrast_fem(vtmlib):
     rel = np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1)
     assert np.all(rel <= 1e-8)
     assert s.info().port_storage_bits in (16, 32)
+
+
+@pytest.mark.parametrize("coupling", [None, 1.0])
+def test_port_fp16_auto_large_responses(vtmlib, coupling):
+    """Responses larger than 96 MB (64^3, 0.19 GB FP32): FP16_AUTO takes the FP16 copy for uncoupled
+    lines and keeps FP32 for coupled ones; the solve reaches 1e-8 both ways, twice in a row."""
+    dims, block = (64, 64, 64), (16, 16, 16)
+    A = inputs.grid_poisson(dims, sigma=1.0, seed=28)
+    b = inputs.rhs_uniform(A.n, 1, seed=28)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    s = vtmlib.Solver(part, z=4.0 if coupling else 1.0, precision="fp32", form="port", port_storage="fp16-auto",
+                      coupling=coupling, check_every=20)
+    assert s.info().port_storage_bits == (32 if coupling else 16)
+    As = A.to_scipy()
+    for _ in range(2):
+        x = np.zeros_like(b)
+        s.solve(b, x, rtol=1e-8, maxit=20000)
+        assert np.linalg.norm(b[0] - As @ x[0]) / np.linalg.norm(b[0]) <= 1e-8
