@@ -147,3 +147,60 @@ def test_invalid_couplings_are_rejected(vtmlib):
     with pytest.raises(vtmlib.VTMError) as e:
         s.input_impedances()
     assert e.value.code == 1  # VTM_ERR_INVALID
+
+
+def _fem_coupled(vtmlib, npts, parts, seed, zscale, gamma):
+    from test_gpu_fem import _maps
+    from test_gpu_port import _fem
+    fem, part, osplit = _fem(vtmlib, npts, parts, seed)
+    cmap, emap = _maps(part, osplit)
+    f = part.line_features()
+    d = np.exp(f[:, 1].astype(np.float64))
+    Z = zscale / (d[0::2] + d[1::2])
+    lib_to_or = emap[0::2] // 2
+    zo = np.empty(len(osplit.vtl))
+    zo[lib_to_or] = Z
+    pr, w = part.line_pairs()
+    Y = coupled.laplacian_admittance(osplit, zo, lib_to_or[pr], gamma * w)
+    return fem, part, osplit, cmap, emap, Z, (pr, gamma * w), Y
+
+
+@pytest.mark.parametrize("nrhs,form", [(1, "band"), (2, "port"), (16, "band")])
+def test_coupled_fem_fp64_matches_oracle(vtmlib, nrhs, form):
+    """Unstructured split (RCB of FEM element centroids, RCM local order): candidate pairs from
+    the library's partition, coupled sweeps against the coupled oracle."""
+    fem, part, osplit, cmap, emap, Z, cpl, Y = _fem_coupled(vtmlib, 4000, 16, 31, 8.0, 1.0)
+    assert len(cpl[1]) > 0
+    b = inputs.rhs_uniform(fem.A.n, nrhs, seed=31)
+    s = vtmlib.Solver(part, z=Z, precision="fp64", nrhs=nrhs, form=form, coupling=cpl)
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(6)
+    copies, waves = _oracle_after(osplit, Y, b, 6)
+    assert _rel(s.copies(), copies[:, cmap]) <= 1e-12
+    assert _rel(s.get_state(), waves[:, emap]) <= 1e-12
+
+
+def test_coupled_fem_fp32_solve(vtmlib):
+    """The 1e-3/1e3 checkerboard FEM with coupled lines in FP32 port form reaches 1e-8."""
+    fem, part, osplit, cmap, emap, Z, cpl, Y = _fem_coupled(vtmlib, 4000, 16, 6, 6.0, 1.0)
+    b = inputs.rhs_uniform(fem.A.n, 2, seed=6)
+    s = vtmlib.Solver(part, z=Z, precision="fp32", nrhs=2, form="port", coupling=cpl)
+    x = np.zeros_like(b)
+    s.solve(b, x, rtol=1e-8, maxit=100000)
+    As = fem.A.to_scipy()
+    assert np.all(np.linalg.norm(b - (As @ x.T).T, axis=1) / np.linalg.norm(b, axis=1) <= 1e-8)
+
+
+def test_coupled_with_flagged_subgraphs(vtmlib):
+    """Z = 1e4 leaves subgraphs nearly floating; their FP32 factorisations are flagged and swept in
+    FP64, with the coupling currents of their ports, beside the FP32 ones."""
+    from test_gpu_port import _fem
+    fem, part, osplit = _fem(vtmlib, 6000, 24, seed=9)
+    s = vtmlib.Solver(part, z=1e4, precision="fp32", form="band", coupling=0.5)
+    assert s.info().flagged_pieces >= 1 and s.info().ncouplings > 0
+    b = inputs.rhs_uniform(fem.A.n, 1, seed=9)
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(5)
+    assert np.isfinite(s.copies()).all() and np.isfinite(s.get_state()).all()
