@@ -118,6 +118,24 @@ def grid_poisson(dims, sigma: float = 0.0, seed: int = 0) -> CSR:
     return _csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def grid_anisotropic9(nx: int, ny: int, rho: float = 0.6) -> CSR:
+    """-(u_xx + 2 rho u_xy + u_yy) on an nx x ny vertex grid, Dirichlet eliminated: the 9-point
+    stencil with centre 4, axis neighbours -1 and diagonal neighbours -rho/2 (along x = y) and
+    +rho/2 (along x = -y).  SPD for |rho| < 1, but a row's off-diagonal sum 4 + 2|rho| exceeds its
+    diagonal: not diagonally dominant.  Vertex id i = x + nx*y."""
+    idx = np.arange(nx * ny, dtype=np.int64).reshape(ny, nx)
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [np.full(nx * ny, 4.0)]
+    for dx, dy, v in ((1, 0, -1.0), (0, 1, -1.0), (1, 1, -0.5 * rho), (1, -1, 0.5 * rho)):
+        ys = np.arange(max(0, -dy), ny - max(0, dy))
+        xs = np.arange(0, nx - dx)
+        a = idx[np.ix_(ys, xs)].ravel()
+        b = idx[np.ix_(ys + dy, xs + dx)].ravel()
+        rows += [a, b]
+        cols += [b, a]
+        vals += [np.full(len(a), v), np.full(len(a), v)]
+    return _csr_from_coo(nx * ny, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
 def random_dd_spd(n: int, avg_degree: float = 4.0, excess: float = 0.1, seed: int = 0) -> CSR:
     """Random sparse symmetric, weakly diagonally dominant matrix with positive excess (SPD).
 

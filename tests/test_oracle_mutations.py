@@ -131,3 +131,31 @@ def test_coupled_current_sign_is_caught(monkeypatch):
     """The twin's current added instead of subtracted in the current update."""
     monkeypatch.setattr(coupled, "current_update", lambda ut, omt, un, Yj: (ut - un) @ Yj + omt)
     assert _coupled_pins_fail()
+
+
+# ---------------------------------------------------------------- general conformal split (App. 1)
+import test_oracle_conformal as TF  # noqa: E402
+from oracle import conformal  # noqa: E402
+
+
+def _conformal_pins_fail():
+    return (_fails(TF.test_app1_two_vertex_construction)
+            and _fails(TF.test_kcl_and_spd_where_the_diagonal_rule_fails, 12, 10, 2, 2, 0.6))
+
+
+def test_schur_share_not_divided_is_caught(monkeypatch):
+    """Both new subgraphs take lam S: the pieces no longer sum back to A."""
+    monkeypatch.setattr(conformal, "boundary_blocks", lambda Ta, Tb, S, lam: (Ta + lam * S, Tb + lam * S))
+    assert _conformal_pins_fail()
+
+
+def test_dropped_completing_square_term_is_caught(monkeypatch):
+    """The beta boundary block without M_Bb M_bb^{-1} M_bB."""
+    orig = conformal.schur_terms
+
+    def no_tb(M, Ia, Ib, B):
+        Ta, Tb, S = orig(M, Ia, Ib, B)
+        return Ta, 0 * Tb, S
+
+    monkeypatch.setattr(conformal, "schur_terms", no_tb)
+    assert _conformal_pins_fail()
