@@ -87,7 +87,20 @@ enum vtm_partition_kind {
    * subgraph are in reverse Cuthill-McKee order (start: a minimum-degree node, smallest id on ties;
    * neighbours by increasing degree, then id).  Lines: the copies of vertex i in subgraphs p and q
    * are joined when an element edge through i has elements of both p and q around it. */
-  VTM_PART_ELEMENTS = 4
+  VTM_PART_ELEMENTS = 4,
+  /* General conformal split of App. 1 (Lemma A1.1, Thm 4.2) for any SPD A, including matrices
+   * that are not diagonally dominant (where step 3's rule returns VTM_ERR_NOT_CONFORMAL).  home[i]
+   * in [0, npieces) is the home subgraph of vertex i (every id needs one vertex).  The id range
+   * [lo, hi) of a subgraph is halved at mid = (lo + hi) / 2 (recursive bisection, N - 1 splits):
+   * alpha = copies with home < mid, the boundary B = alpha copies joined to a beta copy by the
+   * subgraph's matrix M, I_a = alpha \ B, I_b = beta.  Completing the square over each interior,
+   * T_a = M_Ba M_aa^{-1} M_aB, T_b = M_Bb M_bb^{-1} M_bB, S = M_BB - T_a - T_b (SPD); alpha gets
+   * T_a + lambda S on B, beta gets T_b + (1 - lambda) S on new copies of B (both SPD, and they sum
+   * to M).  A new copy's home is the smallest home among its beta neighbours; source shares are
+   * divided lambda : 1 - lambda; one line joins the two copies.  Copies inside a subgraph are in
+   * ascending vertex order.  The boundary blocks are dense and the construction is dense (O(n^3)
+   * work, O(n^2) memory): n <= 8192, else VTM_ERR_INVALID; VTM_ERR_NOT_SPD if A is not SPD. */
+  VTM_PART_CONFORMAL = 5
 };
 
 /* Split rule of GRID and OWNERS (§4 step 3; the paper leaves the shares open, this is the
@@ -129,6 +142,9 @@ typedef struct vtm_partition_spec {
   const int32_t* elem_piece;  /* host, nelem subgraph ids, or NULL for RCB                        */
   const double* elem_coords;  /* host, nelem x coord_dim (RCB)                                    */
   int32_t coord_dim;
+  /* CONFORMAL */
+  const int32_t* home;        /* host, n home subgraph ids                                        */
+  double lambda;              /* share of the boundary Schur complement kept by alpha, (0, 1)     */
 } vtm_partition_spec;
 
 typedef struct vtm_partition vtm_partition;

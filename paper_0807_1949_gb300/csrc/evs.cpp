@@ -391,6 +391,7 @@ void build_explicit(const vtm_partition_spec* sp, vtm_partition* p) {
 
 namespace vtm {
 void build_elements(const vtm_partition_spec* sp, vtm_partition* p);
+void build_conformal(const vtm_partition_spec* sp, vtm_partition* p);
 void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition* p) {
   if (!spec) fail(VTM_ERR_INVALID, "null partition spec");
   copy_and_check_matrix(A, p);
@@ -399,6 +400,7 @@ void build_partition(const vtm_csr* A, const vtm_partition_spec* spec, vtm_parti
     case VTM_PART_OWNERS: build_owners(spec, p); break;
     case VTM_PART_EXPLICIT: build_explicit(spec, p); break;
     case VTM_PART_ELEMENTS: build_elements(spec, p); break;
+    case VTM_PART_CONFORMAL: build_conformal(spec, p); break;
     default: fail(VTM_ERR_INVALID, "unknown partition kind");
   }
   // every copy that has a line must sit in a piece; pieces must be non-empty

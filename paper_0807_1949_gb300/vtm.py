@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 VTM_OK = 0
 STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SYMMETRIC", 3: "NOT_CONFORMAL", 4: "NOT_SPD", 5: "NOT_CONVERGED",
           6: "DIVERGED", 7: "TIMEOUT", 8: "CUDA", 9: "OOM"}
-PART_GRID, PART_OWNERS, PART_EXPLICIT, PART_ELEMENTS = 1, 2, 3, 4
+PART_GRID, PART_OWNERS, PART_EXPLICIT, PART_ELEMENTS, PART_CONFORMAL = 1, 2, 3, 4, 5
 Z_UNIFORM, Z_EXPLICIT, Z_MATCHED, Z_LEARNED = 0, 1, 2, 3
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 8, 64, 4801
 FP64, FP32 = 0, 1
@@ -45,7 +45,8 @@ class _Spec(C.Structure):
                 ("ncopy_lines", C.c_int64), ("line_copy_a", C.c_void_p), ("line_copy_b", C.c_void_p),
                 ("nelem", C.c_int64), ("nodes_per_elem", C.c_int32), ("nnodes", C.c_int64),
                 ("elem_nodes", C.c_void_p), ("elem_mats", C.c_void_p), ("node_unknown", C.c_void_p),
-                ("elem_piece", C.c_void_p), ("elem_coords", C.c_void_p), ("coord_dim", C.c_int32)]
+                ("elem_piece", C.c_void_p), ("elem_coords", C.c_void_p), ("coord_dim", C.c_int32),
+                ("home", C.c_void_p), ("lam", C.c_double)]
 
 
 class PartitionInfo(C.Structure):
@@ -213,7 +214,7 @@ def _csr_struct(A):
 
 
 def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, lines=None, explicit=None,
-                  elements=None, npieces=None) -> Partition:
+                  elements=None, npieces=None, home=None, lam: float = 0.5) -> Partition:
     """vtm_partition_evs.  A: object with n, rowptr, col, val (inputs.CSR).
 
     kind="grid":     dims=(nx, ny[, nz]), block=(sx, sy[, sz]).
@@ -222,6 +223,8 @@ def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, 
                      line_copy_a, line_copy_b).
     kind="elements": elements=dict(elem_nodes (m, k), elem_mats (m, k, k), node_unknown, and either
                      elem_piece (m,) or elem_coords (m, dim) with npieces).
+    kind="conformal": home=(n,) home subgraph of every vertex, lam in (0, 1): the general SPD split
+                     of App. 1 (dense; n <= 8192).
     """
     csr, keep = _csr_struct(A)
     sp = _Spec()
@@ -276,6 +279,12 @@ def partition_evs(A, kind: str = "grid", *, dims=None, block=None, owners=None, 
             hold.append(ec)
             sp.elem_coords, sp.coord_dim = ec.ctypes.data, ec.shape[1]
             sp.npieces = int(npieces)
+    elif kind == "conformal":
+        hm = _arr(home, np.int32)
+        hold.append(hm)
+        sp.kind = PART_CONFORMAL
+        sp.npieces = int(npieces or hm.max() + 1)
+        sp.home, sp.lam = hm.ctypes.data, float(lam)
     else:
         raise ValueError(kind)
     h = C.c_void_p()

@@ -206,3 +206,38 @@ def test_line_pairs_match_oracle(vtmlib, dims, block, sigma):
     assert got.keys() == ref.keys()
     assert all(got[k] == ref[k] for k in ref)
     assert np.all(pr[:, 0] < pr[:, 1])
+
+
+@pytest.mark.parametrize("nx,ny,bx,by,rho,lam", [(12, 10, 2, 2, 0.6, 0.5), (16, 9, 4, 2, 0.9, 0.35),
+                                                  (9, 9, 3, 1, 0.3, 0.7)])
+def test_conformal_partition_matches_oracle(vtmlib, nx, ny, bx, by, rho, lam):
+    """App. 1's general SPD split on a matrix that is not diagonally dominant: the library's
+    (Cholesky-based) pieces, shares and lines against the oracle's (LU-based) to rounding."""
+    from oracle import conformal
+    from test_oracle_conformal import _block_home
+
+    A = inputs.grid_anisotropic9(nx, ny, rho)
+    home = _block_home(nx, ny, bx, by)
+    with pytest.raises(vtmlib.VTMError):   # the diagonal rule cannot split it
+        owners = [tuple(sorted({int(home[i])} | {int(home[k]) for k in A.col[A.rowptr[i]:A.rowptr[i + 1]]}))
+                  for i in range(A.n)]
+        vtmlib.partition_evs(A, "owners", owners=owners, lines=[(0, owners[0][0], owners[0][0])][:0])
+    part = vtmlib.partition_evs(A, "conformal", home=home, lam=lam)
+    _compare_split(part, conformal.split_conformal(A, home, lam=lam), atol=1e-13)
+    assert part.info().nlines == len(conformal.split_conformal(A, home, lam=lam).vtl)
+
+
+def test_conformal_partition_errors(vtmlib):
+    A = inputs.grid_anisotropic9(6, 6, 0.5)
+    home = np.zeros(A.n, np.int32)
+    home[18:] = 1
+    for kw in (dict(home=home, lam=0.0), dict(home=home, lam=1.0), dict(home=home, npieces=3),
+               dict(home=np.full(A.n, 2, np.int32), npieces=2)):
+        with pytest.raises(vtmlib.VTMError) as e:
+            vtmlib.partition_evs(A, "conformal", **kw)
+        assert e.value.code == 1
+    # symmetric with a positive diagonal but indefinite: an interior Cholesky factor breaks down
+    bad = inputs.csr_from_dense(np.eye(A.n) + 2.0 * (np.eye(A.n, k=1) + np.eye(A.n, k=-1)))
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(bad, "conformal", home=home)
+    assert e.value.code == 4
