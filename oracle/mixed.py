@@ -8,7 +8,7 @@ residual b - A x, the accumulated solution and the convergence test stay in FP64
 is classical defect correction (iterative refinement): the sweeps solve A d = r from zero boundary
 variables, x <- x + d, r <- b - A x in FP64, and the sweeps restart on the new r once the inner
 residual has dropped by ``inner_reduction`` or stalls.  This is the structure the library's FP32
-solve uses; the FP64 oracle (vtm.py) remains the judge of every result.
+solve uses; the FP64 oracle (vtm.py) remains the reference for every result.
 
 Why the outer loop is needed: inexact local solves are exact solves of perturbed local matrices,
 i.e. a different split of a perturbed A, so the inner iteration converges to the solution of a
