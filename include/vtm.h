@@ -308,6 +308,11 @@ typedef struct vtm_solver_info {
  * Errors: VTM_ERR_INVALID, VTM_ERR_NOT_SPD, VTM_ERR_OOM, VTM_ERR_CUDA. */
 int vtm_setup(const vtm_partition* p, const vtm_setup_opts* opts, void* cuda_stream, vtm_solver** out);
 int vtm_solver_get_info(const vtm_solver* s, vtm_solver_info* info);
+/* Residual checks of the last vtm_solve, in order: sweeps done at the check, max_r relative
+ * residual ||b_r - A x_r|| / ||b_r|| (FP64) and max_r inner residual (relative to the residual the
+ * current defect-correction phase started from; equal to the former before the first restart).
+ * Host arrays of *count entries; call with NULL arrays to read *count. */
+int vtm_solver_get_history(const vtm_solver* s, int32_t* count, int32_t* sweeps, double* rel, double* inner);
 void vtm_solver_destroy(vtm_solver* s);
 
 /* ----------------------------------------------------------------------------------------------

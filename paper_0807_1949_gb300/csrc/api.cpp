@@ -19,6 +19,7 @@ void solver_get_state(vtm_solver* s, double* waves);
 void solver_set_state(vtm_solver* s, const double* waves);
 void solver_get_copies(vtm_solver* s, double* out);
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info);
+void solver_get_history(const vtm_solver* s, int32_t* count, int32_t* sweeps, double* rel, double* inner);
 void solver_input_impedances(vtm_solver* s, double* r);
 void line_features(const vtm_partition* p, float* out);
 void line_pairs(const vtm_partition* p, std::vector<int64_t>& pairs, std::vector<double>& wts);
@@ -173,6 +174,14 @@ int vtm_solver_get_info(const vtm_solver* s, vtm_solver_info* info) {
   return guarded([&] {
     if (!s || !info) vtm::fail(VTM_ERR_INVALID, "null argument");
     vtm::solver_get_info(s, info);
+    return VTM_OK;
+  });
+}
+
+int vtm_solver_get_history(const vtm_solver* s, int32_t* count, int32_t* sweeps, double* rel, double* inner) {
+  return guarded([&] {
+    if (!s || !count) vtm::fail(VTM_ERR_INVALID, "null argument");
+    vtm::solver_get_history(s, count, sweeps, rel, inner);
     return VTM_OK;
   });
 }

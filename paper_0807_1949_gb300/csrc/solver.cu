@@ -13,6 +13,8 @@
 #include <memory>
 #include <numeric>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "kernels.h"
 
@@ -142,6 +144,9 @@ struct vtm_solver {
   bool coupled = false;
   DevBuf cp_ptr, cp_oth, cp_y;
   std::vector<double> ydiag;         // per line: sum of its coupling conductances (diagonal of Y)
+  // the last vtm_solve's residual checks: sweeps so far, max relative residual, max inner residual
+  std::vector<int32_t> hist_sweeps;
+  std::vector<double> hist_rel, hist_inner;
   vtm_solver_info info{};
 
   // captured CUDA graphs of k back-to-back sweeps, keyed by (k, starting wave buffer)
@@ -160,6 +165,12 @@ struct vtm_solver {
 };
 
 namespace vtm {
+
+// NVTX range for the phases of setup and solve (visible to ncu --nvtx and other NVTX tools).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 static void check_status(vtm_solver* s) {
   int st = 0;
@@ -649,7 +660,10 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   for (size_t q = 0; q + 1 < port_end_ptr.size(); ++q)
     for (int32_t e = port_end_ptr[q]; e < port_end_ptr[q + 1]; ++e) s->end_port[e] = (int32_t)q;
   for (int32_t j = 0; j < np; ++j) s->max_ports = std::max(s->max_ports, pd[j].nports);
-  factor_typed<T>(s);
+  {
+    Range r("vtm_setup/factor");
+    factor_typed<T>(s);
+  }
   plan_hi(s);
 
   // vectors
@@ -671,8 +685,14 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   VTM_CUDA(cudaMallocHost(&s->h_norms, 2 * kMaxRhs * sizeof(double)));
   VTM_CUDA(cudaStreamSynchronize(st));
 
-  autotune_sweep<T>(s);
-  choose_form<T>(s, o, soff, foff);
+  {
+    Range r("vtm_setup/autotune");
+    autotune_sweep<T>(s);
+  }
+  {
+    Range r("vtm_setup/form");
+    choose_form<T>(s, o, soff, foff);
+  }
   s->withhold = o->withhold_slab > 0 ? o->withhold_slab - 1 : -1;  // after tuning: only real sweeps
 
   s->info.npieces = np;
@@ -1204,6 +1224,7 @@ static void assemble(vtm_solver* s, const double* xbase, double* xt) {
 }
 
 vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void* cuda_stream) {
+  Range range("vtm_setup");
   auto t0 = std::chrono::steady_clock::now();
   if (!p || !o) fail(VTM_ERR_INVALID, "null partition or options");
   if (o->precision != VTM_FP32 && o->precision != VTM_FP64) fail(VTM_ERR_INVALID, "unknown precision");
@@ -1284,6 +1305,7 @@ void solver_set_rhs(vtm_solver* s, const double* b, int64_t ldb) {
 }
 
 void solver_iterate(vtm_solver* s, int k) {
+  Range range("vtm_iterate");
   if (k < 0) fail(VTM_ERR_INVALID, "negative sweep count");
   run_sweeps(s, k);
 }
@@ -1294,7 +1316,11 @@ static void read_norms(vtm_solver* s, int cnt) {
 }
 
 int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double rtol, int maxit, vtm_stats* stats) {
+  Range range("vtm_solve");
   auto t0 = std::chrono::steady_clock::now();
+  s->hist_sweeps.clear();
+  s->hist_rel.clear();
+  s->hist_inner.clear();
   const int64_t launches0 = s->launches;
   if (!b || !x || ld < s->n || !(rtol > 0) || maxit < 1) fail(VTM_ERR_INVALID, "vtm_solve: bad arguments");
   const int R = s->R;
@@ -1341,7 +1367,10 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   int last_inner_sweeps = 0;
   while (sweeps < maxit) {
     const int k = std::min(next_k, maxit - sweeps);
-    run_sweeps(s, k);
+    {
+      Range r("vtm_solve/sweeps");
+      run_sweeps(s, k);
+    }
     sweeps += k;
     inner_sweeps += k;
     assemble(s, xacc, xt);
@@ -1361,6 +1390,9 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       rel = std::max(rel, rn / bn[r]);
       inner = std::max(inner, rn / rcur_norm[r]);
     }
+    s->hist_sweeps.push_back(sweeps);
+    s->hist_rel.push_back(rel);
+    s->hist_inner.push_back(inner);
     if (bad) {
       status = VTM_ERR_DIVERGED;
       break;
@@ -1487,6 +1519,13 @@ void solver_get_copies(vtm_solver* s, double* out) {
   else get_copies_typed<double>(s, out);
 }
 void solver_get_info(const vtm_solver* s, vtm_solver_info* info) { *info = s->info; }
+
+void solver_get_history(const vtm_solver* s, int32_t* count, int32_t* sweeps, double* rel, double* inner) {
+  *count = (int32_t)s->hist_sweeps.size();
+  if (sweeps) std::copy(s->hist_sweeps.begin(), s->hist_sweeps.end(), sweeps);
+  if (rel) std::copy(s->hist_rel.begin(), s->hist_rel.end(), rel);
+  if (inner) std::copy(s->hist_inner.begin(), s->hist_inner.end(), inner);
+}
 void solver_get_piece_precision(const vtm_solver* s, int32_t* bits) {
   if (!bits) fail(VTM_ERR_INVALID, "null output");
   std::copy(s->piece_bits.begin(), s->piece_bits.end(), bits);

@@ -100,6 +100,7 @@ def _load():
         "vtm_partition_destroy": (None, [vp]),
         "vtm_setup": (C.c_int, [vp, vp, vp, vp]),
         "vtm_solver_get_info": (C.c_int, [vp, vp]),
+        "vtm_solver_get_history": (C.c_int, [vp, vp, vp, vp, vp]),
         "vtm_solver_destroy": (None, [vp]),
         "vtm_set_rhs": (C.c_int, [vp, vp, i64]),
         "vtm_reset": (C.c_int, [vp]),
@@ -406,6 +407,17 @@ class Solver:
             _check(code)
         st.status = code
         return st
+
+    def history(self) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """Residual checks of the last solve (vtm_solver_get_history): sweeps at each check, max
+        relative residual, max inner (defect-correction phase) residual."""
+        cnt = C.c_int32()
+        _check(_lib.vtm_solver_get_history(self._h, C.byref(cnt), None, None, None))
+        sw = np.empty(cnt.value, np.int32)
+        rel = np.empty(cnt.value, np.float64)
+        inner = np.empty(cnt.value, np.float64)
+        _check(_lib.vtm_solver_get_history(self._h, C.byref(cnt), _ptr(sw), _ptr(rel), _ptr(inner)))
+        return sw, rel, inner
 
     def impedances(self) -> np.ndarray:
         """Line impedances in use, (nlines,)."""
