@@ -237,11 +237,12 @@ typedef struct vtm_setup_opts {
                               arithmetic; the sweeps then match the FP64 oracle to about 2^-11
                               per sweep and the FP64
                               defect correction restores the tolerance; a phase on FP16
-                              responses restarts once its inner residual is below 4 x 2^-11);
+                              responses restarts once its inner residual is below 4 x 2^-11,
+                              and with coupled lines once a check gains less than a factor 2);
                               FP16_AUTO takes FP16
                               when the responses exceed 96 MB (streamed from HBM rather than
-                              held in L2) and the lines are uncoupled, and returns to FP32 for
-                              good once a defect-correction step gains less than a factor 10   */
+                              held in L2), and returns to FP32 for good once a defect-correction
+                              step gains less than a factor 10                                 */
   /* Coupled lines (§7.2, Thm 7.1).  Lines that join the same two subgraphs form a bundle; a
    * conductance y_p >= 0 between two lines t, t' of one bundle makes the bundle's admittance
    * Y = Z^{-1} = diag(1/Z_t) + sum_p y_p (e_t - e_t')(e_t - e_t')^T, symmetric positive definite,

@@ -1049,11 +1049,8 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   if constexpr (sizeof(T) == 4) {
     // FP16_AUTO only where the sweep streams S_j from HBM: responses that stay in the 126 MB L2
     // gain nothing from half the bytes and would pay the extra sweeps of FP16 rounding
-    // ... and not for coupled lines: their faster contraction meets the FP16 floor sooner, which at
-    // 128^3 cost two to four times the sweeps (and extra restarts) that half the bytes save
     const bool l2_resident = s_bytes <= 96.0 * (1 << 20);
-    if (!tc && (o->port_storage == VTM_STORE_FP16 ||
-                (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident && !s->coupled))) {
+    if (!tc && (o->port_storage == VTM_STORE_FP16 || (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident))) {
       s->Sh.alloc((size_t)s_tiles * kNB * kNB * sizeof(__half));
       s->hscale.alloc((size_t)std::max<int64_t>(1, s_tiles) * sizeof(float));  // one scale per tile
       VTM_CUDA(launch_port_to_half(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(), s->Sh.as<__half>(),
@@ -1429,7 +1426,11 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       s->info.port_storage_bits = 32;
       drop_graphs(s);
     }
-    if (refine && inner < 1.0 && (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m))) {
+    // coupled lines on FP16 responses: while such a phase makes progress it gains far more than a
+    // factor 2 per check, so a check that gains less has met the FP16 floor
+    const bool half_floor = s->port_half && s->coupled && inner > 0.5 * prev_inner && inner_sweeps >= 2 * m;
+    if (refine && inner < 1.0 &&
+        (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || half_floor)) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);
       s->vr.swap(s->vrt);

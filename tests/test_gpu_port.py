@@ -287,15 +287,15 @@ def test_port_fp16_auto_on_high_contrast_fem(vtmlib):
 
 @pytest.mark.parametrize("coupling", [None, 1.0])
 def test_port_fp16_auto_large_responses(vtmlib, coupling):
-    """Responses larger than 96 MB (64^3, 0.19 GB FP32): FP16_AUTO takes the FP16 copy for uncoupled
-    lines and keeps FP32 for coupled ones; the solve reaches 1e-8 both ways, twice in a row."""
+    """Responses larger than 96 MB (64^3, 0.19 GB FP32): FP16_AUTO takes the FP16 copy, for coupled
+    lines with the FP16-floor restart rule; the solve reaches 1e-8 both ways, twice in a row."""
     dims, block = (64, 64, 64), (16, 16, 16)
     A = inputs.grid_poisson(dims, sigma=1.0, seed=28)
     b = inputs.rhs_uniform(A.n, 1, seed=28)
     part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
     s = vtmlib.Solver(part, z=4.0 if coupling else 1.0, precision="fp32", form="port", port_storage="fp16-auto",
                       coupling=coupling, check_every=20)
-    assert s.info().port_storage_bits == (32 if coupling else 16)
+    assert s.info().port_storage_bits == 16
     As = A.to_scipy()
     for _ in range(2):
         x = np.zeros_like(b)
