@@ -115,14 +115,22 @@ def oracle_sweep_sample(workload: str, sweeps: int) -> dict:
                 sample=len(split.subgraphs), sample_dims=dims, sweeps=sweeps, seconds=dt)
 
 
-def cpu_baseline(workload: str, sweeps_to_tol: int, sweeps=6) -> dict:
+def oracle_sample_child(workload: str, sweeps: int):
+    """oracle_sweep_sample in a child process limited to one host thread (numpy/scipy BLAS and
+    OpenMP), so that the reported core count is the one used.  Returns (result dict or None, stderr)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-child",
            json.dumps(dict(workload=workload, sweeps=sweeps))]
     out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
-        return dict(value=None, unit="ms", cores=1, kind="oracle", error=out.stderr[-300:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
+        return None, out.stderr[-300:]
+    return json.loads(out.stdout.strip().splitlines()[-1]), ""
+
+
+def cpu_baseline(workload: str, sweeps_to_tol: int, sweeps=6) -> dict:
+    r, err = oracle_sample_child(workload, sweeps)
+    if r is None:
+        return dict(value=None, unit="ms", cores=1, kind="oracle", error=err)
     per_sweep_ms = r["sec_per_piece_sweep"] * r["total_pieces"] * 1e3
     return dict(value=round(per_sweep_ms * sweeps_to_tol, 3), unit="ms", cores=1, kind="oracle",
                 per_sweep_ms=round(per_sweep_ms, 3),
@@ -247,11 +255,14 @@ def run_reference(args):
     ksweeps = reference_sweeps(args.workload)
     vals = []
     for _ in range(args.warmup):
-        oracle_sweep_sample(args.workload, 1)
+        oracle_sample_child(args.workload, 1)
     t0 = time.perf_counter()
     info = None
     for _ in range(args.steps):
-        info = oracle_sweep_sample(args.workload, 10)
+        info, err = oracle_sample_child(args.workload, 10)
+        if info is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed: " + err.strip()[-200:]}))
+            return 0
         vals.append(info["sec_per_piece_sweep"] * info["total_pieces"] * ksweeps * 1e3)
     dt = time.perf_counter() - t0
     v = statistics.median(vals)
