@@ -913,6 +913,18 @@ static void ubase_typed(vtm_solver* s) {
   s->ubase_ok = true;
 }
 
+// Port form, at the start of a defect-correction phase (zero waves): the first sweep of the phase
+// is a band sweep from zero incident waves, which is exactly the solve that gives u_base, so it
+// serves as both (one sweep fewer than computing u_base separately).
+template <typename T>
+static void first_sweep_typed(vtm_solver* s) {
+  sweeps_typed<T>(s, 1);
+  VTM_CUDA(launch_gather_ports<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(), s->R,
+                                  s->xc.as<T>(), s->ubase.as<T>(), s->stream));
+  s->launches++;
+  s->ubase_ok = true;
+}
+
 static void ensure_ubase(vtm_solver* s) {
   if (!s->port_form || s->ubase_ok) return;
   if (s->precision == VTM_FP32) ubase_typed<float>(s);
@@ -1362,6 +1374,15 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   int next_k = m;
   double last_inner = -1.0;
   int last_inner_sweeps = 0;
+  // port form: the first sweep of every phase also gives u_base (first_sweep_typed)
+  auto phase_start = [&]() {
+    if (!s->port_form) return;
+    if (s->precision == VTM_FP32) first_sweep_typed<float>(s);
+    else first_sweep_typed<double>(s);
+    ++sweeps;
+    ++inner_sweeps;
+  };
+  phase_start();
   while (sweeps < maxit) {
     const int k = std::min(next_k, maxit - sweeps);
     {
@@ -1447,6 +1468,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       last_inner = -1.0;
       next_k = m;
       trial_fresh = false;
+      phase_start();
       continue;
     }
     prev_inner = inner;
