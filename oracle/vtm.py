@@ -140,15 +140,20 @@ class VTM:
 
     def assemble(self, state: State) -> np.ndarray:
         """x_i = mean over the copies of vertex i of the last local solutions; (R, n)."""
-        R = state.u.shape[0]
-        acc = np.zeros((R, self.split.n))
-        cnt = np.zeros(self.split.n)
-        for j, g in enumerate(self.split.subgraphs):
-            if state.x_local[j] is None:
-                continue
-            np.add.at(acc.T, g.vertices, state.x_local[j].T)
-            np.add.at(cnt, g.vertices, 1.0)
-        return acc / np.maximum(cnt, 1.0)[None, :]
+        return assemble(self.split, state)
+
+
+def assemble(split: SplitGraph, state: State) -> np.ndarray:
+    """x_i = mean over the copies of vertex i of the last local solutions; (R, n)."""
+    R = state.u.shape[0]
+    acc = np.zeros((R, split.n))
+    cnt = np.zeros(split.n)
+    for j, g in enumerate(split.subgraphs):
+        if state.x_local[j] is None:
+            continue
+        np.add.at(acc.T, g.vertices, state.x_local[j].T)
+        np.add.at(cnt, g.vertices, 1.0)
+    return acc / np.maximum(cnt, 1.0)[None, :]
 
 
 def relative_residual(A, b: np.ndarray, x: np.ndarray) -> np.ndarray:
@@ -200,3 +205,38 @@ def solve(split: SplitGraph, A, b: np.ndarray, Z, rtol: float = 1e-10, maxit: in
             if np.max(rr) <= rtol:
                 return SolveResult(x=x, sweeps=k, history=hist, state=st)
     return SolveResult(x=m.assemble(st), sweeps=maxit, history=hist, state=st)
+
+
+def residual_from_ports(split: SplitGraph, state: State) -> np.ndarray:
+    """b - A x̄ of the assembled iterate (x̄ = mean of the copies) from port data alone, (R, n).
+
+    KCL (Thm 4.1, App. 2) gives b - A x̄ = sum_j S_j (b̃_j - Ã_j x̄|_j), S_j the scatter of subgraph
+    j's copies to their vertices.  Every local solve satisfies eq. 5.8, which with the current update
+    reads Ã_j x_j = b̃_j + P_j omega_j (omega the inflow currents of the sweep), so
+
+        b - A x̄ = sum_j S_j (Ã_j D_j - P_j omega_j),     D_j = x_j - x̄|_j.
+
+    D_j vanishes on copies of vertices with one copy, so only the port potentials u, the currents
+    omega and the columns of Ã_j at the ports are needed: no interior unknown.  This holds for the
+    coupled lines of §7.2 as well (their current update keeps the same local equation)."""
+    R = state.u.shape[0]
+    xbar = assemble(split, state)                                   # mean of the copies
+    out = np.zeros((R, split.n))
+    piece_of_end = np.empty(2 * len(split.vtl), dtype=np.int64)
+    local_of_end = np.empty(2 * len(split.vtl), dtype=np.int64)
+    piece_of_end[0::2], local_of_end[0::2] = split.vtl[:, 0], split.vtl[:, 1]
+    piece_of_end[1::2], local_of_end[1::2] = split.vtl[:, 2], split.vtl[:, 3]
+    for j, g in enumerate(split.subgraphs):
+        ends = np.nonzero(piece_of_end == j)[0]
+        ports = np.unique(local_of_end[ends])
+        D = np.zeros((R, len(g.vertices)))
+        # D_j on the ports: the port potential of the copy (its u) minus the mean of the copies
+        u_port = {}
+        for e in ends:
+            u_port[int(local_of_end[e])] = state.u[:, e]
+        for c in ports:
+            D[:, c] = u_port[int(c)] - xbar[:, g.vertices[c]]
+        contrib = (g.A[:, ports] @ D[:, ports].T).T                   # Ã_j D_j: port columns only
+        np.add.at(contrib.T, local_of_end[ends], -state.omega[:, ends].T)
+        np.add.at(out.T, g.vertices, contrib.T)
+    return out
