@@ -241,3 +241,24 @@ def test_conformal_partition_errors(vtmlib):
     with pytest.raises(vtmlib.VTMError) as e:
         vtmlib.partition_evs(bad, "conformal", home=home)
     assert e.value.code == 4
+
+
+def test_line_pairs_match_oracle_on_fem_split(vtmlib):
+    """Candidate couplings on an unstructured split (RCB of element centroids, RCM local order):
+    the same pairs of lines (identified by vertex and subgraphs) and weights as the oracle."""
+    from oracle import coupled
+
+    fem = inputs.fem_delaunay(3000, seed=14)
+    part = vtmlib.partition_evs(fem.A, "elements", elements=dict(
+        elem_nodes=fem.elem_nodes, elem_mats=fem.elem_mats, node_unknown=fem.node_unknown,
+        elem_coords=fem.centroids), npieces=12)
+    osplit = evs.split_by_elements(fem.A, fem.elem_nodes, fem.elem_mats, fem.node_unknown, evs.rcb(fem.centroids, 12))
+    pr, w = part.line_pairs()
+    opr, ow = coupled.adjacent_line_pairs(osplit, fem.A)
+    q = part.lines()
+    lib_key = [(int(part.piece(int(a))[0][la]), frozenset((int(a), int(b)))) for a, la, b, lb in q]
+    or_key = [(int(osplit.subgraphs[a].vertices[la]), frozenset((int(a), int(b)))) for a, la, b, lb in osplit.vtl]
+    got = {frozenset((lib_key[t], lib_key[u])): x for (t, u), x in zip(pr, w)}
+    ref = {frozenset((or_key[t], or_key[u])): x for (t, u), x in zip(opr, ow)}
+    assert len(got) == len(pr) > 0 and got.keys() == ref.keys()
+    assert all(abs(got[k] - ref[k]) <= 1e-15 * abs(ref[k]) for k in ref)
