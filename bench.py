@@ -127,7 +127,7 @@ def oracle_sample_child(workload: str, sweeps: int):
     return json.loads(out.stdout.strip().splitlines()[-1]), ""
 
 
-def cpu_baseline(workload: str, sweeps_to_tol: int, sweeps=6) -> dict:
+def cpu_baseline(workload: str, sweeps_to_tol: int, count_source: str, sweeps=6) -> dict:
     r, err = oracle_sample_child(workload, sweeps)
     if r is None:
         return dict(value=None, unit="ms", cores=1, kind="oracle", error=err)
@@ -136,7 +136,7 @@ def cpu_baseline(workload: str, sweeps_to_tol: int, sweeps=6) -> dict:
                 per_sweep_ms=round(per_sweep_ms, 3),
                 sample=(f"FP64 oracle, {r['sweeps']} sweeps of a {r['sample_dims']} grid = {r['sample']} subgraphs of "
                         f"the workload's block shape ({r['seconds']:.1f} s), scaled to {r['total_pieces']} subgraphs "
-                        f"and to {sweeps_to_tol} sweeps (plain FP64 method's count to 1e-8); factorisation excluded"))
+                        f"and to {sweeps_to_tol} sweeps ({count_source}); factorisation excluded"))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -499,8 +499,13 @@ def run_vtm(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline and w["kind"] == "grid":
-        ks = plain["sweeps"] if plain else sweeps
-        cpu = cpu_baseline(args.workload, ks)
+        ks = reference_sweeps(args.workload)
+        src = "the plain FP64 method's count to 1e-8, from the oracle's own run"
+        if ks <= 0 and plain:
+            ks, src = plain["sweeps"], "the plain FP64 method's count to 1e-8 on this GPU"
+        elif ks <= 0:
+            ks, src = sweeps, "this run's sweep count; the plain method was not run"
+        cpu = cpu_baseline(args.workload, ks, src)
         if cpu.get("value") is not None and R > 1:
             cpu["value"] = round(cpu["value"] * R, 3)
             cpu["sample"] += f"; times {R} right-hand sides"
