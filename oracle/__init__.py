@@ -20,6 +20,8 @@ Modules, each following the paper in its own order and notation:
                  reflection law, candidate line pairs.
 * ``conformal``— App. 1 and Thm 4.2: the general conformal split of an SPD matrix by completing the
                  square over each interior.
+* ``n2n``      — Table 1 as neighbour-to-neighbour message passing, one thread per subgraph, with
+                 late, reordered and dropped messages (host-side failure detection).
 * ``mlp``, ``features`` — the FP64 perceptron and line features the learned impedances are
                  checked against.
 

@@ -114,25 +114,31 @@ class VTM:
     def sweep(self, state: State, b: np.ndarray, pieces=None) -> State:
         """One synchronous VTM iteration (Table 1 steps 3-5) over ``pieces`` (default all)."""
         b = np.atleast_2d(b)
-        R = b.shape[0]
-        e = self.ends
         new_u = state.u.copy()
         new_om = state.omega.copy()
         x_local = list(state.x_local)
         todo = self.pieces if pieces is None else pieces
         for j in todo:
-            r = self.split.local_rhs(b, j).copy()
-            mine = self.ends_at[j]
-            for t in mine:                       # eq. 5.8 right-hand side, from eq. 5.6
-                tw = e.twin[t]
-                r[:, e.local[t]] += (state.u[:, tw] - e.Z[t] * state.omega[:, tw]) / e.Z[t]
-            x = self.factor[j].solve(r)          # eq. 5.8 local SPD solve
-            x_local[j] = x
-            for t in mine:                       # current update after eq. 5.8
-                tw = e.twin[t]
-                new_u[:, t] = x[:, e.local[t]]
-                new_om[:, t] = (state.u[:, tw] - new_u[:, t]) / e.Z[t] - state.omega[:, tw]
+            x_local[j] = self.piece_step(j, state.u, state.omega, b, new_u, new_om)
         return State(u=new_u, omega=new_om, x_local=x_local)
+
+    def piece_step(self, j: int, u: np.ndarray, omega: np.ndarray, b: np.ndarray, new_u: np.ndarray,
+                   new_om: np.ndarray) -> np.ndarray:
+        """Table 1 steps 3-5 for subgraph j: reads the twins' pair (u, omega) of the previous
+        iteration from ``u``, ``omega`` and writes its own ends' new pair into ``new_u``,
+        ``new_om``; returns the local solution (R, n_j)."""
+        e = self.ends
+        r = self.split.local_rhs(b, j).copy()
+        mine = self.ends_at[j]
+        for t in mine:                           # eq. 5.8 right-hand side, from eq. 5.6
+            tw = e.twin[t]
+            r[:, e.local[t]] += (u[:, tw] - e.Z[t] * omega[:, tw]) / e.Z[t]
+        x = self.factor[j].solve(r)              # eq. 5.8 local SPD solve
+        for t in mine:                           # current update after eq. 5.8
+            tw = e.twin[t]
+            new_u[:, t] = x[:, e.local[t]]
+            new_om[:, t] = (u[:, tw] - new_u[:, t]) / e.Z[t] - omega[:, tw]
+        return x
 
     def waves_out(self, state: State) -> np.ndarray:
         """Outgoing wave u_e - Z_e omega_e of each end: the left side of eq. 5.6 seen from the twin."""
