@@ -179,13 +179,18 @@ def test_committed_models_are_well_formed():
     import json
     import os
     from paper_0807_1949_gb300 import learned_z
-    for name in ("z_poisson2d-256.json", "z_poisson3d.json"):
+    for name in ("z_poisson2d-256.json", "z_poisson3d.json", "z_poisson3d-wide.json"):
         with open(os.path.join(learned_z.MODELS, name)) as f:
             d = json.load(f)
         p = np.asarray(d["params"])
         assert p.shape == (4801,) and np.all(np.isfinite(p))
         ms = d["median_sweeps"]
-        assert ms["learned"] < ms["z1"] and ms["learned"] < ms["matched"]
+        assert ms["learned"] < ms["z1"] and ms["learned"] < ms.get("matched", np.inf)
+        # the coupled-line rule selected on held-out seeds, and its gain on the test seeds
+        c = d["coupling"]
+        assert c["z_scale"] > 0 and c["gamma"] > 0 and c["select_seeds"] >= 1
+        assert c["median_sweeps"]["coupled"] < c["median_sweeps"]["learned"]
+        assert len(c["eval"]) == d["test_seeds"]
 
 
 @pytest.mark.parametrize("dims,block,sigma", [((32, 32), (16, 16), 0.0), ((12, 11), (4, 5), 1.0),
