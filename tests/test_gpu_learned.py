@@ -7,12 +7,12 @@ must reach the tolerance in far fewer sweeps than Z = 1 and than the paper's mat
 import numpy as np
 import pytest
 
-from paper_0807_1949_gb300 import learned_z
-
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0807_1949_gb300 import learned_z  # noqa: E402  (loads the library; GPU runs only)
 
 
 @pytest.mark.parametrize("seed", [200_001, 200_002])

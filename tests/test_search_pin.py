@@ -9,7 +9,7 @@ import numpy as np
 
 from oracle import evs, features, theory
 from oracle import vtm as ovtm
-from paper_0807_1949_gb300 import inputs, learned_z
+from paper_0807_1949_gb300 import inputs
 
 
 class _OracleEvaluator:
@@ -26,7 +26,9 @@ class _OracleEvaluator:
         return r if math.isfinite(r) else 1e30
 
 
-def test_search_finds_the_spectral_radius_optimum():
+def test_search_finds_the_spectral_radius_optimum(vtmlib):
+    from paper_0807_1949_gb300 import learned_z   # loads the library (built by the vtmlib fixture)
+
     dims, block = (29, 9), (7, 9)          # four subgraphs along x: one line per port (level one)
     A = inputs.grid_poisson(dims, sigma=0.0)
     split = evs.split_grid(A, dims, block)
