@@ -267,3 +267,32 @@ def test_line_pairs_match_oracle_on_fem_split(vtmlib):
     ref = {frozenset((or_key[t], or_key[u])): x for (t, u), x in zip(opr, ow)}
     assert len(got) == len(pr) > 0 and got.keys() == ref.keys()
     assert all(abs(got[k] - ref[k]) <= 1e-15 * abs(ref[k]) for k in ref)
+
+
+def test_header_is_plain_c_and_links(vtmlib, tmp_path):
+    """include/vtm.h is a C ABI: it compiles as C99 (-pedantic) and a C program links against the
+    library and calls it (host-only entry points)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text('#include "vtm.h"\n'
+                   "int main(void) {\n"
+                   "  vtm_setup_opts o = {0}; vtm_partition_spec sp = {0}; (void)o; (void)sp;\n"
+                   "  int64_t out[2];\n"
+                   "  double coords[4] = {0.0, 1.0, 2.0, 3.0};\n"
+                   "  int32_t parts[4];\n"
+                   "  if (vtm_rcb(coords, 4, 1, 2, parts) != VTM_OK) return 2;\n"
+                   "  (void)out;\n"
+                   "  return vtm_version() == 1 && parts[0] != parts[3] ? 0 : 1;\n"
+                   "}\n")
+    libdir = os.path.dirname(vtmlib.library_path())
+    exe = tmp_path / "t"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-lvtm", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
