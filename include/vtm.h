@@ -327,8 +327,9 @@ int vtm_set_rhs(vtm_solver* s, const double* b, int64_t ldb);
 int vtm_reset(vtm_solver* s);
 /* Run `sweeps` synchronous sweeps on the solver's stream (asynchronous): each sweep gathers the
  * incident wave of every line end from its twin (w_in[e] = w_out_prev[twin(e)]), solves every
- * K_j x_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8) with the stored factor, and emits
- * w_out[e] = 2 u_e - w_in[e] (the left side u - Z omega of eq. 5.6 seen from the twin).
+ * K_j x_j = b̃_j + sum_e w_in[e]/Z_e e_c (eq. 5.8) with the stored factor (coupled lines:
+ * b̃_j + P_j Y_j w_in, §7.2), and emits w_out[e] = 2 u_e - w_in[e] (the left side u - Z omega of
+ * eq. 5.6 seen from the twin).
  * PORT form: the first sweeps - 1 sweeps update the ports only; the last one is a band sweep, so
  * the local solutions x_j (vtm_get_copies) always belong to the last sweep. */
 int vtm_iterate(vtm_solver* s, int32_t sweeps);
@@ -336,7 +337,7 @@ int vtm_iterate(vtm_solver* s, int32_t sweeps);
 /* Solve A x = b to max_r ||b_r - A x_r||_2 / ||b_r||_2 <= rtol (FP64 residual on the device,
  * checked every check_every sweeps), from zero waves.  FP32 solvers wrap the sweeps in FP64
  * defect correction.  b, x: host or device, column-major n x nrhs, leading dimension ld.
- * st may be NULL.  Returns VTM_ERR_NOT_CONVERGED after maxit sweeps (x holds the last iterate),
+ * st may be NULL; vtm_solver_get_history returns the residual at every check.  Returns VTM_ERR_NOT_CONVERGED after maxit sweeps (x holds the last iterate),
  * VTM_ERR_DIVERGED on NaN/Inf. */
 typedef struct vtm_stats {
   int32_t sweeps;          /* total sweeps                                        */
