@@ -62,7 +62,7 @@ METRIC = "time to rel. residual 1e-8 (learned-Z batched vs plain VTM) on 1 GB300
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="vtm", choices=["vtm", "reference"])
     p.add_argument("--workload", default="poisson3d-128", choices=list(WORKLOADS))
