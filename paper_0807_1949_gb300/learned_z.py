@@ -21,7 +21,15 @@ Families:
   fem2d          P1 FEM on Delaunay triangulations of 50k-200k points, checkerboard 1e-3/1e3 on 8x8,
                  RCB into ~500-copy subgraphs (the local shape of the 1M-point, 2000-subgraph run)
 
+Coupled lines (§7.2): with --couple the trained model is kept and a coupled-line rule is selected
+on top of it: every line's impedance is scaled by z_scale and every candidate pair of lines of a
+bundle (Partition.line_pairs) gets the conductance gamma |a_ik|; (z_scale, gamma) minimises the
+geometric mean of sweeps to 1e-8 over six seeds (200000..) that neither training nor testing uses,
+and learned vs learned + coupled is reported on the held-out test seeds.  The rule is stored in the
+model file ("coupling") and applied by bench.py --coupling model.
+
 Run:  python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --train 200 --test 60
+      python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --couple --test 8
 """
 from __future__ import annotations
 
