@@ -418,13 +418,16 @@ int vtm_mlp_adam_step(vtm_mlp* m, float lr, float beta1, float beta2, float eps,
  * whose device memory is reserved up front by a framework's caching allocator, or a loop that
  * cannot afford cudaMalloc/cudaFree synchronising the device.  It calls no allocating routine:
  * its only scratch is a 128-byte file-scope device array (2 * VTM_NOALLOC_MAX_RHS doubles) that
- * every device which loads the library holds until the process exits.
+ * every device holds, once it is loaded there (below), until the process exits.
  *   n, rowptr (n+1 int64), col (int32), val (double): A in full CSR, DEVICE memory.
  *   b, x: DEVICE, column-major n x nrhs with leading dimensions ldb, ldx >= n.
  *   rel: DEVICE, nrhs doubles (output).  nrhs in [1, VTM_NOALLOC_MAX_RHS], else VTM_ERR_INVALID.
  * Asynchronous on cuda_stream.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Every call reuses the same array (cleared at the start of each call), so calls that
+ * (cudaGetSymbolAddress) with that device current; under CUDA's default lazy loading that look-up
+ * also loads the array onto the device, which allocates device memory.  vtm_setup performs it for
+ * its device; a caller that never calls vtm_setup makes one warm-up call per device before it
+ * reserves device memory up front, and before any stream capture.  Later calls allocate nothing.
+ * Every call reuses the same array (cleared at the start of each call), so calls that
  * overlap on the GPU — from two streams or two host threads — race and return wrong values:
  * serialise them. */
 int vtm_relative_residual_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,

@@ -165,6 +165,8 @@ int vtm_setup(const vtm_partition* p, const vtm_setup_opts* opts, void* cuda_str
   return guarded([&] {
     if (!out) vtm::fail(VTM_ERR_INVALID, "out is NULL");
     *out = nullptr;
+    // load the allocation-free residual's scratch now, while the caller can still allocate
+    vtm::noalloc_prepare_current_device();
     *out = vtm::create_solver(p, opts, cuda_stream);
     return VTM_OK;
   });

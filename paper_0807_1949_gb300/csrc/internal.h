@@ -17,6 +17,8 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string& msg);
 void set_last_error(const std::string& msg);
+// Puts the allocation-free residual's scratch array on the current device (noalloc.cu).
+void noalloc_prepare_current_device();
 
 }  // namespace vtm
 

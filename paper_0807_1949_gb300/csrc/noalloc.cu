@@ -6,8 +6,14 @@
 // allocator (a raw cudaMalloc there can fail even though the framework still has free blocks), or
 // a latency-critical loop that must not call cudaMalloc/cudaFree because they can synchronise the
 // device.  For them this entry point keeps its only scratch — the per-right-hand-side sums of
-// squares — in a file-scope device array that exists from the moment the library is loaded on a
-// device until the process exits.  The caller passes every input and the output.
+// squares — in a file-scope device array that the device holds from the moment this code is
+// loaded onto it until the process exits.  The caller passes every input and the output.
+//
+// CUDA loads a library's device code lazily by default: the array (and this file's kernel) are
+// put on a device, which allocates device memory, when the first call on that device looks up the
+// array's address.  vtm_setup does that look-up for its device, so a caller that built a solver
+// has nothing left to load; any other caller makes one warm-up call per device before device
+// memory is reserved up front (and before any stream capture).  Later calls allocate nothing.
 #include <mutex>
 #include <string>
 
@@ -50,6 +56,11 @@ __global__ void k_noalloc_finish(int nrhs, const double* __restrict__ sums, doub
 }
 
 }  // namespace
+
+namespace vtm {
+// Loads the array onto the current device and caches its address (called by vtm_setup).
+void noalloc_prepare_current_device() { scratch_for_current_device(); }
+}  // namespace vtm
 
 extern "C" int vtm_relative_residual_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
                                              int32_t nrhs, const double* b, int64_t ldb, const double* x,

@@ -507,15 +507,37 @@ def relative_residual_noalloc(rowptr, col, val, b, x, rel, stream=None):
     """vtm_relative_residual_noalloc on device tensors: rel[r] = ||b_r - A x_r|| / ||b_r||.
 
     For callers that must not allocate device memory at call time; the library uses a fixed
-    128-byte device array as its only scratch.  rowptr (int64), col (int32), val, b, x (float64,
-    shape (nrhs, n)) and rel (float64, nrhs) are CUDA tensors.  Asynchronous on ``stream``.
+    128-byte device array as its only scratch.  rowptr (int64, n + 1), col (int32), val (float64),
+    b and x (float64, shape (nrhs, n) or (n,), contiguous, same shape) and rel (float64, at least
+    nrhs entries) are CUDA tensors on one device; the call runs on that device, asynchronously on
+    ``stream``.  Arguments are checked here so that no kernel reads or writes past a tensor.
     """
+    want = (("rowptr", rowptr, "torch.int64"), ("col", col, "torch.int32"), ("val", val, "torch.float64"),
+            ("b", b, "torch.float64"), ("x", x, "torch.float64"), ("rel", rel, "torch.float64"))
+    for name, t, dt in want:
+        if not hasattr(t, "data_ptr") or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if str(t.dtype) != dt or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt.split('.')[1]} tensor")
+        if t.device != b.device:
+            raise ValueError(f"{name} is on {t.device}, b on {b.device}: all tensors must share one device")
+    if rowptr.dim() != 1 or rowptr.numel() < 2:
+        raise ValueError("rowptr must hold n + 1 >= 2 entries")
     n = int(rowptr.numel()) - 1
+    if col.numel() != val.numel():
+        raise ValueError("col and val must have one entry per stored element")
+    if tuple(x.shape) != tuple(b.shape) or b.dim() not in (1, 2) or b.shape[-1] != n:
+        raise ValueError(f"b and x must both have shape (nrhs, {n}) or ({n},)")
     nrhs = int(b.shape[0]) if b.dim() == 2 else 1
-    _check(_lib.vtm_relative_residual_noalloc(n, C.c_void_p(rowptr.data_ptr()), C.c_void_p(col.data_ptr()),
-                                              C.c_void_p(val.data_ptr()), nrhs, C.c_void_p(b.data_ptr()), n,
-                                              C.c_void_p(x.data_ptr()), n, C.c_void_p(rel.data_ptr()),
-                                              _stream_handle(stream)))
+    if rel.numel() < nrhs:
+        raise ValueError(f"rel holds {rel.numel()} entries, {nrhs} needed")
+    import torch
+
+    with torch.cuda.device(b.device):
+        _check(_lib.vtm_relative_residual_noalloc(n, C.c_void_p(rowptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                                  C.c_void_p(val.data_ptr()), nrhs, C.c_void_p(b.data_ptr()), n,
+                                                  C.c_void_p(x.data_ptr()), n, C.c_void_p(rel.data_ptr()),
+                                                  _stream_handle(stream)))
 
 
 def version() -> int:

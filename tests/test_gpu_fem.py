@@ -5,6 +5,7 @@ import pytest
 from oracle import evs
 from oracle import vtm as ovtm
 from paper_0807_1949_gb300 import inputs
+from test_precision_bounds import TOL_FP16, TOL_FP32  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -42,7 +43,7 @@ def _maps(part, osplit):
     return cmap, np.array(emap)
 
 
-@pytest.mark.parametrize("precision,nrhs,tol", [("fp64", 1, 1e-12), ("fp64", 16, 1e-12), ("fp32", 16, 5e-4)])
+@pytest.mark.parametrize("precision,nrhs,tol", [("fp64", 1, 1e-12), ("fp64", 16, 1e-12), ("fp32", 16, TOL_FP32)])
 def test_fem_sweeps_match_oracle(vtmlib, precision, nrhs, tol):
     fem, part, osplit = _setup(vtmlib, 3000, 12, seed=5)
     b = inputs.rhs_uniform(fem.A.n, nrhs, seed=5)

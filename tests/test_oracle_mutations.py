@@ -159,3 +159,28 @@ def test_dropped_completing_square_term_is_caught(monkeypatch):
 
     monkeypatch.setattr(conformal, "schur_terms", no_tb)
     assert _conformal_pins_fail()
+
+
+@pytest.mark.parametrize("mistake", ["diag_in_coupling", "own_weight_as_twin", "inverse_size_ratio",
+                                     "equal_share_weight"])
+def test_line_feature_mistakes_are_caught(monkeypatch, mistake):
+    """Feature 4 with the copy's own diagonal, feature 5 from the copy instead of its twin,
+    feature 7 as log(n_j / n), feature 1 as a_ii / |O(i)| (an equal share instead of §4 step 3)."""
+    import test_oracle_mlp as M
+    from oracle import features
+    orig = features.line_features
+
+    def broken(split, A):
+        f = orig(split, A).copy()
+        if mistake == "diag_in_coupling":
+            f[:, 4] = np.log(np.exp(f[:, 4]) + np.exp(f[:, 1]))
+        elif mistake == "own_weight_as_twin":
+            f[:, 5] = f[:, 1]
+        elif mistake == "inverse_size_ratio":
+            f[:, 7] = -f[:, 7]
+        else:
+            f[:, 1] = f[:, 0] - f[:, 2]
+        return f
+
+    monkeypatch.setattr(features, "line_features", broken)
+    assert _fails(M.test_line_features_hand_computed) or _fails(M.test_line_features_ragged_subgraph_sizes)
