@@ -41,6 +41,13 @@ WORKLOADS = {
     # large multi-RHS run: 256^3, sigma = 1.5, 4096 subgraphs, 32 right-hand sides per sweep
     "poisson3d-256-r32": dict(kind="grid", dims=(256, 256, 256), block=(16, 16, 16), sigma=1.5, nrhs=32,
                               z="learned:poisson3d-wide", coupling="model", rtol=1e-8),
+    # mid-size multi-RHS case of the same family (512 subgraphs)
+    "poisson3d-128-r32": dict(kind="grid", dims=(128, 128, 128), block=(16, 16, 16), sigma=1.5, nrhs=32,
+                              z="learned:poisson3d-wide", coupling="model", rtol=1e-8),
+    # small case of the multi-RHS kernel for profiler captures: 96^3 in 12^3 blocks (512 subgraphs of
+    # 866 ports, 0.9 GB of port responses > L2, about 3.5 GB on the device)
+    "poisson3d-96b12-r32": dict(kind="grid", dims=(96, 96, 96), block=(12, 12, 12), sigma=1.5, nrhs=32,
+                                z="learned:poisson3d-wide", coupling="model", rtol=1e-8),
     # uneven batching: P1 FEM on the Delaunay triangulation of 1M points, 2000 RCB subgraphs, 16 RHS.
     # The one-level method does not reach 1e-8 here in any practical number of sweeps (contrast 1e6),
     # so a step is a fixed number of sweeps and the line reports the residual it reaches.

@@ -231,18 +231,20 @@ typedef struct vtm_setup_opts {
                               substitution once per batch of sweeps to refresh the interior
                               unknowns; AUTO (0) takes PORT where it moves fewer bytes per sweep,
                               fits in shared memory (nrhs <= 8) and in device memory            */
-  int32_t port_storage;    /* PORT form, FP32 solvers, nrhs <= 8: storage of S_j (VTM_STORE_*):
-                              NATIVE (0) the solver precision; FP16 halves the bytes of a sweep
-                              (each 32 x 32 tile of S_j scaled by its largest entry, FP32
-                              arithmetic; the sweeps then match the FP64 oracle to about 2^-11
-                              per sweep and the FP64
-                              defect correction restores the tolerance; a phase on FP16
-                              responses restarts once its inner residual is below 4 x 2^-11,
-                              and with coupled lines once a check gains less than a factor 2);
-                              FP16_AUTO takes FP16
-                              when the responses exceed 96 MB (streamed from HBM rather than
-                              held in L2), and returns to FP32 for good once a defect-correction
-                              step gains less than a factor 10                                 */
+  int32_t port_storage;    /* PORT form, FP32 solvers: storage of S_j (VTM_STORE_*).
+                              nrhs <= 8: NATIVE (0) the solver precision; FP16 halves the bytes
+                              of a sweep (each 32 x 32 tile of S_j scaled by its largest entry,
+                              FP32 arithmetic; the sweeps then match the FP64 oracle to about
+                              2^-11 per sweep and the FP64 defect correction restores the
+                              tolerance; a phase on FP16 responses restarts once its inner
+                              residual is below 4 x 2^-11, and with coupled lines once a check
+                              gains less than a factor 2); FP16_AUTO takes FP16 when the
+                              responses exceed 96 MB (streamed from HBM rather than held in L2),
+                              and returns to FP32 for good once a defect-correction step gains
+                              less than a factor 10.
+                              nrhs 16 / 32 (tensor cores): S_j / sigma_j is kept as fp16 pairs
+                              hi + lo (about 2^-22 relative); NATIVE and FP16_AUTO stream both
+                              halves, FP16 streams the hi half only (half the bytes, 2^-11)    */
   /* Coupled lines (§7.2, Thm 7.1).  Lines that join the same two subgraphs form a bundle; a
    * conductance y_p >= 0 between two lines t, t' of one bundle makes the bundle's admittance
    * Y = Z^{-1} = diag(1/Z_t) + sum_p y_p (e_t - e_t')(e_t - e_t')^T, symmetric positive definite,
@@ -293,7 +295,7 @@ typedef struct vtm_solver_info {
   int32_t sweep_variant;       /* 0: one CTA works each block step in turn; 1: pipelined (warp 0
                                   finishes block k while the others prepare block k+1)        */
   int32_t sweep_form;          /* VTM_FORM_BAND or VTM_FORM_PORT (after AUTO was resolved)    */
-  int64_t port_bytes;          /* PORT: bytes of the stored port responses S_j                */
+  int64_t port_bytes;          /* PORT: bytes of the port responses S_j one sweep streams     */
   double port_setup_ms;        /* PORT: device time of computing S_j (unit-source solves)     */
   double port_sweep_ms;        /* PORT: device time of one port-form sweep                    */
   int64_t nports;              /* port copies (copies with at least one line end)             */

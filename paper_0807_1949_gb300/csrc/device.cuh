@@ -41,8 +41,8 @@ struct PieceDesc {
   int32_t end_off;     // first (sorted) line end of the piece
   int32_t nends;
   int64_t row_off;     // first padded row of the piece in per-row arrays (sum of earlier n_pad)
-  int64_t s_off;       // first 32 x 32 tile (port.cu) or 128 x 32 chunk (port_tc.cu) of S_j
-  int64_t v_off;       // first 32 x 32 chunk of the piece in the port-vector scratch (port_tc.cu)
+  int64_t s_off;       // first 32 x 32 tile (port.cu) or 128 x 128 FP32 setup block (port_tc.cu) of S_j
+  int64_t h_off;       // port_tc.cu: byte offset of the piece's fp16 port-response blocks
 };
 
 // ------------------------------------------------------------------ PTX wrappers (sm_90+)

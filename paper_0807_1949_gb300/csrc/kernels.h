@@ -97,9 +97,13 @@ cudaError_t launch_port_to_half(const PieceDesc* pieces, int npieces, const floa
 
 // Tensor-core port-response sweep for 16 / 32 right-hand sides (port_tc.cu), FP32 solvers.
 struct PortTCArgs {
-  const PieceDesc* pieces;
-  const float* S;              // 128 x 32 chunks of S_j (whole matrix), tensor-core layout
-  float* sglob;                // port-vector scratch: s^T in 32 x 32 chunks
+  const PieceDesc* pieces;     // subgraphs of the launch (largest first); CTA c takes c, c + grid, ...
+  int npieces;
+  const unsigned char* S16;    // lower block triangle of S_j / sigma_j as fp16 hi / lo panels (h_off)
+  const float* sig_s;          // sigma_j per subgraph of the launch
+  unsigned char* scratch;      // per CTA two slots of n4max s^T tiles (R x 512 bytes each)
+  int n4max;                   // most 128-port super-rows of a subgraph
+  int tmem_cols;               // tensor-memory columns per CTA (power of two >= n4max R)
   const float* ubase;          // ports x R
   const float* wprev;          // ends x R
   float* wnext;
@@ -109,17 +113,18 @@ struct PortTCArgs {
   CoupleRef<float> cpl;        // coupled lines (cpl.ptr == nullptr: none)
   int* status;
   long wait_limit;
-  const int2* items;           // (subgraph, 128-port super-row) per CTA of the product kernel
 };
 
-int64_t port_blocks_tc(int nports);       // 128 x 32 S chunks of one subgraph
-int64_t port_vec_chunks_tc(int nports);   // 32 x 32 s^T chunks of one subgraph
-size_t port_tc_smem_bytes();
+int64_t port_f16_bytes(int nports);   // fp16 hi / lo blocks of one subgraph (1 KB multiple)
+int64_t port_f32_blocks(int nports);  // 128 x 128 FP32 blocks of the lower triangle (setup)
+size_t port_tc_smem_bytes(int R, bool lo);
 cudaError_t port_tc_configure(int R);
-// Two launches: the port vectors (one CTA per subgraph), then the product (one CTA per item).
-cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, int nitems, cudaStream_t st);
-cudaError_t launch_gather_port_response_tc(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs,
-                                           int b, const float* xc, float* S, cudaStream_t st);
+// One persistent launch per sweep (grid <= SMs); lo = use the lo half of S_j (FP32-accurate).
+cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, bool lo, int grid, cudaStream_t st);
+cudaError_t launch_gather_port_blocks(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs, int b,
+                                      const float* xc, float* S32, cudaStream_t st);
+cudaError_t launch_port_blocks_to_f16(const PieceDesc* pieces, int npieces, const float* S32, unsigned char* S16,
+                                      float* sig, cudaStream_t st);
 
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;

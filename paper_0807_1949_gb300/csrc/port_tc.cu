@@ -1,53 +1,71 @@
 // Port-response sweep for 16 or 32 right-hand sides on the 5th-generation tensor cores.
 //
 // Per subgraph the sweep needs y = S_j s (then u = u_base + y, w_out = 2u - w_in; see port.cu for
-// the method).  With R = 16/32 columns this is a dense matrix product, so it runs as tcgen05.mma
-// (kind::tf32, FP32 accumulation in tensor memory), both operands K-major:
+// the method).  With R = 16/32 columns this is a dense product, run as tcgen05.mma (kind::f16,
+// FP32 accumulation in tensor memory).
 //
-//  * S_j is stored whole (both triangles, FP32) as 128 x 32 chunks (I, c): ports 128 I .. 128 I +
-//    127 by ports 32 c .. 32 c + 31, in the 128-byte-swizzled K-major layout the tensor core reads
-//    (rows of 128 bytes, 16-byte units XOR-ed with the row index mod 8, 8-row groups 1024 bytes
-//    apart), the chunks of a row of super-blocks contiguous.  A symmetric half would need the
-//    transposed operand (MN-major), which this build does not use for TF32.
-//  * Three TF32 products keep FP32 accuracy (the split of Ootomo and Yokota, "Recovering single
-//    precision accuracy from Tensor Cores while surpassing the FP32 theoretical peak performance",
-//    2022): with hi(x) the TF32 truncation of x and lo(x) = x - hi(x) (exact in FP32),
-//    S s ~ hi(S) hi(s) + hi(S) lo(s) + lo(S) hi(s).  hi(S) is what the tensor core reads from the
-//    FP32 chunk itself; lo(S) is formed in shared memory by six converter warps; hi(s) and lo(s)
-//    are written by the CTA to a global scratch (sᵀ: 32 columns x ports, zero padding), 2 x 4 KB
-//    per 32 ports.  The dropped lo(S) lo(s) term and the TF32 truncation of the lo parts are
-//    below 2^-21 relative to |S||s|.
-//  * Chunk (I, c) adds S_Ic s_c to y_I: 3 x 4 MMAs of M = 128, N = 32, K = 8.  y lives in tensor
-//    memory: 128 lanes (one port each) x 32 columns per super-row, up to 16 super-rows (2048
-//    ports) in 512 columns.
+// Storage of S_j.  S_j is symmetric (the open-circuit impedance matrix of Def. 7.1 over all ports,
+// the S of eq. A3.3), so only its lower block triangle is kept: 128 x 128 blocks (I, J), J <= I,
+// row by row.  Block (I, J) serves two products: y_I += S_IJ s_J reads it K-major and
+// y_J += S_IJ^T s_I reads the same bytes as an MN-major (transposed) operand.  Each block is four
+// 128-byte-swizzled panels [hi, cols 0-63][hi, cols 64-127][lo, 0-63][lo, 64-127] of h_I rows
+// (rows of 128 bytes, 16-byte units XOR-ed with the row mod 8, 8-row groups 1024 bytes apart);
+// h_I = 128 except for the last super-row, whose height is its port count rounded up to 16.  The
+// values are S_j / sigma_j with sigma_j the power of two at or above max |S_j|, hi = fp16(x) and
+// lo = fp16(x - hi), so hi + lo keeps about 22 significant bits.  Transposed fp16 operands work on
+// this tensor core; kind::tf32 with the same MN-major descriptor returns zeros, which is why the
+// storage is fp16 pairs and not FP32.
 //
-// Two launches per sweep.  k_port_vec_tc (one CTA per subgraph) writes hi(s) and lo(s).  Then
-// k_port_sweep_tc works on items (subgraph, 128-port super-row I), 256 threads, two CTAs per SM,
-// warp-specialised over a 3-stage bulk-copy ring (S chunk + hi(s) + lo(s) = 24 KB) and a 2-buffer
-// lo(S) ring: warp 0 issues the bulk copies (mbarrier complete_tx), warps 2-7 form lo(S), warp 1
-// issues the MMAs into 32 tensor-memory columns and releases stages and lo buffers with
-// tcgen05.commit; then every warp reads its quarter of the 128 lanes and half of the columns and
-// writes the waves.  Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its
-// copies and MMAs finish, frees its tensor memory and returns.
+// Products.  The port vector s = sum_e w_in[e] / Z_e (plus coupling currents) is split the same
+// way per subgraph and column: s / sigma_r = s_hi + s_lo (sigma_r a power of two).  Per block and
+// K step: hi(S) s_hi + hi(S) s_lo (+ lo(S) s_hi when the lo half is used), FP32 accumulation.
+// With the lo half the products keep about 2^-21 of |S||s| (the dropped lo(S) s_lo term and the
+// fp16 roundings); without it (FP16 storage, half the bytes) S carries fp16 rounding, 2^-11 of
+// sigma_j, and the FP64 defect correction absorbs it as for the FP16 tiles of port.cu.
+//
+// One persistent kernel per sweep, one CTA per SM looping over subgraphs, 320 threads:
+//  * warp 0 streams blocks (and the s_J tile of off-diagonal blocks) through a ring of bulk copies
+//    (mbarrier complete_tx), and the s_I tile of each super-row into a 2-slot row buffer;
+//  * warp 1 issues the MMAs: y_I at tensor-memory columns I R .. I R + R - 1, lane = port, all
+//    super-rows of a subgraph held at once (n4 R <= 512 columns); tcgen05.commit releases stages,
+//    row buffers and, after the last block, hands the accumulators to the epilogue;
+//  * warps 2-9 compute the next subgraph's s (two passes over the incoming waves: the column
+//    maxima, then the split values written to a per-CTA global scratch slot that stays in L2), then
+//    run the epilogue of the current one: tcgen05.ld of the accumulators, u = u_base +
+//    sigma_j sigma_r y, w_out[e] = 2u - w_in[e].
+// Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its copies and MMAs
+// finish, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace vtm {
 
 namespace {
 
-constexpr int kTB = 128;                        // ports per super-row (MMA M)
-constexpr int kTN = 32;                         // accumulator columns per super-row (MMA N)
-constexpr int kKC = 32;                         // ports per K chunk
-constexpr uint32_t kChunkBytes = kTB * kKC * 4; // S chunk: 128 x 32 FP32
-constexpr uint32_t kVecBytes = kTN * kKC * 4;   // s chunk: 32 columns x 32 ports
-// bulk-copy stage: S chunk | hi(s) | lo(s); lo(S) goes to a separate ring of kLoBufs buffers
-constexpr uint32_t kStageBytes = kChunkBytes + 2 * kVecBytes;
-constexpr int kTcStages = 3;
-constexpr int kLoBufs = 2;
-constexpr uint32_t kTmemCols = 32;              // one super-row of accumulators per CTA
-constexpr int kTcThreads = 256;
-constexpr int kConvWarps = 6;                   // warps 2..7
-constexpr uint32_t kHiMask = 0xFFFFE000u;       // TF32: sign, exponent, 10 mantissa bits
+constexpr int kSB = 128;                // ports per super-block (MMA M; K extent of a block)
+constexpr int kTcThreads = 320;         // warp 0 copies, warp 1 MMA, warps 2..9 vectors / epilogue
+constexpr int kVecThreads = 256;
+constexpr int kVecBar = 1;              // named barrier of the vector warps
+
+__host__ __device__ __forceinline__ int n_super(int nports) { return (nports + kSB - 1) / kSB; }
+
+// Stored rows of super-row I (a multiple of 16).
+__host__ __device__ __forceinline__ int sb_rows(int nports, int I) {
+  const int n4 = n_super(nports);
+  if (I < n4 - 1) return kSB;
+  return ((nports - kSB * I) + 15) & ~15;
+}
+
+// Byte offset of block (I, J) from the subgraph's first block (hi + lo: 512 bytes per row).
+__host__ __device__ __forceinline__ int64_t blk_off(int nports, int I, int J) {
+  return (int64_t)I * (I + 1) / 2 * (kSB * 512) + (int64_t)J * sb_rows(nports, I) * 512;
+}
+
+// Byte offset of (row, fp16 column 0..63) inside a 128-byte-swizzled panel.
+__host__ __device__ __forceinline__ uint32_t swz16(int row, int col) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((col * 2) >> 4) ^ (row & 7)) << 4) + ((col * 2) & 15));
+}
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -56,25 +74,33 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 // Shared-memory matrix descriptor: start address, leading / stride byte offsets (16-byte units),
-// descriptor version 1, 128-byte swizzle.
+// descriptor version 1, 128-byte swizzle.  K-major operands: LBO unused, SBO = 1024 (8-row
+// groups).  MN-major operands: LBO = the stride between 64-element groups along M (one panel),
+// SBO = 1024 (8-row groups along K).  The start address sits in the low 14 bits (16-byte units),
+// so a descriptor of address + d is the descriptor of address plus d / 16.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor, kind::tf32: FP32 accumulator, A and B TF32, M = 128, N = 32; a_mn / b_mn
-// select MN-major operands.
-__host__ __device__ constexpr uint32_t idesc_tf32(bool a_mn, bool b_mn) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTB >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 accumulator, A and B fp16, M = 128, N = R; a_mn selects
+// an MN-major A.
+__host__ __device__ constexpr uint32_t idesc_f16(bool a_mn, int N) {
+  return (1u << 4) | ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kSB >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
+}
+
+// The same with the accumulate flag known to be set.
+__device__ __forceinline__ void mma_f16_acc(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc) {
+  asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(dtmem), "l"(ad), "l"(bd), "r"(idesc)
+               : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -85,7 +111,29 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void vec_sync() { asm volatile("bar.sync %0, %1;" ::"n"(kVecBar), "n"(kVecThreads) : "memory"); }
+
+template <int R>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[R]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -98,147 +146,216 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & kHiMask); }
+// Ring geometry of one variant: bytes of a stage's S block and s tile, stage count.
+template <int R, bool LO>
+struct Ring {
+  static constexpr uint32_t kBlk = kSB * (LO ? 512u : 256u);  // largest S block moved per stage
+  static constexpr uint32_t kVec = (uint32_t)R * 512u;        // s tile: hi / lo x 2 panels of R rows
+  static constexpr uint32_t kStage = kBlk + kVec;
+  static constexpr int kStages = LO ? 2 : 3;
+  static constexpr uint32_t kBytes = 1024 + 1024 + kStages * kStage + 2 * kVec;
+};
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+// The MMAs of one block (I, J) of height h: y_I += S_IJ s_J (A K-major: the block's two panels
+// along K; B = the s tile bv) and, off the diagonal, y_J += S_IJ^T s_I (A MN-major: M over the two
+// panels at LBO = one panel, K = the block's rows in steps of 16; B = the row tile si).  Products
+// per K step: hi(S) s_hi, hi(S) s_lo and, with LO, lo(S) s_hi.  Descriptors are formed once and
+// advanced by address offsets (16-byte units in the low bits); with kFull the panel stride is the
+// compile-time 16 KB of a full-height block and every loop unrolls.
+template <int R, bool LO, bool kFull>
+__device__ __forceinline__ void block_mmas(uint32_t sb, uint32_t bv, uint32_t si, int h, uint32_t dI, uint32_t dJ,
+                                           bool first, bool transposed) {
+  constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
+  constexpr uint32_t vpan = (uint32_t)R * 128 / 16;           // s tile panel, 16-byte units
+  const uint32_t panel = kFull ? (uint32_t)kSB * 128 : (uint32_t)h * 128;
+  const uint32_t pan = panel / 16;
+  const uint64_t aK = sdesc(sb, 16, 1024), aT = sdesc(sb, panel, 1024);
+  const uint64_t bB = sdesc(bv, 16, 1024), bR = sdesc(si, 16, 1024);
+#pragma unroll
+  for (int kk = 0; kk < kSB / 16; ++kk) {
+    const uint32_t p = kk >> 2, o = (kk & 3) * 2;               // panel, 32-byte step in 16-byte units
+    const uint64_t aH = aK + p * pan + o, bH = bB + p * vpan + o, bL = bB + (2 + p) * vpan + o;
+    if (kk == 0) mma_f16(dI, aH, bH, idK, first ? 0u : 1u);
+    else mma_f16_acc(dI, aH, bH, idK);
+    mma_f16_acc(dI, aH, bL, idK);
+    if constexpr (LO) mma_f16_acc(dI, aK + (2 + p) * pan + o, bH, idK);
+  }
+  if (!transposed) return;
+  const int nk = kFull ? kSB / 16 : h / 16;
+#pragma unroll
+  for (int kk = 0; kk < kSB / 16; ++kk) {
+    if (!kFull && kk >= nk) break;
+    const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+    const uint64_t aH = aT + kk * 128, bH = bR + p * vpan + o, bL = bR + (2 + p) * vpan + o;  // 2048 B per kk
+    mma_f16_acc(dJ, aH, bH, idT);
+    mma_f16_acc(dJ, aH, bL, idT);
+    if constexpr (LO) mma_f16_acc(dJ, aT + 2 * pan + kk * 128, bH, idT);
+  }
 }
 
-// Byte offset of (row, 4-byte column) inside a 128-byte-swizzled block of 128-byte rows.
-__host__ __device__ __forceinline__ uint32_t swz(int row, int col) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((col * 4) >> 4) ^ (row & 7)) << 4) + ((col * 4) & 15));
+// s_p for one port and all R columns: sum over its ends of w_in / Z_e plus the coupling currents.
+template <int R>
+__device__ __forceinline__ void port_vector(const PortTCArgs& a, int port, float (&v)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = 0.f;
+  const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
+  for (int e = e0; e < e1; ++e) {
+    const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+    const float iz = a.invz[e];
+#pragma unroll
+    for (int k = 0; k < R / 4; ++k) {
+      const float4 x = w[k];
+      v[4 * k] += x.x * iz;
+      v[4 * k + 1] += x.y * iz;
+      v[4 * k + 2] += x.z * iz;
+      v[4 * k + 3] += x.w * iz;
+    }
+  }
+  if (a.cpl.ptr)
+    for (int k = a.cpl.ptr[port]; k < a.cpl.ptr[port + 1]; ++k) {
+      const float yk = a.cpl.y[k];
+      const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
+#pragma unroll
+      for (int kk = 0; kk < R / 4; ++kk) {
+        const float4 x = w[kk];
+        v[4 * kk] += yk * x.x;
+        v[4 * kk + 1] += yk * x.y;
+        v[4 * kk + 2] += yk * x.z;
+        v[4 * kk + 3] += yk * x.w;
+      }
+    }
 }
 
 }  // namespace
 
-int64_t port_blocks_tc(int nports) {
-  const int64_t n4 = (nports + kTB - 1) / kTB, nkc = (nports + kKC - 1) / kKC;
-  return n4 * nkc;
+int64_t port_f16_bytes(int nports) {
+  if (nports <= 0) return 0;
+  const int n4 = n_super(nports);
+  const int64_t b = blk_off(nports, n4 - 1, 0) + (int64_t)n4 * sb_rows(nports, n4 - 1) * 512;
+  return (b + 1023) & ~int64_t(1023);
 }
 
-int64_t port_vec_chunks_tc(int nports) { return 2 * ((nports + kKC - 1) / kKC); }
+int64_t port_f32_blocks(int nports) {
+  const int64_t n4 = n_super(nports);
+  return n4 * (n4 + 1) / 2;
+}
 
-size_t port_tc_smem_bytes() { return 1024 + 1024 + (size_t)kTcStages * kStageBytes + (size_t)kLoBufs * kChunkBytes; }
+size_t port_tc_smem_bytes(int R, bool lo) {
+  if (R == 16) return lo ? Ring<16, true>::kBytes : Ring<16, false>::kBytes;
+  return lo ? Ring<32, true>::kBytes : Ring<32, false>::kBytes;
+}
 
-// S_j columns cc = b * Rs + r from unit-source solves into the chunk layout (whole matrix).
-__global__ void k_gather_port_response_tc(const PieceDesc* __restrict__ pieces, const int32_t* __restrict__ port_local,
-                                          int Rs, int b, const float* __restrict__ xc, float* __restrict__ S) {
+// S_j columns cc = b * Rs + r from unit-source solves into FP32 128 x 128 row-major blocks of the
+// lower block triangle (block (I, J) at s_off + I (I + 1) / 2 + J; diagonal blocks whole).
+__global__ void k_gather_port_blocks(const PieceDesc* __restrict__ pieces, const int32_t* __restrict__ port_local,
+                                     int Rs, int b, const float* __restrict__ xc, float* __restrict__ S32) {
   const PieceDesc pd = pieces[blockIdx.x];
-  const int nkc = (pd.nports + kKC - 1) / kKC;
   for (int i = threadIdx.x; i < pd.nports * Rs; i += blockDim.x) {
     const int q = i / Rs, r = i % Rs;
     const int cc = b * Rs + r;
     if (cc >= pd.nports) continue;
-    const int64_t chunk = pd.s_off + (int64_t)(q / kTB) * nkc + cc / kKC;
-    S[chunk * (kChunkBytes / 4) + swz(q % kTB, cc % kKC) / 4] =
+    const int I = q / kSB, J = cc / kSB;
+    if (J > I) continue;
+    const int64_t blk = pd.s_off + (int64_t)I * (I + 1) / 2 + J;
+    S32[blk * (kSB * kSB) + (q % kSB) * kSB + cc % kSB] =
         xc[((size_t)pd.copy_off + port_local[pd.port_off + q]) * Rs + r];
   }
 }
 
-// hi(s), lo(s) per subgraph: s = sum_e w_in[e] / Z_e per port and column as sᵀ chunks (row =
-// column r of the right-hand side, 128 bytes = 32 ports), zero padding.  Warp w takes chunks w,
-// w + 8, ...; lane = port of the chunk, so each store of a column writes one 128-byte row and
-// the R wave loads of a lane are independent.
-template <int R>
-__global__ void __launch_bounds__(kTcThreads) k_port_vec_tc(const PortTCArgs a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const PieceDesc pd = a.pieces[blockIdx.x];
-  const int np = pd.nports;
-  const int nkc = (np + kKC - 1) / kKC;
-  float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
-  for (int c = warp; c < nkc; c += kTcThreads / 32) {
-    const int p = c * kKC + lane;
-    int e0 = 0, e1 = 0, tw = 0;
-    float iz = 0.f;
-    if (p < np) {
-      e0 = a.port_end_ptr[pd.port_off + p];
-      e1 = a.port_end_ptr[pd.port_off + p + 1];
-      tw = a.twin[e0];
-      iz = a.invz[e0];
-    }
-    float v[kTN];
-    const float4* w0 = reinterpret_cast<const float4*>(a.wprev + (size_t)tw * R);
+// FP32 blocks -> fp16 hi / lo panels of the sweep's layout; sigma_j = 2^e >= max |S_j|.
+__global__ void k_port_blocks_to_f16(const PieceDesc* __restrict__ pieces, const float* __restrict__ S32,
+                                     unsigned char* __restrict__ S16, float* __restrict__ sig) {
+  const PieceDesc pd = pieces[blockIdx.x];
+  const int P = pd.nports;
+  if (P == 0) return;
+  const int n4 = n_super(P);
+  const int64_t nblk = (int64_t)n4 * (n4 + 1) / 2;
+  const float* src = S32 + pd.s_off * (kSB * kSB);
+  float m = 0.f;
+  for (int64_t k = threadIdx.x; k < nblk * kSB * kSB; k += blockDim.x) m = fmaxf(m, fabsf(src[k]));
+  __shared__ float red[32];
 #pragma unroll
-    for (int k = 0; k < R / 4; ++k) {
-      const float4 x = (e1 > e0) ? w0[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-      v[4 * k] = x.x * iz;
-      v[4 * k + 1] = x.y * iz;
-      v[4 * k + 2] = x.z * iz;
-      v[4 * k + 3] = x.w * iz;
-    }
-#pragma unroll
-    for (int r = R; r < kTN; ++r) v[r] = 0.f;
-    for (int e = e0 + 1; e < e1; ++e) {
-      const float* we = a.wprev + (size_t)a.twin[e] * R;
-      const float ize = a.invz[e];
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] += we[r] * ize;
-    }
-    if (a.cpl.ptr && p < np)
-      for (int k = a.cpl.ptr[pd.port_off + p]; k < a.cpl.ptr[pd.port_off + p + 1]; ++k) {
-        const float yk = a.cpl.y[k];
-        const float4* wt = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
-#pragma unroll
-        for (int kk = 0; kk < R / 4; ++kk) {
-          const float4 x = wt[kk];
-          v[4 * kk] += yk * x.x;
-          v[4 * kk + 1] += yk * x.y;
-          v[4 * kk + 2] += yk * x.z;
-          v[4 * kk + 3] += yk * x.w;
-        }
+  for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+    int e = 0;
+    if (mm > 0.f) frexpf(mm, &e);
+    red[0] = ldexpf(1.f, e);  // power of two >= mm (1 for an all-zero matrix)
+    sig[blockIdx.x] = red[0];
+  }
+  __syncthreads();
+  const float inv = 1.f / red[0];
+  unsigned char* dst = S16 + pd.h_off;
+  for (int I = 0; I < n4; ++I) {
+    const int h = sb_rows(P, I);
+    for (int J = 0; J <= I; ++J) {
+      const float* blk = src + ((int64_t)I * (I + 1) / 2 + J) * (kSB * kSB);
+      unsigned char* o = dst + blk_off(P, I, J);
+      const uint32_t panel = (uint32_t)h * 128;
+      for (int k = threadIdx.x; k < h * kSB; k += blockDim.x) {
+        const int row = k / kSB, col = k % kSB;
+        const float x = blk[k] * inv;
+        const __half hi = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(hi));
+        const uint32_t off = (uint32_t)(col / 64) * panel + swz16(row, col % 64);
+        *reinterpret_cast<__half*>(o + off) = hi;
+        *reinterpret_cast<__half*>(o + 2 * panel + off) = lo;
       }
-    float* hi_c = sg + (size_t)(2 * c) * (kVecBytes / 4);
-    float* lo_c = hi_c + kVecBytes / 4;
-#pragma unroll
-    for (int r = 0; r < kTN; ++r) {
-      const float hi = tf32_hi(v[r]);
-      hi_c[swz(r, lane) / 4] = hi;
-      lo_c[swz(r, lane) / 4] = v[r] - hi;
     }
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kTcThreads, 2) k_port_sweep_tc(const PortTCArgs a) {
+template <int R, bool LO>
+__global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArgs a) {
+  using G = Ring<R, LO>;
+  constexpr int S = G::kStages;
   extern __shared__ unsigned char smem_raw[];
   __shared__ volatile int abort_flag;
+  __shared__ volatile int vstop_a, vstop_b;
+  __shared__ float red[8][R];
+  __shared__ float ssig[2][R];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [kTcStages] bulk copies landed
-  uint64_t* empty = full + kTcStages;                // [kTcStages] MMAs done reading the stage
-  uint64_t* conv = empty + kTcStages;                // [kLoBufs] lo(S) written
-  uint64_t* lofree = conv + kLoBufs;                 // [kLoBufs] MMAs done reading lo(S)
-  uint64_t* done = lofree + kLoBufs;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [S] block (+ s_J tile) landed
+  uint64_t* empty = full + S;                        // [S] MMAs done with the stage
+  uint64_t* rowfull = empty + S;                     // [2] s_I tile landed
+  uint64_t* rowempty = rowfull + 2;                  // [2] MMAs done with the s_I tile
+  uint64_t* sready = rowempty + 2;                   // [2] scratch slot written
+  uint64_t* accfull = sready + 2;                    // accumulators complete
+  uint64_t* accempty = accfull + 1;                  // accumulators read by the epilogue
+  uint64_t* done = accempty + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   const uint32_t stage0 = base + 1024;
-  const uint32_t lo0 = stage0 + kTcStages * kStageBytes;
-  unsigned char* stage0_ptr = sm + 1024;
-  unsigned char* lo0_ptr = stage0_ptr + kTcStages * kStageBytes;
+  const uint32_t row0 = stage0 + S * G::kStage;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int2 item = a.items[blockIdx.x];
-  const PieceDesc pd = a.pieces[item.x];
-  const int I = item.y;
-  const int np = pd.nports;
-  const int nkc = (np + kKC - 1) / kKC;
+  const int npc = (a.npieces - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // subgraphs of this CTA
+  const size_t slot_bytes = (size_t)a.n4max * G::kVec;
+  unsigned char* scratch = a.scratch + (size_t)blockIdx.x * 2 * slot_bytes;
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int s = 0; s < kLoBufs; ++s) {
-      mbar_init(&conv[s], kConvWarps);
-      mbar_init(&lofree[s], 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&rowfull[s], 1);
+      mbar_init(&rowempty[s], 1);
+      mbar_init(&sready[s], 1);
     }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, 1);
     mbar_init(done, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(kTmemCols)
+                 "r"(a.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -246,160 +363,267 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_port_sweep_tc(const PortTCArg
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const float* sg = a.sglob + pd.v_off * (kVecBytes / 4);
 
   if (warp == 0) {
-    // ---- producer: chunk c of super-row I and its port-vector chunk c
+    // ---- producer: per subgraph, per super-row the s_I tile, per block the block and s_J tile
     if (lane == 0) {
-      const float* Sp = a.S + (pd.s_off + (int64_t)I * nkc) * (kChunkBytes / 4);
-      int c = 0;
-      for (; c < nkc && !abort_flag; ++c) {
-        const int st = c % kTcStages;
-        if (c >= kTcStages &&
-            !mbar_wait_bounded(&empty[st], (uint32_t)(((c / kTcStages) - 1) & 1), a.wait_limit)) {
+      int64_t gblk = 0, grow = 0;
+      for (int k = 0; k < npc && !abort_flag; ++k) {
+        const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
+        const int P = pd.nports, n4 = n_super(P);
+        if (!mbar_wait_bounded(&sready[k & 1], (uint32_t)((k >> 1) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
         }
-        const uint32_t sb = stage0 + st * kStageBytes;
-        mbar_arrive_expect_tx(&full[st], kStageBytes);
-        bulk_g2s(sb, Sp + (int64_t)c * (kChunkBytes / 4), kChunkBytes, &full[st]);
-        bulk_g2s(sb + kChunkBytes, sg + (size_t)(2 * c) * (kVecBytes / 4), 2 * kVecBytes, &full[st]);
+        const unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
+        const unsigned char* Sp = a.S16 + pd.h_off;
+        for (int I = 0; I < n4 && !abort_flag; ++I) {
+          const int rb = (int)(grow & 1);
+          if (grow >= 2 && !mbar_wait_bounded(&rowempty[rb], (uint32_t)(((grow >> 1) - 1) & 1), a.wait_limit)) {
+            abort_flag = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&rowfull[rb], G::kVec);
+          bulk_g2s(row0 + rb * G::kVec, slot + (size_t)I * G::kVec, G::kVec, &rowfull[rb]);
+          ++grow;
+          const int h = sb_rows(P, I);
+          const uint32_t sbytes = (uint32_t)h * (LO ? 512u : 256u);
+          for (int J = 0; J <= I; ++J) {
+            const int st = (int)(gblk % S);
+            if (gblk >= S && !mbar_wait_bounded(&empty[st], (uint32_t)(((gblk / S) - 1) & 1), a.wait_limit)) {
+              abort_flag = 1;
+              break;
+            }
+            const uint32_t sb = stage0 + st * G::kStage;
+            mbar_arrive_expect_tx(&full[st], sbytes + (J < I ? G::kVec : 0u));
+            bulk_g2s(sb, Sp + blk_off(P, I, J), sbytes, &full[st]);
+            if (J < I) bulk_g2s(sb + G::kBlk, slot + (size_t)J * G::kVec, G::kVec, &full[st]);
+            ++gblk;
+          }
+        }
       }
-      // the copies of the last stages must land before the shared memory can go away
-      for (int c2 = (c > kTcStages ? c - kTcStages : 0); c2 < c; ++c2)
-        mbar_wait_bounded(&full[c2 % kTcStages], (uint32_t)((c2 / kTcStages) & 1), kDrainPolls);
+      // copies still in flight must land before the shared memory can go away
+      for (int64_t g = (gblk > S ? gblk - S : 0); g < gblk; ++g)
+        mbar_wait_bounded(&full[g % S], (uint32_t)((g / S) & 1), kDrainPolls);
+      for (int64_t g = (grow > 2 ? grow - 2 : 0); g < grow; ++g)
+        mbar_wait_bounded(&rowfull[g & 1], (uint32_t)((g >> 1) & 1), kDrainPolls);
     }
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t kId = idesc_tf32(false, false);  // both operands K-major
-      for (int c = 0; c < nkc; ++c) {
-        const int st = c % kTcStages, lb = c % kLoBufs;
-        // conv[lb] for chunk c implies full[st] (the converters waited for it)
-        if (abort_flag || !mbar_wait_bounded(&conv[lb], (uint32_t)((c / kLoBufs) & 1), a.wait_limit)) {
+      int64_t gblk = 0, grow = 0;
+      for (int k = 0; k < npc && !abort_flag; ++k) {
+        const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
+        const int P = pd.nports, n4 = n_super(P);
+        if (k > 0 && !mbar_wait_bounded(accempty, (uint32_t)((k - 1) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t sb = stage0 + st * kStageBytes;
-        const uint32_t sS = sb, sL = lo0 + lb * kChunkBytes, vH = sb + kChunkBytes, vL = vH + kVecBytes;
-#pragma unroll
-        for (int kk = 0; kk < kKC / 8; ++kk) {
-          const uint64_t aH = sdesc(sS + kk * 32, 16, 1024), aL = sdesc(sL + kk * 32, 16, 1024);
-          const uint64_t bH = sdesc(vH + kk * 32, 16, 1024), bL = sdesc(vL + kk * 32, 16, 1024);
-          mma_tf32(tmem, aH, bH, kId, (c > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem, aH, bL, kId, 1u);
-          mma_tf32(tmem, aL, bH, kId, 1u);
+        for (int I = 0; I < n4 && !abort_flag; ++I) {
+          const int rb = (int)(grow & 1);
+          if (!mbar_wait_bounded(&rowfull[rb], (uint32_t)((grow >> 1) & 1), a.wait_limit)) {
+            abort_flag = 1;
+            break;
+          }
+          const uint32_t si = row0 + rb * G::kVec;
+          const int h = sb_rows(P, I);
+          for (int J = 0; J <= I; ++J) {
+            const int st = (int)(gblk % S);
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((gblk / S) & 1), a.wait_limit)) {
+              abort_flag = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = stage0 + st * G::kStage;
+            const uint32_t bv = (J == I) ? si : sb + G::kBlk;
+            const uint32_t dI = tmem + (uint32_t)(I * R), dJ = tmem + (uint32_t)(J * R);
+            if (h == kSB) block_mmas<R, LO, true>(sb, bv, si, h, dI, dJ, J == 0, J < I);
+            else block_mmas<R, LO, false>(sb, bv, si, h, dI, dJ, J == 0, J < I);
+            mma_commit(&empty[st]);
+            ++gblk;
+          }
+          mma_commit(&rowempty[rb]);
+          ++grow;
         }
-        mma_commit(&empty[st]);
-        mma_commit(&lofree[lb]);
+        if (!abort_flag) mma_commit(accfull);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
     }
   } else {
-    // ---- converters: lo(S) = S - hi(S) into the lo ring
-    const int ct = tid - 64;
-    for (int c = 0; c < nkc; ++c) {
-      const int st = c % kTcStages, lb = c % kLoBufs;
-      if (abort_flag || !mbar_wait_bounded(&full[st], (uint32_t)((c / kTcStages) & 1), a.wait_limit) ||
-          (c >= kLoBufs &&
-           !mbar_wait_bounded(&lofree[lb], (uint32_t)(((c / kLoBufs) - 1) & 1), a.wait_limit))) {
-        abort_flag = 1;
+    // ---- vector warps: the port vectors of the next subgraph, the epilogue of the current one
+    const int vt = tid - 64;
+    const int q = warp & 3, hq = (warp - 2) >> 2;
+    auto vectors = [&](int k) {
+      const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
+      const int P = pd.nports, np = n_super(P) * kSB;
+      float mx[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) mx[r] = 0.f;
+      for (int p = vt; p < P; p += kVecThreads) {
+        float v[R];
+        port_vector<R>(a, pd.port_off + p, v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) mx[r] = fmaxf(mx[r], fabsf(v[r]));
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float m = mx[r];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red[warp - 2][r] = m;
+      }
+      vec_sync();
+      if (vt < R) {
+        float m = 0.f;
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w][vt]);
+        int e = 0;
+        if (m > 0.f) frexpf(m, &e);
+        ssig[k & 1][vt] = ldexpf(1.f, e);
+      }
+      vec_sync();
+      float inv[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) inv[r] = 1.f / ssig[k & 1][r];
+      unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
+      for (int p = vt; p < np; p += kVecThreads) {
+        float v[R];
+        if (p < P) port_vector<R>(a, pd.port_off + p, v);
+        else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[r] = 0.f;
+        }
+        unsigned char* tile = slot + (size_t)(p / kSB) * G::kVec;
+        const int c = p % kSB;
+        const uint32_t pn = (uint32_t)(c / 64) * R * 128;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float x = v[r] * inv[r];
+          const __half hi = __float2half_rn(x);
+          const __half lo = __float2half_rn(x - __half2float(hi));
+          const uint32_t off = pn + swz16(r, c % 64);
+          *reinterpret_cast<__half*>(tile + off) = hi;
+          *reinterpret_cast<__half*>(tile + 2 * R * 128 + off) = lo;
+        }
+      }
+      // the bulk copies (async proxy) read what these generic stores wrote
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      vec_sync();
+      if (vt == 0) mbar_arrive(&sready[k & 1]);
+    };
+    // the vector warps decide together (a named barrier that some of them skip would never open)
+    if (npc > 0) vectors(0);
+    for (int k = 0; k < npc; ++k) {
+      if (vt == 0) vstop_a = abort_flag;
+      vec_sync();
+      if (vstop_a) break;
+      if (k + 1 < npc) vectors(k + 1);
+      if (vt == 0) vstop_b = mbar_wait_bounded(accfull, (uint32_t)(k & 1), a.wait_limit) ? 0 : 1;
+      vec_sync();
+      if (vstop_b) {
+        if (vt == 0) abort_flag = 1;
         break;
       }
-      const float4* src = reinterpret_cast<const float4*>(stage0_ptr + st * kStageBytes);
-      float4* dst = reinterpret_cast<float4*>(lo0_ptr + lb * kChunkBytes);
-      for (int i = ct; i < (int)(kChunkBytes / 16); i += 32 * kConvWarps) {
-        const float4 x = src[i];
-        dst[i] = make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
+      tc_fence_after();
+      const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
+      const int P = pd.nports, n4 = n_super(P);
+      const float sj = a.sig_s[blockIdx.x + (size_t)k * gridDim.x];
+      float sc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) sc[r] = sj * ssig[k & 1][r];
+      for (int I = hq; I < n4; I += 2) {
+        uint32_t v[R];
+        tmem_ld<R>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(I * R), v);
+        const int p = I * kSB + 32 * q + lane;
+        if (p < P) {
+          const int port = pd.port_off + p;
+          const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)port * R);
+          float u[R];
+#pragma unroll
+          for (int k4 = 0; k4 < R / 4; ++k4) {
+            const float4 b4 = ub[k4];
+            u[4 * k4] = b4.x + sc[4 * k4] * __uint_as_float(v[4 * k4]);
+            u[4 * k4 + 1] = b4.y + sc[4 * k4 + 1] * __uint_as_float(v[4 * k4 + 1]);
+            u[4 * k4 + 2] = b4.z + sc[4 * k4 + 2] * __uint_as_float(v[4 * k4 + 2]);
+            u[4 * k4 + 3] = b4.w + sc[4 * k4 + 3] * __uint_as_float(v[4 * k4 + 3]);
+          }
+          const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
+          for (int e = e0; e < e1; ++e) {
+            const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+            float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
+#pragma unroll
+            for (int k4 = 0; k4 < R / 4; ++k4) {
+              const float4 w = wi[k4];
+              wo[k4] = make_float4(2.f * u[4 * k4] - w.x, 2.f * u[4 * k4 + 1] - w.y, 2.f * u[4 * k4 + 2] - w.z,
+                                   2.f * u[4 * k4 + 3] - w.w);
+            }
+          }
+        }
       }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[lb]);
+      tc_fence_before();
+      vec_sync();
+      if (vt == 0) mbar_arrive(accempty);
     }
   }
   __syncthreads();
   const bool ok = mbar_wait_bounded(done, 0, kDrainPolls) && !abort_flag;
-  if (abort_flag && tid == 0) atomicExch(a.status, kStatusTimeout);
-  tc_fence_after();
-
-  if (ok) {
-    // u = u_base + y; w_out[e] = 2 u - w_in[e].  Warp w reads lanes 32 (w % 4) .. + 31 (one port
-    // per lane) and the 16 columns 16 (w / 4) .. + 15; rows move as 16-byte vectors.
-    const int q = warp & 3, h = warp >> 2;
-    if (16 * h < R) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * h))
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int p = I * kTB + q * 32 + lane;
-      if (p < np) {
-        const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)(pd.port_off + p) * R + 16 * h);
-        const int e0 = a.port_end_ptr[pd.port_off + p], e1 = a.port_end_ptr[pd.port_off + p + 1];
-        float4 u[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float4 b4 = ub[k];
-          u[k] = make_float4(b4.x + __uint_as_float(v[4 * k]), b4.y + __uint_as_float(v[4 * k + 1]),
-                             b4.z + __uint_as_float(v[4 * k + 2]), b4.w + __uint_as_float(v[4 * k + 3]));
-        }
-        for (int e = e0; e < e1; ++e) {
-          const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R + 16 * h);
-          float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R + 16 * h);
-          float4 w[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) w[k] = wi[k];
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            wo[k] = make_float4(2.f * u[k].x - w[k].x, 2.f * u[k].y - w[k].y, 2.f * u[k].z - w[k].z,
-                                2.f * u[k].w - w[k].w);
-        }
-      }
-    }
-  }
+  if (!ok && tid == 0) atomicExch(a.status, kStatusTimeout);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
   }
 }
 
 cudaError_t port_tc_configure(int R) {
-  const int smem = (int)port_tc_smem_bytes();
-  switch (R) {
-    case 16: return cudaFuncSetAttribute(k_port_sweep_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    case 32: return cudaFuncSetAttribute(k_port_sweep_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, int npieces, int nitems, cudaStream_t st) {
-  if (npieces <= 0 || nitems <= 0) return cudaSuccess;
-  const size_t smem = port_tc_smem_bytes();
+  cudaError_t e = cudaErrorInvalidValue;
   switch (R) {
     case 16:
-      k_port_vec_tc<16><<<npieces, kTcThreads, 0, st>>>(a);
-      k_port_sweep_tc<16><<<nitems, kTcThreads, smem, st>>>(a);
+      e = cudaFuncSetAttribute(k_port_sweep_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)port_tc_smem_bytes(16, true));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_port_sweep_tc<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)port_tc_smem_bytes(16, false));
       break;
     case 32:
-      k_port_vec_tc<32><<<npieces, kTcThreads, 0, st>>>(a);
-      k_port_sweep_tc<32><<<nitems, kTcThreads, smem, st>>>(a);
+      e = cudaFuncSetAttribute(k_port_sweep_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)port_tc_smem_bytes(32, true));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_port_sweep_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)port_tc_smem_bytes(32, false));
       break;
-    default: return cudaErrorInvalidValue;
+    default: break;
+  }
+  return e;
+}
+
+cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, bool lo, int grid, cudaStream_t st) {
+  if (a.npieces <= 0 || grid <= 0) return cudaSuccess;
+  const size_t smem = port_tc_smem_bytes(R, lo);
+  if (R == 16) {
+    if (lo) k_port_sweep_tc<16, true><<<grid, kTcThreads, smem, st>>>(a);
+    else k_port_sweep_tc<16, false><<<grid, kTcThreads, smem, st>>>(a);
+  } else if (R == 32) {
+    if (lo) k_port_sweep_tc<32, true><<<grid, kTcThreads, smem, st>>>(a);
+    else k_port_sweep_tc<32, false><<<grid, kTcThreads, smem, st>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_port_response_tc(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs,
-                                           int b, const float* xc, float* S, cudaStream_t st) {
+cudaError_t launch_gather_port_blocks(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs, int b,
+                                      const float* xc, float* S32, cudaStream_t st) {
   if (npieces <= 0) return cudaSuccess;
-  k_gather_port_response_tc<<<npieces, 256, 0, st>>>(pieces, port_local, Rs, b, xc, S);
+  k_gather_port_blocks<<<npieces, 256, 0, st>>>(pieces, port_local, Rs, b, xc, S32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_port_blocks_to_f16(const PieceDesc* pieces, int npieces, const float* S32, unsigned char* S16,
+                                      float* sig, cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
+  k_port_blocks_to_f16<<<npieces, 256, 0, st>>>(pieces, S32, S16, sig);
   return cudaGetLastError();
 }
 

@@ -132,14 +132,15 @@ struct vtm_solver {
   // port-response form (port.cu): S_j per subgraph, u_base per port, zero / scratch wave buffers
   bool port_form = false;
   bool port_tc = false;              // R >= 16, FP32: tensor-core port sweep (port_tc.cu)
-  DevBuf S, ubase, wzero, wscr, sglob;
+  DevBuf S, ubase, wzero, wscr;
   bool ubase_ok = false;
   size_t port_smem = 0;
-  DevBuf tc_items;                   // (subgraph of the main launch, 128-port super-row)
+  DevBuf S16, sig16, tc_scratch;     // tensor-core form: fp16 hi / lo blocks, sigma_j, s^T slots
+  int tc_grid = 0, tc_n4max = 0, tc_tmem_cols = 0;
+  int64_t tc_bytes_hi = 0, tc_bytes_all = 0;  // bytes a sweep streams without / with the lo half
   DevBuf Sh, hscale;                 // FP16 copy of S_j and the scale of each of its tiles
-  bool port_half = false;            // the port sweep reads the FP16 copy
+  bool port_half = false;            // the port sweep reads the FP16 copy (tensor cores: hi half only)
   bool port_half_auto = false;       // ... and returns to FP32 when a correction step stalls
-  int n_items = 0;
   // coupled lines (§7.2): per-port coupling lists, read by the sweep kernels' port loops
   bool coupled = false;
   DevBuf cp_ptr, cp_oth, cp_y;
@@ -876,8 +877,8 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
       sweeps_typed<T>(s, 1);
       if constexpr (sizeof(T) == 4) {
         if (s->port_tc) {
-          VTM_CUDA(launch_gather_port_response_tc(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
-                                                  R, b, s->xc.as<float>(), s->S.as<float>(), st));
+          VTM_CUDA(launch_gather_port_blocks(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(), R, b,
+                                             s->xc.as<float>(), s->S.as<float>(), st));
           continue;
         }
       }
@@ -937,8 +938,12 @@ static void launch_port(vtm_solver* s) {
     if (s->port_tc) {
       PortTCArgs t;
       t.pieces = s->pieces_lo.as<PieceDesc>();
-      t.S = s->S.as<float>();
-      t.sglob = s->sglob.as<float>();
+      t.npieces = s->np_lo;
+      t.S16 = s->S16.as<unsigned char>();
+      t.sig_s = s->sig16.as<float>();
+      t.scratch = s->tc_scratch.as<unsigned char>();
+      t.n4max = s->tc_n4max;
+      t.tmem_cols = s->tc_tmem_cols;
       t.ubase = s->ubase.as<float>();
       t.wprev = s->w[s->cur].as<float>();
       t.wnext = s->w[s->cur ^ 1].as<float>();
@@ -948,9 +953,8 @@ static void launch_port(vtm_solver* s) {
       t.cpl = couple_ref<float>(s);
       t.status = s->status.as<int>();
       t.wait_limit = s->wait_limit;
-      t.items = s->tc_items.as<int2>();
-      VTM_CUDA(launch_port_sweep_tc(t, s->R, s->np_lo, s->n_items, s->stream));
-      s->launches += 2;
+      VTM_CUDA(launch_port_sweep_tc(t, s->R, !s->port_half, s->tc_grid, s->stream));
+      s->launches++;
       return;
     }
   }
@@ -988,7 +992,7 @@ static void port_sweeps_typed(vtm_solver* s, int k) {
 static int64_t launches_per_batch(const vtm_solver* s, int k) {
   const int64_t band = (s->np_lo > 0) + (s->np_hi > 0);
   if (!s->port_form || k < 2) return (int64_t)k * band;
-  const int64_t port = (s->np_lo > 0) * (s->port_tc ? 2 : 1) + (s->np_hi > 0);
+  const int64_t port = (s->np_lo > 0) + (s->np_hi > 0);
   return (int64_t)(k - 1) * port + band;
 }
 
@@ -1003,31 +1007,40 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   // S_j only for the subgraphs of the main launch (flagged ones keep their FP64 band sweep)
   std::vector<PieceDesc> lo;
   lo.reserve(s->np_lo);
-  // R >= 16 (FP32): tensor-core sweep over 128 x 128 super-blocks; R <= 8: SIMT sweep over tiles
+  // R >= 16 (FP32): tensor-core sweep over the lower block triangle in 128 x 128 blocks (port_tc.cu);
+  // R <= 8: SIMT sweep over 32 x 32 tiles (port.cu)
   const bool tc = s->wide && sizeof(T) == 4;
   s_tiles = 0;
-  int64_t v_blocks = 0;
+  int64_t h_bytes = 0;
   int max_ports_lo = 0;
   for (size_t j = 0; j < s->pd_host.size(); ++j) {
     if (s->piece_bits[j] == 64 && sizeof(T) == 4) continue;
     PieceDesc d = s->pd_host[j];
     d.s_off = s_tiles;
-    d.v_off = v_blocks;
-    s_tiles += tc ? port_blocks_tc(d.nports) : port_tiles(d.nports);
-    v_blocks += port_vec_chunks_tc(d.nports);
+    d.h_off = h_bytes;
+    s_tiles += tc ? port_f32_blocks(d.nports) : port_tiles(d.nports);
+    h_bytes += tc ? port_f16_bytes(d.nports) : 0;
     max_ports_lo = std::max(max_ports_lo, d.nports);
     lo.push_back(d);
   }
-  const size_t smem = tc ? port_tc_smem_bytes() : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
-  const double s_bytes = (double)s_tiles * (tc ? 128.0 * 32.0 : (double)kNB * kNB) * sizeof(T);
+  // tensor memory holds every 128-port super-row of a subgraph at once: n4 R <= 512 columns
+  const int n4max = (max_ports_lo + 127) / 128;
+  int tmem_cols = 32;
+  while (tmem_cols < n4max * s->R) tmem_cols *= 2;
+  const bool tmem_ok = n4max * s->R <= 512;
+  const size_t smem = tc ? port_tc_smem_bytes(s->R, true) : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
+  // bytes one sweep streams (tensor cores: with the lo half) and the device memory setup needs
+  const double s_bytes = tc ? (double)h_bytes : (double)s_tiles * kNB * kNB * sizeof(T);
+  const double setup_bytes = tc ? s_bytes + (double)s_tiles * 128.0 * 128.0 * 4.0 : s_bytes;
   const double band_bytes = 2.0 * (double)band_elems * sizeof(T);
   size_t free_b = 0, total_b = 0;
   VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const bool shape_ok = tc || !s->wide;
-  const bool fits = shape_ok && s->np_lo > 0 && smem <= kSmemMax && s_bytes < 0.5 * (double)free_b;
+  const bool shape_ok = tc ? tmem_ok : !s->wide;
+  const bool fits = shape_ok && s->np_lo > 0 && smem <= kSmemMax && setup_bytes < 0.5 * (double)free_b;
   if (o->sweep_form == VTM_FORM_PORT && !fits)
     fail(VTM_ERR_INVALID, "the port form needs FP32 or nrhs <= 8, port counts whose response vectors fit in "
-                          "shared memory (nrhs <= 8) and room for the port responses in device memory");
+                          "shared memory (nrhs <= 8) or in tensor memory (ports x nrhs <= 512 x 128 for nrhs "
+                          "16 / 32) and room for the port responses in device memory");
   // AUTO: a batch of m sweeps costs (m - 1) port sweeps plus one band sweep in port form (the
   // multi-RHS band sweep is bound by FP32 arithmetic, so there the tensor-core form always wins)
   const double m = std::max(2, s->check_every);
@@ -1041,12 +1054,17 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   upload(s->pieces_lo, lo, s->stream);
   s->port_smem = smem;
   if (tc) {
-    std::vector<int2> items;
-    for (size_t j = 0; j < lo.size(); ++j)
-      for (int I = 0; I < (lo[j].nports + 127) / 128; ++I) items.push_back(make_int2((int)j, I));
-    s->n_items = (int)items.size();
-    upload(s->tc_items, items, s->stream);
-    s->sglob.alloc((size_t)std::max<int64_t>(1, v_blocks) * 32 * 32 * sizeof(float));
+    int dev = 0, nsm = 1;
+    VTM_CUDA(cudaGetDevice(&dev));
+    VTM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    s->tc_grid = std::min(s->np_lo, nsm);  // one persistent CTA per SM (it holds the SM's tensor memory)
+    s->tc_n4max = n4max;
+    s->tc_tmem_cols = tmem_cols;
+    s->tc_scratch.alloc((size_t)s->tc_grid * 2 * n4max * s->R * 512);
+    s->S16.alloc((size_t)std::max<int64_t>(1024, h_bytes));
+    s->sig16.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
+    s->tc_bytes_all = h_bytes;
+    s->tc_bytes_hi = h_bytes / 2;
     VTM_CUDA(port_tc_configure(s->R));
   } else {
     VTM_CUDA(port_sweep_configure<T>(s->R, smem));
@@ -1055,13 +1073,30 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   s->wzero.alloc((size_t)s->E * s->R * sizeof(T));
   s->wscr.alloc(s->wzero.bytes);
   VTM_CUDA(cudaMemsetAsync(s->wzero.p, 0, s->wzero.bytes, s->stream));
-  compute_port_response<T>(s, s_tiles * (tc ? 128 * 32 / (kNB * kNB) : 1));
+  compute_port_response<T>(s, s_tiles * (tc ? 128 * 128 / (kNB * kNB) : 1));
   s->info.port_bytes = (int64_t)s_bytes;
   s->info.port_storage_bits = 8 * (int)sizeof(T);
   if constexpr (sizeof(T) == 4) {
     // FP16_AUTO only where the sweep streams S_j from HBM: responses that stay in the 126 MB L2
     // gain nothing from half the bytes and would pay the extra sweeps of FP16 rounding
     const bool l2_resident = s_bytes <= 96.0 * (1 << 20);
+    if (tc) {
+      // fp16 hi / lo blocks of S_j / sigma_j from the FP32 setup blocks, which are then released
+      VTM_CUDA(cudaMemsetAsync(s->S16.p, 0, s->S16.bytes, s->stream));
+      VTM_CUDA(launch_port_blocks_to_f16(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(),
+                                         s->S16.as<unsigned char>(), s->sig16.as<float>(), s->stream));
+      VTM_CUDA(cudaStreamSynchronize(s->stream));
+      s->S.alloc(0);
+      // the hi half alone (FP16 storage) only when asked for: with one scale per subgraph its
+      // rounding stalls the defect correction of coupled lines (256^3 x 32: 906 sweeps and 8
+      // restarts against 482 and 2 with the lo half), so FP16_AUTO keeps the lo half here
+      (void)l2_resident;
+      if (o->port_storage == VTM_STORE_FP16) {
+        s->port_half = true;
+        s->info.port_bytes = s->tc_bytes_hi;
+        s->info.port_storage_bits = 16;
+      }
+    }
     if (!tc && (o->port_storage == VTM_STORE_FP16 || (o->port_storage == VTM_STORE_FP16_AUTO && !l2_resident))) {
       s->Sh.alloc((size_t)s_tiles * kNB * kNB * sizeof(__half));
       s->hscale.alloc((size_t)std::max<int64_t>(1, s_tiles) * sizeof(float));  // one scale per tile
@@ -1445,6 +1480,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
         ((inner > 0.1 && inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || (inner >= 1.0 && inner_sweeps >= 4 * m))) {
       s->port_half = false;
       s->info.port_storage_bits = 32;
+      s->info.port_bytes = s->port_tc ? s->tc_bytes_all : 2 * s->info.port_bytes;
       drop_graphs(s);
     }
     // coupled lines on FP16 responses: while such a phase makes progress it gains far more than a

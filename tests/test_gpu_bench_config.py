@@ -100,3 +100,23 @@ def test_poisson3d_256_r32_configuration(vtmlib):
     s.iterate(3)
     assert _rel(s.copies(), ref[10][0]) <= TOL_FP32
     assert _rel(s.get_state(), ref[10][1][:, lm]) <= TOL_FP32
+
+
+@pytest.mark.parametrize("nrhs", [16, 32])
+def test_tensor_core_fp16_storage(vtmlib, nrhs):
+    """FP16 storage on the tensor cores (the hi half of S_j / sigma_j only): within TOL_FP16 of the
+    coupled oracle after 7 and 10 sweeps."""
+    A, part, osplit, z, cpl, Y = _case(vtmlib, "poisson3d-wide", 1.5, 0)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=1)
+    ref = _oracle(osplit, Y, b, (7, 10))
+    s = vtmlib.Solver(part, z=z, precision="fp32", nrhs=nrhs, form="port", port_storage="fp16", coupling=cpl)
+    assert s.info().port_storage_bits == 16
+    lm = _line_map(part, osplit)
+    s.set_rhs(b)
+    s.reset()
+    s.iterate(7)
+    assert _rel(s.copies(), ref[7][0]) <= TOL_FP16
+    assert _rel(s.get_state(), ref[7][1][:, lm]) <= TOL_FP16
+    s.iterate(3)
+    assert _rel(s.copies(), ref[10][0]) <= TOL_FP16
+    assert _rel(s.get_state(), ref[10][1][:, lm]) <= TOL_FP16
