@@ -44,9 +44,13 @@ namespace vtm {
 namespace {
 
 constexpr int kSB = 128;                // ports per super-block (MMA M; K extent of a block)
-constexpr int kTcThreads = 320;         // warp 0 copies, warp 1 MMA, warps 2..9 vectors / epilogue
-constexpr int kVecThreads = 256;
+constexpr int kEpiWarps = 4;            // epilogue: one warp per tensor-memory lane quadrant
+constexpr int kVecWarps = 8;            // port vectors
+constexpr int kTcThreads = 32 * (2 + kEpiWarps + kVecWarps);  // warp 0 copies, warp 1 MMA
+constexpr int kVecThreads = 32 * kVecWarps;
 constexpr int kVecBar = 1;              // named barrier of the vector warps
+constexpr int kEpiBar = 2;              // named barrier of the epilogue warps
+constexpr int kMaxSuper = 16;           // super-rows per subgraph (tensor memory: n4 R <= 512)
 
 __host__ __device__ __forceinline__ int n_super(int nports) { return (nports + kSB - 1) / kSB; }
 
@@ -71,6 +75,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// The same with an L2 cache policy (evict-first for data read once per sweep).
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
 }
 
 // Shared-memory matrix descriptor: start address, leading / stride byte offsets (16-byte units),
@@ -116,6 +130,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void vec_sync() { asm volatile("bar.sync %0, %1;" ::"n"(kVecBar), "n"(kVecThreads) : "memory"); }
+__device__ __forceinline__ void epi_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(kEpiBar), "n"(32 * kEpiWarps) : "memory");
+}
 
 template <int R>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[R]);
@@ -159,12 +176,13 @@ struct Ring {
 // The MMAs of one block (I, J) of height h: y_I += S_IJ s_J (A K-major: the block's two panels
 // along K; B = the s tile bv) and, off the diagonal, y_J += S_IJ^T s_I (A MN-major: M over the two
 // panels at LBO = one panel, K = the block's rows in steps of 16; B = the row tile si).  Products
-// per K step: hi(S) s_hi, hi(S) s_lo and, with LO, lo(S) s_hi.  Descriptors are formed once and
-// advanced by address offsets (16-byte units in the low bits); with kFull the panel stride is the
-// compile-time 16 KB of a full-height block and every loop unrolls.
+// per K step: hi(S) s_hi, hi(S) s_lo and, with LO, lo(S) s_hi.  first / first_t: the product
+// overwrites y_I / y_J instead of adding.  Descriptors are formed once and advanced by address
+// offsets (16-byte units in the low bits); with kFull the panel stride is the compile-time 16 KB
+// of a full-height block and every loop unrolls.
 template <int R, bool LO, bool kFull>
 __device__ __forceinline__ void block_mmas(uint32_t sb, uint32_t bv, uint32_t si, int h, uint32_t dI, uint32_t dJ,
-                                           bool first, bool transposed) {
+                                           bool first, bool first_t, bool transposed) {
   constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
   constexpr uint32_t vpan = (uint32_t)R * 128 / 16;           // s tile panel, 16-byte units
   const uint32_t panel = kFull ? (uint32_t)kSB * 128 : (uint32_t)h * 128;
@@ -187,7 +205,8 @@ __device__ __forceinline__ void block_mmas(uint32_t sb, uint32_t bv, uint32_t si
     if (!kFull && kk >= nk) break;
     const uint32_t p = kk >> 2, o = (kk & 3) * 2;
     const uint64_t aH = aT + kk * 128, bH = bR + p * vpan + o, bL = bR + (2 + p) * vpan + o;  // 2048 B per kk
-    mma_f16_acc(dJ, aH, bH, idT);
+    if (kk == 0) mma_f16(dJ, aH, bH, idT, first_t ? 0u : 1u);
+    else mma_f16_acc(dJ, aH, bH, idT);
     mma_f16_acc(dJ, aH, bL, idT);
     if constexpr (LO) mma_f16_acc(dJ, aT + 2 * pan + kk * 128, bH, idT);
   }
@@ -314,8 +333,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   constexpr int S = G::kStages;
   extern __shared__ unsigned char smem_raw[];
   __shared__ volatile int abort_flag;
-  __shared__ volatile int vstop_a, vstop_b;
-  __shared__ float red[8][R];
+  __shared__ volatile int vstop, vstop_v;
+  __shared__ float red[kVecWarps][R];
   __shared__ float ssig[2][R];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -325,9 +344,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   uint64_t* rowfull = empty + S;                     // [2] s_I tile landed
   uint64_t* rowempty = rowfull + 2;                  // [2] MMAs done with the s_I tile
   uint64_t* sready = rowempty + 2;                   // [2] scratch slot written
-  uint64_t* accfull = sready + 2;                    // accumulators complete
-  uint64_t* accempty = accfull + 1;                  // accumulators read by the epilogue
-  uint64_t* done = accempty + 1;
+  uint64_t* rready = sready + 2;                     // [kMaxSuper] accumulator y_I complete
+  uint64_t* accempty = rready + kMaxSuper;           // every accumulator read by the epilogue
+  uint64_t* slotfree = accempty + 1;                 // [2] epilogue of the slot's last subgraph done
+  uint64_t* done = slotfree + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   const uint32_t stage0 = base + 1024;
   const uint32_t row0 = stage0 + S * G::kStage;
@@ -335,7 +355,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int npc = (a.npieces - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // subgraphs of this CTA
   const size_t slot_bytes = (size_t)a.n4max * G::kVec;
-  unsigned char* scratch = a.scratch + (size_t)blockIdx.x * 2 * slot_bytes;
+  unsigned char* scratch = a.scratch + (size_t)blockIdx.x * (2 * slot_bytes + (size_t)a.n4max * kSB * R * 4);
+  float* stage32 = reinterpret_cast<float*>(scratch + 2 * slot_bytes);  // FP32 port vectors, ports x R
 
   if (tid == 0) {
     abort_flag = 0;
@@ -347,8 +368,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       mbar_init(&rowfull[s], 1);
       mbar_init(&rowempty[s], 1);
       mbar_init(&sready[s], 1);
+      mbar_init(&slotfree[s], 1);
     }
-    mbar_init(accfull, 1);
+    for (int s = 0; s < kMaxSuper; ++s) mbar_init(&rready[s], 1);
     mbar_init(accempty, 1);
     mbar_init(done, 1);
     fence_mbar_init();
@@ -365,8 +387,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   const uint32_t tmem = *tslot;
 
   if (warp == 0) {
-    // ---- producer: per subgraph, per super-row the s_I tile, per block the block and s_J tile
+    // ---- producer: super-rows in descending order; per row the s_I tile, per block (I, J),
+    // J = 0 .. I, the block and the s_J tile.  The blocks are read once per sweep: evict first.
     if (lane == 0) {
+      uint64_t policy;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
       int64_t gblk = 0, grow = 0;
       for (int k = 0; k < npc && !abort_flag; ++k) {
         const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
@@ -377,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         }
         const unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
         const unsigned char* Sp = a.S16 + pd.h_off;
-        for (int I = 0; I < n4 && !abort_flag; ++I) {
+        for (int I = n4 - 1; I >= 0 && !abort_flag; --I) {
           const int rb = (int)(grow & 1);
           if (grow >= 2 && !mbar_wait_bounded(&rowempty[rb], (uint32_t)(((grow >> 1) - 1) & 1), a.wait_limit)) {
             abort_flag = 1;
@@ -396,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
             }
             const uint32_t sb = stage0 + st * G::kStage;
             mbar_arrive_expect_tx(&full[st], sbytes + (J < I ? G::kVec : 0u));
-            bulk_g2s(sb, Sp + blk_off(P, I, J), sbytes, &full[st]);
+            bulk_g2s_hint(sb, Sp + blk_off(P, I, J), sbytes, &full[st], policy);
             if (J < I) bulk_g2s(sb + G::kBlk, slot + (size_t)J * G::kVec, G::kVec, &full[st]);
             ++gblk;
           }
@@ -409,7 +434,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         mbar_wait_bounded(&rowfull[g & 1], (uint32_t)((g >> 1) & 1), kDrainPolls);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer
+    // ---- MMA issuer.  In descending row order y_I is complete once row I is done (the rows
+    // below only add to y_J, J < I), so its epilogue runs while the MMAs go on.  The first row
+    // processed (n4 - 1) initialises every accumulator: y_{n4-1} through its direct product with
+    // J = 0, every other y_J through the transposed product of block (n4 - 1, J).
     if (lane == 0) {
       int64_t gblk = 0, grow = 0;
       for (int k = 0; k < npc && !abort_flag; ++k) {
@@ -420,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
           break;
         }
         tc_fence_after();
-        for (int I = 0; I < n4 && !abort_flag; ++I) {
+        for (int I = n4 - 1; I >= 0 && !abort_flag; --I) {
           const int rb = (int)(grow & 1);
           if (!mbar_wait_bounded(&rowfull[rb], (uint32_t)((grow >> 1) & 1), a.wait_limit)) {
             abort_flag = 1;
@@ -438,23 +466,107 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
             const uint32_t sb = stage0 + st * G::kStage;
             const uint32_t bv = (J == I) ? si : sb + G::kBlk;
             const uint32_t dI = tmem + (uint32_t)(I * R), dJ = tmem + (uint32_t)(J * R);
-            if (h == kSB) block_mmas<R, LO, true>(sb, bv, si, h, dI, dJ, J == 0, J < I);
-            else block_mmas<R, LO, false>(sb, bv, si, h, dI, dJ, J == 0, J < I);
+            const bool top = (I == n4 - 1);
+            if (h == kSB) block_mmas<R, LO, true>(sb, bv, si, h, dI, dJ, top && J == 0, top, J < I);
+            else block_mmas<R, LO, false>(sb, bv, si, h, dI, dJ, top && J == 0, top, J < I);
             mma_commit(&empty[st]);
             ++gblk;
           }
           mma_commit(&rowempty[rb]);
+          mma_commit(&rready[I]);  // y_I is final
           ++grow;
         }
-        if (!abort_flag) mma_commit(accfull);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
     }
+  } else if (warp < 2 + kEpiWarps) {
+    // ---- epilogue warps (one per tensor-memory lane quadrant): u = u_base + sigma_j sigma_r y_I,
+    // w_out[e] = 2 u - w_in[e], super-row by super-row as the MMA issuer completes them
+    // (rready[I] completes once per subgraph that has a super-row I, so its phases are counted per
+    // barrier; sready[k & 1] also orders the sigma_r written with subgraph k's port vectors)
+    const int q = warp & 3;
+    uint32_t uses = 0;  // tid 64: parity of the next phase of each row barrier, one bit per super-row
+    bool stop = false;
+    for (int k = 0; k < npc && !stop; ++k) {
+      const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
+      const int P = pd.nports, n4 = n_super(P);
+      const float sj = a.sig_s[blockIdx.x + (size_t)k * gridDim.x];
+      if (tid == 64) vstop = mbar_wait_bounded(&sready[k & 1], (uint32_t)((k >> 1) & 1), a.wait_limit) ? 0 : 1;
+      epi_sync();
+      stop = vstop != 0;
+      epi_sync();
+      for (int I = n4 - 1; I >= 0 && !stop; --I) {
+        // the four warps decide together: one lane waits, the named barrier publishes the outcome
+        if (tid == 64) {
+          vstop = mbar_wait_bounded(&rready[I], (uses >> I) & 1u, a.wait_limit) ? 0 : 1;
+          uses ^= 1u << I;
+        }
+        epi_sync();
+        stop = vstop != 0;
+        epi_sync();
+        if (stop) break;
+        tc_fence_after();
+        uint32_t v[R];
+        tmem_ld<R>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(I * R), v);
+        const int p = I * kSB + 32 * q + lane;
+        if (p < P) {
+          const int port = pd.port_off + p;
+          const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)port * R);
+          const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
+#pragma unroll
+          for (int k4 = 0; k4 < R / 4; ++k4) {
+            const float4 b4 = __ldg(ub + k4);
+            const float u0 = b4.x + sj * ssig[k & 1][4 * k4] * __uint_as_float(v[4 * k4]);
+            const float u1 = b4.y + sj * ssig[k & 1][4 * k4 + 1] * __uint_as_float(v[4 * k4 + 1]);
+            const float u2 = b4.z + sj * ssig[k & 1][4 * k4 + 2] * __uint_as_float(v[4 * k4 + 2]);
+            const float u3 = b4.w + sj * ssig[k & 1][4 * k4 + 3] * __uint_as_float(v[4 * k4 + 3]);
+            v[4 * k4] = __float_as_uint(u0);
+            v[4 * k4 + 1] = __float_as_uint(u1);
+            v[4 * k4 + 2] = __float_as_uint(u2);
+            v[4 * k4 + 3] = __float_as_uint(u3);
+          }
+          for (int e = e0; e < e1; ++e) {
+            const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+            float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
+#pragma unroll
+            for (int k4 = 0; k4 < R / 4; ++k4) {
+              const float4 w = __ldg(wi + k4);
+              wo[k4] = make_float4(2.f * __uint_as_float(v[4 * k4]) - w.x, 2.f * __uint_as_float(v[4 * k4 + 1]) - w.y,
+                                   2.f * __uint_as_float(v[4 * k4 + 2]) - w.z,
+                                   2.f * __uint_as_float(v[4 * k4 + 3]) - w.w);
+            }
+          }
+        }
+      }
+      if (stop) {
+        if (tid == 64) abort_flag = 1;
+        break;
+      }
+      tc_fence_before();
+      epi_sync();
+      if (tid == 64) {
+        mbar_arrive(accempty);
+        mbar_arrive(&slotfree[k & 1]);
+      }
+    }
   } else {
-    // ---- vector warps: the port vectors of the next subgraph, the epilogue of the current one
-    const int vt = tid - 64;
-    const int q = warp & 3, hq = (warp - 2) >> 2;
-    auto vectors = [&](int k) {
+    // ---- vector warps: the port vectors s of subgraph k, one gather pass (FP32 values to a
+    // staging area and the column maxima), then the fp16 split into the scratch slot k & 1.  Slot
+    // and sigma_r of subgraph k are free again once the epilogue of subgraph k - 2 is done
+    // (slotfree[k & 1] completes once per subgraph of that slot).
+    const int vt = tid - 32 * (2 + kEpiWarps);
+    const int vw = vt >> 5;
+    for (int k = 0; k < npc; ++k) {
+      if (k >= 2) {
+        if (vt == 0) vstop_v = mbar_wait_bounded(&slotfree[k & 1], (uint32_t)(((k >> 1) - 1) & 1), a.wait_limit) ? 0 : 1;
+        vec_sync();
+        const bool stop = vstop_v != 0;
+        vec_sync();
+        if (stop) {
+          if (vt == 0) abort_flag = 1;
+          break;
+        }
+      }
       const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
       const int P = pd.nports, np = n_super(P) * kSB;
       float mx[R];
@@ -463,106 +575,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       for (int p = vt; p < P; p += kVecThreads) {
         float v[R];
         port_vector<R>(a, pd.port_off + p, v);
+        float4* o = reinterpret_cast<float4*>(stage32 + (size_t)p * R);
 #pragma unroll
-        for (int r = 0; r < R; ++r) mx[r] = fmaxf(mx[r], fabsf(v[r]));
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          o[k4] = make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
+          mx[4 * k4] = fmaxf(mx[4 * k4], fabsf(v[4 * k4]));
+          mx[4 * k4 + 1] = fmaxf(mx[4 * k4 + 1], fabsf(v[4 * k4 + 1]));
+          mx[4 * k4 + 2] = fmaxf(mx[4 * k4 + 2], fabsf(v[4 * k4 + 2]));
+          mx[4 * k4 + 3] = fmaxf(mx[4 * k4 + 3], fabsf(v[4 * k4 + 3]));
+        }
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float m = mx[r];
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) red[warp - 2][r] = m;
+        if (lane == 0) red[vw][r] = m;
       }
       vec_sync();
       if (vt < R) {
         float m = 0.f;
-        for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w][vt]);
+        for (int w = 0; w < kVecWarps; ++w) m = fmaxf(m, red[w][vt]);
         int e = 0;
         if (m > 0.f) frexpf(m, &e);
-        ssig[k & 1][vt] = ldexpf(1.f, e);
+        ssig[k & 1][vt] = ldexpf(1.f, e);  // power of two >= max |s_r|
       }
       vec_sync();
-      float inv[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) inv[r] = 1.f / ssig[k & 1][r];
       unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
       for (int p = vt; p < np; p += kVecThreads) {
-        float v[R];
-        if (p < P) port_vector<R>(a, pd.port_off + p, v);
-        else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[r] = 0.f;
-        }
         unsigned char* tile = slot + (size_t)(p / kSB) * G::kVec;
         const int c = p % kSB;
         const uint32_t pn = (uint32_t)(c / 64) * R * 128;
+        const float4* src = reinterpret_cast<const float4*>(stage32 + (size_t)p * R);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float x = v[r] * inv[r];
-          const __half hi = __float2half_rn(x);
-          const __half lo = __float2half_rn(x - __half2float(hi));
-          const uint32_t off = pn + swz16(r, c % 64);
-          *reinterpret_cast<__half*>(tile + off) = hi;
-          *reinterpret_cast<__half*>(tile + 2 * R * 128 + off) = lo;
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 x4 = (p < P) ? src[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = 4 * k4 + i;
+            const float x = xs[i] / ssig[k & 1][r];
+            const __half hi = __float2half_rn(x);
+            const __half lo = __float2half_rn(x - __half2float(hi));
+            const uint32_t off = pn + swz16(r, c % 64);
+            *reinterpret_cast<__half*>(tile + off) = hi;
+            *reinterpret_cast<__half*>(tile + 2 * R * 128 + off) = lo;
+          }
         }
       }
       // the bulk copies (async proxy) read what these generic stores wrote
       asm volatile("fence.proxy.async.global;" ::: "memory");
       vec_sync();
       if (vt == 0) mbar_arrive(&sready[k & 1]);
-    };
-    // the vector warps decide together (a named barrier that some of them skip would never open)
-    if (npc > 0) vectors(0);
-    for (int k = 0; k < npc; ++k) {
-      if (vt == 0) vstop_a = abort_flag;
-      vec_sync();
-      if (vstop_a) break;
-      if (k + 1 < npc) vectors(k + 1);
-      if (vt == 0) vstop_b = mbar_wait_bounded(accfull, (uint32_t)(k & 1), a.wait_limit) ? 0 : 1;
-      vec_sync();
-      if (vstop_b) {
-        if (vt == 0) abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
-      const int P = pd.nports, n4 = n_super(P);
-      const float sj = a.sig_s[blockIdx.x + (size_t)k * gridDim.x];
-      float sc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) sc[r] = sj * ssig[k & 1][r];
-      for (int I = hq; I < n4; I += 2) {
-        uint32_t v[R];
-        tmem_ld<R>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(I * R), v);
-        const int p = I * kSB + 32 * q + lane;
-        if (p < P) {
-          const int port = pd.port_off + p;
-          const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)port * R);
-          float u[R];
-#pragma unroll
-          for (int k4 = 0; k4 < R / 4; ++k4) {
-            const float4 b4 = ub[k4];
-            u[4 * k4] = b4.x + sc[4 * k4] * __uint_as_float(v[4 * k4]);
-            u[4 * k4 + 1] = b4.y + sc[4 * k4 + 1] * __uint_as_float(v[4 * k4 + 1]);
-            u[4 * k4 + 2] = b4.z + sc[4 * k4 + 2] * __uint_as_float(v[4 * k4 + 2]);
-            u[4 * k4 + 3] = b4.w + sc[4 * k4 + 3] * __uint_as_float(v[4 * k4 + 3]);
-          }
-          const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
-          for (int e = e0; e < e1; ++e) {
-            const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
-            float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
-#pragma unroll
-            for (int k4 = 0; k4 < R / 4; ++k4) {
-              const float4 w = wi[k4];
-              wo[k4] = make_float4(2.f * u[4 * k4] - w.x, 2.f * u[4 * k4 + 1] - w.y, 2.f * u[4 * k4 + 2] - w.z,
-                                   2.f * u[4 * k4 + 3] - w.w);
-            }
-          }
-        }
-      }
-      tc_fence_before();
-      vec_sync();
-      if (vt == 0) mbar_arrive(accempty);
     }
   }
   __syncthreads();

@@ -1060,7 +1060,7 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     s->tc_grid = std::min(s->np_lo, nsm);  // one persistent CTA per SM (it holds the SM's tensor memory)
     s->tc_n4max = n4max;
     s->tc_tmem_cols = tmem_cols;
-    s->tc_scratch.alloc((size_t)s->tc_grid * 2 * n4max * s->R * 512);
+    s->tc_scratch.alloc((size_t)s->tc_grid * ((size_t)2 * n4max * s->R * 512 + (size_t)n4max * 128 * s->R * 4));
     s->S16.alloc((size_t)std::max<int64_t>(1024, h_bytes));
     s->sig16.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
     s->tc_bytes_all = h_bytes;
