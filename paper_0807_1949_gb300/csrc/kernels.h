@@ -101,6 +101,7 @@ struct PortTCArgs {
   int npieces;
   const unsigned char* S16;    // lower block triangle of S_j / sigma_j as fp16 hi / lo panels (h_off)
   const float* sig_s;          // sigma_j per subgraph of the launch
+  const float* gscale;         // g_p = sqrt(S_pp) per port (diagonal balance of S_j)
   unsigned char* scratch;      // per CTA two slots of n4max s^T tiles (R x 512 bytes each)
   int n4max;                   // most 128-port super-rows of a subgraph
   int tmem_cols;               // tensor-memory columns per CTA (power of two >= n4max R)
@@ -115,6 +116,7 @@ struct PortTCArgs {
   long wait_limit;
 };
 
+constexpr int kTcMaxSuper = 16;       // 128-port super-rows per subgraph on the tensor cores
 int64_t port_f16_bytes(int nports);   // fp16 hi / lo blocks of one subgraph (1 KB multiple)
 int64_t port_f32_blocks(int nports);  // 128 x 128 FP32 blocks of the lower triangle (setup)
 size_t port_tc_smem_bytes(int R, bool lo);
@@ -124,7 +126,7 @@ cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, bool lo, int grid, 
 cudaError_t launch_gather_port_blocks(const PieceDesc* pieces, int npieces, const int32_t* port_local, int Rs, int b,
                                       const float* xc, float* S32, cudaStream_t st);
 cudaError_t launch_port_blocks_to_f16(const PieceDesc* pieces, int npieces, const float* S32, unsigned char* S16,
-                                      float* sig, cudaStream_t st);
+                                      float* sig, float* gscale, cudaStream_t st);
 
 constexpr int kWideWindow = 512;
 constexpr int kMaxRhs = 32;

@@ -11,8 +11,10 @@
 // 128-byte-swizzled panels [hi, cols 0-63][hi, cols 64-127][lo, 0-63][lo, 64-127] of h_I rows
 // (rows of 128 bytes, 16-byte units XOR-ed with the row mod 8, 8-row groups 1024 bytes apart);
 // h_I = 128 except for the last super-row, whose height is its port count rounded up to 16.  The
-// values are S_j / sigma_j with sigma_j the power of two at or above max |S_j|, hi = fp16(x) and
-// lo = fp16(x - hi), so hi + lo keeps about 22 significant bits.  Transposed fp16 operands work on
+// values are those of the diagonally balanced S'_j = G^-1 S_j G^-1 (G = diag(sqrt(S_pp)), so that
+// S'_pp = 1 and |S'_pq| <= 1 even across coefficient jumps of many decades) divided by sigma_j, the
+// power of two at or above max |S'_j|; hi = fp16(x) and lo = fp16(x - hi), so hi + lo keeps about
+// 22 significant bits.  The port vector is balanced the other way (s' = G s) and y = G^-1 S' s'.  Transposed fp16 operands work on
 // this tensor core; kind::tf32 with the same MN-major descriptor returns zeros, which is why the
 // storage is fp16 pairs and not FP32.
 //
@@ -50,7 +52,7 @@ constexpr int kTcThreads = 32 * (2 + kEpiWarps + kVecWarps);  // warp 0 copies, 
 constexpr int kVecThreads = 32 * kVecWarps;
 constexpr int kVecBar = 1;              // named barrier of the vector warps
 constexpr int kEpiBar = 2;              // named barrier of the epilogue warps
-constexpr int kMaxSuper = 16;           // super-rows per subgraph (tensor memory: n4 R <= 512)
+constexpr int kMaxSuper = kTcMaxSuper;  // super-rows per subgraph (and tensor memory: n4 R <= 512)
 
 __host__ __device__ __forceinline__ int n_super(int nports) { return (nports + kSB - 1) / kSB; }
 
@@ -281,18 +283,40 @@ __global__ void k_gather_port_blocks(const PieceDesc* __restrict__ pieces, const
   }
 }
 
-// FP32 blocks -> fp16 hi / lo panels of the sweep's layout; sigma_j = 2^e >= max |S_j|.
+// FP32 blocks -> fp16 hi / lo panels of the sweep's layout.  S_j is first balanced by its diagonal,
+// S'_pq = S_pq / (g_p g_q) with g_p = sqrt(S_pp) (so S'_pp = 1 and |S'_pq| <= 1, S_j being SPD):
+// across a coefficient jump the entries of S_j span many decades (a soft region's input impedances
+// are orders of magnitude above a stiff one's), which one scale per subgraph would push below the
+// fp16 range.  g_p goes to gscale[port]; sigma_j = 2^e >= max |S'| (about 1) to sig.
 __global__ void k_port_blocks_to_f16(const PieceDesc* __restrict__ pieces, const float* __restrict__ S32,
-                                     unsigned char* __restrict__ S16, float* __restrict__ sig) {
+                                     unsigned char* __restrict__ S16, float* __restrict__ sig,
+                                     float* __restrict__ gscale) {
   const PieceDesc pd = pieces[blockIdx.x];
   const int P = pd.nports;
   if (P == 0) return;
   const int n4 = n_super(P);
-  const int64_t nblk = (int64_t)n4 * (n4 + 1) / 2;
   const float* src = S32 + pd.s_off * (kSB * kSB);
-  float m = 0.f;
-  for (int64_t k = threadIdx.x; k < nblk * kSB * kSB; k += blockDim.x) m = fmaxf(m, fabsf(src[k]));
+  __shared__ float g[kMaxSuper * kSB];  // 1 / g_p, zero-padded
   __shared__ float red[32];
+  for (int p = threadIdx.x; p < n4 * kSB; p += blockDim.x) {
+    float gi = 0.f;
+    if (p < P) {
+      const int I = p / kSB, r = p % kSB;
+      const float d = src[((int64_t)I * (I + 1) / 2 + I) * (kSB * kSB) + r * kSB + r];
+      const float gp = d > 0.f ? sqrtf(d) : 1.f;
+      gscale[pd.port_off + p] = gp;
+      gi = 1.f / gp;
+    }
+    g[p] = gi;
+  }
+  __syncthreads();
+  float m = 0.f;
+  for (int I = 0; I < n4; ++I)
+    for (int J = 0; J <= I; ++J) {
+      const float* blk = src + ((int64_t)I * (I + 1) / 2 + J) * (kSB * kSB);
+      for (int k = threadIdx.x; k < kSB * kSB; k += blockDim.x)
+        m = fmaxf(m, fabsf(blk[k] * g[I * kSB + k / kSB] * g[J * kSB + k % kSB]));
+    }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -316,7 +340,7 @@ __global__ void k_port_blocks_to_f16(const PieceDesc* __restrict__ pieces, const
       const uint32_t panel = (uint32_t)h * 128;
       for (int k = threadIdx.x; k < h * kSB; k += blockDim.x) {
         const int row = k / kSB, col = k % kSB;
-        const float x = blk[k] * inv;
+        const float x = blk[k] * g[I * kSB + row] * g[J * kSB + col] * inv;
         const __half hi = __float2half_rn(x);
         const __half lo = __float2half_rn(x - __half2float(hi));
         const uint32_t off = (uint32_t)(col / 64) * panel + swz16(row, col % 64);
@@ -513,13 +537,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
           const int port = pd.port_off + p;
           const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)port * R);
           const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
+          const float gs = sj * a.gscale[port];  // y = D^-1 (sigma_j S'') (sigma_r s'')
 #pragma unroll
           for (int k4 = 0; k4 < R / 4; ++k4) {
             const float4 b4 = __ldg(ub + k4);
-            const float u0 = b4.x + sj * ssig[k & 1][4 * k4] * __uint_as_float(v[4 * k4]);
-            const float u1 = b4.y + sj * ssig[k & 1][4 * k4 + 1] * __uint_as_float(v[4 * k4 + 1]);
-            const float u2 = b4.z + sj * ssig[k & 1][4 * k4 + 2] * __uint_as_float(v[4 * k4 + 2]);
-            const float u3 = b4.w + sj * ssig[k & 1][4 * k4 + 3] * __uint_as_float(v[4 * k4 + 3]);
+            const float u0 = b4.x + gs * ssig[k & 1][4 * k4] * __uint_as_float(v[4 * k4]);
+            const float u1 = b4.y + gs * ssig[k & 1][4 * k4 + 1] * __uint_as_float(v[4 * k4 + 1]);
+            const float u2 = b4.z + gs * ssig[k & 1][4 * k4 + 2] * __uint_as_float(v[4 * k4 + 2]);
+            const float u3 = b4.w + gs * ssig[k & 1][4 * k4 + 3] * __uint_as_float(v[4 * k4 + 3]);
             v[4 * k4] = __float_as_uint(u0);
             v[4 * k4 + 1] = __float_as_uint(u1);
             v[4 * k4 + 2] = __float_as_uint(u2);
@@ -575,6 +600,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       for (int p = vt; p < P; p += kVecThreads) {
         float v[R];
         port_vector<R>(a, pd.port_off + p, v);
+        const float gp = a.gscale[pd.port_off + p];  // s' = D^-1 s, D = diag(1 / g)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] *= gp;
         float4* o = reinterpret_cast<float4*>(stage32 + (size_t)p * R);
 #pragma unroll
         for (int k4 = 0; k4 < R / 4; ++k4) {
@@ -685,9 +713,9 @@ cudaError_t launch_gather_port_blocks(const PieceDesc* pieces, int npieces, cons
 }
 
 cudaError_t launch_port_blocks_to_f16(const PieceDesc* pieces, int npieces, const float* S32, unsigned char* S16,
-                                      float* sig, cudaStream_t st) {
+                                      float* sig, float* gscale, cudaStream_t st) {
   if (npieces <= 0) return cudaSuccess;
-  k_port_blocks_to_f16<<<npieces, 256, 0, st>>>(pieces, S32, S16, sig);
+  k_port_blocks_to_f16<<<npieces, 256, 0, st>>>(pieces, S32, S16, sig, gscale);
   return cudaGetLastError();
 }
 

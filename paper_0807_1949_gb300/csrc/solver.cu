@@ -136,6 +136,7 @@ struct vtm_solver {
   bool ubase_ok = false;
   size_t port_smem = 0;
   DevBuf S16, sig16, tc_scratch;     // tensor-core form: fp16 hi / lo blocks, sigma_j, s^T slots
+  DevBuf gscale;                     // tensor-core form: sqrt(S_pp) per port (diagonal balance)
   int tc_grid = 0, tc_n4max = 0, tc_tmem_cols = 0;
   int64_t tc_bytes_hi = 0, tc_bytes_all = 0;  // bytes a sweep streams without / with the lo half
   DevBuf Sh, hscale;                 // FP16 copy of S_j and the scale of each of its tiles
@@ -941,6 +942,7 @@ static void launch_port(vtm_solver* s) {
       t.npieces = s->np_lo;
       t.S16 = s->S16.as<unsigned char>();
       t.sig_s = s->sig16.as<float>();
+      t.gscale = s->gscale.as<float>();
       t.scratch = s->tc_scratch.as<unsigned char>();
       t.n4max = s->tc_n4max;
       t.tmem_cols = s->tc_tmem_cols;
@@ -1027,7 +1029,7 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   const int n4max = (max_ports_lo + 127) / 128;
   int tmem_cols = 32;
   while (tmem_cols < n4max * s->R) tmem_cols *= 2;
-  const bool tmem_ok = n4max * s->R <= 512;
+  const bool tmem_ok = n4max * s->R <= 512 && n4max <= kTcMaxSuper;
   const size_t smem = tc ? port_tc_smem_bytes(s->R, true) : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
   // bytes one sweep streams (tensor cores: with the lo half) and the device memory setup needs
   const double s_bytes = tc ? (double)h_bytes : (double)s_tiles * kNB * kNB * sizeof(T);
@@ -1063,6 +1065,8 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     s->tc_scratch.alloc((size_t)s->tc_grid * ((size_t)2 * n4max * s->R * 512 + (size_t)n4max * 128 * s->R * 4));
     s->S16.alloc((size_t)std::max<int64_t>(1024, h_bytes));
     s->sig16.alloc((size_t)std::max(1, s->np_lo) * sizeof(float));
+    s->gscale.alloc((size_t)std::max(1, s->nports) * sizeof(float));
+    VTM_CUDA(cudaMemsetAsync(s->gscale.p, 0, s->gscale.bytes, s->stream));
     s->tc_bytes_all = h_bytes;
     s->tc_bytes_hi = h_bytes / 2;
     VTM_CUDA(port_tc_configure(s->R));
@@ -1084,7 +1088,8 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
       // fp16 hi / lo blocks of S_j / sigma_j from the FP32 setup blocks, which are then released
       VTM_CUDA(cudaMemsetAsync(s->S16.p, 0, s->S16.bytes, s->stream));
       VTM_CUDA(launch_port_blocks_to_f16(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->S.as<float>(),
-                                         s->S16.as<unsigned char>(), s->sig16.as<float>(), s->stream));
+                                         s->S16.as<unsigned char>(), s->sig16.as<float>(),
+                                         s->gscale.as<float>(), s->stream));
       VTM_CUDA(cudaStreamSynchronize(s->stream));
       s->S.alloc(0);
       // the hi half alone (FP16 storage) only when asked for: with one scale per subgraph its

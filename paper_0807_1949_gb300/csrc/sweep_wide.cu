@@ -15,25 +15,40 @@ namespace vtm {
 
 namespace {
 
+// Threads of the multi-RHS kernel: one CTA per SM fits (the slab ring and the vector window fill
+// the shared memory), so it carries 16 warps to hide the latency of each block step.
+constexpr int kWideThreads = 512;
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+  } else {
+    const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+    v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+  }
+}
+
 template <typename T, int R>
 struct WideLayout {
   static constexpr int kRG = kNB / 4;           // row groups (rows rg, rg+8, rg+16, rg+24)
   static constexpr int kCG = R / 4;             // column groups of 4
   static constexpr int kTiles = kRG * kCG;      // thread tiles per block product
-  static constexpr int kKS = kSweepThreads / kTiles;  // K splits
-  static_assert(kKS >= 1 && kSweepThreads % kTiles == 0, "tile mapping");
+  static constexpr int kKS = kWideThreads / kTiles;  // K splits
+  static_assert(kKS >= 1 && kWideThreads % kTiles == 0, "tile mapping");
 };
 
 }  // namespace
 
 size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap) {
   const int tiles = (kNB / 4) * (R / 4);
-  const int ks = kSweepThreads / tiles;
+  const int ks = kWideThreads / tiles;
   return 128 + elem * ((size_t)stages * slot_elems + (size_t)cap * R + (size_t)ks * kNB * R + 2 * (size_t)kNB * R);
 }
 
 template <typename T, typename TV, int R>
-__global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs<T, TV> a) {
+__global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<T, TV> a) {
   using LY = WideLayout<T, R>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
@@ -77,7 +92,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   };
   if (tid == 0)
     for (int s = 0; s < S && s < total; ++s) issue(s);
-  for (int i = tid; i < kCap * R; i += kSweepThreads) Yw[i] = T(0);
+  for (int i = tid; i < kCap * R; i += kWideThreads) Yw[i] = T(0);
   __syncthreads();
 
   // thread tile of the block products
@@ -91,7 +106,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
     const int k0 = (fwd ? s : total - 1 - s) * kNB;
     if (fwd) {
       // rows k0..k0+31 enter the window: b̃ plus the incident waves of their ports / Z
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         const int row = k0 + r;
         Yw[(size_t)(row & kMask) * R + c] = row < pd.n ? (T)bg[(size_t)row * R + c] : T(0);
@@ -101,7 +116,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
         const int p0 = pcur;
         int p1 = p0;
         while (p1 < pd.nports && a.port_local[pd.port_off + p1] < k0 + kNB) ++p1;
-        for (int i = tid; i < (p1 - p0) * R; i += kSweepThreads) {
+        for (int i = tid; i < (p1 - p0) * R; i += kWideThreads) {
           const int q = p0 + i / R, c = i % R;
           const int l = a.port_local[pd.port_off + q];
           T acc = T(0);
@@ -115,7 +130,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       }
     } else if (s > nblk) {
       // backward: rows k0 - off .. k0 - off + 31 enter the window from the stored y
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         const int row = k0 - off + r;
         if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = yg ? yg[(size_t)row * R + c] : (T)xg[(size_t)row * R + c];
@@ -134,15 +149,28 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
       const int q0 = (off * ks) / LY::kKS, q1 = (off * (ks + 1)) / LY::kKS;
-      for (int q = q0; q < q1; ++q) {
-        const T* y = Yw + (size_t)((k0 - off + q) & kMask) * R + 4 * cg;
+      // columns q < 31 lie left of the band start of some rows (entry q - r < 0): only there the
+      // rows need a test
+      const int qs = min(q1, max(q0, kNB - 1));
+      for (int q = q0; q < qs; ++q) {
         T yv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) yv[j] = y[j];
+        load4(Yw + (size_t)((k0 - off + q) & kMask) * R + 4 * cg, yv);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = rg + 8 * i;
           const T l = (q >= r) ? L[r * Wp + q - r] : T(0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += l * yv[j];
+        }
+      }
+      const T* Lrow = L + rg * (Wp - 1);
+#pragma unroll 2
+      for (int q = qs; q < q1; ++q) {
+        T yv[4];
+        load4(Yw + (size_t)((k0 - off + q) & kMask) * R + 4 * cg, yv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const T l = Lrow[8 * i * (Wp - 1) + q];
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] += l * yv[j];
         }
@@ -152,7 +180,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
 #pragma unroll
         for (int j = 0; j < 4; ++j) part[((size_t)ks * kNB + rg + 8 * i) * R + 4 * cg + j] = acc[i][j];
       __syncthreads();
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         T v = Yw[(size_t)((k0 + r) & kMask) * R + c];
 #pragma unroll
@@ -161,7 +189,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       }
       __syncthreads();
       // y_B = inv(L_KK) t
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         const T* Lr = L + r * Wp + off - r;
         T v = T(0);
@@ -174,14 +202,14 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       }
     } else {
       // x_B = inv(L_KK)^T y_B
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         T v = T(0);
         for (int r2 = r; r2 < kNB; ++r2) v += L[r2 * Wp + off - r2 + r] * Yw[(size_t)((k0 + r2) & kMask) * R + c];
         XB[i] = v;
       }
       __syncthreads();
-      for (int i = tid; i < kNB * R; i += kSweepThreads) {
+      for (int i = tid; i < kNB * R; i += kWideThreads) {
         const int r = i / R, c = i % R;
         if (k0 + r < pd.n) xg[(size_t)(k0 + r) * R + c] = (TV)XB[i];
         Yw[(size_t)((k0 + r) & kMask) * R + c] = XB[i];
@@ -190,7 +218,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
       // tiles of 4 consecutive q x 4 columns, split over the threads
       constexpr int kQT = 4;
       const int nq = (off + kQT - 1) / kQT;
-      for (int tile = tid; tile < nq * LY::kCG; tile += kSweepThreads) {
+      for (int tile = tid; tile < nq * LY::kCG; tile += kWideThreads) {
         const int qb = (tile / LY::kCG) * kQT, cc = (tile % LY::kCG) * 4;
         T acc[kQT][4];
 #pragma unroll
@@ -235,7 +263,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweep_wide(const SweepArgs
   }
   __syncthreads();
   // w_out[e] = 2 x_c - w_in[e]
-  for (int i = tid; i < pd.nports * R; i += kSweepThreads) {
+  for (int i = tid; i < pd.nports * R; i += kWideThreads) {
     const int q = i / R, c = i % R;
     const int l = a.port_local[pd.port_off + q];
     const T x = (T)xg[(size_t)l * R + c];
@@ -261,7 +289,7 @@ cudaError_t sweep_wide_configure(int R, size_t smem) {
 template <typename TF, typename TV>
 cudaError_t launch_sweep_wide(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st) {
   if (npieces <= 0) return cudaSuccess;
-  dim3 grid(npieces), block(kSweepThreads);
+  dim3 grid(npieces), block(kWideThreads);
   switch (R) {
     case 16: k_sweep_wide<TF, TV, 16><<<grid, block, smem, st>>>(a); break;
     case 32: k_sweep_wide<TF, TV, 32><<<grid, block, smem, st>>>(a); break;
