@@ -52,7 +52,6 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<
   using LY = WideLayout<T, R>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int abort_flag;
-  __shared__ int pcur;
   const int tid = threadIdx.x;
   const PieceDesc pd = a.pieces[blockIdx.x];
   const int S = a.stages;
@@ -77,7 +76,6 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<
 
   if (tid == 0) {
     abort_flag = 0;
-    pcur = 0;
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
     fence_proxy_async_smem();
@@ -100,42 +98,76 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<
   const int tt = tid % LY::kTiles;
   const int rg = tt / LY::kCG, cg = tt % LY::kCG;
 
+  // r = b̃ + P (Y w_in) for every row of the subgraph first (the port currents gathered from the
+  // twins' waves by all threads at once), into the y storage, which the forward pass then reads
+  // row block by row block and overwrites with y.
+  if (yg) {
+    for (int i = tid; i < pd.n * R; i += kWideThreads) yg[i] = (T)bg[i];
+  } else {
+    for (int i = tid; i < pd.n * R; i += kWideThreads) xg[i] = bg[i];
+  }
+  __syncthreads();
+  for (int i = tid; i < pd.nports * R; i += kWideThreads) {
+    const int q = i / R, c = i % R;
+    T acc = T(0);
+    for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
+      acc += (T)a.wprev[(size_t)a.twin[e] * R + c] * (T)a.invz[e];
+    if (a.cpl.ptr) acc += coupling_current<T, TV>(a.cpl, pd.port_off + q, c, R, a.wprev);
+    const size_t at = (size_t)a.port_local[pd.port_off + q] * R + c;
+    if (yg) yg[at] += acc;
+    else xg[at] = (TV)((T)xg[at] + acc);
+  }
+  __syncthreads();
+
+  // The inputs of a block step are loaded one step ahead into registers, so that their global
+  // latency overlaps the block products of the step before: forward, the rows k0 .. k0 + 31 of r;
+  // backward, the stored y of the rows k0 - off .. k0 - off + 31.
+  constexpr int kPer = kNB * R / kWideThreads;  // elements of a 32-row block per thread
+  static_assert(kPer >= 1 && (kNB * R) % kWideThreads == 0, "block elements per thread");
+  T in_v[kPer];
+  auto prefetch = [&](int s2) {
+    if (s2 >= total) return;
+    const bool f2 = s2 < nblk;
+    const int k2 = (f2 ? s2 : total - 1 - s2) * kNB;
+    if (f2) {
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = tid + j * kWideThreads;
+        const int row = k2 + i / R;
+        in_v[j] = row < pd.n ? (yg ? yg[(size_t)row * R + i % R] : (T)xg[(size_t)row * R + i % R]) : T(0);
+      }
+    } else if (s2 > nblk) {
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = tid + j * kWideThreads;
+        const int row = k2 - off + i / R, c = i % R;
+        in_v[j] = row >= 0 ? (yg ? yg[(size_t)row * R + c] : (T)xg[(size_t)row * R + c]) : T(0);
+      }
+    }
+  };
+  prefetch(0);
+
   int s = 0;
   for (; s < total; ++s) {
     const bool fwd = s < nblk;
     const int k0 = (fwd ? s : total - 1 - s) * kNB;
     if (fwd) {
-      // rows k0..k0+31 enter the window: b̃ plus the incident waves of their ports / Z
-      for (int i = tid; i < kNB * R; i += kWideThreads) {
-        const int r = i / R, c = i % R;
-        const int row = k0 + r;
-        Yw[(size_t)(row & kMask) * R + c] = row < pd.n ? (T)bg[(size_t)row * R + c] : T(0);
-      }
-      __syncthreads();
-      {
-        const int p0 = pcur;
-        int p1 = p0;
-        while (p1 < pd.nports && a.port_local[pd.port_off + p1] < k0 + kNB) ++p1;
-        for (int i = tid; i < (p1 - p0) * R; i += kWideThreads) {
-          const int q = p0 + i / R, c = i % R;
-          const int l = a.port_local[pd.port_off + q];
-          T acc = T(0);
-          for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
-            acc += (T)a.wprev[(size_t)a.twin[e] * R + c] * (T)a.invz[e];
-          if (a.cpl.ptr) acc += coupling_current<T, TV>(a.cpl, pd.port_off + q, c, R, a.wprev);
-          Yw[(size_t)(l & kMask) * R + c] += acc;
-        }
-        __syncthreads();
-        if (tid == 0) pcur = p1;
+      // rows k0..k0+31 of r enter the window
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = tid + j * kWideThreads;
+        Yw[(size_t)((k0 + i / R) & kMask) * R + i % R] = in_v[j];
       }
     } else if (s > nblk) {
       // backward: rows k0 - off .. k0 - off + 31 enter the window from the stored y
-      for (int i = tid; i < kNB * R; i += kWideThreads) {
-        const int r = i / R, c = i % R;
-        const int row = k0 - off + r;
-        if (row >= 0) Yw[(size_t)(row & kMask) * R + c] = yg ? yg[(size_t)row * R + c] : (T)xg[(size_t)row * R + c];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = tid + j * kWideThreads;
+        const int row = k0 - off + i / R;
+        if (row >= 0) Yw[(size_t)(row & kMask) * R + i % R] = in_v[j];
       }
     }
+    prefetch(s + 1);
     const int slot = s % S;
     if (!mbar_wait_bounded(&bars[slot], (uint32_t)((s / S) & 1), a.wait_limit)) abort_flag = 1;
     __syncthreads();
@@ -188,25 +220,38 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<
         TB[i] = v;
       }
       __syncthreads();
-      // y_B = inv(L_KK) t
-      for (int i = tid; i < kNB * R; i += kWideThreads) {
-        const int r = i / R, c = i % R;
-        const T* Lr = L + r * Wp + off - r;
-        T v = T(0);
-        for (int c2 = 0; c2 <= r; ++c2) v += Lr[c2] * TB[c2 * R + c];
-        Yw[(size_t)((k0 + r) & kMask) * R + c] = v;
-        if (k0 + r < pd.n) {
-          if (yg) yg[(size_t)(k0 + r) * R + c] = v;
-          else xg[(size_t)(k0 + r) * R + c] = (TV)v;
+      // y_B = inv(L_KK) t; a thread takes rows r and 31 - r (r + 1 and 32 - r terms: balanced)
+      for (int i = tid; i < kNB * R / 2; i += kWideThreads) {
+        const int rr[2] = {i / R, kNB - 1 - i / R};
+        const int c = i % R;
+        T v[2] = {T(0), T(0)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const T* Lr = L + rr[h] * Wp + off - rr[h];
+          for (int c2 = 0; c2 <= rr[h]; ++c2) v[h] += Lr[c2] * TB[c2 * R + c];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = rr[h];
+          Yw[(size_t)((k0 + r) & kMask) * R + c] = v[h];
+          if (k0 + r < pd.n) {
+            if (yg) yg[(size_t)(k0 + r) * R + c] = v[h];
+            else xg[(size_t)(k0 + r) * R + c] = (TV)v[h];
+          }
         }
       }
     } else {
-      // x_B = inv(L_KK)^T y_B
-      for (int i = tid; i < kNB * R; i += kWideThreads) {
-        const int r = i / R, c = i % R;
-        T v = T(0);
-        for (int r2 = r; r2 < kNB; ++r2) v += L[r2 * Wp + off - r2 + r] * Yw[(size_t)((k0 + r2) & kMask) * R + c];
-        XB[i] = v;
+      // x_B = inv(L_KK)^T y_B; rows r and 31 - r per thread (32 - r and r + 1 terms)
+      for (int i = tid; i < kNB * R / 2; i += kWideThreads) {
+        const int rr[2] = {i / R, kNB - 1 - i / R};
+        const int c = i % R;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = rr[h];
+          T v = T(0);
+          for (int r2 = r; r2 < kNB; ++r2) v += L[r2 * Wp + off - r2 + r] * Yw[(size_t)((k0 + r2) & kMask) * R + c];
+          XB[r * R + c] = v;
+        }
       }
       __syncthreads();
       for (int i = tid; i < kNB * R; i += kWideThreads) {
@@ -226,16 +271,30 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_sweep_wide(const SweepArgs<
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
         const int rmax = min(kNB - 1, qb + kQT - 1);
-        for (int r = 0; r <= rmax; ++r) {
-          T xv[4];
+        if (qb >= kNB - 1 && qb + kQT <= off) {
+          // every entry q - r of the tile lies inside the band row: no tests
+          for (int r = 0; r <= rmax; ++r) {
+            T xv[4];
+            load4(XB + r * R + cc, xv);
+            const T* Lr = L + r * (Wp - 1) + qb;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) xv[j] = XB[r * R + cc + j];
+            for (int i = 0; i < kQT; ++i) {
+              const T l = Lr[i];
 #pragma unroll
-          for (int i = 0; i < kQT; ++i) {
-            const int q = qb + i;
-            const T l = (q >= r && q < off) ? L[r * Wp + q - r] : T(0);
+              for (int j = 0; j < 4; ++j) acc[i][j] += l * xv[j];
+            }
+          }
+        } else {
+          for (int r = 0; r <= rmax; ++r) {
+            T xv[4];
+            load4(XB + r * R + cc, xv);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] += l * xv[j];
+            for (int i = 0; i < kQT; ++i) {
+              const int q = qb + i;
+              const T l = (q >= r && q < off) ? L[r * Wp + q - r] : T(0);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[i][j] += l * xv[j];
+            }
           }
         }
 #pragma unroll
