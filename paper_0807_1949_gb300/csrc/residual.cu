@@ -48,41 +48,61 @@ __global__ void k_split(int64_t ncopies, int R, const int64_t* __restrict__ copy
   for (int r = 0; r < R; ++r) bt[c * R + r] = (T)(s * src[v + r * ld]);
 }
 
-template <typename T>
+// Thread (vertex or row i, column group blockIdx.y): RG right-hand sides per thread, so that the
+// row of A (or the copy list of the vertex) is read once per group and each column's accesses to
+// the column-major vectors are coalesced across neighbouring threads.
+template <typename T, int RG>
 __global__ void k_assemble(int64_t n, int R, const int64_t* __restrict__ vc_ptr, const int64_t* __restrict__ vc_copy,
                            const T* __restrict__ xc, const double* __restrict__ xbase, double* __restrict__ xt, int64_t ld) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RG;
   if (i >= n) return;
   const int64_t lo = vc_ptr[i], hi = vc_ptr[i + 1];
   const double inv = 1.0 / (double)(hi - lo);
-  for (int r = 0; r < R; ++r) {
-    double s = 0.0;
-    for (int64_t k = lo; k < hi; ++k) s += (double)xc[vc_copy[k] * R + r];
-    xt[i + r * ld] = (xbase ? xbase[i + r * ld] : 0.0) + s * inv;
+  double s[RG];
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) s[rr] = 0.0;
+  for (int64_t k = lo; k < hi; ++k) {
+    const T* p = xc + vc_copy[k] * R + r0;  // the copy's RG values are contiguous
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) s[rr] += (double)p[rr];
+  }
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) {
+    const int64_t at = i + (int64_t)(r0 + rr) * ld;
+    xt[at] = (xbase ? xbase[at] : 0.0) + s[rr] * inv;
   }
 }
 
+template <int RG>
 __global__ void k_residual(int64_t n, int R, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const double* __restrict__ val, const double* __restrict__ b, int64_t ldb,
                            const double* __restrict__ x, int64_t ldx, double* __restrict__ res, int64_t ldr,
                            double* norms) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RG;
   double sq[kMaxR];
 #pragma unroll
   for (int r = 0; r < kMaxR; ++r) sq[r] = 0.0;
   if (i < n) {
     const int64_t lo = rowptr[i], hi = rowptr[i + 1];
+    double ax[RG];
 #pragma unroll
-    for (int r = 0; r < kMaxR; ++r) {
-      if (r >= R) break;
-      double ax = 0.0;
-      for (int64_t k = lo; k < hi; ++k) ax += val[k] * x[col[k] + r * ldx];
-      const double ri = b[i + r * ldb] - ax;
-      if (res) res[i + r * ldr] = ri;
-      sq[r] = ri * ri;
+    for (int rr = 0; rr < RG; ++rr) ax[rr] = 0.0;
+    for (int64_t k = lo; k < hi; ++k) {
+      const double v = val[k];
+      const double* xk = x + col[k];
+#pragma unroll
+      for (int rr = 0; rr < RG; ++rr) ax[rr] += v * xk[(int64_t)(r0 + rr) * ldx];
+    }
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) {
+      const double ri = b[i + (int64_t)(r0 + rr) * ldb] - ax[rr];
+      if (res) res[i + (int64_t)(r0 + rr) * ldr] = ri;
+      sq[rr] = ri * ri;
     }
   }
-  block_accumulate(sq, R, norms);
+  block_accumulate(sq, RG, norms + r0);
 }
 
 __global__ void k_sqnorm(int64_t n, int R, const double* __restrict__ v, int64_t ld, double* norms) {
@@ -140,18 +160,29 @@ cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, con
   return cudaGetLastError();
 }
 
+// Column groups of min(R, 8) right-hand sides (R is 1, 2, 4, 8, 16 or 32; other counts go one by one).
 template <typename T>
 cudaError_t launch_assemble(int64_t n, int R, const int64_t* vc_ptr, const int64_t* vc_copy, const T* xc,
                             const double* xbase, double* xt, int64_t ld, cudaStream_t st) {
-  k_assemble<T><<<nblocks(n), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
+  if (n <= 0) return cudaSuccess;
+  const unsigned bx = nblocks(n);
+  if (R % 8 == 0) k_assemble<T, 8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
+  else if (R % 4 == 0) k_assemble<T, 4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
+  else if (R % 2 == 0) k_assemble<T, 2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
+  else k_assemble<T, 1><<<dim3(bx, R), kBS, 0, st>>>(n, R, vc_ptr, vc_copy, xc, xbase, xt, ld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
                             const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
                             double* norms, cudaStream_t st) {
-  if (R > kMaxR) return cudaErrorInvalidValue;
-  k_residual<<<nblocks(n), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  if (R > kMaxR || R < 1) return cudaErrorInvalidValue;
+  if (n <= 0) return cudaSuccess;
+  const unsigned bx = nblocks(n);
+  if (R % 8 == 0) k_residual<8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  else if (R % 4 == 0) k_residual<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  else if (R % 2 == 0) k_residual<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  else k_residual<1><<<dim3(bx, R), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
   return cudaGetLastError();
 }
 
