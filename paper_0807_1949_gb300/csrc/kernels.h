@@ -77,12 +77,19 @@ struct PortArgs {
   const int32_t* twin;
   const T* invz;
   CoupleRef<T> cpl;            // coupled lines (cpl.ptr == nullptr: none)
+  int det;                     // per-warp column accumulators summed in a fixed order (bitwise
+                               // reproducible); 0: shared-memory atomics
 };
 
+// Shared memory the deterministic SIMT port sweep may take (it keeps three CTAs per SM with FP16
+// storage).
+constexpr size_t kPortDetSmem = 72 * 1024;
+
 __host__ __device__ int64_t port_tiles(int nports);
-size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports);
+size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports, bool det);
+bool port_sweep_det_fits(size_t elem, int R, int max_ports);
 template <typename T>
-cudaError_t port_sweep_configure(int R, size_t smem);
+cudaError_t port_sweep_configure(int R, size_t smem, bool det);
 template <typename T>
 cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st);
 template <typename T>

@@ -139,8 +139,13 @@ __global__ void k_gather_ports(const PieceDesc* __restrict__ pieces, const int32
 }
 
 // One sweep in port-response form, one CTA per subgraph, R right-hand sides.
-// Shared memory: s (n_pad_ports x R) and the accumulator y (same size).
-template <typename T, typename TS, int R>
+// Shared memory: s (n_pad_ports x R), the accumulator y (same size) and, with DET, one accumulator
+// of the same size per warp.  Warp w takes the tiles w, w + 8, ... of the stored lower block
+// triangle (so the eight warps stream neighbouring tiles).  With DET every warp adds its tiles'
+// row and column parts to its own accumulator (in each add the 32 lanes hit 32 different ports),
+// and the accumulators are summed in warp order at the end: identical runs agree bit for bit.
+// Without DET (the accumulators would not fit) the warps add to y with shared-memory atomics.
+template <typename T, typename TS, int R, bool DET>
 __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port_sweep(const PortArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const PieceDesc pd = a.pieces[blockIdx.x];
@@ -151,6 +156,11 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
   T* sv = reinterpret_cast<T*>(smem);
   T* yv = sv + (size_t)npad * R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kSweepThreads / 32;
+  T* const yacc = DET ? yv + (size_t)(1 + warp) * npad * R : yv;  // where this warp adds its parts
+  if constexpr (DET) {
+    for (int i = tid; i < kWarps * npad * R; i += kSweepThreads) yv[(size_t)npad * R + i] = T(0);
+  }
 
   // s_q = sum_e w_in[e] / Z_e, w_in[e] = w_prev[twin[e]]; kU entries per thread at a time, their
   // end ranges, twins and waves loaded in three independent rounds
@@ -194,7 +204,6 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
   const int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
   const int pa = lane >> 2, pb = lane & 3;  // patch: rows 4 pa .. +3, columns 8 pb .. +7
   // each warp keeps the next tile's loads in flight while it works on the current one
-  constexpr int kWarps = kSweepThreads / 32;
   RawPatch<TS> cur, nxt;
   // FP16 storage: each tile was divided by its own largest |entry|; the two reduced sums of a
   // tile are multiplied back before they are added to y
@@ -240,7 +249,12 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
           rp[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
         }
       }
-      atomicAdd(&yv[((size_t)I * kNB + 4 * pa + pb) * R + r], (sizeof(TS) == 2) ? rp[0] * sc : rp[0]);
+      {
+        const T v = (sizeof(TS) == 2) ? rp[0] * sc : rp[0];
+        T* at = &yacc[((size_t)I * kNB + 4 * pa + pb) * R + r];
+        if constexpr (DET) *at += v;
+        else atomicAdd(at, v);
+      }
       if (I != J) {
         // column part: 8 partial column sums over this lane's 4 rows, reduce-scattered over the 8
         // lanes of the same column group (xor 16, 8, 4): lane (pa, pb) ends with column 8 pb + pa
@@ -262,11 +276,24 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
             cp[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4 * h);
           }
         }
-        atomicAdd(&yv[((size_t)J * kNB + 8 * pb + pa) * R + r], (sizeof(TS) == 2) ? cp[0] * sc : cp[0]);
+        const T v = (sizeof(TS) == 2) ? cp[0] * sc : cp[0];
+        T* at = &yacc[((size_t)J * kNB + 8 * pb + pa) * R + r];
+        if constexpr (DET) *at += v;
+        else atomicAdd(at, v);
       }
     }
   }
   __syncthreads();
+  if constexpr (DET) {
+    // y = the warps' accumulators, summed in warp order
+    for (int i = tid; i < npad * R; i += kSweepThreads) {
+      T v = T(0);
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) v += yv[(size_t)(1 + w) * npad * R + i];
+      yv[i] = v;
+    }
+    __syncthreads();
+  }
 
   // w_out[e] = 2 (u_base + y)_q - w_in[e]
   for (int i0 = tid; i0 < np * R; i0 += kSweepThreads * kU) {
@@ -298,39 +325,43 @@ __global__ void __launch_bounds__(kSweepThreads, sizeof(TS) == 2 ? 3 : 2) k_port
   }
 }
 
-size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports) {
+size_t port_sweep_smem_bytes(size_t elem, int R, int max_ports, bool det) {
   const size_t npad = (size_t)((max_ports + kNB - 1) / kNB) * kNB;
-  return 2 * npad * R * elem;
+  return (det ? 2 + kSweepThreads / 32 : 2) * npad * R * elem;
 }
 
-template <typename T, typename TS>
+bool port_sweep_det_fits(size_t elem, int R, int max_ports) {
+  return port_sweep_smem_bytes(elem, R, max_ports, true) <= kPortDetSmem;
+}
+
+template <typename T, typename TS, bool DET>
 static cudaError_t port_configure_ts(int R, size_t smem) {
   const int b = (int)smem;
   switch (R) {
-    case 1: return cudaFuncSetAttribute(k_port_sweep<T, TS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 2: return cudaFuncSetAttribute(k_port_sweep<T, TS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 4: return cudaFuncSetAttribute(k_port_sweep<T, TS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 8: return cudaFuncSetAttribute(k_port_sweep<T, TS, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 1: return cudaFuncSetAttribute(k_port_sweep<T, TS, 1, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 2: return cudaFuncSetAttribute(k_port_sweep<T, TS, 2, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 4: return cudaFuncSetAttribute(k_port_sweep<T, TS, 4, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 8: return cudaFuncSetAttribute(k_port_sweep<T, TS, 8, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
-cudaError_t port_sweep_configure(int R, size_t smem) {
-  cudaError_t e = port_configure_ts<T, T>(R, smem);
+cudaError_t port_sweep_configure(int R, size_t smem, bool det) {
+  cudaError_t e = det ? port_configure_ts<T, T, true>(R, smem) : port_configure_ts<T, T, false>(R, smem);
   if constexpr (sizeof(T) == 4) {
-    if (e == cudaSuccess) e = port_configure_ts<T, __half>(R, smem);
+    if (e == cudaSuccess) e = det ? port_configure_ts<T, __half, true>(R, smem) : port_configure_ts<T, __half, false>(R, smem);
   }
   return e;
 }
 
-template <typename T, typename TS>
+template <typename T, typename TS, bool DET>
 static cudaError_t port_launch_ts(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
   switch (R) {
-    case 1: k_port_sweep<T, TS, 1><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 2: k_port_sweep<T, TS, 2><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 4: k_port_sweep<T, TS, 4><<<npieces, kSweepThreads, smem, st>>>(a); break;
-    case 8: k_port_sweep<T, TS, 8><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 1: k_port_sweep<T, TS, 1, DET><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 2: k_port_sweep<T, TS, 2, DET><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 4: k_port_sweep<T, TS, 4, DET><<<npieces, kSweepThreads, smem, st>>>(a); break;
+    case 8: k_port_sweep<T, TS, 8, DET><<<npieces, kSweepThreads, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -340,9 +371,10 @@ template <typename T>
 cudaError_t launch_port_sweep(const PortArgs<T>& a, int R, int npieces, size_t smem, cudaStream_t st) {
   if (npieces <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (a.Sh) return port_launch_ts<T, __half>(a, R, npieces, smem, st);
+    if (a.Sh) return a.det ? port_launch_ts<T, __half, true>(a, R, npieces, smem, st)
+                           : port_launch_ts<T, __half, false>(a, R, npieces, smem, st);
   }
-  return port_launch_ts<T, T>(a, R, npieces, smem, st);
+  return a.det ? port_launch_ts<T, T, true>(a, R, npieces, smem, st) : port_launch_ts<T, T, false>(a, R, npieces, smem, st);
 }
 
 // FP16 copy of the FP32 tiles of one subgraph per CTA, one warp per tile: each tile is divided by
@@ -395,7 +427,7 @@ cudaError_t launch_gather_ports(const PieceDesc* pieces, int npieces, const int3
 }
 
 #define VTM_PORT_INST(T)                                                                                       \
-  template cudaError_t port_sweep_configure<T>(int, size_t);                                                   \
+  template cudaError_t port_sweep_configure<T>(int, size_t, bool);                                             \
   template cudaError_t launch_port_sweep<T>(const PortArgs<T>&, int, int, size_t, cudaStream_t);               \
   template cudaError_t launch_gather_port_response<T>(const PieceDesc*, int, const int32_t*, int, int, const T*, \
                                                       T*, cudaStream_t);                                        \

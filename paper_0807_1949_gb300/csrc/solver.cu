@@ -135,6 +135,7 @@ struct vtm_solver {
   DevBuf S, ubase, wzero, wscr;
   bool ubase_ok = false;
   size_t port_smem = 0;
+  bool port_det = false;             // SIMT port sweep: fixed-order (bitwise reproducible) reduction
   DevBuf S16, sig16, tc_scratch;     // tensor-core form: fp16 hi / lo blocks, sigma_j, s^T slots
   DevBuf gscale;                     // tensor-core form: sqrt(S_pp) per port (diagonal balance)
   int tc_grid = 0, tc_n4max = 0, tc_tmem_cols = 0;
@@ -961,6 +962,7 @@ static void launch_port(vtm_solver* s) {
     }
   }
   PortArgs<T> a;
+  a.det = s->port_det ? 1 : 0;
   a.Sh = s->port_half ? s->Sh.p : nullptr;
   a.scale = s->hscale.as<float>();
   a.pieces = s->pieces_lo.as<PieceDesc>();
@@ -1030,7 +1032,8 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
   int tmem_cols = 32;
   while (tmem_cols < n4max * s->R) tmem_cols *= 2;
   const bool tmem_ok = n4max * s->R <= 512 && n4max <= kTcMaxSuper;
-  const size_t smem = tc ? port_tc_smem_bytes(s->R, true) : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo);
+  const bool det = !tc && port_sweep_det_fits(sizeof(T), s->R, max_ports_lo);
+  const size_t smem = tc ? port_tc_smem_bytes(s->R, true) : port_sweep_smem_bytes(sizeof(T), s->R, max_ports_lo, det);
   // bytes one sweep streams (tensor cores: with the lo half) and the device memory setup needs
   const double s_bytes = tc ? (double)h_bytes : (double)s_tiles * kNB * kNB * sizeof(T);
   const double setup_bytes = tc ? s_bytes + (double)s_tiles * 128.0 * 128.0 * 4.0 : s_bytes;
@@ -1071,7 +1074,8 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     s->tc_bytes_hi = h_bytes / 2;
     VTM_CUDA(port_tc_configure(s->R));
   } else {
-    VTM_CUDA(port_sweep_configure<T>(s->R, smem));
+    VTM_CUDA(port_sweep_configure<T>(s->R, smem, det));
+    s->port_det = det;
   }
   s->ubase.alloc((size_t)std::max(1, s->nports) * s->R * sizeof(T));
   s->wzero.alloc((size_t)s->E * s->R * sizeof(T));

@@ -48,19 +48,23 @@ def test_band_sweeps_are_bitwise_reproducible(vtmlib, precision, nrhs):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-def test_port_sweeps_reproducible_to_rounding(vtmlib):
-    """The SIMT port sweep combines its warps' tile products with shared-memory atomics, so the
-    summation order, and the last bits, may change between runs; identical runs must agree to
-    rounding (FP64: 1e-13 of the largest wave)."""
+@pytest.mark.parametrize("precision,nrhs,storage", [("fp64", 1, "native"), ("fp32", 1, "fp16"), ("fp32", 2, "native"),
+                                                    ("fp32", 16, "native"), ("fp32", 32, "fp16")])
+def test_port_sweeps_are_bitwise_reproducible(vtmlib, precision, nrhs, storage):
+    """The SIMT port sweep hands each block row of S_j to one warp and sums the warps' column parts in
+    a fixed order; the tensor-core sweep issues its products from one thread in a fixed order and
+    reduces its column maxima without atomics.  Identical runs agree bit for bit, coupled lines
+    included."""
     dims, block = (40, 37, 21), (8, 8, 8)
     A = inputs.grid_poisson(dims, sigma=0.9, seed=53)
-    b = inputs.rhs_uniform(A.n, 1, seed=53)
+    b = inputs.rhs_uniform(A.n, nrhs, seed=53)
     part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
     out = []
     for _ in range(2):
-        s = vtmlib.Solver(part, z=2.0, precision="fp64", form="port", coupling=0.5)
+        s = vtmlib.Solver(part, z=2.0, precision=precision, nrhs=nrhs, form="port", coupling=0.5, port_storage=storage)
+        assert s.info().sweep_form == 2
         s.set_rhs(b)
         s.reset()
         s.iterate(12)
-        out.append(s.get_state())
-    assert np.max(np.abs(out[0] - out[1])) <= 1e-13 * np.max(np.abs(out[0]))
+        out.append((s.get_state(), s.copies()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
