@@ -28,8 +28,17 @@ geometric mean of sweeps to 1e-8 over six seeds (200000..) that neither training
 and learned vs learned + coupled is reported on the held-out test seeds.  The rule is stored in the
 model file ("coupling") and applied by bench.py --coupling model.
 
+Baselines (--baselines): the trained network against the best uniform Z (a scan fitted on eight
+training seeds) and against the search family with one global parameter set (the median of the
+training set's searched parameters), uncoupled and coupled (each rule with its own (scale, gamma)
+selected on seeds 200000..); held-out medians stored in the model file under "baselines".
+Training-set size (--saturation n1,n2,..): networks retrained on the first n searched problems,
+held-out median sweeps stored under "saturation".
+
 Run:  python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --train 200 --test 60
       python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --couple --test 8
+      python -m paper_0807_1949_gb300.learned_z --family poisson3d-wide --baselines --test 8
+      python -m paper_0807_1949_gb300.learned_z --family poisson2d-256 --saturation 50,100,200,400,800 --test 60
 """
 from __future__ import annotations
 
@@ -272,6 +281,129 @@ def evaluate_coupled(model: vtm.MLP, family: str, seeds, scale: float, gamma: fl
     return rows
 
 
+def geomean_sweeps(rows) -> float:
+    """Geometric mean of sweeps to tolerance, a solve that did not converge counted as 40000."""
+    return float(np.exp(np.mean(np.log([r["sweeps"] if r["converged"] else 40000 for r in rows]))))
+
+
+def fit_uniform(family: str, seeds, rtol=1e-8, verbose=True) -> tuple[float, dict]:
+    """The best uniform impedance of a family: the Z of a coarse-to-fine scan (factors of 2, then
+    sqrt(2)) with the smallest geometric mean of sweeps to rtol over ``seeds``."""
+    evs = []
+    for sd in seeds:
+        A, dims, block, sigma, b = problem(family, sd)
+        evs.append(Evaluator(A, dims, block, b))
+    scores = {}
+
+    def score(z):
+        key = round(z, 6)
+        if key not in scores:
+            scores[key] = geomean_sweeps([ev.to_tolerance(z, rtol) for ev in evs])
+            if verbose:
+                print(f"uniform Z {z:.4g}: geometric mean {scores[key]:.1f} sweeps", flush=True)
+        return scores[key]
+
+    best = min((0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0), key=score)
+    for f in (math.sqrt(2.0), 2 ** 0.25):
+        best = min((best / f, best, best * f), key=score)
+    return best, {str(k): v for k, v in scores.items()}
+
+
+def global_theta(meta: dict) -> tuple:
+    """One rule for the whole family: the componentwise median of the per-problem searched parameters
+    of the training set."""
+    th = np.array([m["theta"] + [0.0] * (4 - len(m["theta"])) for m in meta["search"]], np.float64)
+    return tuple(float(v) for v in np.median(th, axis=0))
+
+
+def select_uniform_coupling(family: str, seeds, z0: float, scales, gammas, rtol=1e-8, verbose=True):
+    """The coupled-line rule on top of a uniform impedance: (scale, gamma) with the smallest geometric
+    mean of sweeps over ``seeds`` for Z = scale z0 on every line and y_p = gamma |a_ik|."""
+    table = {}
+    for sd in seeds:
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        for c in scales:
+            for g in gammas:
+                r = ev.to_tolerance(c * z0, rtol, coupling=g)
+                table.setdefault((c, g), []).append(r["sweeps"] if r["converged"] else 40000)
+        if verbose:
+            print(f"uniform coupling scan seed {sd}: " +
+                  " ".join(f"{c}/{g}:{table[(c, g)][-1]}" for c in scales for g in gammas), flush=True)
+    gm = {k: float(np.exp(np.mean(np.log(v)))) for k, v in table.items()}
+    return min(gm, key=gm.get), {f"{c}/{g}": v for (c, g), v in gm.items()}
+
+
+def baselines(path: str, test: int, fit_seeds: int = 8, verbose=True) -> dict:
+    """What the trained network gains over the method without it: held-out sweeps to 1e-8 for Z = 1,
+    the best uniform Z (fitted on training seeds), the search family with one global parameter set
+    (the median of the training set's searched parameters) and the learned impedances, uncoupled
+    and with coupled lines (each with its own (scale, gamma) selected on seeds 200000..200005)."""
+    with open(path) as f:
+        meta = json.load(f)
+    family = meta["family"]
+    model = load(path)
+    zu, uscan = fit_uniform(family, range(fit_seeds), verbose=verbose)
+    th = global_theta(meta)
+    cu = meta.get("coupling")
+    scales = (1.0, 2.0, 3.0, 4.0, 6.0)
+    gammas = (0.5, 0.75, 1.0, 1.5)
+    (uc, ug), ucscan = select_uniform_coupling(family, range(200_000, 200_006), zu, scales, gammas, verbose=verbose)
+    rows = []
+    for sd in range(100_000, 100_000 + test):
+        A, dims, block, sigma, b = problem(family, sd)
+        ev = Evaluator(A, dims, block, b)
+        zl = model_impedances(ev, model)
+        row = dict(seed=sd, sigma=sigma, z1=ev.to_tolerance(1.0), best_uniform=ev.to_tolerance(zu),
+                   global_theta=ev.to_tolerance(family_z(ev.feats, th)), learned=ev.to_tolerance(zl),
+                   uniform_coupled=ev.to_tolerance(uc * zu, coupling=ug))
+        if cu:
+            row["learned_coupled"] = ev.to_tolerance(cu["z_scale"] * zl, coupling=cu["gamma"])
+        rows.append(row)
+        if verbose:
+            print(f"seed {sd}: " + "  ".join(f"{k} {v['sweeps']}" for k, v in row.items() if isinstance(v, dict)),
+                  flush=True)
+    keys = [k for k in rows[0] if isinstance(rows[0][k], dict)]
+    med = {k: float(np.median([r[k]["sweeps"] for r in rows])) for k in keys}
+    out = dict(best_uniform_z=zu, fit_seeds=fit_seeds, uniform_scan=uscan, global_theta=list(th),
+               uniform_coupling=dict(z_scale=uc, gamma=ug, scan_geomean_sweeps=ucscan), eval=rows, median_sweeps=med)
+    meta["baselines"] = out
+    with open(path, "w") as f:
+        json.dump(meta, f)
+    if verbose:
+        print("median sweeps to 1e-8 on held-out seeds:", med, flush=True)
+    return out
+
+
+def saturation(family: str, sizes, test: int, epochs: int = 60, verbose=True) -> dict:
+    """Held-out median sweeps of networks trained on the first n searched problems of the family's
+    model file (the searched parameters are stored there; only the features are recomputed)."""
+    path = os.path.join(MODELS, f"z_{family}.json")
+    with open(path) as f:
+        meta = json.load(f)
+    feats, targets = [], []
+    for m in meta["search"][:max(sizes)]:
+        A, dims, block, sigma, b = problem(family, m["seed"])
+        ev = Evaluator(A, dims, block, b)
+        feats.append(ev.feats)
+        targets.append(np.repeat(np.log(family_z(ev.feats, m["theta"])), 2).astype(np.float32))
+    evs = []
+    for sd in range(100_000, 100_000 + test):
+        A, dims, block, sigma, b = problem(family, sd)
+        evs.append(Evaluator(A, dims, block, b))
+    curve = {}
+    for n in sizes:
+        model = vtm.MLP(seed=1)
+        train(model, np.concatenate(feats[:n]), np.concatenate(targets[:n]), epochs=epochs)
+        curve[str(n)] = float(np.median([ev.to_tolerance(model)["sweeps"] for ev in evs]))
+        if verbose:
+            print(f"trained on {n} problems: held-out median {curve[str(n)]} sweeps", flush=True)
+    meta["saturation"] = dict(sizes=list(sizes), test_seeds=test, epochs=epochs, median_sweeps=curve)
+    with open(path, "w") as f:
+        json.dump(meta, f)
+    return curve
+
+
 def save(model: vtm.MLP, path: str, **meta):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
@@ -300,7 +432,20 @@ def main():
                          "200000.. and evaluate it on the held-out seeds; stored in the model file")
     ap.add_argument("--couple-scales", default="2,3,4,5,6")
     ap.add_argument("--couple-gammas", default="0.5,0.75,1,1.5")
+    ap.add_argument("--baselines", action="store_true",
+                    help="keep the trained model; evaluate it on the held-out seeds against the best uniform Z "
+                         "(fitted on training seeds) and one global parameter set of the search family, "
+                         "uncoupled and coupled; stored in the model file")
+    ap.add_argument("--saturation", default=None,
+                    help="comma-separated training-set sizes: retrain on the first n searched problems of the "
+                         "model file and report the held-out median sweeps")
     a = ap.parse_args()
+    if a.baselines:
+        baselines(a.out or os.path.join(MODELS, f"z_{a.family}.json"), a.test)
+        return
+    if a.saturation:
+        saturation(a.family, tuple(int(v) for v in a.saturation.split(",")), a.test, epochs=a.epochs)
+        return
     if a.couple:
         path = a.out or os.path.join(MODELS, f"z_{a.family}.json")
         with open(path) as f:
