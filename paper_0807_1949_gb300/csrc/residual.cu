@@ -38,14 +38,29 @@ __device__ void block_accumulate(const double* v, int R, double* norms) {
 }
 }  // namespace
 
-template <typename T>
+// Thread (copy c, columns 4 g .. 4 g + 3): the four values of a copy go out in one vector store
+// (b̃ is copies x R with R contiguous; R % 4 == 0 here, other R one column per thread).
+template <typename T, int CG>
 __global__ void k_split(int64_t ncopies, int R, const int64_t* __restrict__ copy_vertex, const double* __restrict__ share,
                         const double* __restrict__ src, int64_t ld, T* __restrict__ bt) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * CG;
   if (c >= ncopies) return;
   const int64_t v = copy_vertex[c];
   const double s = share[c];
-  for (int r = 0; r < R; ++r) bt[c * R + r] = (T)(s * src[v + r * ld]);
+  T o[CG];
+#pragma unroll
+  for (int j = 0; j < CG; ++j) o[j] = (T)(s * src[v + (int64_t)(r0 + j) * ld]);
+  T* q = bt + c * R + r0;
+  if constexpr (CG == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(q) = make_float4(o[0], o[1], o[2], o[3]);
+  } else if constexpr (CG == 4 && sizeof(T) == 8) {
+    reinterpret_cast<double2*>(q)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(q)[1] = make_double2(o[2], o[3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < CG; ++j) q[j] = o[j];
+  }
 }
 
 // Thread (vertex or row i, column group blockIdx.y): RG right-hand sides per thread, so that the
@@ -63,9 +78,24 @@ __global__ void k_assemble(int64_t n, int R, const int64_t* __restrict__ vc_ptr,
 #pragma unroll
   for (int rr = 0; rr < RG; ++rr) s[rr] = 0.0;
   for (int64_t k = lo; k < hi; ++k) {
-    const T* p = xc + vc_copy[k] * R + r0;  // the copy's RG values are contiguous
+    const T* p = xc + vc_copy[k] * R + r0;  // the copy's RG values are contiguous (and 16-byte
+                                            // aligned when RG is 4 or 8: R and r0 are multiples of RG)
+    if constexpr (RG % 4 == 0 && sizeof(T) == 4) {
 #pragma unroll
-    for (int rr = 0; rr < RG; ++rr) s[rr] += (double)p[rr];
+      for (int g = 0; g < RG / 4; ++g) {
+        const float4 v = reinterpret_cast<const float4*>(p)[g];
+        s[4 * g] += v.x, s[4 * g + 1] += v.y, s[4 * g + 2] += v.z, s[4 * g + 3] += v.w;
+      }
+    } else if constexpr (RG % 2 == 0 && sizeof(T) == 8) {
+#pragma unroll
+      for (int g = 0; g < RG / 2; ++g) {
+        const double2 v = reinterpret_cast<const double2*>(p)[g];
+        s[2 * g] += v.x, s[2 * g + 1] += v.y;
+      }
+    } else {
+#pragma unroll
+      for (int rr = 0; rr < RG; ++rr) s[rr] += (double)p[rr];
+    }
   }
 #pragma unroll
   for (int rr = 0; rr < RG; ++rr) {
@@ -103,6 +133,107 @@ __global__ void k_residual(int64_t n, int R, const int64_t* __restrict__ rowptr,
     }
   }
   block_accumulate(sq, RG, norms + r0);
+}
+
+// The same residual with fixed-order sums: block (x, y) writes the squared norms of its rows'
+// residuals, column by column, to part[r * gridDim.x + x] (summed over the block's warps in warp
+// order), and k_finish_norms adds each column's partials in index order.  The row's entries of A
+// are loaded eight at a time before the products, so that the loads of x for all of them are in
+// flight together.
+template <int RG>
+__global__ void __launch_bounds__(kBS) k_residual_part(int64_t n, int R, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                        const double* __restrict__ b, int64_t ldb,
+                                                        const double* __restrict__ x, int64_t ldx,
+                                                        double* __restrict__ res, int64_t ldr, double* __restrict__ part) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RG;
+  double sq[RG];
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) sq[rr] = 0.0;
+  if (i < n) {
+    const int64_t lo = rowptr[i], hi = rowptr[i + 1];
+    double ax[RG];
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) ax[rr] = 0.0;
+    for (int64_t k0 = lo; k0 < hi; k0 += 8) {
+      int c[8];
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = k0 + u < hi ? col[k0 + u] : 0;
+        v[u] = k0 + u < hi ? val[k0 + u] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (k0 + u < hi) {
+          const double* xk = x + c[u] + (int64_t)r0 * ldx;
+#pragma unroll
+          for (int rr = 0; rr < RG; ++rr) ax[rr] += v[u] * xk[(int64_t)rr * ldx];
+        }
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) {
+      const double ri = b[i + (int64_t)(r0 + rr) * ldb] - ax[rr];
+      if (res) res[i + (int64_t)(r0 + rr) * ldr] = ri;
+      sq[rr] = ri * ri;
+    }
+  }
+  __shared__ double red[kBS / 32][RG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) {
+    const double t = warp_sum(sq[rr]);
+    if (lane == 0) red[warp][rr] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < RG) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBS / 32; ++w) t += red[w][threadIdx.x];
+    part[(int64_t)(r0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <int RG>
+__global__ void __launch_bounds__(kBS) k_sqnorm_part(int64_t n, const double* __restrict__ v, int64_t ld,
+                                                      double* __restrict__ part) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RG;
+  __shared__ double red[kBS / 32][RG];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) {
+    const double t = i < n ? v[i + (int64_t)(r0 + rr) * ld] : 0.0;
+    const double w = warp_sum(t * t);
+    if (lane == 0) red[warp][rr] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < RG) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBS / 32; ++w) t += red[w][threadIdx.x];
+    part[(int64_t)(r0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// norms[r] = sum of part[r * nparts + 0 .. nparts - 1]: thread t adds the partials t, t + kBS, ... in
+// order, then the block's sums are combined in a fixed tree.
+__global__ void __launch_bounds__(kBS) k_finish_norms(int nparts, const double* __restrict__ part, double* norms) {
+  const int r = blockIdx.x;
+  const double* p = part + (int64_t)r * nparts;
+  double t = 0.0;
+  for (int j = threadIdx.x; j < nparts; j += kBS) t += p[j];
+  __shared__ double red[kBS / 32];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double u = threadIdx.x < kBS / 32 ? red[threadIdx.x] : 0.0;
+    u = warp_sum(u);
+    if (threadIdx.x == 0) norms[r] = u;
+  }
 }
 
 __global__ void k_sqnorm(int64_t n, int R, const double* __restrict__ v, int64_t ld, double* norms) {
@@ -156,7 +287,9 @@ static unsigned nblocks(int64_t n) { return (unsigned)((n + kBS - 1) / kBS); }
 template <typename T>
 cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, const double* share, const double* src,
                          int64_t ld, T* bt, cudaStream_t st) {
-  if (ncopies > 0) k_split<T><<<nblocks(ncopies), kBS, 0, st>>>(ncopies, R, copy_vertex, share, src, ld, bt);
+  if (ncopies <= 0) return cudaSuccess;
+  if (R % 4 == 0) k_split<T, 4><<<dim3(nblocks(ncopies), R / 4), kBS, 0, st>>>(ncopies, R, copy_vertex, share, src, ld, bt);
+  else k_split<T, 1><<<dim3(nblocks(ncopies), R), kBS, 0, st>>>(ncopies, R, copy_vertex, share, src, ld, bt);
   return cudaGetLastError();
 }
 
@@ -183,6 +316,35 @@ cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32
   else if (R % 4 == 0) k_residual<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
   else if (R % 2 == 0) k_residual<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
   else k_residual<1><<<dim3(bx, R), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, norms);
+  return cudaGetLastError();
+}
+
+int64_t norm_parts(int64_t n) { return (int64_t)nblocks(n); }
+
+cudaError_t launch_residual_det(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
+                                const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
+                                double* part, double* norms, cudaStream_t st) {
+  if (R > kMaxR || R < 1) return cudaErrorInvalidValue;
+  if (n <= 0) return cudaMemsetAsync(norms, 0, R * sizeof(double), st);
+  const unsigned bx = nblocks(n);
+  if (R % 8 == 0) k_residual_part<8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
+  else if (R % 4 == 0) k_residual_part<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
+  else if (R % 2 == 0) k_residual_part<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
+  else k_residual_part<1><<<dim3(bx, R), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
+  k_finish_norms<<<R, kBS, 0, st>>>((int)bx, part, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqnorm_det(int64_t n, int R, const double* v, int64_t ld, double* part, double* norms,
+                              cudaStream_t st) {
+  if (R > kMaxR || R < 1) return cudaErrorInvalidValue;
+  if (n <= 0) return cudaMemsetAsync(norms, 0, R * sizeof(double), st);
+  const unsigned bx = nblocks(n);
+  if (R % 8 == 0) k_sqnorm_part<8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, v, ld, part);
+  else if (R % 4 == 0) k_sqnorm_part<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, v, ld, part);
+  else if (R % 2 == 0) k_sqnorm_part<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, v, ld, part);
+  else k_sqnorm_part<1><<<dim3(bx, R), kBS, 0, st>>>(n, v, ld, part);
+  k_finish_norms<<<R, kBS, 0, st>>>((int)bx, part, norms);
   return cudaGetLastError();
 }
 
