@@ -530,6 +530,8 @@ def run_vtm(args):
     # defect-correction phase starts with one (u_base from zero waves)
     band_sweeps = (stats[-1].checks + stats[-1].restarts + 1) if solver.info().sweep_form == 2 else sweeps
     launches = sum(s_.launches for s_ in stats)
+    hs, hr, hi = solver.history()   # the FP64 checks of the last timed solve: [sweeps, rel, inner]
+    check_history = [[int(a_), float("%.3g" % b_), float("%.3g" % c_)] for a_, b_, c_ in zip(hs, hr, hi)]
     bits_now = solver.info().port_storage_bits
     dtype_desc = ("f32 (f16-stored port responses, f64 residual + defect correction)"
                   if sinfo.sweep_form == 2 and bits_now == 16 else "f32 (f64 residual + defect correction)")
@@ -683,7 +685,8 @@ def run_vtm(args):
            "band_sweeps": int(band_sweeps), "port_sweeps": int(sweeps - band_sweeps) if port else 0,
            "port_setup_ms": round(sinfo.port_setup_ms, 1) if port else None,
            "port_bytes": int(sinfo.port_bytes) if port else None,
-           "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "e2e_reps": e2e_reps, "plain": plain}
+           "sweep_ctas_per_sm": sinfo.sweep_ctas_per_sm, "e2e_reps": e2e_reps,
+           "check_history": check_history, "plain": plain}
     cfg.update({k: w[k] for k in ("dims", "block", "sigma", "npoints") if k in w})
     line = {
         "metric": METRIC if not fixed else ("time for %d VTM sweeps x %d right-hand sides on 1 GB300 "

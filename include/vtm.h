@@ -223,7 +223,10 @@ typedef struct vtm_setup_opts {
   int32_t sweep_variant;   /* 0 or 1: single-block sweep (the autotuner picks the staging depth);
                               2: pipelined sweep (nrhs <= 2; VTM_ERR_INVALID if no staging depth
                               fits).  The pipelined schedule is never chosen automatically: it
-                              measured slower on every workload tried                          */
+                              measured slower on every workload tried.
+                              3: FP32, nrhs 16 / 32: the multi-RHS band sweep on the SIMT cores
+                              only (by default its products run on the tensor cores when every
+                              half-bandwidth is at most 384)                                   */
   int32_t sweep_form;      /* how a sweep obtains the port values u = P^T x_j (VTM_FORM_*):
                               BAND substitutes through the banded factor of K_j every sweep;
                               PORT precomputes the port response S_j = P^T K_j^{-1} P at setup
@@ -304,6 +307,10 @@ typedef struct vtm_solver_info {
   int32_t factor_tc;           /* 1: the FP32 factorisation ran its trailing updates on the
                                   tensor cores (half-bandwidth 64 .. 384)                       */
   int64_t ncouplings;          /* coupled line pairs with y > 0 (0: uncoupled lines)           */
+  int32_t band_tc;             /* 1: the multi-RHS band sweep (FP32, nrhs 16 / 32) runs its
+                                  products on the tensor cores (factor balanced by its row norms,
+                                  fp16 hi / lo panels of 128-row groups, FP32 accumulation)     */
+  int64_t band_tc_bytes;       /* bytes of that tensor-core factor (each sweep reads it twice)  */
 } vtm_solver_info;
 
 /* Build the local matrices K_j = Ã_j + sum_e Z_e^{-1} e_c e_c^T (eq. 5.8), factor them on the

@@ -43,6 +43,7 @@ struct PieceDesc {
   int64_t row_off;     // first padded row of the piece in per-row arrays (sum of earlier n_pad)
   int64_t s_off;       // first 32 x 32 tile (port.cu) or 128 x 128 FP32 setup block (port_tc.cu) of S_j
   int64_t h_off;       // port_tc.cu: byte offset of the piece's fp16 port-response blocks
+  int64_t wt_off;      // sweep_wide_tc.cu: byte offset of the piece's tensor-core factor groups
 };
 
 // ------------------------------------------------------------------ PTX wrappers (sm_90+)

@@ -38,6 +38,7 @@ struct SweepArgs {
   TF* yspill;                  // wide kernel: forward result y in factor precision, n_pad x R per
                                // piece at row_off (nullptr: y goes through xc, TF == TV)
   CoupleRef<TV> cpl;           // coupled lines: per-port coupling lists (cpl.ptr == nullptr: none)
+  const unsigned char* wt;     // tensor-core factor of sweep_wide_tc.cu (nullptr: not built)
 };
 
 size_t sweep_smem_bytes(size_t elem, int R, int stages, int slot_elems, int ys_elems, int win_elems);
@@ -56,6 +57,19 @@ template <typename TF, typename TV>
 cudaError_t sweep_pipe_occupancy(int R, size_t smem, int* ctas_per_sm);
 template <typename TF, typename TV>
 cudaError_t launch_sweep_pipe(const SweepArgs<TF, TV>& a, int R, int npieces, size_t smem, cudaStream_t st);
+
+// Multi-RHS sweep with the band products on the tensor cores (R = 16, 32; FP32 solvers): the factor
+// of each subgraph, balanced and split into fp16 hi / lo panels of 128-row groups, built once from
+// the FP32 band factor (sweep_wide_tc.cu).  Half-bandwidths up to 128 kWideTcMaxTiles.
+constexpr int kWideTcMaxTiles = 3;
+int64_t wide_tc_bytes(int n, int w);
+bool wide_tc_fits(int w);
+int wide_tc_groups(int n);
+size_t wide_tc_smem_bytes(int R);
+cudaError_t wide_tc_configure(int R);
+cudaError_t launch_wide_tc_factor(const PieceDesc* pieces, int npieces, int max_groups, const float* band,
+                                  unsigned char* wt, cudaStream_t st);
+cudaError_t launch_sweep_wide_tc(const SweepArgs<float, float>& a, int R, int npieces, cudaStream_t st);
 
 // Wide variant (R = 16, 32): vectors spill to xc, a circular window of 512 rows stays in shared memory.
 size_t sweep_wide_smem_bytes(size_t elem, int R, int stages, int slot_elems, int cap);
@@ -181,6 +195,14 @@ cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32
                             double* norms, cudaStream_t st);
 // norms[r] += ||v_r||^2
 cudaError_t launch_sqnorm(int64_t n, int R, const double* v, int64_t ld, double* norms, cudaStream_t st);
+// The same two with fixed-order sums (identical inputs give identical norms): norms[r] = ||res_r||^2
+// (resp. ||v_r||^2), through the scratch part of norm_parts(n) * R doubles.
+int64_t norm_parts(int64_t n);
+cudaError_t launch_residual_det(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
+                                const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
+                                double* part, double* norms, cudaStream_t st);
+cudaError_t launch_sqnorm_det(int64_t n, int R, const double* v, int64_t ld, double* part, double* norms,
+                              cudaStream_t st);
 // dst[i + r*ldd] = src[i + r*lds]
 cudaError_t launch_copy2d(int64_t n, int R, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st);
 

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <type_traits>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -91,7 +92,7 @@ struct vtm_solver {
 
   DevBuf pieces, factor, factor_u, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status;
   DevBuf a_rowptr, a_col, a_val, vc_ptr, vc_copy, copy_vertex, share;
-  DevBuf vb, vx, vxt, vr, vrt, norms;
+  DevBuf vb, vx, vxt, vr, vrt, norms, nparts;  // nparts: per-block partial sums of the residual norms
   double* h_norms = nullptr;  // pinned: [R] residual^2, [R] b^2 ... plus status
   int cur = 0;                // wave buffer holding the last outgoing waves
   bool have_copies = false;
@@ -111,6 +112,11 @@ struct vtm_solver {
   std::vector<int32_t> end_port;     // internal end -> port
   int max_w = 0, max_pad = 0, max_ports = 0;
   bool wide = false;                 // R >= 16: windowed multi-RHS sweep kernel
+  // FP32, every half-bandwidth <= 384: the tensor-core form of that sweep (sweep_wide_tc.cu)
+  bool wt_ok = false, wide_tc = false;
+  int64_t wt_bytes = 0;
+  int wt_max_groups = 0;
+  DevBuf wt;
   bool pipe = false;                 // R <= 2: pipelined sweep kernel chosen by the autotuner
   struct Cand {
     int stages;
@@ -439,6 +445,23 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
   upload(s->cp_y, yv, s->stream);
 }
 
+// The tensor-core factor of the subgraphs of the main launch (FP32 band factor -> balanced fp16
+// panels), when every half-bandwidth allows it and it fits in device memory with room to spare.
+static bool build_wide_tc(vtm_solver* s) {
+  if (!s->wt_ok || s->np_lo == 0) return false;
+  size_t free_b = 0, total_b = 0;
+  VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  if ((double)s->wt_bytes > 0.6 * (double)free_b) return false;
+  s->wt.alloc((size_t)s->wt_bytes);
+  VTM_CUDA(wide_tc_configure(s->R));
+  VTM_CUDA(launch_wide_tc_factor(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->wt_max_groups, s->factor.as<float>(),
+                                 s->wt.as<unsigned char>(), s->stream));
+  VTM_CUDA(cudaStreamSynchronize(s->stream));
+  s->info.band_tc = 1;
+  s->info.band_tc_bytes = s->wt_bytes;
+  return true;
+}
+
 template <typename T>
 static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_solver* s) {
   cudaStream_t st = s->stream;
@@ -571,6 +594,15 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     max_pad = std::max(max_pad, n_pad);
     max_ends = std::max(max_ends, pd[j].nends);
   }
+  if (sizeof(T) == 4 && o->sweep_variant != 3) {
+    s->wt_ok = true;
+    for (int32_t j = 0; j < np; ++j) {
+      if (!wide_tc_fits(pd[j].w)) s->wt_ok = false;
+      pd[j].wt_off = s->wt_bytes;
+      s->wt_bytes += wide_tc_bytes(pd[j].n, pd[j].w);
+      s->wt_max_groups = std::max(s->wt_max_groups, wide_tc_groups(pd[j].n));
+    }
+  }
 
   // ---- sweep shared-memory plan: every staging depth that fits is a tuning candidate
   const int R = s->R;
@@ -668,6 +700,9 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
     factor_typed<T>(s);
   }
   plan_hi(s);
+  if constexpr (sizeof(T) == 4) {
+    if (s->wide && build_wide_tc(s)) s->wide_tc = true;
+  }
 
   // vectors
   s->bt.alloc((size_t)C * R * sizeof(T));
@@ -685,6 +720,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   s->vr.alloc(nv);
   s->vrt.alloc(nv);
   s->norms.alloc(2 * kMaxRhs * sizeof(double));
+  s->nparts.alloc((size_t)norm_parts(p->n) * R * sizeof(double));
   VTM_CUDA(cudaMallocHost(&s->h_norms, 2 * kMaxRhs * sizeof(double)));
   VTM_CUDA(cudaStreamSynchronize(st));
 
@@ -747,11 +783,19 @@ static SweepArgs<TF, TV> sweep_args(vtm_solver* s, int write_x, bool hi) {
   a.cap = hi ? s->hi_cap : s->cap;
   a.yspill = (hi && s->wide) ? s->hi_yspill.as<TF>() : nullptr;
   a.cpl = couple_ref<TV>(s);
+  a.wt = (!hi && s->wide_tc) ? s->wt.as<unsigned char>() : nullptr;
   return a;
 }
 
 template <typename TF, typename TV>
 static void launch_one(vtm_solver* s, const SweepArgs<TF, TV>& a, int np, size_t smem, bool pipe) {
+  if constexpr (std::is_same_v<TF, float> && std::is_same_v<TV, float>) {
+    if (s->wide && a.wt) {
+      VTM_CUDA(launch_sweep_wide_tc(a, s->R, np, s->stream));
+      s->launches++;
+      return;
+    }
+  }
   if (s->wide) VTM_CUDA((launch_sweep_wide<TF, TV>(a, s->R, np, smem, s->stream)));
   else if (pipe) VTM_CUDA((launch_sweep_pipe<TF, TV>(a, s->R, np, smem, s->stream)));
   else VTM_CUDA((launch_sweep<TF, TV>(a, s->R, np, smem, s->stream)));
@@ -782,7 +826,9 @@ static void autotune_sweep(vtm_solver* s) {
   float best = 1e30f;
   int best_st = s->stage_cands.back();
   bool best_pipe = false;
-  for (const auto& c : s->cands) {
+  // the tensor-core multi-RHS sweep has no staging depth to choose: time it once
+  const std::vector<vtm_solver::Cand> cands = s->wide_tc ? std::vector<vtm_solver::Cand>{{best_st, false}} : s->cands;
+  for (const auto& c : cands) {
     s->stages = c.stages;
     s->pipe = c.pipe;
     s->sweep_smem = sweep_smem_for(s, sizeof(T), c.stages, c.pipe);
@@ -851,6 +897,19 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
     wsc.alloc(w0.bytes);
     VTM_CUDA(cudaMemsetAsync(w0.p, 0, w0.bytes, st));
     VTM_CUDA((sweep_wide_configure<T, T>(Rs, sm_lo)));
+    // the tensor-core form of the multi-RHS sweep where it applies (FP32 band factor, half-bandwidths
+    // <= 384), its factor kept only for these solves
+    DevBuf wt_tmp;
+    if constexpr (sizeof(T) == 4) {
+      size_t fb = 0, tb = 0;
+      VTM_CUDA(cudaMemGetInfo(&fb, &tb));
+      if (s->wt_ok && s->np_lo > 0 && (double)s->wt_bytes < 0.4 * (double)fb) {
+        wt_tmp.alloc((size_t)s->wt_bytes);
+        VTM_CUDA(wide_tc_configure(Rs));
+        VTM_CUDA(launch_wide_tc_factor(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->wt_max_groups, s->factor.as<float>(),
+                                       wt_tmp.as<unsigned char>(), st));
+      }
+    }
     const int nb = (s->max_ports + Rs - 1) / Rs;
     for (int b = 0; b < nb; ++b) {
       VTM_CUDA(launch_unit_rhs<T>(s->pieces.as<PieceDesc>(), np, s->port_local.as<int32_t>(), Rs, b, bt32.as<T>(), st));
@@ -864,7 +923,13 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
         a.withhold = -1;
         a.yspill = nullptr;
         a.cpl.ptr = nullptr;  // unit sources, zero waves: no coupling current
-        VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
+        a.wt = wt_tmp.as<unsigned char>();
+        if constexpr (sizeof(T) == 4) {
+          if (a.wt) VTM_CUDA(launch_sweep_wide_tc(a, Rs, s->np_lo, st));
+          else VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
+        } else {
+          VTM_CUDA((launch_sweep_wide<T, T>(a, Rs, s->np_lo, sm_lo, st)));
+        }
       }
       VTM_CUDA(launch_gather_port_response<T>(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->port_local.as<int32_t>(),
                                               Rs, b, xc32.as<T>(), s->S.as<T>(), st));
@@ -1329,7 +1394,7 @@ vtm_solver* create_solver(const vtm_partition* p, const vtm_setup_opts* o, void*
   s->check_every = o->check_every > 0 ? o->check_every : 10;
   s->inner_reduction = o->inner_reduction > 0 ? o->inner_reduction : 1e-4;
   if (o->wait_polls < 0) fail(VTM_ERR_INVALID, "wait_polls must be >= 0");
-  if (o->sweep_variant < 0 || o->sweep_variant > 2) fail(VTM_ERR_INVALID, "sweep_variant must be 0, 1 or 2");
+  if (o->sweep_variant < 0 || o->sweep_variant > 3) fail(VTM_ERR_INVALID, "sweep_variant must be 0, 1, 2 or 3");
   if (o->sweep_form < 0 || o->sweep_form > 2) fail(VTM_ERR_INVALID, "sweep_form must be 0, 1 or 2");
   if (o->port_storage < 0 || o->port_storage > 2) fail(VTM_ERR_INVALID, "port_storage must be 0, 1 or 2");
   if (o->wait_polls > 0) s->wait_limit = (long)o->wait_polls;
@@ -1390,9 +1455,9 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   double* norms = s->norms.as<double>();
   VTM_CUDA(cudaMemsetAsync(norms, 0, 2 * kMaxRhs * sizeof(double), st));
   VTM_CUDA(cudaMemsetAsync(s->status.p, 0, sizeof(int), st));
-  VTM_CUDA(launch_sqnorm(n, R, db, n, norms + kMaxRhs, st));
+  VTM_CUDA(launch_sqnorm_det(n, R, db, n, s->nparts.as<double>(), norms + kMaxRhs, st));
   VTM_CUDA(launch_copy2d(n, R, db, n, s->vr.as<double>(), n, st));
-  s->launches += 2;
+  s->launches += 3;
   read_norms(s, 2 * kMaxRhs);
   std::vector<double> bn(R);
   for (int r = 0; r < R; ++r) bn[r] = s->h_norms[kMaxRhs + r] > 0 ? std::sqrt(s->h_norms[kMaxRhs + r]) : 1.0;
@@ -1412,12 +1477,17 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   double prev_inner = INFINITY, rel = INFINITY;
   int status = VTM_ERR_NOT_CONVERGED;
   bool trial_fresh = false;  // xt holds the assembled iterate of the last check
-  // Port form: a batch's last sweep is a band sweep, which costs several port sweeps, so after two
-  // checks of the same inner solve the next batch is sized from the observed rate to end near the
-  // next event (rtol, or the restart threshold of the defect correction), between m and 8 m sweeps.
+  // Port form: a batch's last sweep is a band sweep, which costs several port sweeps, so batches are
+  // sized from the observed contraction rate to end near the next event (rtol, or the restart
+  // threshold of the defect correction), between m and 8 m sweeps.  The rate is measured between
+  // two checks of the same inner solve.  A correction phase starts from zero waves and its inner
+  // residual first grows (to several times the residual it corrects) before it falls, so its first
+  // check comes after 2 m sweeps, and the batch after it is sized from the rate of the phase
+  // before (every phase iterates the same operator).
   int next_k = m;
   double last_inner = -1.0;
   int last_inner_sweeps = 0;
+  double phase_rate = -1.0;  // per-sweep contraction of the inner residual, last measured
   // port form: the first sweep of every phase also gives u_base (first_sweep_typed)
   auto phase_start = [&]() {
     if (!s->port_form) return;
@@ -1436,10 +1506,9 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     sweeps += k;
     inner_sweeps += k;
     assemble(s, xacc, xt);
-    VTM_CUDA(cudaMemsetAsync(norms, 0, kMaxRhs * sizeof(double), st));
-    VTM_CUDA(launch_residual(n, R, s->a_rowptr.as<int64_t>(), s->a_col.as<int32_t>(), s->a_val.as<double>(), db, n,
-                             xt, n, rt, n, norms, st));
-    s->launches++;
+    VTM_CUDA(launch_residual_det(n, R, s->a_rowptr.as<int64_t>(), s->a_col.as<int32_t>(), s->a_val.as<double>(), db,
+                                 n, xt, n, rt, n, s->nparts.as<double>(), norms, st));
+    s->launches += 2;
     read_norms(s, R);
     ++checks;
     check_status(s);
@@ -1470,11 +1539,17 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     // sweeps on FP16 port responses stall near the FP16 rounding level of the inner solve, so such a
     // phase restarts once it is within a few units of 2^-11 instead of waiting for the stall
     const double reduction = s->port_half ? std::max(s->inner_reduction, kHalfReduction) : s->inner_reduction;
+    double rate = -1.0;
     if (s->port_form && last_inner > 0 && inner > 0 && inner < last_inner && inner_sweeps > last_inner_sweeps) {
-      const double rate = std::pow(inner / last_inner, 1.0 / (inner_sweeps - last_inner_sweeps));
+      rate = std::pow(inner / last_inner, 1.0 / (inner_sweeps - last_inner_sweeps));
+      if (inner <= 0.5 * last_inner) phase_rate = rate;  // an interval of real progress, not a stall
+    } else if (s->port_form && last_inner < 0 && restarts > 0 && inner > 0) {
+      rate = phase_rate;  // first check of a correction phase
+    }
+    if (rate > 0.0 && rate < 1.0) {
       double need = rtol / rel;                                   // reduction to reach rtol
       if (refine) need = std::max(need, reduction / inner);           // or the restart threshold
-      if (rate < 1.0 && need < 1.0) {
+      if (need < 1.0) {
         const double kk = std::ceil(1.05 * std::log(need) / std::log(rate));
         next_k = (int)std::min<double>(8.0 * m, std::max<double>(m, kk));
       }
@@ -1511,7 +1586,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       inner_sweeps = 0;
       prev_inner = INFINITY;
       last_inner = -1.0;
-      next_k = m;
+      next_k = s->port_form ? 2 * m : m;
       trial_fresh = false;
       phase_start();
       continue;

@@ -1,0 +1,708 @@
+// One VTM sweep for 16 or 32 right-hand sides with the band products on the tensor cores (Table 1
+// steps 3-5, eq. 5.6 / 5.8 per column; the same sweep as sweep_wide.cu).
+//
+// Factor.  Row i of the subgraph's factor L (K_j = L L^T, eq. 5.8) is scaled by d_i = 1 / ||L_i||_2
+// (the rows of D^-1/2 L, D = diag(K_j), have unit norm, so every entry lies in [-1, 1]); the sweep
+// solves (D^-1/2 L)(D^-1/2 L)^T x~ = D^-1/2 r and returns x = D^-1/2 x~.  Rows go in groups of
+// 128.  Group g (rows k0 = 128 g ..) keeps two operands, each as fp16 pairs hi = fp16(v),
+// lo = fp16(2^11 (v - hi)) (about 22 significant bits together, lo a normal fp16 number down to
+// |v| ~ 2^-14) in 128 x 64 panels of the 128-byte-swizzled K-major layout of tcgen05:
+//  * the entries left of the group, columns k0 - 128 T .. k0 - 1 (T = ceil(w / 128) tiles, w the
+//    half-bandwidth): 2 T panels;
+//  * the inverse of the group's 128 x 128 diagonal block, G_g = inv(L~_gg) (lower triangular; the
+//    balanced factor keeps its entries of order one): 2 panels.
+//
+// Forward pass, group by group: t = r~_g - L~_(g, left) y_left (M = 128, N = R, K = 128 T), then
+// y_g = G_g t (K = 128).  Backward pass, groups in descending order: x~_g = G_g^T t with
+// t = y~_g minus what the later groups have added to the group's accumulator, then
+// L~_(g, left)^T x~_g (the same panels read MN-major: M = 128 rows of one tile, K = the group's 128
+// rows) adds to the accumulators of the T groups to its left; group h collects the contributions
+// of groups h + 1 .. h + T in one tensor-memory accumulator, which it reads once.  G_g^T is G_g's
+// panels read MN-major.  Every product is three fp16 products per K step with FP32 accumulation in
+// tensor memory: hi hi into one accumulator, hi lo + lo hi into a second one scaled back by 2^-11.
+// The vector operands (the window of y, t, x~) are fp16 hi / lo of v / sigma, sigma a power of two
+// per column at or above max |r~| (forward) or max |y~| (backward).
+//
+// Warps: 0 streams the panels through a ring of 4 slots of 32 KB (bulk copies), 1 issues the MMAs,
+// 3-10 move the vectors (256 threads, thread = one row of the group and half of the columns: the
+// tensor-memory loads, the fp16 operands, the results).  Every wait is bounded; a CTA that gives up
+// records VTM_ERR_TIMEOUT, lets its copies and MMAs finish, frees its tensor memory and returns.
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace vtm {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kG = 128;                              // rows per group (MMA M)
+constexpr int kMaxT = kWideTcMaxTiles;               // tiles left of a group (half-bandwidth <= 384)
+constexpr int kNWC = 2 * (kMaxT + 1);                // 64-row chunks of the forward window
+constexpr int kSlots = 4;                            // ring slots of 32 KB
+constexpr int kSimtWarps = 8;
+constexpr int kWtThreads = 32 * (3 + kSimtWarps);
+constexpr int kSimtThreads = 32 * kSimtWarps;
+constexpr int kSimtBar = 1;
+constexpr uint32_t kChunk = 16384;                   // one fp16 panel: 128 rows x 64 columns
+constexpr uint32_t kSlotBytes = 2 * kChunk;
+constexpr uint32_t kDBytes = 512;                    // the group's 128 row scales d_i
+constexpr float kLoScale = 2048.f;                   // lo halves are stored times 2^11
+
+// Group layout: [hi of the 2 T left panels][lo of them][hi of G_g (2 panels)][lo of G_g][d]
+__host__ __device__ __forceinline__ int wt_tiles(int w) { return w <= 0 ? 1 : (w + kG - 1) / kG; }
+__host__ __device__ __forceinline__ int64_t wt_group_bytes(int T) { return (4LL * T + 4) * kChunk + kDBytes; }
+__host__ __device__ __forceinline__ int wt_groups(int n) { return (n + kG - 1) / kG; }
+
+template <int R>
+struct WtLayout {
+  static constexpr uint32_t kWinChunk = 256u * R;    // hi + lo panels (R rows x 128 bytes each)
+  static constexpr uint32_t kWin = kSlots * kSlotBytes;         // forward window (backward: x~)
+  static constexpr uint32_t kB2 = kWin + kNWC * kWinChunk;      // t of the group (K = 128)
+  static constexpr uint32_t kEnd = kB2 + 2 * kWinChunk;
+  static constexpr uint32_t kBytes = 1024 + 1024 + kEnd;        // alignment slack + barrier page
+};
+
+__device__ __forceinline__ void simt_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(kSimtBar), "n"(kSimtThreads) : "memory");
+}
+
+// Bounded wait that also gives up once another role has set the abort flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, long limit, volatile int* abort_flag) {
+  for (long it = 0; it < limit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ float pow2_at_or_above(float m) {
+  int e = 0;
+  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+  frexpf(m, &e);
+  return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ void split_store(unsigned char* hi_panel, unsigned char* lo_panel, uint32_t off, float v) {
+  const __half h = __float2half_rn(v);
+  *reinterpret_cast<__half*>(hi_panel + off) = h;
+  *reinterpret_cast<__half*>(lo_panel + off) = __float2half_rn((v - __half2float(h)) * kLoScale);
+}
+
+// Dynamic shared memory of the factor kernel: G_g (128 x kXs), one block row of L~_gg (32 x 97) and
+// a 32 x 33 product.
+constexpr int kXs = 132;
+constexpr size_t kFactorSmem = (size_t)(kG * kXs + 32 * 97 + 32 * 33) * sizeof(float);
+
+}  // namespace
+
+int64_t wide_tc_bytes(int n, int w) { return (int64_t)wt_groups(n) * wt_group_bytes(wt_tiles(w)); }
+bool wide_tc_fits(int w) { return wt_tiles(w) <= kMaxT; }
+int wide_tc_groups(int n) { return wt_groups(n); }
+
+size_t wide_tc_smem_bytes(int R) { return R == 16 ? WtLayout<16>::kBytes : WtLayout<32>::kBytes; }
+
+// The tensor-core factor of group blockIdx.y of subgraph blockIdx.x from its FP32 band factor (whose
+// 32 x 32 diagonal blocks hold the inverses of the Cholesky blocks).  Rows past the band storage
+// (n_pad .. 128 ng) are identity rows.  G_g by block forward substitution over the four 32-row
+// blocks: G_ii = inv(L~_ii), G_ij = -G_ii sum_{k=j}^{i-1} L~_ik G_kj.
+__global__ void __launch_bounds__(256) k_wide_tc_factor(const PieceDesc* __restrict__ pieces, const float* __restrict__ band,
+                                                         unsigned char* __restrict__ wt) {
+  const PieceDesc pd = pieces[blockIdx.x];
+  const int g = blockIdx.y;
+  if (g >= wt_groups(pd.n)) return;
+  const int T = wt_tiles(pd.w), Wp = pd.Wp, off = Wp - 1, k0 = g * kG;
+  unsigned char* gb = wt + pd.wt_off + (int64_t)g * wt_group_bytes(T);
+  const float* L = band + pd.factor_off;
+  extern __shared__ float fsm[];
+  float* X = fsm;                 // G_g, [128][kXs]
+  float* lt = X + kG * kXs;       // block row i of L~_gg left of its diagonal block, [32][97]
+  float* pb = lt + 32 * 97;       // [32][33]
+  __shared__ float inv[4][32][33];  // stored inverse diagonal blocks
+  __shared__ float lkk[4][32][33];  // the Cholesky blocks recovered from them (for the row norms)
+  __shared__ float dsh[kG];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto entry = [&](int row, int col) -> float {  // L[row][col] inside the band storage, else 0
+    if (row >= pd.n_pad || col < 0 || col < row - off || col > row) return 0.f;
+    return L[(int64_t)row * Wp + (col - row + off)];
+  };
+  for (int e = tid; e < 4 * 32 * 32; e += blockDim.x) {
+    const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+    const int row = k0 + 32 * b + r;
+    float v;
+    if (row >= pd.n_pad) v = (r == c) ? 1.f : 0.f;
+    else v = (c <= r) ? entry(row, k0 + 32 * b + c) : 0.f;
+    inv[b][r][c] = v;
+  }
+  for (int e = tid; e < kG * kXs; e += blockDim.x) X[e] = 0.f;
+  __syncthreads();
+  if (warp < 4) {
+    // solve inv * X = I column by column (lane = column j): X = L_KK, lower triangular
+    const int b = warp, j = lane;
+    for (int i = 0; i < 32; ++i) {
+      if (i < j) {
+        lkk[b][i][j] = 0.f;
+        continue;
+      }
+      float s = (i == j) ? 1.f : 0.f;
+      for (int k = j; k < i; ++k) s -= inv[b][i][k] * lkk[b][k][j];
+      lkk[b][i][j] = s / inv[b][i][i];
+    }
+  }
+  __syncthreads();
+  if (tid < kG) {
+    const int row = k0 + tid;
+    float s = 1.f;
+    if (row < pd.n_pad) {
+      const int b = tid >> 5, r = tid & 31;
+      s = 0.f;
+      for (int c = 0; c <= r; ++c) s += lkk[b][r][c] * lkk[b][r][c];
+      const int cb = row - (row & 31);
+      for (int col = max(0, row - off); col < cb; ++col) {
+        const float v = entry(row, col);
+        s += v * v;
+      }
+    }
+    dsh[tid] = s > 0.f ? rsqrtf(s) : 1.f;
+  }
+  __syncthreads();
+  // G_ii = inv(D^-1/2 L_ii) = inv(L_ii) D^1/2
+  for (int e = tid; e < 4 * 32 * 32; e += blockDim.x) {
+    const int b = e >> 10, r = (e >> 5) & 31, c = e & 31;
+    X[(32 * b + r) * kXs + 32 * b + c] = inv[b][r][c] / dsh[32 * b + c];
+  }
+  __syncthreads();
+  const int pr = tid >> 3, pc = (tid & 7) * 4;  // this thread's 4 entries of a 32 x 32 block
+  for (int i = 1; i < 4; ++i) {
+    for (int e = tid; e < 32 * 32 * i; e += blockDim.x) {
+      const int r = e / (32 * i), m = e % (32 * i);
+      lt[r * 97 + m] = entry(k0 + 32 * i + r, k0 + m) * dsh[32 * i + r];
+    }
+    __syncthreads();
+    for (int j = i - 1; j >= 0; --j) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int m = 32 * j; m < 32 * i; ++m) {
+        const float l = lt[pr * 97 + m];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(l, X[m * kXs + 32 * j + pc + u], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pb[pr * 33 + pc + u] = acc[u];
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = 0.f;
+      for (int m = 0; m < 32; ++m) {
+        const float gm = X[(32 * i + pr) * kXs + 32 * i + m];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fmaf(gm, pb[m * 33 + pc + u], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) X[(32 * i + pr) * kXs + 32 * j + pc + u] = -acc[u];
+      __syncthreads();
+    }
+  }
+  // panels of G_g: columns 64 c .. 64 c + 63 in panel c
+  for (int e = tid; e < kG * kG; e += blockDim.x) {
+    const int r = e >> 7, c = e & 127;
+    split_store(gb + (size_t)(4 * T + (c >> 6)) * kChunk, gb + (size_t)(4 * T + 2 + (c >> 6)) * kChunk,
+                swz16(r, c & 63), X[r * kXs + c]);
+  }
+  // the left panels: chunk c covers columns k0 - 128 T + 64 c .. + 63
+  for (int e = tid; e < 2 * T * kG * 64; e += blockDim.x) {
+    const int c = e / (kG * 64), r = (e >> 6) & (kG - 1), kk = e & 63;
+    const int row = k0 + r, col = k0 - kG * T + 64 * c + kk;
+    split_store(gb + (size_t)c * kChunk, gb + (size_t)(2 * T + c) * kChunk, swz16(r, kk), entry(row, col) * dsh[r]);
+  }
+  float* dd = reinterpret_cast<float*>(gb + (size_t)(4 * T + 4) * kChunk);
+  if (tid < kG) dd[tid] = dsh[tid];
+}
+
+template <int R>
+__global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs<float, float> a) {
+  using LY = WtLayout<R>;
+  constexpr int kHalf = R / 2;            // columns of a SIMT thread (row = tensor-memory lane)
+  constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
+  // tensor memory: [0, 2R) forward left product D1 | D2, [2R, 4R) the product with G_g,
+  // [4R, 12R) backward accumulators of four groups
+  constexpr uint32_t kTmemCols = 12 * R > 256 ? 512 : 256;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+  uint64_t* full = bars;                 // [kSlots] ring slots landed
+  uint64_t* empty = bars + kSlots;       // [kSlots] MMAs done with the slot
+  uint64_t* accfull = bars + 8;          // forward: left product of the group complete
+  uint64_t* bready = bars + 9;           // forward: the group's y is in the window
+  uint64_t* tready = bars + 10;          // the group's t operand is written (both passes)
+  uint64_t* yready = bars + 11;          // the product with G_g is complete (both passes)
+  uint64_t* baccready = bars + 12;       // backward: the next group's accumulator is complete
+  uint64_t* xready = bars + 13;          // backward: the group's x~ operand is written
+  uint64_t* xfree = bars + 14;           // backward: the MMAs are done with that operand
+  uint64_t* done = bars + 15;            // every MMA has completed
+  constexpr int kBars = 16;
+  volatile int* flags = reinterpret_cast<volatile int*>(bars + kBars);  // [0] abort, [1] SIMT decision
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBars + 2);
+  float* sigf = reinterpret_cast<float*>(sm + 256);  // [R] forward operand scale per column
+  float* sigb = sigf + 32;                           // [R] backward
+  float* scr = reinterpret_cast<float*>(sm + 512);   // [8][R / 2] column maxima of the SIMT warps
+  const uint32_t regA = base + 1024;
+  unsigned char* pA = sm + 1024;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const PieceDesc pd = a.pieces[blockIdx.x];
+  const int n = pd.n, T = wt_tiles(pd.w), ng = wt_groups(n);
+  const int64_t GB = wt_group_bytes(T);
+  const unsigned char* gb0 = a.wt + pd.wt_off;
+  float* xg = a.xc + (size_t)pd.copy_off * R;
+  const float* bg = a.bt + (size_t)pd.copy_off * R;
+  auto dval = [&](int row) -> float {
+    return *reinterpret_cast<const float*>(gb0 + (int64_t)(row / kG) * GB + (size_t)(4 * T + 4) * kChunk +
+                                           (size_t)(row % kG) * 4);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
+    flags[0] = 0;
+    flags[1] = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // ---- r~ = D^-1/2 (b~ + P (Y w_in)) (port currents from the twins' waves) into xc, and the column
+  // maxima of r~ (a port row also counts with its value before the currents: sigma only has to be
+  // at or above max |r~|)
+  {
+    float mx[4] = {0.f, 0.f, 0.f, 0.f};  // columns 4 (tid % (R / 4)) .. + 3 (kWtThreads is a multiple of R / 4)
+    const float4* b4 = reinterpret_cast<const float4*>(bg);
+    float4* x4 = reinterpret_cast<float4*>(xg);
+    constexpr int kU = 4;
+    for (int i0 = tid; i0 < n * (R / 4); i0 += kWtThreads * kU) {
+      float4 v[kU];
+      float dv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * kWtThreads;
+        v[u] = i < n * (R / 4) ? b4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dv[u] = i < n * (R / 4) ? dval(i / (R / 4)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * kWtThreads;
+        if (i < n * (R / 4)) {
+          const float4 o = make_float4(v[u].x * dv[u], v[u].y * dv[u], v[u].z * dv[u], v[u].w * dv[u]);
+          x4[i] = o;
+          mx[0] = fmaxf(mx[0], fabsf(o.x)), mx[1] = fmaxf(mx[1], fabsf(o.y));
+          mx[2] = fmaxf(mx[2], fabsf(o.z)), mx[3] = fmaxf(mx[3], fabsf(o.w));
+        }
+      }
+    }
+    __syncthreads();
+    float mp = 0.f;  // port rows: column tid % R
+    for (int i = tid; i < pd.nports * R; i += kWtThreads) {
+      const int q = i / R, c = i % R;
+      float acc = 0.f;
+      for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
+        acc += a.wprev[(size_t)a.twin[e] * R + c] * a.invz[e];
+      if (a.cpl.ptr) acc += coupling_current<float, float>(a.cpl, pd.port_off + q, c, R, a.wprev);
+      const int row = a.port_local[pd.port_off + q];
+      float* at = xg + (size_t)row * R + c;
+      const float v = *at + dval(row) * acc;
+      *at = v;
+      mp = fmaxf(mp, fabsf(v));
+    }
+    // per column: the 4-wide maxima of the threads with tid % (R / 4) == c / 4, and mp of tid % R == c
+    float* red = reinterpret_cast<float*>(pA + LY::kWin);  // the window, zeroed below
+    reinterpret_cast<float4*>(red)[tid] = make_float4(mx[0], mx[1], mx[2], mx[3]);
+    red[4 * kWtThreads + tid] = mp;
+    __syncthreads();
+    if (tid < R) {
+      float m = 0.f;
+      for (int t = tid / 4; t < kWtThreads; t += R / 4) m = fmaxf(m, red[4 * t + (tid & 3)]);
+      for (int t = tid; t < kWtThreads; t += R) m = fmaxf(m, red[4 * kWtThreads + t]);
+      sigf[tid] = pow2_at_or_above(m);
+    }
+    __syncthreads();
+    // the forward window starts as zeros (the columns left of row 0)
+    uint4* win = reinterpret_cast<uint4*>(pA + LY::kWin);
+    for (int i = tid; i < (int)(kNWC * LY::kWinChunk / 16); i += kWtThreads) win[i] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---- panels, in the order the MMAs take them.  Forward, per group: the 2 T left chunks (hi + lo
+    // of one chunk per slot), then G_g's hi pair and lo pair.  Backward, per group in descending
+    // order: G_g's hi and lo pairs, then the hi and lo pairs of tiles T - 1 .. 0 (tiles left of row 0
+    // skipped).  The panels are read once per pass: evict first.
+    if (lane == 0) {
+      uint64_t pol;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+      int cnt = 0;
+      auto next = [&](const unsigned char* src0, const unsigned char* src1) -> bool {
+        const int slot = cnt % kSlots;
+        if (cnt >= kSlots && !wait_or_abort(&empty[slot], (uint32_t)(((cnt / kSlots) - 1) & 1), a.wait_limit, flags))
+          return false;
+        if (cnt != a.withhold) {  // testing hook: this copy's wait can only run out
+          mbar_arrive_expect_tx(&full[slot], kSlotBytes);
+          if (src1) {
+            bulk_g2s_hint(regA + slot * kSlotBytes, src0, kChunk, &full[slot], pol);
+            bulk_g2s_hint(regA + slot * kSlotBytes + kChunk, src1, kChunk, &full[slot], pol);
+          } else {
+            bulk_g2s_hint(regA + slot * kSlotBytes, src0, kSlotBytes, &full[slot], pol);
+          }
+        }
+        ++cnt;
+        return true;
+      };
+      bool ok = true;
+      for (int g = 0; g < ng && ok && !flags[0]; ++g) {
+        const unsigned char* src = gb0 + (int64_t)g * GB;
+        for (int c = 0; c < 2 * T && ok; ++c) ok = next(src + (size_t)c * kChunk, src + (size_t)(2 * T + c) * kChunk);
+        if (ok) ok = next(src + (size_t)(4 * T) * kChunk, nullptr);
+        if (ok) ok = next(src + (size_t)(4 * T + 2) * kChunk, nullptr);
+      }
+      for (int k = 0; k < ng && ok && !flags[0]; ++k) {
+        const int g = ng - 1 - k;
+        const unsigned char* src = gb0 + (int64_t)g * GB;
+        ok = next(src + (size_t)(4 * T) * kChunk, nullptr);
+        if (ok) ok = next(src + (size_t)(4 * T + 2) * kChunk, nullptr);
+        for (int m = T - 1; m >= 0 && ok; --m) {
+          if (g - T + m < 0) continue;
+          ok = next(src + (size_t)(2 * m) * kChunk, nullptr);
+          if (ok) ok = next(src + (size_t)(2 * T + 2 * m) * kChunk, nullptr);
+        }
+      }
+      if (!ok) flags[0] = 1;
+      // copies still in flight must land before the shared memory can go away
+      for (int c = (cnt > kSlots ? cnt - kSlots : 0); c < cnt; ++c)
+        if (c != a.withhold) mbar_wait_bounded(&full[c % kSlots], (uint32_t)((c / kSlots) & 1), kDrainPolls);
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      int cnt = 0;
+      bool ok = true;
+      const uint32_t dL = tmem, dG = tmem + 2 * R;
+      const uint32_t b2 = regA + LY::kB2, xb = regA + LY::kWin;
+      auto take = [&](uint32_t& slot_addr) -> bool {
+        const int slot = cnt % kSlots;
+        if (!wait_or_abort(&full[slot], (uint32_t)((cnt / kSlots) & 1), a.wait_limit, flags)) return false;
+        tc_fence_after();
+        slot_addr = regA + slot * kSlotBytes;
+        return true;
+      };
+      auto give = [&]() {
+        mma_commit(&empty[cnt % kSlots]);
+        ++cnt;
+      };
+      // the product with G_g (forward) or G_g^T (backward) of the t operand, into dG
+      auto g_product = [&](bool transposed) -> bool {
+        const uint32_t id = transposed ? idT : idK;
+        uint32_t s0, s1;
+        if (!take(s0)) return false;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+          const uint64_t a0 =
+              transposed ? sdesc(s0, kChunk, 1024) + (uint64_t)(kk * 128) : sdesc(s0 + p * kChunk, 16, 1024) + o;
+          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
+          mma_f16(dG, a0, bH, id, kk == 0 ? 0u : 1u);
+          mma_f16(dG + R, a0, bL, id, kk == 0 ? 0u : 1u);
+        }
+        give();
+        if (!take(s1)) return false;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+          const uint64_t a1 =
+              transposed ? sdesc(s1, kChunk, 1024) + (uint64_t)(kk * 128) : sdesc(s1 + p * kChunk, 16, 1024) + o;
+          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o;
+          mma_f16_acc(dG + R, a1, bH, id);
+        }
+        give();
+        mma_commit(yready);
+        return true;
+      };
+      // forward: chunk c of group g reads the window rows of group g - T + c / 2 (published through
+      // bready; the groups before g - 1 were waited for during group g - 1)
+      for (int g = 0; g < ng && ok; ++g) {
+        bool waited = false;
+        for (int c = 0; c < 2 * T && ok; ++c) {
+          const int gr = g - T + (c >> 1);
+          if (gr == g - 1 && gr >= 0 && !waited) {
+            if (!(ok = wait_or_abort(bready, (uint32_t)((g - 1) & 1), a.wait_limit, flags))) break;
+            waited = true;
+            tc_fence_after();
+          }
+          uint32_t sa;
+          if (!(ok = take(sa))) break;
+          const uint64_t aH = sdesc(sa, 16, 1024), aL = sdesc(sa + kChunk, 16, 1024);
+          const int wc = ((2 * gr + (c & 1)) % kNWC + kNWC) % kNWC;
+          const uint64_t bH = sdesc(regA + LY::kWin + wc * LY::kWinChunk, 16, 1024);
+          const uint64_t bL = bH + (uint64_t)(R * 8);  // lo panel: R rows of 128 bytes further
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = 2 * kk;  // 32 bytes per K step of 16
+            mma_f16(dL, aH + o, bH + o, idK, (c == 0 && kk == 0) ? 0u : 1u);
+            mma_f16(dL + R, aH + o, bL + o, idK, (c == 0 && kk == 0) ? 0u : 1u);
+            mma_f16_acc(dL + R, aL + o, bH + o, idK);
+          }
+          give();
+        }
+        if (!ok) break;
+        mma_commit(accfull);
+        if (!(ok = wait_or_abort(tready, (uint32_t)(g & 1), a.wait_limit, flags))) break;
+        tc_fence_after();
+        ok = g_product(false);
+      }
+      // backward: x~_g = G_g^T t, then group g adds L~_(g, left)^T x~_g to the accumulators of
+      // groups g - T .. g - 1 (tile T - 1 first: group g - 1 reads its accumulator next)
+      for (int k = 0; k < ng && ok; ++k) {
+        const int g = ng - 1 - k;
+        if (!(ok = wait_or_abort(tready, (uint32_t)((ng + k) & 1), a.wait_limit, flags))) break;
+        tc_fence_after();
+        if (!(ok = g_product(true))) break;
+        if (!(ok = wait_or_abort(xready, (uint32_t)(k & 1), a.wait_limit, flags))) break;
+        tc_fence_after();
+        for (int m = T - 1; m >= 0 && ok; --m) {
+          const int h = g - T + m;
+          if (h < 0) continue;
+          const uint32_t d = tmem + 4 * R + (uint32_t)((h & 3) * 2 * R);
+          const bool first = (g == min(h + T, ng - 1));
+          uint32_t sa;
+          if (!(ok = take(sa))) break;
+          const uint64_t aT = sdesc(sa, kChunk, 1024);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+            const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
+            const uint64_t at = aT + (uint64_t)(kk * 128);  // 16 rows of 128 bytes per K step
+            mma_f16(d, at, bH, idT, (first && kk == 0) ? 0u : 1u);
+            mma_f16(d + R, at, bL, idT, (first && kk == 0) ? 0u : 1u);
+          }
+          give();
+          if (!(ok = take(sa))) break;
+          const uint64_t aTl = sdesc(sa, kChunk, 1024);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+            const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o;
+            mma_f16_acc(d + R, aTl + (uint64_t)(kk * 128), bH, idT);
+          }
+          give();
+          if (m == T - 1) mma_commit(baccready);
+        }
+        if (ok) mma_commit(xfree);
+      }
+      if (!ok) flags[0] = 1;
+      mma_commit(done);  // arrives once every MMA issued above has completed
+    }
+  } else if (warp >= 3) {
+    // ---- SIMT warps: thread = row rq of the group (tensor-memory lane), columns c0 .. c0 + R/2 - 1
+    const int st = tid - 96;
+    const int q = warp & 3;
+    const int half = (warp - 3) >> 2;
+    const int rq = 32 * q + lane;
+    const int c0 = half * kHalf;
+    const uint32_t tl = (uint32_t)(32 * q) << 16;
+    unsigned char* b2p = pA + LY::kB2;
+    auto decide = [&](uint64_t* bar, uint32_t parity) -> bool {
+      if (st == 0) flags[1] = wait_or_abort(bar, parity, a.wait_limit, flags) ? 0 : 1;
+      simt_sync();
+      const bool ok = flags[1] == 0;
+      simt_sync();
+      if (!ok && st == 0) flags[0] = 1;
+      return ok;
+    };
+    auto load_rows = [&](int g, float (&v)[kHalf]) {
+      const int row = g * kG + rq;
+      const bool in = g >= 0 && row < n;
+      const float4* src = reinterpret_cast<const float4*>(xg + (size_t)(in ? row : 0) * R + c0);
+#pragma unroll
+      for (int c4 = 0; c4 < kHalf / 4; ++c4) {
+        const float4 x = in ? src[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * c4] = x.x, v[4 * c4 + 1] = x.y, v[4 * c4 + 2] = x.z, v[4 * c4 + 3] = x.w;
+      }
+    };
+    // v = D1 + 2^-11 D2 of the accumulator pair at tensor-memory column col
+    auto tmem_pair = [&](uint32_t col, float (&v)[kHalf]) {
+      uint32_t a1[kHalf], a2[kHalf];
+      tmem_ld<kHalf>(tmem + tl + col + c0, a1);
+      tmem_ld<kHalf>(tmem + tl + col + R + c0, a2);
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) v[c] = __uint_as_float(a1[c]) + __uint_as_float(a2[c]) * (1.f / kLoScale);
+    };
+    // fp16 hi / lo of v / sigma as row rq of a K-major operand (K = the row in the group, panel row
+    // = column)
+    auto put_operand = [&](unsigned char* chunk0, const float (&v)[kHalf], const float* sig) {
+      unsigned char* pan = chunk0 + (rq >> 6) * LY::kWinChunk;
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) split_store(pan, pan + R * 128, swz16(c0 + c, rq & 63), v[c] / sig[c0 + c]);
+    };
+    float cmax[kHalf];
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c) cmax[c] = 0.f;
+    bool ok = true;
+    float rv[kHalf];
+    load_rows(0, rv);
+    // forward
+    for (int g = 0; g < ng && ok; ++g) {
+      if (!(ok = decide(accfull, (uint32_t)(g & 1)))) break;
+      tc_fence_after();
+      float t[kHalf];
+      tmem_pair(0, t);
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigf[c0 + c] * t[c];
+      put_operand(b2p, t, sigf);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      simt_sync();
+      if (st == 0) mbar_arrive(tready);
+      load_rows(g + 1 < ng ? g + 1 : -1, rv);
+      if (!(ok = decide(yready, (uint32_t)(g & 1)))) break;
+      tc_fence_after();
+      float y[kHalf];
+      tmem_pair(2 * R, y);
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) {
+        y[c] *= sigf[c0 + c];
+        cmax[c] = fmaxf(cmax[c], fabsf(y[c]));
+      }
+      const int row = g * kG + rq;
+      if (row < n) {
+        float4* dst = reinterpret_cast<float4*>(xg + (size_t)row * R + c0);
+#pragma unroll
+        for (int c4 = 0; c4 < kHalf / 4; ++c4) dst[c4] = make_float4(y[4 * c4], y[4 * c4 + 1], y[4 * c4 + 2], y[4 * c4 + 3]);
+      }
+      // the window chunks 2 g, 2 g + 1 (the last group's y is read by no MMA)
+      if (g < ng - 1) put_operand(pA + LY::kWin + ((2 * g) % kNWC) * LY::kWinChunk, y, sigf);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      simt_sync();
+      if (st == 0) mbar_arrive(bready);
+    }
+    // backward operand scale: power of two at or above max |y~| per column (rows: lanes and the four
+    // quadrant warps of this column half)
+    if (ok) {
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) {
+        float m = cmax[c];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        cmax[c] = m;
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) scr[(warp - 3) * kHalf + c] = cmax[c];
+      simt_sync();
+      if (st < R) {
+        const int hh = st / kHalf, c = st % kHalf;
+        float m = 0.f;
+        for (int w = 0; w < 4; ++w) m = fmaxf(m, scr[(4 * hh + w) * kHalf + c]);
+        sigb[st] = pow2_at_or_above(m);
+      }
+      simt_sync();
+    }
+    // backward
+    if (ok) load_rows(ng - 1, rv);
+    for (int k = 0; k < ng && ok; ++k) {
+      const int g = ng - 1 - k;
+      float t[kHalf];
+      if (g + 1 <= ng - 1) {
+        if (!(ok = decide(baccready, (uint32_t)((k - 1) & 1)))) break;
+        tc_fence_after();
+        tmem_pair(4 * R + (uint32_t)((g & 3) * 2 * R), t);
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigb[c0 + c] * t[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) t[c] = rv[c];
+      }
+      put_operand(b2p, t, sigb);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      simt_sync();
+      if (st == 0) mbar_arrive(tready);
+      const int row = g * kG + rq;
+      const float drow = row < n ? dval(row) : 0.f;
+      load_rows(g - 1, rv);
+      if (!(ok = decide(yready, (uint32_t)((ng + k) & 1)))) break;
+      tc_fence_after();
+      float x[kHalf];
+      tmem_pair(2 * R, x);
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) x[c] *= sigb[c0 + c];
+      if (row < n) {
+        float4* dst = reinterpret_cast<float4*>(xg + (size_t)row * R + c0);
+#pragma unroll
+        for (int c4 = 0; c4 < kHalf / 4; ++c4)
+          dst[c4] = make_float4(x[4 * c4] * drow, x[4 * c4 + 1] * drow, x[4 * c4 + 2] * drow, x[4 * c4 + 3] * drow);
+      }
+      // the MMAs of the previous group must be done with the x~ operand before it is rewritten
+      if (k >= 1 && !(ok = decide(xfree, (uint32_t)((k - 1) & 1)))) break;
+      put_operand(pA + LY::kWin, x, sigb);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      simt_sync();
+      if (st == 0) mbar_arrive(xready);
+    }
+    if (!ok && st == 0) flags[0] = 1;
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(done, 0, kDrainPolls) && !flags[0];
+  if (!ok && tid == 0) atomicExch(a.status, kStatusTimeout);
+  if (ok) {
+    // w_out[e] = 2 x_c - w_in[e]
+    for (int i = tid; i < pd.nports * R; i += kWtThreads) {
+      const int qq = i / R, c = i % R;
+      const float x = xg[(size_t)a.port_local[pd.port_off + qq] * R + c];
+      for (int e = a.port_end_ptr[pd.port_off + qq]; e < a.port_end_ptr[pd.port_off + qq + 1]; ++e)
+        a.wnext[(size_t)e * R + c] = 2.f * x - a.wprev[(size_t)a.twin[e] * R + c];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+cudaError_t wide_tc_configure(int R) {
+  cudaError_t e = cudaFuncSetAttribute(k_wide_tc_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFactorSmem);
+  if (e != cudaSuccess) return e;
+  if (R == 16)
+    return cudaFuncSetAttribute(k_sweep_wide_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)WtLayout<16>::kBytes);
+  if (R == 32)
+    return cudaFuncSetAttribute(k_sweep_wide_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)WtLayout<32>::kBytes);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wide_tc_factor(const PieceDesc* pieces, int npieces, int max_groups, const float* band,
+                                  unsigned char* wt, cudaStream_t st) {
+  if (npieces <= 0 || max_groups <= 0) return cudaSuccess;
+  k_wide_tc_factor<<<dim3(npieces, max_groups), 256, kFactorSmem, st>>>(pieces, band, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_wide_tc(const SweepArgs<float, float>& a, int R, int npieces, cudaStream_t st) {
+  if (npieces <= 0) return cudaSuccess;
+  if (!a.wt) return cudaErrorInvalidValue;
+  if (R == 16) k_sweep_wide_tc<16><<<npieces, kWtThreads, WtLayout<16>::kBytes, st>>>(a);
+  else if (R == 32) k_sweep_wide_tc<32><<<npieces, kWtThreads, WtLayout<32>::kBytes, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace vtm

@@ -72,7 +72,7 @@ class SolverInfo(C.Structure):
                 ("sweep_variant", C.c_int32), ("sweep_form", C.c_int32), ("port_bytes", C.c_int64),
                 ("port_setup_ms", C.c_double), ("port_sweep_ms", C.c_double),
                 ("nports", C.c_int64), ("port_storage_bits", C.c_int32), ("factor_tc", C.c_int32),
-                ("ncouplings", C.c_int64)]
+                ("ncouplings", C.c_int64), ("band_tc", C.c_int32), ("band_tc_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -327,7 +327,8 @@ class Solver:
     precision: "fp64" or "fp32".  nrhs: 1, 2, 4, 8, 16 or 32.
     sweep_variant: "auto" or "single" (one CTA works each block step in turn; the setup-time
     autotuner picks the staging depth) or "pipelined" (warp 0 finishes block k while the other
-    warps prepare block k+1; nrhs <= 2; opt-in only, it measured slower everywhere).
+    warps prepare block k+1; nrhs <= 2; opt-in only, it measured slower everywhere) or "simt"
+    (FP32, nrhs 16 / 32: the multi-RHS band sweep without its tensor-core products).
     coupling: coupled lines of §7.2.  None (uncoupled), a number gamma (every candidate pair of
     Partition.line_pairs() gets the conductance gamma |a_ik|), or (pairs (m, 2), y (m,)).
     Right-hand sides / solutions: (nrhs, n) float64 arrays or tensors, host or device.
@@ -351,7 +352,7 @@ class Solver:
             o.ncouplings, o.couplings, o.coupling_y = len(y), pairs.ctypes.data, y.ctypes.data
             ckeep = (pairs, y)
         o.port_storage = {"native": 0, "fp16": 1, "fp16-auto": 2}[port_storage]
-        o.sweep_variant = {"auto": 0, "single": 1, "pipelined": 2}[sweep_variant]
+        o.sweep_variant = {"auto": 0, "single": 1, "pipelined": 2, "simt": 3}[sweep_variant]
         o.sweep_form = {"auto": 0, "band": 1, "port": 2}[form]
         zarr = None
         if isinstance(z, MLP):
