@@ -79,6 +79,9 @@ def parse():
     p.add_argument("--workload", default="poisson3d-256-r32", choices=list(WORKLOADS))
     p.add_argument("--check-every", type=int, default=20,
                    help="sweeps between FP64 residual checks (a port-form batch ends with one band sweep)")
+    p.add_argument("--inner-reduction", type=float, default=0.0,
+                   help="FP32 defect correction: restart once the inner residual has dropped by this factor "
+                        "(0: the library's default)")
     p.add_argument("--form", default="auto", choices=["auto", "band", "port"])
     p.add_argument("--port-storage", default="fp16-auto", choices=["native", "fp16", "fp16-auto"],
                    help="port form, nrhs <= 8: storage of the port responses")
@@ -495,6 +498,7 @@ def run_vtm(args):
     zarg, carg, cdesc = coupling_arg(args.coupling if args.coupling is not None else w.get("coupling"),
                                      zrule, zarg, zdesc, vtm, part)
     solver = vtm.Solver(part, z=zarg, precision="fp32", nrhs=R, stream=stream, check_every=args.check_every,
+                        inner_reduction=args.inner_reduction,
                         form=args.form, port_storage=args.port_storage, z_init=w.get("z_init", 1.0), coupling=carg)
     sinfo = solver.info()
     bd = torch.tensor(b, device="cuda")

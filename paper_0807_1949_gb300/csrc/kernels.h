@@ -63,6 +63,7 @@ cudaError_t launch_sweep_pipe(const SweepArgs<TF, TV>& a, int R, int npieces, si
 // the FP32 band factor (sweep_wide_tc.cu).  Half-bandwidths up to 128 kWideTcMaxTiles.
 constexpr int kWideTcMaxTiles = 3;
 int64_t wide_tc_bytes(int n, int w);
+int64_t wide_tc_zero_bytes();  // the zero panel the factor buffer starts with
 bool wide_tc_fits(int w);
 int wide_tc_groups(int n);
 size_t wide_tc_smem_bytes(int R);

@@ -453,6 +453,7 @@ static bool build_wide_tc(vtm_solver* s) {
   VTM_CUDA(cudaMemGetInfo(&free_b, &total_b));
   if ((double)s->wt_bytes > 0.6 * (double)free_b) return false;
   s->wt.alloc((size_t)s->wt_bytes);
+  VTM_CUDA(cudaMemsetAsync(s->wt.p, 0, (size_t)wide_tc_zero_bytes(), s->stream));
   VTM_CUDA(wide_tc_configure(s->R));
   VTM_CUDA(launch_wide_tc_factor(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->wt_max_groups, s->factor.as<float>(),
                                  s->wt.as<unsigned char>(), s->stream));
@@ -596,6 +597,7 @@ static void setup_typed(const vtm_partition* p, const vtm_setup_opts* o, vtm_sol
   }
   if (sizeof(T) == 4 && o->sweep_variant != 3) {
     s->wt_ok = true;
+    s->wt_bytes = wide_tc_zero_bytes();
     for (int32_t j = 0; j < np; ++j) {
       if (!wide_tc_fits(pd[j].w)) s->wt_ok = false;
       pd[j].wt_off = s->wt_bytes;
@@ -905,6 +907,7 @@ static void compute_port_response(vtm_solver* s, int64_t s_tiles) {
       VTM_CUDA(cudaMemGetInfo(&fb, &tb));
       if (s->wt_ok && s->np_lo > 0 && (double)s->wt_bytes < 0.4 * (double)fb) {
         wt_tmp.alloc((size_t)s->wt_bytes);
+        VTM_CUDA(cudaMemsetAsync(wt_tmp.p, 0, (size_t)wide_tc_zero_bytes(), st));
         VTM_CUDA(wide_tc_configure(Rs));
         VTM_CUDA(launch_wide_tc_factor(s->pieces_lo.as<PieceDesc>(), s->np_lo, s->wt_max_groups, s->factor.as<float>(),
                                        wt_tmp.as<unsigned char>(), st));
@@ -1540,9 +1543,15 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     // phase restarts once it is within a few units of 2^-11 instead of waiting for the stall
     const double reduction = s->port_half ? std::max(s->inner_reduction, kHalfReduction) : s->inner_reduction;
     double rate = -1.0;
-    if (s->port_form && last_inner > 0 && inner > 0 && inner < last_inner && inner_sweeps > last_inner_sweeps) {
-      rate = std::pow(inner / last_inner, 1.0 / (inner_sweeps - last_inner_sweeps));
-      if (inner <= 0.5 * last_inner) phase_rate = rate;  // an interval of real progress, not a stall
+    bool slow = false;  // the inner solve has met its floor
+    const int batch = inner_sweeps - last_inner_sweeps;
+    if (s->port_form && last_inner > 0 && inner > 0 && batch > 0) {
+      const double r_obs = std::pow(inner / last_inner, 1.0 / batch);
+      // an interval that gained less than a quarter of what the last healthy one gained per sweep
+      // (on the log scale) is a stall
+      slow = phase_rate > 0.0 && inner < 1.0 && std::log(r_obs) > 0.25 * std::log(phase_rate);
+      if (inner < last_inner) rate = r_obs;
+      if (inner <= 0.5 * last_inner) phase_rate = r_obs;  // an interval of real progress
     } else if (s->port_form && last_inner < 0 && restarts > 0 && inner > 0) {
       rate = phase_rate;  // first check of a correction phase
     }
@@ -1554,6 +1563,9 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
         next_k = (int)std::min<double>(8.0 * m, std::max<double>(m, kk));
       }
     }
+    // a correction phase usually ends on its FP32 floor, which only a second check can show: after a
+    // long batch in such a phase the next check comes after m sweeps
+    if (s->port_form && refine && restarts > 0 && last_inner > 0 && batch > 4 * m) next_k = m;
     last_inner = inner;
     last_inner_sweeps = inner_sweeps;
     // accept the trial only when it improves on the residual it started from
@@ -1571,7 +1583,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     // factor 2 per check, so a check that gains less has met the FP16 floor
     const bool half_floor = s->port_half && s->coupled && inner > 0.5 * prev_inner && inner_sweeps >= 2 * m;
     if (refine && inner < 1.0 &&
-        (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || half_floor)) {
+        (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || half_floor || slow)) {
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);
       s->vr.swap(s->vrt);

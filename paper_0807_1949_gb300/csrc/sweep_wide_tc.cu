@@ -8,7 +8,8 @@
 // lo = fp16(2^11 (v - hi)) (about 22 significant bits together, lo a normal fp16 number down to
 // |v| ~ 2^-14) in 128 x 64 panels of the 128-byte-swizzled K-major layout of tcgen05:
 //  * the entries left of the group, columns k0 - 128 T .. k0 - 1 (T = ceil(w / 128) tiles, w the
-//    half-bandwidth): 2 T panels;
+//    half-bandwidth): 2 T panels, of which the first is left out when it lies entirely left of the
+//    band (w <= 128 T - 64; its products are zero);
 //  * the inverse of the group's 128 x 128 diagonal block, G_g = inv(L~_gg) (lower triangular; the
 //    balanced factor keeps its entries of order one): 2 panels.
 //
@@ -23,9 +24,11 @@
 // The vector operands (the window of y, t, x~) are fp16 hi / lo of v / sigma, sigma a power of two
 // per column at or above max |r~| (forward) or max |y~| (backward).
 //
-// Warps: 0 streams the panels through a ring of 4 slots of 32 KB (bulk copies), 1 issues the MMAs,
-// 3-10 move the vectors (256 threads, thread = one row of the group and half of the columns: the
-// tensor-memory loads, the fp16 operands, the results).  Every wait is bounded; a CTA that gives up
+// Warps: 0 streams the panels through a ring of 16 KB slots (bulk copies, one panel each), 1 issues
+// the MMAs, 3-10 move the vectors (256 threads, thread = one row of the group and half of the
+// columns: the tensor-memory loads, the fp16 operands, the results).  The forward left product has
+// two tensor-memory buffers, so that the part of group g + 1's product that does not need y_g runs
+// while the SIMT warps finish group g.  Every wait is bounded; a CTA that gives up
 // records VTM_ERR_TIMEOUT, lets its copies and MMAs finish, frees its tensor memory and returns.
 #include "kernels.h"
 #include "tc.cuh"
@@ -38,29 +41,34 @@ namespace {
 
 constexpr int kG = 128;                              // rows per group (MMA M)
 constexpr int kMaxT = kWideTcMaxTiles;               // tiles left of a group (half-bandwidth <= 384)
-constexpr int kNWC = 2 * (kMaxT + 1);                // 64-row chunks of the forward window
-constexpr int kSlots = 4;                            // ring slots of 32 KB
+constexpr int kNWC = 2 * kMaxT;                      // 64-row chunks of the forward window
 constexpr int kSimtWarps = 8;
 constexpr int kWtThreads = 32 * (3 + kSimtWarps);
 constexpr int kSimtThreads = 32 * kSimtWarps;
 constexpr int kSimtBar = 1;
-constexpr uint32_t kChunk = 16384;                   // one fp16 panel: 128 rows x 64 columns
-constexpr uint32_t kSlotBytes = 2 * kChunk;
+constexpr uint32_t kChunk = 16384;                   // one fp16 panel: 128 rows x 64 columns (a ring slot)
+constexpr uint32_t kZeroBytes = kChunk;              // a zero panel at the start of the factor buffer
 constexpr uint32_t kDBytes = 512;                    // the group's 128 row scales d_i
 constexpr float kLoScale = 2048.f;                   // lo halves are stored times 2^11
 
-// Group layout: [hi of the 2 T left panels][lo of them][hi of G_g (2 panels)][lo of G_g][d]
+// Group layout, z = 1 when the first left panel is left out (w <= 128 T - 64), nl = 2 T - z:
+// [hi of left panels z .. 2 T - 1][lo of them][hi of G_g (2 panels)][lo of G_g][d]
 __host__ __device__ __forceinline__ int wt_tiles(int w) { return w <= 0 ? 1 : (w + kG - 1) / kG; }
-__host__ __device__ __forceinline__ int64_t wt_group_bytes(int T) { return (4LL * T + 4) * kChunk + kDBytes; }
+__host__ __device__ __forceinline__ int wt_zlead(int w) { return (w <= kG * wt_tiles(w) - 64) ? 1 : 0; }
+__host__ __device__ __forceinline__ int wt_nleft(int w) { return 2 * wt_tiles(w) - wt_zlead(w); }
+__host__ __device__ __forceinline__ int64_t wt_group_bytes(int w) { return (2LL * wt_nleft(w) + 4) * kChunk + kDBytes; }
 __host__ __device__ __forceinline__ int wt_groups(int n) { return (n + kG - 1) / kG; }
 
 template <int R>
 struct WtLayout {
   static constexpr uint32_t kWinChunk = 256u * R;    // hi + lo panels (R rows x 128 bytes each)
-  static constexpr uint32_t kWin = kSlots * kSlotBytes;         // forward window (backward: x~)
+  // ring slots: what the 227 KB leave after the window, the t operand and 2 KB of barriers, even
+  static constexpr int kSlots = (int)((232448u - 2048u - (kNWC + 2) * kWinChunk) / kChunk) & ~1;
+  static constexpr uint32_t kWin = kSlots * kChunk;             // forward window (backward: x~)
   static constexpr uint32_t kB2 = kWin + kNWC * kWinChunk;      // t of the group (K = 128)
   static constexpr uint32_t kEnd = kB2 + 2 * kWinChunk;
   static constexpr uint32_t kBytes = 1024 + 1024 + kEnd;        // alignment slack + barrier page
+  static_assert(kBytes <= 232448u, "shared memory");
 };
 
 __device__ __forceinline__ void simt_sync() {
@@ -96,7 +104,8 @@ constexpr size_t kFactorSmem = (size_t)(kG * kXs + 32 * 97 + 32 * 33) * sizeof(f
 
 }  // namespace
 
-int64_t wide_tc_bytes(int n, int w) { return (int64_t)wt_groups(n) * wt_group_bytes(wt_tiles(w)); }
+int64_t wide_tc_bytes(int n, int w) { return (int64_t)wt_groups(n) * wt_group_bytes(w); }
+int64_t wide_tc_zero_bytes() { return kZeroBytes; }
 bool wide_tc_fits(int w) { return wt_tiles(w) <= kMaxT; }
 int wide_tc_groups(int n) { return wt_groups(n); }
 
@@ -111,8 +120,8 @@ __global__ void __launch_bounds__(256) k_wide_tc_factor(const PieceDesc* __restr
   const PieceDesc pd = pieces[blockIdx.x];
   const int g = blockIdx.y;
   if (g >= wt_groups(pd.n)) return;
-  const int T = wt_tiles(pd.w), Wp = pd.Wp, off = Wp - 1, k0 = g * kG;
-  unsigned char* gb = wt + pd.wt_off + (int64_t)g * wt_group_bytes(T);
+  const int T = wt_tiles(pd.w), z = wt_zlead(pd.w), nl = wt_nleft(pd.w), Wp = pd.Wp, off = Wp - 1, k0 = g * kG;
+  unsigned char* gb = wt + pd.wt_off + (int64_t)g * wt_group_bytes(pd.w);
   const float* L = band + pd.factor_off;
   extern __shared__ float fsm[];
   float* X = fsm;                 // G_g, [128][kXs]
@@ -204,27 +213,29 @@ __global__ void __launch_bounds__(256) k_wide_tc_factor(const PieceDesc* __restr
   // panels of G_g: columns 64 c .. 64 c + 63 in panel c
   for (int e = tid; e < kG * kG; e += blockDim.x) {
     const int r = e >> 7, c = e & 127;
-    split_store(gb + (size_t)(4 * T + (c >> 6)) * kChunk, gb + (size_t)(4 * T + 2 + (c >> 6)) * kChunk,
+    split_store(gb + (size_t)(2 * nl + (c >> 6)) * kChunk, gb + (size_t)(2 * nl + 2 + (c >> 6)) * kChunk,
                 swz16(r, c & 63), X[r * kXs + c]);
   }
-  // the left panels: chunk c covers columns k0 - 128 T + 64 c .. + 63
-  for (int e = tid; e < 2 * T * kG * 64; e += blockDim.x) {
-    const int c = e / (kG * 64), r = (e >> 6) & (kG - 1), kk = e & 63;
+  // the left panels: panel c (c = z .. 2 T - 1) covers columns k0 - 128 T + 64 c .. + 63
+  for (int e = tid; e < nl * kG * 64; e += blockDim.x) {
+    const int c = z + e / (kG * 64), r = (e >> 6) & (kG - 1), kk = e & 63;
     const int row = k0 + r, col = k0 - kG * T + 64 * c + kk;
-    split_store(gb + (size_t)c * kChunk, gb + (size_t)(2 * T + c) * kChunk, swz16(r, kk), entry(row, col) * dsh[r]);
+    split_store(gb + (size_t)(c - z) * kChunk, gb + (size_t)(nl + c - z) * kChunk, swz16(r, kk),
+                entry(row, col) * dsh[r]);
   }
-  float* dd = reinterpret_cast<float*>(gb + (size_t)(4 * T + 4) * kChunk);
+  float* dd = reinterpret_cast<float*>(gb + (size_t)(2 * nl + 4) * kChunk);
   if (tid < kG) dd[tid] = dsh[tid];
 }
 
 template <int R>
 __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs<float, float> a) {
   using LY = WtLayout<R>;
+  constexpr int kSlots = LY::kSlots;
   constexpr int kHalf = R / 2;            // columns of a SIMT thread (row = tensor-memory lane)
   constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
-  // tensor memory: [0, 2R) forward left product D1 | D2, [2R, 4R) the product with G_g,
-  // [4R, 12R) backward accumulators of four groups
-  constexpr uint32_t kTmemCols = 12 * R > 256 ? 512 : 256;
+  // tensor memory: [0, 4R) the forward left product of groups g even / odd (D1 | D2 each),
+  // [4R, 6R) the product with G_g, [6R, 14R) backward accumulators of four groups
+  constexpr uint32_t kTmemCols = 14 * R > 256 ? 512 : 256;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -232,33 +243,40 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
   uint64_t* full = bars;                 // [kSlots] ring slots landed
   uint64_t* empty = bars + kSlots;       // [kSlots] MMAs done with the slot
-  uint64_t* accfull = bars + 8;          // forward: left product of the group complete
-  uint64_t* bready = bars + 9;           // forward: the group's y is in the window
-  uint64_t* tready = bars + 10;          // the group's t operand is written (both passes)
-  uint64_t* yready = bars + 11;          // the product with G_g is complete (both passes)
-  uint64_t* baccready = bars + 12;       // backward: the next group's accumulator is complete
-  uint64_t* xready = bars + 13;          // backward: the group's x~ operand is written
-  uint64_t* xfree = bars + 14;           // backward: the MMAs are done with that operand
-  uint64_t* done = bars + 15;            // every MMA has completed
-  constexpr int kBars = 16;
+  uint64_t* accfull = bars + 2 * kSlots;      // forward: left product of the group complete
+  uint64_t* bready = accfull + 1;        // forward: the group's y is in the window
+  uint64_t* tready = accfull + 2;        // the group's t operand is written (both passes)
+  uint64_t* yready = accfull + 3;        // the product with G_g is complete (both passes)
+  uint64_t* baccready = accfull + 4;     // backward: the next group's accumulator is complete
+  uint64_t* xready = accfull + 5;        // backward: the group's x~ operand is written
+  uint64_t* xfree = accfull + 6;         // backward: the MMAs are done with that operand
+  uint64_t* done = accfull + 7;          // every MMA has completed
+  const int kBars = 2 * kSlots + 8;
   volatile int* flags = reinterpret_cast<volatile int*>(bars + kBars);  // [0] abort, [1] SIMT decision
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kBars + 2);
-  float* sigf = reinterpret_cast<float*>(sm + 256);  // [R] forward operand scale per column
+  static_assert(8 * (2 * kSlots + 8) + 16 <= 384, "barrier page");
+  float* sigf = reinterpret_cast<float*>(sm + 384);  // [R] forward operand scale per column
   float* sigb = sigf + 32;                           // [R] backward
-  float* scr = reinterpret_cast<float*>(sm + 512);   // [8][R / 2] column maxima of the SIMT warps
   const uint32_t regA = base + 1024;
   unsigned char* pA = sm + 1024;
+  float* scr = reinterpret_cast<float*>(pA + LY::kB2);  // [8][R / 2] column maxima (t operand is free then)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const PieceDesc pd = a.pieces[blockIdx.x];
-  const int n = pd.n, T = wt_tiles(pd.w), ng = wt_groups(n);
-  const int64_t GB = wt_group_bytes(T);
+  const int n = pd.n, T = wt_tiles(pd.w), z = wt_zlead(pd.w), nl = wt_nleft(pd.w), ng = wt_groups(n);
+  const int64_t GB = wt_group_bytes(pd.w);
   const unsigned char* gb0 = a.wt + pd.wt_off;
+  const unsigned char* zero_panel = a.wt;  // the factor buffer starts with a zero panel
   float* xg = a.xc + (size_t)pd.copy_off * R;
   const float* bg = a.bt + (size_t)pd.copy_off * R;
   auto dval = [&](int row) -> float {
-    return *reinterpret_cast<const float*>(gb0 + (int64_t)(row / kG) * GB + (size_t)(4 * T + 4) * kChunk +
+    return *reinterpret_cast<const float*>(gb0 + (int64_t)(row / kG) * GB + (size_t)(2 * nl + 4) * kChunk +
                                            (size_t)(row % kG) * 4);
+  };
+  // left panel c (hi, or lo with lo = 1) of group g; c < z: the zero panel
+  auto left_panel = [&](int g, int c, int lo) -> const unsigned char* {
+    if (c < z) return zero_panel;
+    return gb0 + (int64_t)g * GB + (size_t)(lo * nl + c - z) * kChunk;
   };
 
   if (tid == 0) {
@@ -338,47 +356,59 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
   }
   const uint32_t tmem = *tslot;
 
+  // Order of the panels (the MMA issuer takes them in the same order).  Forward: group 0's left
+  // panels, then per group g: the left panels of group g + 1 that do not read y_g ("early"), G_g's
+  // hi and lo pairs, the two that do ("late").  Backward, per group in descending order: G_g's pairs,
+  // then the hi and lo pairs of tiles T - 1 .. 0 (tiles left of row 0 skipped).  A left panel is its
+  // hi then its lo half; left panels c < z are not stored (or read) forward and come from the zero
+  // panel backward.
+  const int nearly = 2 * T - 2;  // left panels of a group that do not read the previous group's y
+
   if (warp == 0) {
-    // ---- panels, in the order the MMAs take them.  Forward, per group: the 2 T left chunks (hi + lo
-    // of one chunk per slot), then G_g's hi pair and lo pair.  Backward, per group in descending
-    // order: G_g's hi and lo pairs, then the hi and lo pairs of tiles T - 1 .. 0 (tiles left of row 0
-    // skipped).  The panels are read once per pass: evict first.
+    // ---- panels: one 16 KB bulk copy per slot, read once per pass (evict first)
     if (lane == 0) {
       uint64_t pol;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
       int cnt = 0;
-      auto next = [&](const unsigned char* src0, const unsigned char* src1) -> bool {
+      bool ok = true;
+      auto next = [&](const unsigned char* src) {
+        if (!ok) return;
         const int slot = cnt % kSlots;
-        if (cnt >= kSlots && !wait_or_abort(&empty[slot], (uint32_t)(((cnt / kSlots) - 1) & 1), a.wait_limit, flags))
-          return false;
+        if (cnt >= kSlots && !wait_or_abort(&empty[slot], (uint32_t)(((cnt / kSlots) - 1) & 1), a.wait_limit, flags)) {
+          ok = false;
+          return;
+        }
         if (cnt != a.withhold) {  // testing hook: this copy's wait can only run out
-          mbar_arrive_expect_tx(&full[slot], kSlotBytes);
-          if (src1) {
-            bulk_g2s_hint(regA + slot * kSlotBytes, src0, kChunk, &full[slot], pol);
-            bulk_g2s_hint(regA + slot * kSlotBytes + kChunk, src1, kChunk, &full[slot], pol);
-          } else {
-            bulk_g2s_hint(regA + slot * kSlotBytes, src0, kSlotBytes, &full[slot], pol);
-          }
+          mbar_arrive_expect_tx(&full[slot], kChunk);
+          bulk_g2s_hint(regA + slot * kChunk, src, kChunk, &full[slot], pol);
         }
         ++cnt;
-        return true;
       };
-      bool ok = true;
+      auto left = [&](int g, int c0, int c1) {
+        for (int c = (c0 > z ? c0 : z); c < c1; ++c) {
+          next(left_panel(g, c, 0));
+          next(left_panel(g, c, 1));
+        }
+      };
+      auto gpanels = [&](int g) {
+        const unsigned char* src = gb0 + (int64_t)g * GB + (size_t)(2 * nl) * kChunk;
+        for (int i = 0; i < 4; ++i) next(src + (size_t)i * kChunk);
+      };
+      left(0, 0, 2 * T);
       for (int g = 0; g < ng && ok && !flags[0]; ++g) {
-        const unsigned char* src = gb0 + (int64_t)g * GB;
-        for (int c = 0; c < 2 * T && ok; ++c) ok = next(src + (size_t)c * kChunk, src + (size_t)(2 * T + c) * kChunk);
-        if (ok) ok = next(src + (size_t)(4 * T) * kChunk, nullptr);
-        if (ok) ok = next(src + (size_t)(4 * T + 2) * kChunk, nullptr);
+        if (g + 1 < ng) left(g + 1, 0, nearly);
+        gpanels(g);
+        if (g + 1 < ng) left(g + 1, nearly, 2 * T);
       }
       for (int k = 0; k < ng && ok && !flags[0]; ++k) {
         const int g = ng - 1 - k;
-        const unsigned char* src = gb0 + (int64_t)g * GB;
-        ok = next(src + (size_t)(4 * T) * kChunk, nullptr);
-        if (ok) ok = next(src + (size_t)(4 * T + 2) * kChunk, nullptr);
+        gpanels(g);
         for (int m = T - 1; m >= 0 && ok; --m) {
           if (g - T + m < 0) continue;
-          ok = next(src + (size_t)(2 * m) * kChunk, nullptr);
-          if (ok) ok = next(src + (size_t)(2 * T + 2 * m) * kChunk, nullptr);
+          next(left_panel(g, 2 * m, 0));
+          next(left_panel(g, 2 * m + 1, 0));
+          next(left_panel(g, 2 * m, 1));
+          next(left_panel(g, 2 * m + 1, 1));
         }
       }
       if (!ok) flags[0] = 1;
@@ -391,78 +421,94 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
     if (lane == 0) {
       int cnt = 0;
       bool ok = true;
-      const uint32_t dL = tmem, dG = tmem + 2 * R;
+      const uint32_t dG = tmem + 4 * R;
       const uint32_t b2 = regA + LY::kB2, xb = regA + LY::kWin;
-      auto take = [&](uint32_t& slot_addr) -> bool {
+      auto take = [&]() -> uint32_t {  // the next slot's address, 0 if the wait gave up
         const int slot = cnt % kSlots;
-        if (!wait_or_abort(&full[slot], (uint32_t)((cnt / kSlots) & 1), a.wait_limit, flags)) return false;
+        if (!wait_or_abort(&full[slot], (uint32_t)((cnt / kSlots) & 1), a.wait_limit, flags)) {
+          ok = false;
+          return 0u;
+        }
         tc_fence_after();
-        slot_addr = regA + slot * kSlotBytes;
-        return true;
+        return regA + slot * kChunk;
       };
-      auto give = [&]() {
-        mma_commit(&empty[cnt % kSlots]);
-        ++cnt;
+      auto give = [&](int k) {  // the last k slots taken are free once the MMAs issued so far complete
+        for (int i = 0; i < k; ++i) mma_commit(&empty[(cnt + i) % kSlots]);
+        cnt += k;
       };
-      // the product with G_g (forward) or G_g^T (backward) of the t operand, into dG
-      auto g_product = [&](bool transposed) -> bool {
-        const uint32_t id = transposed ? idT : idK;
-        uint32_t s0, s1;
-        if (!take(s0)) return false;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const uint32_t p = kk >> 2, o = (kk & 3) * 2;
-          const uint64_t a0 =
-              transposed ? sdesc(s0, kChunk, 1024) + (uint64_t)(kk * 128) : sdesc(s0 + p * kChunk, 16, 1024) + o;
-          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
-          mma_f16(dG, a0, bH, id, kk == 0 ? 0u : 1u);
-          mma_f16(dG + R, a0, bL, id, kk == 0 ? 0u : 1u);
-        }
-        give();
-        if (!take(s1)) return false;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const uint32_t p = kk >> 2, o = (kk & 3) * 2;
-          const uint64_t a1 =
-              transposed ? sdesc(s1, kChunk, 1024) + (uint64_t)(kk * 128) : sdesc(s1 + p * kChunk, 16, 1024) + o;
-          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o;
-          mma_f16_acc(dG + R, a1, bH, id);
-        }
-        give();
-        mma_commit(yready);
-        return true;
-      };
-      // forward: chunk c of group g reads the window rows of group g - T + c / 2 (published through
-      // bready; the groups before g - 1 were waited for during group g - 1)
-      for (int g = 0; g < ng && ok; ++g) {
-        bool waited = false;
-        for (int c = 0; c < 2 * T && ok; ++c) {
-          const int gr = g - T + (c >> 1);
-          if (gr == g - 1 && gr >= 0 && !waited) {
-            if (!(ok = wait_or_abort(bready, (uint32_t)((g - 1) & 1), a.wait_limit, flags))) break;
-            waited = true;
+      // left panels c0 .. c1 - 1 of group g into the accumulator pair at d (first issued one
+      // overwrites when first is set); window rows of group g - T + c / 2
+      auto left_product = [&](int g, int c0, int c1, uint32_t d, bool first) {
+        for (int c = (c0 > z ? c0 : z); c < c1 && ok; ++c) {
+          const uint32_t sh = take();
+          if (!ok) return;
+          const uint32_t sl = regA + ((cnt + 1) % kSlots) * kChunk;
+          {
+            const int slot = (cnt + 1) % kSlots;
+            if (!(ok = wait_or_abort(&full[slot], (uint32_t)(((cnt + 1) / kSlots) & 1), a.wait_limit, flags))) return;
             tc_fence_after();
           }
-          uint32_t sa;
-          if (!(ok = take(sa))) break;
-          const uint64_t aH = sdesc(sa, 16, 1024), aL = sdesc(sa + kChunk, 16, 1024);
+          const int gr = g - T + (c >> 1);
           const int wc = ((2 * gr + (c & 1)) % kNWC + kNWC) % kNWC;
+          const uint64_t aH = sdesc(sh, 16, 1024), aL = sdesc(sl, 16, 1024);
           const uint64_t bH = sdesc(regA + LY::kWin + wc * LY::kWinChunk, 16, 1024);
           const uint64_t bL = bH + (uint64_t)(R * 8);  // lo panel: R rows of 128 bytes further
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t o = 2 * kk;  // 32 bytes per K step of 16
-            mma_f16(dL, aH + o, bH + o, idK, (c == 0 && kk == 0) ? 0u : 1u);
-            mma_f16(dL + R, aH + o, bL + o, idK, (c == 0 && kk == 0) ? 0u : 1u);
-            mma_f16_acc(dL + R, aL + o, bH + o, idK);
+            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+            mma_f16(d, aH + o, bH + o, idK, acc);
+            mma_f16(d + R, aH + o, bL + o, idK, acc);
+            mma_f16_acc(d + R, aL + o, bH + o, idK);
           }
-          give();
+          first = false;
+          give(2);
         }
+      };
+      // the product with G_g (forward) or G_g^T (backward) of the t operand, into dG
+      auto g_product = [&](bool transposed) {
+        const uint32_t id = transposed ? idT : idK;
+        const uint32_t h0 = take();
+        if (!ok) return;
+        uint32_t slots[4] = {h0, 0u, 0u, 0u};
+        for (int i = 1; i < 4; ++i) {
+          const int slot = (cnt + i) % kSlots;
+          if (!(ok = wait_or_abort(&full[slot], (uint32_t)(((cnt + i) / kSlots) & 1), a.wait_limit, flags))) return;
+          slots[i] = regA + slot * kChunk;
+        }
+        tc_fence_after();
+        // hi panels 0, 1 in slots 0, 1 (adjacent: the ring has an even slot count and every pair
+        // starts at an even slot), lo panels in slots 2, 3
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t p = kk >> 2, o = (kk & 3) * 2;
+          const uint64_t ah = transposed ? sdesc(slots[0], kChunk, 1024) + (uint64_t)(kk * 128)
+                                         : sdesc(slots[p], 16, 1024) + o;
+          const uint64_t al = transposed ? sdesc(slots[2], kChunk, 1024) + (uint64_t)(kk * 128)
+                                         : sdesc(slots[2 + p], 16, 1024) + o;
+          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
+          mma_f16(dG, ah, bH, id, kk == 0 ? 0u : 1u);
+          mma_f16(dG + R, ah, bL, id, kk == 0 ? 0u : 1u);
+          mma_f16_acc(dG + R, al, bH, id);
+        }
+        give(4);
+        mma_commit(yready);
+      };
+      // forward
+      left_product(0, 0, 2 * T, tmem, true);
+      if (ok) mma_commit(accfull);
+      for (int g = 0; g < ng && ok; ++g) {
+        const uint32_t dn = tmem + (uint32_t)(((g + 1) & 1) * 2 * R);
+        if (g + 1 < ng) left_product(g + 1, 0, nearly, dn, true);
         if (!ok) break;
-        mma_commit(accfull);
         if (!(ok = wait_or_abort(tready, (uint32_t)(g & 1), a.wait_limit, flags))) break;
         tc_fence_after();
-        ok = g_product(false);
+        g_product(false);
+        if (!ok || g + 1 >= ng) break;
+        if (!(ok = wait_or_abort(bready, (uint32_t)(g & 1), a.wait_limit, flags))) break;
+        tc_fence_after();
+        left_product(g + 1, nearly, 2 * T, dn, nearly <= z);
+        if (ok) mma_commit(accfull);
       }
       // backward: x~_g = G_g^T t, then group g adds L~_(g, left)^T x~_g to the accumulators of
       // groups g - T .. g - 1 (tile T - 1 first: group g - 1 reads its accumulator next)
@@ -470,35 +516,35 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
         const int g = ng - 1 - k;
         if (!(ok = wait_or_abort(tready, (uint32_t)((ng + k) & 1), a.wait_limit, flags))) break;
         tc_fence_after();
-        if (!(ok = g_product(true))) break;
+        g_product(true);
+        if (!ok) break;
         if (!(ok = wait_or_abort(xready, (uint32_t)(k & 1), a.wait_limit, flags))) break;
         tc_fence_after();
         for (int m = T - 1; m >= 0 && ok; --m) {
           const int h = g - T + m;
           if (h < 0) continue;
-          const uint32_t d = tmem + 4 * R + (uint32_t)((h & 3) * 2 * R);
+          const uint32_t d = tmem + 6 * R + (uint32_t)((h & 3) * 2 * R);
           const bool first = (g == min(h + T, ng - 1));
-          uint32_t sa;
-          if (!(ok = take(sa))) break;
-          const uint64_t aT = sdesc(sa, kChunk, 1024);
+          const uint32_t s0 = take();
+          if (!ok) break;
+          for (int i = 1; i < 4 && ok; ++i) {
+            const int slot = (cnt + i) % kSlots;
+            ok = wait_or_abort(&full[slot], (uint32_t)(((cnt + i) / kSlots) & 1), a.wait_limit, flags);
+          }
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t s2 = regA + ((cnt + 2) % kSlots) * kChunk;
+          const uint64_t aT = sdesc(s0, kChunk, 1024), aTl = sdesc(s2, kChunk, 1024);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
             const uint32_t p = kk >> 2, o = (kk & 3) * 2;
             const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
-            const uint64_t at = aT + (uint64_t)(kk * 128);  // 16 rows of 128 bytes per K step
-            mma_f16(d, at, bH, idT, (first && kk == 0) ? 0u : 1u);
-            mma_f16(d + R, at, bL, idT, (first && kk == 0) ? 0u : 1u);
-          }
-          give();
-          if (!(ok = take(sa))) break;
-          const uint64_t aTl = sdesc(sa, kChunk, 1024);
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint32_t p = kk >> 2, o = (kk & 3) * 2;
-            const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o;
+            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+            mma_f16(d, aT + (uint64_t)(kk * 128), bH, idT, acc);  // 16 rows of 128 bytes per K step
+            mma_f16(d + R, aT + (uint64_t)(kk * 128), bL, idT, acc);
             mma_f16_acc(d + R, aTl + (uint64_t)(kk * 128), bH, idT);
           }
-          give();
+          give(4);
           if (m == T - 1) mma_commit(baccready);
         }
         if (ok) mma_commit(xfree);
@@ -559,7 +605,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(accfull, (uint32_t)(g & 1)))) break;
       tc_fence_after();
       float t[kHalf];
-      tmem_pair(0, t);
+      tmem_pair((uint32_t)((g & 1) * 2 * R), t);
 #pragma unroll
       for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigf[c0 + c] * t[c];
       put_operand(b2p, t, sigf);
@@ -571,7 +617,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(yready, (uint32_t)(g & 1)))) break;
       tc_fence_after();
       float y[kHalf];
-      tmem_pair(2 * R, y);
+      tmem_pair(4 * R, y);
 #pragma unroll
       for (int c = 0; c < kHalf; ++c) {
         y[c] *= sigf[c0 + c];
@@ -620,7 +666,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (g + 1 <= ng - 1) {
         if (!(ok = decide(baccready, (uint32_t)((k - 1) & 1)))) break;
         tc_fence_after();
-        tmem_pair(4 * R + (uint32_t)((g & 3) * 2 * R), t);
+        tmem_pair(6 * R + (uint32_t)((g & 3) * 2 * R), t);
 #pragma unroll
         for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigb[c0 + c] * t[c];
       } else {
@@ -638,7 +684,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(yready, (uint32_t)((ng + k) & 1)))) break;
       tc_fence_after();
       float x[kHalf];
-      tmem_pair(2 * R, x);
+      tmem_pair(4 * R, x);
 #pragma unroll
       for (int c = 0; c < kHalf; ++c) x[c] *= sigb[c0 + c];
       if (row < n) {
