@@ -1,6 +1,8 @@
 // Vector kernels around the sweeps: source splitting (§4 step 3), assembly of the solution from the
 // copies (mean of the copies; at the fixed point all copies agree, Thm 4.1), and the FP64 residual
 // b - A x with per-right-hand-side squared norms (the convergence test of Table 1 step 6).
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace vtm {
@@ -8,6 +10,7 @@ namespace vtm {
 namespace {
 constexpr int kMaxR = kMaxRhs;
 constexpr int kBS = 256;
+constexpr int kNormRows = 8;  // rows per thread in the fixed-order norm kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -73,10 +76,12 @@ __global__ void k_assemble(int64_t n, int R, const int64_t* __restrict__ vc_ptr,
   const int r0 = blockIdx.y * RG;
   if (i >= n) return;
   const int64_t lo = vc_ptr[i], hi = vc_ptr[i + 1];
-  const double inv = 1.0 / (double)(hi - lo);
-  double s[RG];
+  // FP32 copies: their mean in FP32 (the copies carry FP32 rounding already), one FP64 add
+  using A = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  const A inv = A(1) / (A)(hi - lo);
+  A s[RG];
 #pragma unroll
-  for (int rr = 0; rr < RG; ++rr) s[rr] = 0.0;
+  for (int rr = 0; rr < RG; ++rr) s[rr] = A(0);
   for (int64_t k = lo; k < hi; ++k) {
     const T* p = xc + vc_copy[k] * R + r0;  // the copy's RG values are contiguous (and 16-byte
                                             // aligned when RG is 4 or 8: R and r0 are multiples of RG)
@@ -94,13 +99,13 @@ __global__ void k_assemble(int64_t n, int R, const int64_t* __restrict__ vc_ptr,
       }
     } else {
 #pragma unroll
-      for (int rr = 0; rr < RG; ++rr) s[rr] += (double)p[rr];
+      for (int rr = 0; rr < RG; ++rr) s[rr] += (A)p[rr];
     }
   }
 #pragma unroll
   for (int rr = 0; rr < RG; ++rr) {
     const int64_t at = i + (int64_t)(r0 + rr) * ld;
-    xt[at] = (xbase ? xbase[at] : 0.0) + s[rr] * inv;
+    xt[at] = (xbase ? xbase[at] : 0.0) + (double)(s[rr] * inv);
   }
 }
 
@@ -136,48 +141,51 @@ __global__ void k_residual(int64_t n, int R, const int64_t* __restrict__ rowptr,
 }
 
 // The same residual with fixed-order sums: block (x, y) writes the squared norms of its rows'
-// residuals, column by column, to part[r * gridDim.x + x] (summed over the block's warps in warp
-// order), and k_finish_norms adds each column's partials in index order.  The row's entries of A
-// are loaded eight at a time before the products, so that the loads of x for all of them are in
-// flight together.
+// residuals, column by column, to part[r * gridDim.x + x] (each thread sums kNormRows rows, then the
+// block's warps are summed in warp order), and k_finish_norms adds each column's partials in index
+// order.  The row's entries of A are loaded eight at a time before the products, so that the loads
+// of x for all of them are in flight together.  FP64 arithmetic is the bound on this GPU (a small
+// fraction of the FP32 rate), so every thread covers several rows before the butterfly sums.
 template <int RG>
 __global__ void __launch_bounds__(kBS) k_residual_part(int64_t n, int R, const int64_t* __restrict__ rowptr,
                                                         const int32_t* __restrict__ col, const double* __restrict__ val,
                                                         const double* __restrict__ b, int64_t ldb,
                                                         const double* __restrict__ x, int64_t ldx,
                                                         double* __restrict__ res, int64_t ldr, double* __restrict__ part) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int r0 = blockIdx.y * RG;
   double sq[RG];
 #pragma unroll
   for (int rr = 0; rr < RG; ++rr) sq[rr] = 0.0;
-  if (i < n) {
-    const int64_t lo = rowptr[i], hi = rowptr[i + 1];
-    double ax[RG];
+  for (int j = 0; j < kNormRows; ++j) {
+    const int64_t i = (blockIdx.x * (int64_t)kNormRows + j) * blockDim.x + threadIdx.x;
+    if (i < n) {
+      const int64_t lo = rowptr[i], hi = rowptr[i + 1];
+      double ax[RG];
 #pragma unroll
-    for (int rr = 0; rr < RG; ++rr) ax[rr] = 0.0;
-    for (int64_t k0 = lo; k0 < hi; k0 += 8) {
-      int c[8];
-      double v[8];
+      for (int rr = 0; rr < RG; ++rr) ax[rr] = 0.0;
+      for (int64_t k0 = lo; k0 < hi; k0 += 8) {
+        int c[8];
+        double v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        c[u] = k0 + u < hi ? col[k0 + u] : 0;
-        v[u] = k0 + u < hi ? val[k0 + u] : 0.0;
-      }
+        for (int u = 0; u < 8; ++u) {
+          c[u] = k0 + u < hi ? col[k0 + u] : 0;
+          v[u] = k0 + u < hi ? val[k0 + u] : 0.0;
+        }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (k0 + u < hi) {
-          const double* xk = x + c[u] + (int64_t)r0 * ldx;
+        for (int u = 0; u < 8; ++u) {
+          if (k0 + u < hi) {
+            const double* xk = x + c[u] + (int64_t)r0 * ldx;
 #pragma unroll
-          for (int rr = 0; rr < RG; ++rr) ax[rr] += v[u] * xk[(int64_t)rr * ldx];
+            for (int rr = 0; rr < RG; ++rr) ax[rr] += v[u] * xk[(int64_t)rr * ldx];
+          }
         }
       }
-    }
 #pragma unroll
-    for (int rr = 0; rr < RG; ++rr) {
-      const double ri = b[i + (int64_t)(r0 + rr) * ldb] - ax[rr];
-      if (res) res[i + (int64_t)(r0 + rr) * ldr] = ri;
-      sq[rr] = ri * ri;
+      for (int rr = 0; rr < RG; ++rr) {
+        const double ri = b[i + (int64_t)(r0 + rr) * ldb] - ax[rr];
+        if (res) res[i + (int64_t)(r0 + rr) * ldr] = ri;
+        sq[rr] = fma(ri, ri, sq[rr]);
+      }
     }
   }
   __shared__ double red[kBS / 32][RG];
@@ -199,14 +207,23 @@ __global__ void __launch_bounds__(kBS) k_residual_part(int64_t n, int R, const i
 template <int RG>
 __global__ void __launch_bounds__(kBS) k_sqnorm_part(int64_t n, const double* __restrict__ v, int64_t ld,
                                                       double* __restrict__ part) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int r0 = blockIdx.y * RG;
   __shared__ double red[kBS / 32][RG];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double sq[RG];
+#pragma unroll
+  for (int rr = 0; rr < RG; ++rr) sq[rr] = 0.0;
+  for (int j = 0; j < kNormRows; ++j) {
+    const int64_t i = (blockIdx.x * (int64_t)kNormRows + j) * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < RG; ++rr) {
+      const double t = i < n ? v[i + (int64_t)(r0 + rr) * ld] : 0.0;
+      sq[rr] = fma(t, t, sq[rr]);
+    }
+  }
 #pragma unroll
   for (int rr = 0; rr < RG; ++rr) {
-    const double t = i < n ? v[i + (int64_t)(r0 + rr) * ld] : 0.0;
-    const double w = warp_sum(t * t);
+    const double w = warp_sum(sq[rr]);
     if (lane == 0) red[warp][rr] = w;
   }
   __syncthreads();
@@ -283,6 +300,7 @@ __global__ void k_gather_diag(const PieceDesc* __restrict__ pieces, const int32_
 }
 
 static unsigned nblocks(int64_t n) { return (unsigned)((n + kBS - 1) / kBS); }
+static unsigned nblocks_norm(int64_t n) { return (unsigned)((n + kBS * kNormRows - 1) / (kBS * kNormRows)); }
 
 template <typename T>
 cudaError_t launch_split(int64_t ncopies, int R, const int64_t* copy_vertex, const double* share, const double* src,
@@ -319,14 +337,14 @@ cudaError_t launch_residual(int64_t n, int R, const int64_t* rowptr, const int32
   return cudaGetLastError();
 }
 
-int64_t norm_parts(int64_t n) { return (int64_t)nblocks(n); }
+int64_t norm_parts(int64_t n) { return (int64_t)nblocks_norm(n); }
 
 cudaError_t launch_residual_det(int64_t n, int R, const int64_t* rowptr, const int32_t* col, const double* val,
                                 const double* b, int64_t ldb, const double* x, int64_t ldx, double* res, int64_t ldr,
                                 double* part, double* norms, cudaStream_t st) {
   if (R > kMaxR || R < 1) return cudaErrorInvalidValue;
   if (n <= 0) return cudaMemsetAsync(norms, 0, R * sizeof(double), st);
-  const unsigned bx = nblocks(n);
+  const unsigned bx = nblocks_norm(n);
   if (R % 8 == 0) k_residual_part<8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
   else if (R % 4 == 0) k_residual_part<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
   else if (R % 2 == 0) k_residual_part<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, R, rowptr, col, val, b, ldb, x, ldx, res, ldr, part);
@@ -339,7 +357,7 @@ cudaError_t launch_sqnorm_det(int64_t n, int R, const double* v, int64_t ld, dou
                               cudaStream_t st) {
   if (R > kMaxR || R < 1) return cudaErrorInvalidValue;
   if (n <= 0) return cudaMemsetAsync(norms, 0, R * sizeof(double), st);
-  const unsigned bx = nblocks(n);
+  const unsigned bx = nblocks_norm(n);
   if (R % 8 == 0) k_sqnorm_part<8><<<dim3(bx, R / 8), kBS, 0, st>>>(n, v, ld, part);
   else if (R % 4 == 0) k_sqnorm_part<4><<<dim3(bx, R / 4), kBS, 0, st>>>(n, v, ld, part);
   else if (R % 2 == 0) k_sqnorm_part<2><<<dim3(bx, R / 2), kBS, 0, st>>>(n, v, ld, part);
