@@ -77,6 +77,7 @@ __device__ __forceinline__ void simt_sync() {
 
 // Bounded wait that also gives up once another role has set the abort flag.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, long limit, volatile int* abort_flag) {
+  if (mbar_test_wait(bar, parity)) return true;  // most waits find the phase complete
   for (long it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
@@ -233,9 +234,16 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
   constexpr int kSlots = LY::kSlots;
   constexpr int kHalf = R / 2;            // columns of a SIMT thread (row = tensor-memory lane)
   constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
-  // tensor memory: [0, 4R) the forward left product of groups g even / odd (D1 | D2 each),
-  // [4R, 6R) the product with G_g, [6R, 14R) backward accumulators of four groups
-  constexpr uint32_t kTmemCols = 14 * R > 256 ? 512 : 256;
+  // N = 2R: the hi and lo panels of a vector operand lie one after the other (R rows of 128 bytes
+  // each), so hi(A) [v_hi | v_lo] is one MMA into the accumulator pair D1 | D2
+  constexpr uint32_t idK2 = idesc_f16(false, 2 * R), idT2 = idesc_f16(true, 2 * R);
+  // Tensor memory.  Consecutive MMAs into one accumulator wait for each other, so every product
+  // alternates its K steps between two accumulator sets (summed when read); a set is D1 | D2 (2R
+  // columns).  Forward: [0, 8R) the left products of groups g even / odd, [8R, 12R) the product with
+  // G_g.  Backward: [0, 12R) the accumulators of three groups (h mod 3: a group receives from the
+  // T <= 3 groups after it), [12R, 16R) the product with G_g^T.
+  constexpr uint32_t kTmemCols = 16 * R;
+  constexpr uint32_t kSet = 2 * R;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -321,28 +329,58 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       }
     }
     __syncthreads();
-    float mp = 0.f;  // port rows: column tid % R
-    for (int i = tid; i < pd.nports * R; i += kWtThreads) {
-      const int q = i / R, c = i % R;
-      float acc = 0.f;
-      for (int e = a.port_end_ptr[pd.port_off + q]; e < a.port_end_ptr[pd.port_off + q + 1]; ++e)
-        acc += a.wprev[(size_t)a.twin[e] * R + c] * a.invz[e];
-      if (a.cpl.ptr) acc += coupling_current<float, float>(a.cpl, pd.port_off + q, c, R, a.wprev);
-      const int row = a.port_local[pd.port_off + q];
-      float* at = xg + (size_t)row * R + c;
-      const float v = *at + dval(row) * acc;
-      *at = v;
-      mp = fmaxf(mp, fabsf(v));
+    // port rows, one port per thread with its R columns in registers (16-byte loads of the R-wide
+    // wave rows): r~ += d_row (sum_e w_in[e] / Z_e + coupling currents)
+    float mp[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) mp[c] = 0.f;
+    for (int q = tid; q < pd.nports; q += kWtThreads) {
+      const int port = pd.port_off + q;
+      float acc[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) acc[c] = 0.f;
+      for (int e = a.port_end_ptr[port]; e < a.port_end_ptr[port + 1]; ++e) {
+        const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+        const float iz = a.invz[e];
+#pragma unroll
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 x = w[k4];
+          acc[4 * k4] += x.x * iz, acc[4 * k4 + 1] += x.y * iz, acc[4 * k4 + 2] += x.z * iz, acc[4 * k4 + 3] += x.w * iz;
+        }
+      }
+      if (a.cpl.ptr)
+        for (int k = a.cpl.ptr[port]; k < a.cpl.ptr[port + 1]; ++k) {
+          const float yk = a.cpl.y[k];
+          const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
+#pragma unroll
+          for (int k4 = 0; k4 < R / 4; ++k4) {
+            const float4 x = w[k4];
+            acc[4 * k4] += yk * x.x, acc[4 * k4 + 1] += yk * x.y, acc[4 * k4 + 2] += yk * x.z, acc[4 * k4 + 3] += yk * x.w;
+          }
+        }
+      const int row = a.port_local[port];
+      const float dv = dval(row);
+      float4* xr = reinterpret_cast<float4*>(xg + (size_t)row * R);
+#pragma unroll
+      for (int k4 = 0; k4 < R / 4; ++k4) {
+        float4 x = xr[k4];
+        x.x += dv * acc[4 * k4], x.y += dv * acc[4 * k4 + 1], x.z += dv * acc[4 * k4 + 2], x.w += dv * acc[4 * k4 + 3];
+        xr[k4] = x;
+        mp[4 * k4] = fmaxf(mp[4 * k4], fabsf(x.x)), mp[4 * k4 + 1] = fmaxf(mp[4 * k4 + 1], fabsf(x.y));
+        mp[4 * k4 + 2] = fmaxf(mp[4 * k4 + 2], fabsf(x.z)), mp[4 * k4 + 3] = fmaxf(mp[4 * k4 + 3], fabsf(x.w));
+      }
     }
-    // per column: the 4-wide maxima of the threads with tid % (R / 4) == c / 4, and mp of tid % R == c
+    // per column: the 4-wide maxima of the threads with tid % (R / 4) == c / 4, and every thread's
+    // port-row maximum
     float* red = reinterpret_cast<float*>(pA + LY::kWin);  // the window, zeroed below
     reinterpret_cast<float4*>(red)[tid] = make_float4(mx[0], mx[1], mx[2], mx[3]);
-    red[4 * kWtThreads + tid] = mp;
+#pragma unroll
+    for (int c = 0; c < R; ++c) red[4 * kWtThreads + c * kWtThreads + tid] = mp[c];
     __syncthreads();
     if (tid < R) {
       float m = 0.f;
       for (int t = tid / 4; t < kWtThreads; t += R / 4) m = fmaxf(m, red[4 * t + (tid & 3)]);
-      for (int t = tid; t < kWtThreads; t += R) m = fmaxf(m, red[4 * kWtThreads + t]);
+      for (int t = 0; t < kWtThreads; ++t) m = fmaxf(m, red[4 * kWtThreads + tid * kWtThreads + t]);
       sigf[tid] = pow2_at_or_above(m);
     }
     __syncthreads();
@@ -421,7 +459,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
     if (lane == 0) {
       int cnt = 0;
       bool ok = true;
-      const uint32_t dG = tmem + 4 * R;
+      const uint32_t dGf = tmem + 8 * R, dGb = tmem + 12 * R;
       const uint32_t b2 = regA + LY::kB2, xb = regA + LY::kWin;
       auto take = [&]() -> uint32_t {  // the next slot's address, 0 if the wait gave up
         const int slot = cnt % kSlots;
@@ -439,6 +477,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       // left panels c0 .. c1 - 1 of group g into the accumulator pair at d (first issued one
       // overwrites when first is set); window rows of group g - T + c / 2
       auto left_product = [&](int g, int c0, int c1, uint32_t d, bool first) {
+        int ks = 0;  // K steps issued by this call: set ks & 1, the first step of a set overwrites
         for (int c = (c0 > z ? c0 : z); c < c1 && ok; ++c) {
           const uint32_t sh = take();
           if (!ok) return;
@@ -452,22 +491,19 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
           const int wc = ((2 * gr + (c & 1)) % kNWC + kNWC) % kNWC;
           const uint64_t aH = sdesc(sh, 16, 1024), aL = sdesc(sl, 16, 1024);
           const uint64_t bH = sdesc(regA + LY::kWin + wc * LY::kWinChunk, 16, 1024);
-          const uint64_t bL = bH + (uint64_t)(R * 8);  // lo panel: R rows of 128 bytes further
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
+          for (int kk = 0; kk < 4; ++kk, ++ks) {
             const uint32_t o = 2 * kk;  // 32 bytes per K step of 16
-            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-            mma_f16(d, aH + o, bH + o, idK, acc);
-            mma_f16(d + R, aH + o, bL + o, idK, acc);
-            mma_f16_acc(d + R, aL + o, bH + o, idK);
+            const uint32_t ds = d + (uint32_t)(ks & 1) * kSet;
+            mma_f16(ds, aH + o, bH + o, idK2, (first && ks < 2) ? 0u : 1u);
+            mma_f16_acc(ds + R, aL + o, bH + o, idK);
           }
-          first = false;
           give(2);
         }
       };
-      // the product with G_g (forward) or G_g^T (backward) of the t operand, into dG
-      auto g_product = [&](bool transposed) {
-        const uint32_t id = transposed ? idT : idK;
+      // the product with G_g (forward) or G_g^T (backward) of the t operand, into the sets at dG
+      auto g_product = [&](bool transposed, uint32_t dG) {
+        const uint32_t id = transposed ? idT : idK, id2 = transposed ? idT2 : idK2;
         const uint32_t h0 = take();
         if (!ok) return;
         uint32_t slots[4] = {h0, 0u, 0u, 0u};
@@ -486,10 +522,10 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
                                          : sdesc(slots[p], 16, 1024) + o;
           const uint64_t al = transposed ? sdesc(slots[2], kChunk, 1024) + (uint64_t)(kk * 128)
                                          : sdesc(slots[2 + p], 16, 1024) + o;
-          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
-          mma_f16(dG, ah, bH, id, kk == 0 ? 0u : 1u);
-          mma_f16(dG + R, ah, bL, id, kk == 0 ? 0u : 1u);
-          mma_f16_acc(dG + R, al, bH, id);
+          const uint64_t bH = sdesc(b2 + p * LY::kWinChunk, 16, 1024) + o;
+          const uint32_t ds = dG + (uint32_t)(kk & 1) * kSet;
+          mma_f16(ds, ah, bH, id2, kk < 2 ? 0u : 1u);
+          mma_f16_acc(ds + R, al, bH, id);
         }
         give(4);
         mma_commit(yready);
@@ -498,12 +534,12 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       left_product(0, 0, 2 * T, tmem, true);
       if (ok) mma_commit(accfull);
       for (int g = 0; g < ng && ok; ++g) {
-        const uint32_t dn = tmem + (uint32_t)(((g + 1) & 1) * 2 * R);
+        const uint32_t dn = tmem + (uint32_t)(((g + 1) & 1) * 2 * kSet);
         if (g + 1 < ng) left_product(g + 1, 0, nearly, dn, true);
         if (!ok) break;
         if (!(ok = wait_or_abort(tready, (uint32_t)(g & 1), a.wait_limit, flags))) break;
         tc_fence_after();
-        g_product(false);
+        g_product(false, dGf);
         if (!ok || g + 1 >= ng) break;
         if (!(ok = wait_or_abort(bready, (uint32_t)(g & 1), a.wait_limit, flags))) break;
         tc_fence_after();
@@ -516,14 +552,14 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
         const int g = ng - 1 - k;
         if (!(ok = wait_or_abort(tready, (uint32_t)((ng + k) & 1), a.wait_limit, flags))) break;
         tc_fence_after();
-        g_product(true);
+        g_product(true, dGb);
         if (!ok) break;
         if (!(ok = wait_or_abort(xready, (uint32_t)(k & 1), a.wait_limit, flags))) break;
         tc_fence_after();
         for (int m = T - 1; m >= 0 && ok; --m) {
           const int h = g - T + m;
           if (h < 0) continue;
-          const uint32_t d = tmem + 6 * R + (uint32_t)((h & 3) * 2 * R);
+          const uint32_t d = tmem + (uint32_t)((h % 3) * 2 * kSet);
           const bool first = (g == min(h + T, ng - 1));
           const uint32_t s0 = take();
           if (!ok) break;
@@ -538,11 +574,10 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
             const uint32_t p = kk >> 2, o = (kk & 3) * 2;
-            const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o, bL = bH + (uint64_t)(R * 8);
-            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-            mma_f16(d, aT + (uint64_t)(kk * 128), bH, idT, acc);  // 16 rows of 128 bytes per K step
-            mma_f16(d + R, aT + (uint64_t)(kk * 128), bL, idT, acc);
-            mma_f16_acc(d + R, aTl + (uint64_t)(kk * 128), bH, idT);
+            const uint64_t bH = sdesc(xb + p * LY::kWinChunk, 16, 1024) + o;
+            const uint32_t ds = d + (uint32_t)(kk & 1) * kSet;
+            mma_f16(ds, aT + (uint64_t)(kk * 128), bH, idT2, (first && kk < 2) ? 0u : 1u);  // 16 rows of 128 bytes per K step
+            mma_f16_acc(ds + R, aTl + (uint64_t)(kk * 128), bH, idT);
           }
           give(4);
           if (m == T - 1) mma_commit(baccready);
@@ -579,24 +614,38 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
         v[4 * c4] = x.x, v[4 * c4 + 1] = x.y, v[4 * c4 + 2] = x.z, v[4 * c4 + 3] = x.w;
       }
     };
-    // v = D1 + 2^-11 D2 of the accumulator pair at tensor-memory column col
+    // v = D1 + 2^-11 D2 of the two accumulator sets at tensor-memory column col
     auto tmem_pair = [&](uint32_t col, float (&v)[kHalf]) {
-      uint32_t a1[kHalf], a2[kHalf];
+      uint32_t a1[kHalf], a2[kHalf], b1[kHalf], b2[kHalf];
       tmem_ld<kHalf>(tmem + tl + col + c0, a1);
       tmem_ld<kHalf>(tmem + tl + col + R + c0, a2);
+      tmem_ld<kHalf>(tmem + tl + col + kSet + c0, b1);
+      tmem_ld<kHalf>(tmem + tl + col + kSet + R + c0, b2);
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) v[c] = __uint_as_float(a1[c]) + __uint_as_float(a2[c]) * (1.f / kLoScale);
+      for (int c = 0; c < kHalf; ++c)
+        v[c] = (__uint_as_float(a1[c]) + __uint_as_float(b1[c])) +
+               (__uint_as_float(a2[c]) + __uint_as_float(b2[c])) * (1.f / kLoScale);
     };
     // fp16 hi / lo of v / sigma as row rq of a K-major operand (K = the row in the group, panel row
     // = column)
-    auto put_operand = [&](unsigned char* chunk0, const float (&v)[kHalf], const float* sig) {
+    // (sigma is a power of two: multiplying by its reciprocal is exact)
+    auto put_operand = [&](unsigned char* chunk0, const float (&v)[kHalf], const float (&sinv)[kHalf]) {
       unsigned char* pan = chunk0 + (rq >> 6) * LY::kWinChunk;
+      const uint32_t kc = (uint32_t)(rq & 63) * 2;  // byte of this row (K) inside a 128-byte panel row
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) split_store(pan, pan + R * 128, swz16(c0 + c, rq & 63), v[c] / sig[c0 + c]);
+      for (int c = 0; c < kHalf; ++c) {
+        const uint32_t n = (uint32_t)(c0 + c);
+        const uint32_t off = (n >> 3) * 1024 + (n & 7) * 128 + ((((kc >> 4) ^ (n & 7))) << 4) + (kc & 15);
+        split_store(pan, pan + R * 128, off, v[c] * sinv[c]);
+      }
     };
-    float cmax[kHalf];
+    float cmax[kHalf], sg[kHalf], sinv[kHalf];
 #pragma unroll
-    for (int c = 0; c < kHalf; ++c) cmax[c] = 0.f;
+    for (int c = 0; c < kHalf; ++c) {
+      cmax[c] = 0.f;
+      sg[c] = sigf[c0 + c];
+      sinv[c] = 1.f / sg[c];
+    }
     bool ok = true;
     float rv[kHalf];
     load_rows(0, rv);
@@ -605,10 +654,10 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(accfull, (uint32_t)(g & 1)))) break;
       tc_fence_after();
       float t[kHalf];
-      tmem_pair((uint32_t)((g & 1) * 2 * R), t);
+      tmem_pair((uint32_t)((g & 1) * 2 * kSet), t);
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigf[c0 + c] * t[c];
-      put_operand(b2p, t, sigf);
+      for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sg[c] * t[c];
+      put_operand(b2p, t, sinv);
       fence_proxy_async_smem();
       tc_fence_before();
       simt_sync();
@@ -617,10 +666,10 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(yready, (uint32_t)(g & 1)))) break;
       tc_fence_after();
       float y[kHalf];
-      tmem_pair(4 * R, y);
+      tmem_pair(8 * R, y);
 #pragma unroll
       for (int c = 0; c < kHalf; ++c) {
-        y[c] *= sigf[c0 + c];
+        y[c] *= sg[c];
         cmax[c] = fmaxf(cmax[c], fabsf(y[c]));
       }
       const int row = g * kG + rq;
@@ -630,7 +679,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
         for (int c4 = 0; c4 < kHalf / 4; ++c4) dst[c4] = make_float4(y[4 * c4], y[4 * c4 + 1], y[4 * c4 + 2], y[4 * c4 + 3]);
       }
       // the window chunks 2 g, 2 g + 1 (the last group's y is read by no MMA)
-      if (g < ng - 1) put_operand(pA + LY::kWin + ((2 * g) % kNWC) * LY::kWinChunk, y, sigf);
+      if (g < ng - 1) put_operand(pA + LY::kWin + ((2 * g) % kNWC) * LY::kWinChunk, y, sinv);
       fence_proxy_async_smem();
       tc_fence_before();
       simt_sync();
@@ -657,6 +706,11 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
         sigb[st] = pow2_at_or_above(m);
       }
       simt_sync();
+#pragma unroll
+      for (int c = 0; c < kHalf; ++c) {
+        sg[c] = sigb[c0 + c];
+        sinv[c] = 1.f / sg[c];
+      }
     }
     // backward
     if (ok) load_rows(ng - 1, rv);
@@ -666,14 +720,14 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (g + 1 <= ng - 1) {
         if (!(ok = decide(baccready, (uint32_t)((k - 1) & 1)))) break;
         tc_fence_after();
-        tmem_pair(6 * R + (uint32_t)((g & 3) * 2 * R), t);
+        tmem_pair((uint32_t)((g % 3) * 2 * kSet), t);
 #pragma unroll
-        for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sigb[c0 + c] * t[c];
+        for (int c = 0; c < kHalf; ++c) t[c] = rv[c] - sg[c] * t[c];
       } else {
 #pragma unroll
         for (int c = 0; c < kHalf; ++c) t[c] = rv[c];
       }
-      put_operand(b2p, t, sigb);
+      put_operand(b2p, t, sinv);
       fence_proxy_async_smem();
       tc_fence_before();
       simt_sync();
@@ -684,9 +738,9 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       if (!(ok = decide(yready, (uint32_t)((ng + k) & 1)))) break;
       tc_fence_after();
       float x[kHalf];
-      tmem_pair(4 * R, x);
+      tmem_pair(12 * R, x);
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) x[c] *= sigb[c0 + c];
+      for (int c = 0; c < kHalf; ++c) x[c] *= sg[c];
       if (row < n) {
         float4* dst = reinterpret_cast<float4*>(xg + (size_t)row * R + c0);
 #pragma unroll
@@ -695,7 +749,7 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
       }
       // the MMAs of the previous group must be done with the x~ operand before it is rewritten
       if (k >= 1 && !(ok = decide(xfree, (uint32_t)((k - 1) & 1)))) break;
-      put_operand(pA + LY::kWin, x, sigb);
+      put_operand(pA + LY::kWin, x, sinv);
       fence_proxy_async_smem();
       tc_fence_before();
       simt_sync();
@@ -707,12 +761,22 @@ __global__ void __launch_bounds__(kWtThreads, 1) k_sweep_wide_tc(const SweepArgs
   const bool ok = mbar_wait_bounded(done, 0, kDrainPolls) && !flags[0];
   if (!ok && tid == 0) atomicExch(a.status, kStatusTimeout);
   if (ok) {
-    // w_out[e] = 2 x_c - w_in[e]
-    for (int i = tid; i < pd.nports * R; i += kWtThreads) {
-      const int qq = i / R, c = i % R;
-      const float x = xg[(size_t)a.port_local[pd.port_off + qq] * R + c];
-      for (int e = a.port_end_ptr[pd.port_off + qq]; e < a.port_end_ptr[pd.port_off + qq + 1]; ++e)
-        a.wnext[(size_t)e * R + c] = 2.f * x - a.wprev[(size_t)a.twin[e] * R + c];
+    // w_out[e] = 2 x_c - w_in[e], one port per thread, 16-byte rows
+    for (int q = tid; q < pd.nports; q += kWtThreads) {
+      const int port = pd.port_off + q;
+      const float4* xr = reinterpret_cast<const float4*>(xg + (size_t)a.port_local[port] * R);
+      float4 x[R / 4];
+#pragma unroll
+      for (int k4 = 0; k4 < R / 4; ++k4) x[k4] = xr[k4];
+      for (int e = a.port_end_ptr[port]; e < a.port_end_ptr[port + 1]; ++e) {
+        const float4* wi = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
+        float4* wo = reinterpret_cast<float4*>(a.wnext + (size_t)e * R);
+#pragma unroll
+        for (int k4 = 0; k4 < R / 4; ++k4) {
+          const float4 w = wi[k4];
+          wo[k4] = make_float4(2.f * x[k4].x - w.x, 2.f * x[k4].y - w.y, 2.f * x[k4].z - w.z, 2.f * x[k4].w - w.w);
+        }
+      }
     }
   }
   tc_fence_before();
