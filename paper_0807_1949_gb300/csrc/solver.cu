@@ -424,16 +424,20 @@ static void couple_setup(const vtm_partition* p, const vtm_setup_opts* o, vtm_so
       ent.push_back({eport[iu], twin[it], -y});
     }
   }
-  std::stable_sort(ent.begin(), ent.end(), [](const Ent& x, const Ent& y2) { return x.port < y2.port; });
+  // CSR by port, entries of a port in the order they were made (a counting sort: millions of pairs)
   const int nports = (int)port_end_ptr.size() - 1;
   std::vector<int32_t> ptr(nports + 1, 0), oth(ent.size());
   std::vector<T> yv(ent.size());
-  for (size_t k = 0; k < ent.size(); ++k) {
-    ptr[ent[k].port + 1]++;
-    oth[k] = ent[k].oth;
-    yv[k] = (T)ent[k].y;
-  }
+  for (const Ent& x : ent) ptr[x.port + 1]++;
   for (int q = 0; q < nports; ++q) ptr[q + 1] += ptr[q];
+  {
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (const Ent& x : ent) {
+      const int32_t at = fill[x.port]++;
+      oth[at] = x.oth;
+      yv[at] = (T)x.y;
+    }
+  }
   s->info.ncouplings = used;
   if (used == 0) {
     s->ydiag.clear();
