@@ -127,16 +127,24 @@ def _ow_main(conn, dims, block, sigma, nrhs, pieces, shm_names, shapes, coff):
     b = inputs.rhs_uniform(A.n, nrhs, seed=0)
     shm = {k: shared_memory.SharedMemory(name=n) for k, n in shm_names.items()}
     arr = {k: np.ndarray(shapes[k], dtype=np.float64, buffer=shm[k].buf) for k in shm}
+    import time as _time
+    spent = {j: 0.0 for j in pieces}  # seconds in each subgraph's step since the last report
     conn.send("ready")
     while True:
         msg = conn.recv()
         if msg is None:
             break
+        if msg == "times":
+            conn.send(dict(spent))
+            spent = {j: 0.0 for j in pieces}
+            continue
         cur = msg
         u, om = arr["u%d" % cur], arr["o%d" % cur]
         nu, no = arr["u%d" % (cur ^ 1)], arr["o%d" % (cur ^ 1)]
         for j in pieces:
+            t0 = _time.perf_counter()
             x = m.piece_step(j, u, om, b, nu, no)
+            spent[j] += _time.perf_counter() - t0
             arr["x"][:, coff[j]:coff[j + 1]] = x
         conn.send("done")
     for v in shm.values():
@@ -201,11 +209,18 @@ def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: 
         cur = 0
         sweep(cur)                                   # warm-up
         cur ^= 1
+        for cn in conns:                             # reset the per-subgraph clocks
+            cn.send("times")
+            cn.recv()
         t0 = time.perf_counter()
         for _ in range(sweeps):
             sweep(cur)
             cur ^= 1
         t_sweep = (time.perf_counter() - t0) / sweeps
+        spent = {}
+        for cn in conns:
+            cn.send("times")
+            spent.update(cn.recv())
         t0 = time.perf_counter()
         st = ovtm.State(u=arr["u%d" % cur], omega=arr["o%d" % cur],
                         x_local=[arr["x"][:, coff[j]:coff[j + 1]] for j in range(P)])
@@ -232,16 +247,51 @@ def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: 
             else:
                 os.environ[k] = v
     nbw = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(w["dims"], w["block"])]
+    nbs = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(dims, w["block"])]
     total = int(np.prod(nbw))
+    # The work of a subgraph grows with its ports, i.e. with the number of block faces it shares with
+    # neighbours; a small sample has more boundary subgraphs than the workload.  Scale the sample's
+    # time by the workload's work over the sample's, with the mean step time of each class measured
+    # in the sample (classes by neighbour count; a missing class from a linear fit in that count).
+    def faces(idx, nb):
+        return sum((i > 0) + (i < m - 1) for i, m in zip(idx, nb))
+
+    def class_counts(nb):
+        cnt = {}
+        for idx in np.ndindex(*nb):
+            k = faces(idx, nb)
+            cnt[k] = cnt.get(k, 0) + 1
+        return cnt
+
+    blk = np.array(w["block"])
+    per_class = {}
+    for j, g in enumerate(split.subgraphs):
+        coord = np.array(np.unravel_index(int(np.min(g.vertices)), dims))
+        idx = tuple(int(v) for v in np.minimum(coord // blk, np.array(nbs) - 1))
+        per_class.setdefault(faces(idx, nbs), []).append(spent.get(j, 0.0) / sweeps)
+    mean = {k: float(np.mean(v)) for k, v in per_class.items()}
+    ks = sorted(mean)
+    if len(ks) >= 2:
+        slope, icpt = np.polyfit(ks, [mean[k] for k in ks], 1)
+    else:
+        slope, icpt = 0.0, (mean[ks[0]] if ks else 1.0)
+
+    def cost(k):
+        return mean[k] if k in mean else max(icpt + slope * k, 1e-12)
+
+    work = lambda cnt: sum(c * cost(k) for k, c in cnt.items())
+    ratio = work(class_counts(nbw)) / max(work(class_counts(nbs)), 1e-30)
     return dict(t_sweep=t_sweep, t_check=t_check, sample_pieces=P, total_pieces=total, sample_dims=dims,
-                sweeps=sweeps, cores=cores, nrhs=R)
+                sweeps=sweeps, cores=cores, nrhs=R, work_ratio=ratio,
+                n_ratio=float(np.prod(w["dims"])) / float(np.prod(dims)))
 
 
 def oracle_time_to_tol(t: dict, sweeps_to_tol: int, check_every: int = 10) -> float:
     """Milliseconds the oracle needs for sweeps_to_tol sweeps with a check every check_every, scaled
-    from the sample to the workload's subgraphs."""
-    per = t["t_sweep"] + t["t_check"] / check_every
-    return per * sweeps_to_tol * t["total_pieces"] / t["sample_pieces"] * 1e3
+    from the sample to the workload: sweeps by the work ratio of the subgraph classes, checks
+    (assembly and residual, linear in the unknowns) by the ratio of unknowns."""
+    per = t["t_sweep"] * t["work_ratio"] + t["t_check"] * t["n_ratio"] / check_every
+    return per * sweeps_to_tol * 1e3
 
 
 def cpu_baseline(workload: str, sweeps_to_tol: int, count_source: str, sweeps: int = 4) -> dict:
@@ -251,13 +301,14 @@ def cpu_baseline(workload: str, sweeps_to_tol: int, count_source: str, sweeps: i
         return dict(value=None, unit="ms", cores=None, kind="oracle", error=str(e)[-300:])
     v = oracle_time_to_tol(t, sweeps_to_tol)
     return dict(value=round(v, 1), unit="ms", cores=t["cores"], kind="oracle",
-                per_sweep_ms=round((t["t_sweep"] + t["t_check"] / 10) * t["total_pieces"] / t["sample_pieces"] * 1e3, 1),
+                per_sweep_ms=round((t["t_sweep"] * t["work_ratio"] + t["t_check"] * t["n_ratio"] / 10) * 1e3, 1),
                 sample=(f"FP64 oracle (oracle.vtm, Table 1 step per subgraph) on {t['cores']} host cores: "
                         f"{t['sweeps']} sweeps and one residual check of a {list(t['sample_dims'])} grid = "
                         f"{t['sample_pieces']} subgraphs of the workload's block shape, {t['nrhs']} right-hand "
                         f"sides ({t['t_sweep']:.2f} s per sweep, {t['t_check']:.2f} s per check), scaled to "
-                        f"{t['total_pieces']} subgraphs and {sweeps_to_tol} sweeps ({count_source}), a check "
-                        f"every 10 sweeps; factorisation excluded"))
+                        f"{t['total_pieces']} subgraphs (by the measured step time of each class of subgraph: "
+                        f"work ratio {t['work_ratio']:.1f}) and {sweeps_to_tol} sweeps ({count_source}), a "
+                        f"check every 10 sweeps (scaled by the unknowns); factorisation excluded"))
 
 
 # ----------------------------------------------------------------------------- clocks

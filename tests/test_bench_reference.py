@@ -36,8 +36,8 @@ def test_reference_arm_prints_contract_line():
 def test_sample_extrapolation_matches_a_whole_oracle_solve():
     """A 3D grid of 4 x 4 x 4 subgraphs of 9^3 (33^3, sigma = 1): the whole FP64 oracle solve to 1e-8
     (oracle.vtm.solve, one core, residual every 10 sweeps) against the bench's estimate from a
-    2 x 2 x 2 sample of the same block shape (a few sweeps and one check, one core), scaled to the
-    solve's subgraphs and sweeps.  The two agree within 20 %."""
+    3 x 3 x 3 sample of the same block shape (a few sweeps and one check, one core), scaled to the
+    solve's subgraphs (by class of subgraph) and sweeps.  The two agree within 20 %."""
     threadpoolctl = pytest.importorskip("threadpoolctl")
     sys.path.insert(0, ROOT)
     import bench
@@ -63,7 +63,7 @@ def test_sample_extrapolation_matches_a_whole_oracle_solve():
                 if k % 10 == 0 and ovtm.relative_residual(A, b, m.assemble(st))[0] <= 1e-8:
                     break
             whole = time.perf_counter() - t0
-        est = bench.oracle_time_to_tol(bench.oracle_timing(name, sweeps=6, cores=1, nb=2), k) / 1e3
+        est = bench.oracle_time_to_tol(bench.oracle_timing(name, sweeps=6, cores=1, nb=3), k) / 1e3
     finally:
         del bench.WORKLOADS[name]
     assert 0.8 <= est / whole <= 1.25, (est, whole, k)
