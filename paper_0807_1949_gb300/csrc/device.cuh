@@ -69,6 +69,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// Adds `bytes` to the transaction count of the current phase without arriving: a phase fed by
+// several copies issued at different times completes once the one arrival has come and all of
+// their bytes have landed.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
 // 1D bulk copy global -> shared (TMA engine), completion counted on `bar` in bytes.
 // dst, src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -106,6 +113,7 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait on an mbarrier phase: gives up after `limit` polls (each poll may suspend the
 // thread for a hardware-defined slice), returning false so that the caller can record a timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long limit) {
+  if (mbar_test_wait(bar, parity)) return true;  // already complete: no suspend
   for (long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;

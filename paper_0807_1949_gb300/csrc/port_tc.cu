@@ -25,16 +25,19 @@
 // fp16 roundings); without it (FP16 storage, half the bytes) S carries fp16 rounding, 2^-11 of
 // sigma_j, and the FP64 defect correction absorbs it as for the FP16 tiles of port.cu.
 //
-// One persistent kernel per sweep, one CTA per SM looping over subgraphs, 320 threads:
-//  * warp 0 streams blocks (and the s_J tile of off-diagonal blocks) through a ring of bulk copies
-//    (mbarrier complete_tx), and the s_I tile of each super-row into a 2-slot row buffer;
+// One persistent kernel per sweep, one CTA per SM looping over subgraphs, 448 threads:
+//  * warp 0 streams the blocks (and the s_J tile of off-diagonal blocks) through a ring of 16 KB
+//    shared-memory slots by bulk copies (mbarrier complete_tx).  A block's panels go out one pair
+//    at a time, each as soon as its slots are free, so that the next blocks stream in while the
+//    current one is multiplied; the s_I tile of each super-row goes into a 2-slot row buffer;
 //  * warp 1 issues the MMAs: y_I at tensor-memory columns I R .. I R + R - 1, lane = port, all
-//    super-rows of a subgraph held at once (n4 R <= 512 columns); tcgen05.commit releases stages,
-//    row buffers and, after the last block, hands the accumulators to the epilogue;
-//  * warps 2-9 compute the next subgraph's s (two passes over the incoming waves: the column
-//    maxima, then the split values written to a per-CTA global scratch slot that stays in L2), then
-//    run the epilogue of the current one: tcgen05.ld of the accumulators, u = u_base +
-//    sigma_j sigma_r y, w_out[e] = 2u - w_in[e].
+//    super-rows of a subgraph held at once (n4 R <= 512 columns); tcgen05.commit releases stages
+//    and row buffers and hands each finished y_I to the epilogue;
+//  * warps 2-5 run the epilogue of the current subgraph: tcgen05.ld of each y_I (released at once
+//    for the next subgraph's MMAs), u = u_base + sigma_j sigma_r y, w_out[e] = 2u - w_in[e];
+//  * warps 6-13 compute the next subgraph's s (one gather pass: FP32 values to a staging area and
+//    the column maxima, then the split values written to a per-CTA global scratch slot that stays
+//    in L2).
 // Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its copies and MMAs
 // finish, frees its tensor memory and returns.
 #include <cuda_fp16.h>
@@ -76,52 +79,101 @@ __device__ __forceinline__ void epi_sync() {
   asm volatile("bar.sync %0, %1;" ::"n"(kEpiBar), "n"(32 * kEpiWarps) : "memory");
 }
 
-// Ring geometry of one variant: bytes of a stage's S block and s tile, stage count.
-template <int R, bool LO>
-struct Ring {
-  static constexpr uint32_t kBlk = kSB * (LO ? 512u : 256u);  // largest S block moved per stage
-  static constexpr uint32_t kVec = (uint32_t)R * 512u;        // s tile: hi / lo x 2 panels of R rows
-  static constexpr uint32_t kStage = kBlk + kVec;
-  static constexpr int kStages = LO ? 2 : 3;
-  static constexpr uint32_t kBytes = 1024 + 1024 + kStages * kStage + 2 * kVec;
+// Header offsets (bytes from the aligned start).
+constexpr uint32_t kOffFull = 0, kOffEmpty = 64, kOffRowFull = 128, kOffRowEmpty = 144, kOffSReady = 160,
+                   kOffSlotFree = 176, kOffRReady = 192, kOffRowRead = 320, kOffDone = 448, kOffTslot = 456,
+                   kOffFlags = 464, kOffSsig = 512, kOffOwner = 768, kOffRed = 1024;
+static_assert(kOffRReady + 8 * kMaxSuper <= kOffRowRead && kOffRowRead + 8 * kMaxSuper <= kOffDone, "header");
+
+// Shared-memory plan.  The kernel has no static shared memory: up to 1008 bytes to align the start
+// to 1024, a 2 KB header (mbarriers, flags, the column scales sigma_r, the copy warp's slot owners,
+// the vector warps' reduction scratch), a ring of 10 slots of 16 KB that carries the S panels and
+// s_J tiles, then two s_I row tiles.  Ten slots hold two stages of an off-diagonal block with its
+// lo half (four panels and the s_J tile) at once; every further slot is taken from the L1 cache that
+// the gathers of the vector and epilogue warps hit in, which costs more than the extra bytes in
+// flight gain (measured: 9, 10, 11, 12 slots run one sweep in 1.12, 1, 1.08, 1.10 times the time).
+template <int R>
+struct Plan {
+  static constexpr uint32_t kSlot = 16384;              // one panel of a full-height block
+  static constexpr uint32_t kVec = (uint32_t)R * 512u;  // s tile: hi / lo x 2 panels of R rows
+  static constexpr uint32_t kHead = 2048;
+  static constexpr int kSlots = 10;
+  static constexpr uint32_t kRow = kHead + kSlots * kSlot;  // the two row tiles, from the aligned start
+  static constexpr uint32_t kAlloc = 1008 + kRow + 2 * kVec;
+  static_assert(kAlloc <= 227 * 1024, "shared-memory plan");
+  static_assert(kOffSsig + 8 * R <= kOffOwner && kOffOwner + 4 * kSlots <= kOffRed, "header");
 };
+constexpr int kStg = 8;  // stage barriers (full / empty) in use round robin
+
+// Ring slots of one block (stage).  The hi panels (and, with the lo half, the lo panels) take two
+// adjacent slots each: the transposed product reads a pair as one MN-major operand whose halves are
+// one slot apart, so a pair never wraps around the end of the ring.  The s_J tile of an off-diagonal
+// block takes one slot, the ring's last one when a pair would otherwise start there (else that slot
+// is skipped).  Copy warp and MMA issuer place the same sequence of blocks and so agree on every
+// position; `a` counts slots from the start of the launch.
+struct StagePos {
+  int hi, lo, s;
+};
+template <int NS>
+__device__ __forceinline__ StagePos place_stage(int64_t& a, bool lo, bool has_s) {
+  StagePos p{-1, -1, -1};
+  bool s_open = has_s;
+  auto pair = [&]() {
+    if ((int)(a % NS) == NS - 1) {
+      if (s_open) {
+        p.s = NS - 1;
+        s_open = false;
+      }
+      ++a;
+    }
+    const int r = (int)(a % NS);
+    a += 2;
+    return r;
+  };
+  p.hi = pair();
+  if (lo) p.lo = pair();
+  if (s_open) {
+    p.s = (int)(a % NS);
+    ++a;
+  }
+  return p;
+}
 
 // The MMAs of one block (I, J) of height h: y_I += S_IJ s_J (A K-major: the block's two panels
 // along K; B = the s tile bv) and, off the diagonal, y_J += S_IJ^T s_I (A MN-major: M over the two
-// panels at LBO = one panel, K = the block's rows in steps of 16; B = the row tile si).  Products
-// per K step: hi(S) s_hi, hi(S) s_lo and, with LO, lo(S) s_hi.  first / first_t: the product
-// overwrites y_I / y_J instead of adding.  Descriptors are formed once and advanced by address
-// offsets (16-byte units in the low bits); with kFull the panel stride is the compile-time 16 KB
-// of a full-height block and every loop unrolls.
-template <int R, bool LO, bool kFull>
-__device__ __forceinline__ void block_mmas(uint32_t sb, uint32_t bv, uint32_t si, int h, uint32_t dI, uint32_t dJ,
-                                           bool first, bool first_t, bool transposed) {
+// panels of a pair, one ring slot apart; K = the block's rows in steps of 16; B = the row tile si).
+// Products per K step: hi(S) s_hi, hi(S) s_lo and, with LO, lo(S) s_hi.  first / first_t: the
+// product overwrites y_I / y_J instead of adding.  Descriptors are formed once and advanced by
+// address offsets (16-byte units in the low bits).
+template <int R, bool LO>
+__device__ __forceinline__ void block_mmas(uint32_t hiA, uint32_t loA, uint32_t bv, uint32_t si, int h, uint32_t dI,
+                                           uint32_t dJ, bool first, bool first_t, bool transposed) {
   constexpr uint32_t idK = idesc_f16(false, R), idT = idesc_f16(true, R);
-  constexpr uint32_t vpan = (uint32_t)R * 128 / 16;           // s tile panel, 16-byte units
-  const uint32_t panel = kFull ? (uint32_t)kSB * 128 : (uint32_t)h * 128;
-  const uint32_t pan = panel / 16;
-  const uint64_t aK = sdesc(sb, 16, 1024), aT = sdesc(sb, panel, 1024);
+  constexpr uint32_t vpan = (uint32_t)R * 128 / 16;  // s tile panel, 16-byte units
+  constexpr uint32_t pan = Plan<R>::kSlot / 16;      // ring slot, 16-byte units
+  const uint64_t aK = sdesc(hiA, 16, 1024), aKl = sdesc(loA, 16, 1024);
   const uint64_t bB = sdesc(bv, 16, 1024), bR = sdesc(si, 16, 1024);
 #pragma unroll
   for (int kk = 0; kk < kSB / 16; ++kk) {
-    const uint32_t p = kk >> 2, o = (kk & 3) * 2;               // panel, 32-byte step in 16-byte units
+    const uint32_t p = kk >> 2, o = (kk & 3) * 2;  // panel, 32-byte step in 16-byte units
     const uint64_t aH = aK + p * pan + o, bH = bB + p * vpan + o, bL = bB + (2 + p) * vpan + o;
     if (kk == 0) mma_f16(dI, aH, bH, idK, first ? 0u : 1u);
     else mma_f16_acc(dI, aH, bH, idK);
     mma_f16_acc(dI, aH, bL, idK);
-    if constexpr (LO) mma_f16_acc(dI, aK + (2 + p) * pan + o, bH, idK);
+    if constexpr (LO) mma_f16_acc(dI, aKl + p * pan + o, bH, idK);
   }
   if (!transposed) return;
-  const int nk = kFull ? kSB / 16 : h / 16;
+  const uint64_t aT = sdesc(hiA, Plan<R>::kSlot, 1024), aTl = sdesc(loA, Plan<R>::kSlot, 1024);
+  const int nk = h / 16;
 #pragma unroll
   for (int kk = 0; kk < kSB / 16; ++kk) {
-    if (!kFull && kk >= nk) break;
+    if (kk >= nk) break;
     const uint32_t p = kk >> 2, o = (kk & 3) * 2;
     const uint64_t aH = aT + kk * 128, bH = bR + p * vpan + o, bL = bR + (2 + p) * vpan + o;  // 2048 B per kk
     if (kk == 0) mma_f16(dJ, aH, bH, idT, first_t ? 0u : 1u);
     else mma_f16_acc(dJ, aH, bH, idT);
     mma_f16_acc(dJ, aH, bL, idT);
-    if constexpr (LO) mma_f16_acc(dJ, aT + 2 * pan + kk * 128, bH, idT);
+    if constexpr (LO) mma_f16_acc(dJ, aTl + kk * 128, bH, idT);
   }
 }
 
@@ -172,10 +224,7 @@ int64_t port_f32_blocks(int nports) {
   return n4 * (n4 + 1) / 2;
 }
 
-size_t port_tc_smem_bytes(int R, bool lo) {
-  if (R == 16) return lo ? Ring<16, true>::kBytes : Ring<16, false>::kBytes;
-  return lo ? Ring<32, true>::kBytes : Ring<32, false>::kBytes;
-}
+size_t port_tc_smem_bytes(int R, bool) { return R == 16 ? Plan<16>::kAlloc : Plan<32>::kAlloc; }
 
 // S_j columns cc = b * Rs + r from unit-source solves into FP32 128 x 128 row-major blocks of the
 // lower block triangle (block (I, J) at s_off + I (I + 1) / 2 + J; diagonal blocks whole).
@@ -264,38 +313,37 @@ __global__ void k_port_blocks_to_f16(const PieceDesc* __restrict__ pieces, const
 
 template <int R, bool LO>
 __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArgs a) {
-  using G = Ring<R, LO>;
-  constexpr int S = G::kStages;
+  using P = Plan<R>;
+  constexpr int NS = P::kSlots;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ volatile int abort_flag;
-  __shared__ volatile int vstop, vstop_v;
-  __shared__ float red[kVecWarps][R];
-  __shared__ float ssig[2][R];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm);  // [S] block (+ s_J tile) landed
-  uint64_t* empty = full + S;                        // [S] MMAs done with the stage
-  uint64_t* rowfull = empty + S;                     // [2] s_I tile landed
-  uint64_t* rowempty = rowfull + 2;                  // [2] MMAs done with the s_I tile
-  uint64_t* sready = rowempty + 2;                   // [2] scratch slot written
-  uint64_t* rready = sready + 2;                     // [kMaxSuper] accumulator y_I complete
-  uint64_t* accempty = rready + kMaxSuper;           // every accumulator read by the epilogue
-  uint64_t* slotfree = accempty + 1;                 // [2] epilogue of the slot's last subgraph done
-  uint64_t* done = slotfree + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
-  const uint32_t stage0 = base + 1024;
-  const uint32_t row0 = stage0 + S * G::kStage;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kOffFull);          // [kStg] stage landed
+  uint64_t* empty = reinterpret_cast<uint64_t*>(sm + kOffEmpty);        // [kStg] MMAs done with the stage
+  uint64_t* rowfull = reinterpret_cast<uint64_t*>(sm + kOffRowFull);    // [2] s_I tile landed
+  uint64_t* rowempty = reinterpret_cast<uint64_t*>(sm + kOffRowEmpty);  // [2] MMAs done with the s_I tile
+  uint64_t* sready = reinterpret_cast<uint64_t*>(sm + kOffSReady);      // [2] scratch slot written
+  uint64_t* slotfree = reinterpret_cast<uint64_t*>(sm + kOffSlotFree);  // [2] epilogue of the slot's last subgraph done
+  uint64_t* rready = reinterpret_cast<uint64_t*>(sm + kOffRReady);      // [kMaxSuper] accumulator y_I complete
+  uint64_t* rowread = reinterpret_cast<uint64_t*>(sm + kOffRowRead);    // [kMaxSuper] y_I read by the epilogue
+  uint64_t* done = reinterpret_cast<uint64_t*>(sm + kOffDone);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffTslot);
+  volatile int* flags = reinterpret_cast<volatile int*>(sm + kOffFlags);  // abort, epilogue stop, vector stop
+  float (*ssig)[R] = reinterpret_cast<float (*)[R]>(sm + kOffSsig);        // [2][R] sigma_r per scratch slot
+  float (*red)[R] = reinterpret_cast<float (*)[R]>(sm + kOffRed);          // [kVecWarps][R]
+  const uint32_t ring = base + P::kHead;
+  const uint32_t row0 = base + P::kRow;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int npc = (a.npieces - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // subgraphs of this CTA
-  const size_t slot_bytes = (size_t)a.n4max * G::kVec;
+  const size_t slot_bytes = (size_t)a.n4max * P::kVec;
   unsigned char* scratch = a.scratch + (size_t)blockIdx.x * (2 * slot_bytes + (size_t)a.n4max * kSB * R * 4);
   float* stage32 = reinterpret_cast<float*>(scratch + 2 * slot_bytes);  // FP32 port vectors, ports x R
 
   if (tid == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < S; ++s) {
+    flags[0] = flags[1] = flags[2] = 0;
+    for (int s = 0; s < kStg; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -305,8 +353,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       mbar_init(&sready[s], 1);
       mbar_init(&slotfree[s], 1);
     }
-    for (int s = 0; s < kMaxSuper; ++s) mbar_init(&rready[s], 1);
-    mbar_init(accempty, 1);
+    for (int s = 0; s < kMaxSuper; ++s) {
+      mbar_init(&rready[s], 1);
+      mbar_init(&rowread[s], kEpiWarps);
+    }
     mbar_init(done, 1);
     fence_mbar_init();
   }
@@ -320,17 +370,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  volatile int& abort_flag = flags[0];
 
   if (warp == 0) {
-    // ---- producer: super-rows in descending order; per row the s_I tile, per block (I, J),
-    // J = 0 .. I, the block and the s_J tile.  The blocks are read once per sweep: evict first.
+    // ---- copies: super-rows in descending order; per row the s_I tile, per block (I, J),
+    // J = I .. 0, its panels and (off the diagonal) the s_J tile.  Each piece goes out as soon as
+    // its slots are free (the MMAs of the stage that last filled them are complete), so the next
+    // blocks stream in while the current one is multiplied; the stage's full barrier counts the
+    // bytes of every piece and completes after the last piece has been issued and has landed.
+    // The blocks are read once per sweep: evict first.
     if (lane == 0) {
       uint64_t policy;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
-      int64_t gblk = 0, grow = 0;
+      // stage that last filled each slot, in shared memory: a local array would sit in a cache that
+      // the ring leaves small, and this one thread issues every copy
+      int* owner = reinterpret_cast<int*>(sm + kOffOwner);
+      for (int i = 0; i < NS; ++i) owner[i] = -1;
+      int gblk = 0, rel = -1;  // rel: stages 0 .. rel known released
+      int64_t grow = 0, aslot = 0;
+      auto release_upto = [&](int j) -> bool {
+        while (rel < j) {
+          ++rel;
+          if (!mbar_wait_bounded(&empty[rel % kStg], (uint32_t)((rel / kStg) & 1), a.wait_limit)) return false;
+        }
+        return true;
+      };
       for (int k = 0; k < npc && !abort_flag; ++k) {
         const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
-        const int P = pd.nports, n4 = n_super(P);
+        const int Pn = pd.nports, n4 = n_super(Pn);
         if (!mbar_wait_bounded(&sready[k & 1], (uint32_t)((k >> 1) & 1), a.wait_limit)) {
           abort_flag = 1;
           break;
@@ -343,67 +410,100 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
             abort_flag = 1;
             break;
           }
-          mbar_arrive_expect_tx(&rowfull[rb], G::kVec);
-          bulk_g2s(row0 + rb * G::kVec, slot + (size_t)I * G::kVec, G::kVec, &rowfull[rb]);
+          mbar_arrive_expect_tx(&rowfull[rb], P::kVec);
+          bulk_g2s(row0 + rb * P::kVec, slot + (size_t)I * P::kVec, P::kVec, &rowfull[rb]);
           ++grow;
-          const int h = sb_rows(P, I);
-          const uint32_t sbytes = (uint32_t)h * (LO ? 512u : 256u);
-          for (int J = 0; J <= I; ++J) {
-            const int st = (int)(gblk % S);
-            if (gblk >= S && !mbar_wait_bounded(&empty[st], (uint32_t)(((gblk / S) - 1) & 1), a.wait_limit)) {
+          const int h = sb_rows(Pn, I);
+          const uint32_t pbytes = (uint32_t)h * 128;  // one panel
+          for (int J = I; J >= 0; --J) {
+            const int st = (int)(gblk % kStg);
+            // full[st] and empty[st] were last used by stage gblk - kStg
+            bool ok = release_upto(gblk - kStg);
+            const StagePos ps = place_stage<NS>(aslot, LO, J < I);
+            const unsigned char* blk = Sp + blk_off(Pn, I, J);
+            // one pair: two panels of the block into two adjacent slots
+            auto pair = [&](int s0, const unsigned char* src) {
+              ok = ok && release_upto(owner[s0] > owner[s0 + 1] ? owner[s0] : owner[s0 + 1]);
+              if (!ok) return;
+              owner[s0] = owner[s0 + 1] = gblk;
+              const uint32_t dst = ring + (uint32_t)s0 * P::kSlot;
+              mbar_expect_tx(&full[st], 2 * pbytes);
+              if (h == kSB) {
+                bulk_g2s_hint(dst, src, 2 * pbytes, &full[st], policy);
+              } else {
+                bulk_g2s_hint(dst, src, pbytes, &full[st], policy);
+                bulk_g2s_hint(dst + P::kSlot, src + pbytes, pbytes, &full[st], policy);
+              }
+            };
+            pair(ps.hi, blk);
+            if (LO) pair(ps.lo, blk + 2 * pbytes);
+            if (ps.s >= 0) {
+              ok = ok && release_upto(owner[ps.s]);
+              if (ok) {
+                owner[ps.s] = gblk;
+                mbar_expect_tx(&full[st], P::kVec);
+                bulk_g2s(ring + (uint32_t)ps.s * P::kSlot, slot + (size_t)J * P::kVec, P::kVec, &full[st]);
+              }
+            }
+            mbar_arrive(&full[st]);  // completes once what was issued has landed
+            ++gblk;
+            if (!ok) {
               abort_flag = 1;
               break;
             }
-            const uint32_t sb = stage0 + st * G::kStage;
-            mbar_arrive_expect_tx(&full[st], sbytes + (J < I ? G::kVec : 0u));
-            bulk_g2s_hint(sb, Sp + blk_off(P, I, J), sbytes, &full[st], policy);
-            if (J < I) bulk_g2s(sb + G::kBlk, slot + (size_t)J * G::kVec, G::kVec, &full[st]);
-            ++gblk;
           }
         }
       }
       // copies still in flight must land before the shared memory can go away
-      for (int64_t g = (gblk > S ? gblk - S : 0); g < gblk; ++g)
-        mbar_wait_bounded(&full[g % S], (uint32_t)((g / S) & 1), kDrainPolls);
+      for (int g = (gblk > kStg ? gblk - kStg : 0); g < gblk; ++g)
+        mbar_wait_bounded(&full[g % kStg], (uint32_t)((g / kStg) & 1), kDrainPolls);
       for (int64_t g = (grow > 2 ? grow - 2 : 0); g < grow; ++g)
         mbar_wait_bounded(&rowfull[g & 1], (uint32_t)((g >> 1) & 1), kDrainPolls);
     }
   } else if (warp == 1) {
     // ---- MMA issuer.  In descending row order y_I is complete once row I is done (the rows
     // below only add to y_J, J < I), so its epilogue runs while the MMAs go on.  The first row
-    // processed (n4 - 1) initialises every accumulator: y_{n4-1} through its direct product with
-    // J = 0, every other y_J through the transposed product of block (n4 - 1, J).
+    // processed (n4 - 1) initialises every accumulator: y_{n4-1} through the direct product of the
+    // diagonal block, every other y_J through the transposed product of block (n4 - 1, J).  Before
+    // it overwrites y_J it waits until the epilogue has read y_J of the subgraph before (rowread);
+    // that subgraph's epilogue reads its rows in the same descending order, so the MMAs of the
+    // next subgraph start while the last rows of this one are still being written out.
     if (lane == 0) {
-      int64_t gblk = 0, grow = 0;
+      int64_t gblk = 0, grow = 0, aslot = 0;
+      uint32_t pend = 0, wpar = 0;  // rows handed to the epilogue and not yet waited for; parity of the next wait
       for (int k = 0; k < npc && !abort_flag; ++k) {
         const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
-        const int P = pd.nports, n4 = n_super(P);
-        if (k > 0 && !mbar_wait_bounded(accempty, (uint32_t)((k - 1) & 1), a.wait_limit)) {
-          abort_flag = 1;
-          break;
-        }
-        tc_fence_after();
+        const int Pn = pd.nports, n4 = n_super(Pn);
         for (int I = n4 - 1; I >= 0 && !abort_flag; --I) {
           const int rb = (int)(grow & 1);
           if (!mbar_wait_bounded(&rowfull[rb], (uint32_t)((grow >> 1) & 1), a.wait_limit)) {
             abort_flag = 1;
             break;
           }
-          const uint32_t si = row0 + rb * G::kVec;
-          const int h = sb_rows(P, I);
-          for (int J = 0; J <= I; ++J) {
-            const int st = (int)(gblk % S);
-            if (!mbar_wait_bounded(&full[st], (uint32_t)((gblk / S) & 1), a.wait_limit)) {
+          const uint32_t si = row0 + rb * P::kVec;
+          const int h = sb_rows(Pn, I);
+          const bool top = (I == n4 - 1);
+          for (int J = I; J >= 0; --J) {
+            const int st = (int)(gblk % kStg);
+            const StagePos ps = place_stage<NS>(aslot, LO, J < I);
+            if (top && ((pend >> J) & 1u)) {  // first write into y_J (y_I on the diagonal) this subgraph
+              if (!mbar_wait_bounded(&rowread[J], (wpar >> J) & 1u, a.wait_limit)) {
+                abort_flag = 1;
+                break;
+              }
+              wpar ^= 1u << J;
+              pend &= ~(1u << J);
+            }
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((gblk / kStg) & 1), a.wait_limit)) {
               abort_flag = 1;
               break;
             }
             tc_fence_after();
-            const uint32_t sb = stage0 + st * G::kStage;
-            const uint32_t bv = (J == I) ? si : sb + G::kBlk;
+            const uint32_t hiA = ring + (uint32_t)ps.hi * P::kSlot;
+            const uint32_t loA = LO ? ring + (uint32_t)ps.lo * P::kSlot : hiA;
+            const uint32_t bv = (J == I) ? si : ring + (uint32_t)ps.s * P::kSlot;
             const uint32_t dI = tmem + (uint32_t)(I * R), dJ = tmem + (uint32_t)(J * R);
-            const bool top = (I == n4 - 1);
-            if (h == kSB) block_mmas<R, LO, true>(sb, bv, si, h, dI, dJ, top && J == 0, top, J < I);
-            else block_mmas<R, LO, false>(sb, bv, si, h, dI, dJ, top && J == 0, top, J < I);
+            block_mmas<R, LO>(hiA, loA, bv, si, h, dI, dJ, top && J == I, top, J < I);
             mma_commit(&empty[st]);
             ++gblk;
           }
@@ -411,6 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
           mma_commit(&rready[I]);  // y_I is final
           ++grow;
         }
+        pend |= (n4 >= 32 ? ~0u : (1u << n4) - 1u);
       }
       mma_commit(done);  // arrives once every MMA issued above has completed
     }
@@ -418,33 +519,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     // ---- epilogue warps (one per tensor-memory lane quadrant): u = u_base + sigma_j sigma_r y_I,
     // w_out[e] = 2 u - w_in[e], super-row by super-row as the MMA issuer completes them
     // (rready[I] completes once per subgraph that has a super-row I, so its phases are counted per
-    // barrier; sready[k & 1] also orders the sigma_r written with subgraph k's port vectors)
+    // barrier; sready[k & 1] also orders the sigma_r written with subgraph k's port vectors).
+    // Each warp releases y_I (rowread[I]) as soon as its tcgen05.ld has completed.
     const int q = warp & 3;
     uint32_t uses = 0;  // tid 64: parity of the next phase of each row barrier, one bit per super-row
     bool stop = false;
     for (int k = 0; k < npc && !stop; ++k) {
       const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
-      const int P = pd.nports, n4 = n_super(P);
+      const int Pn = pd.nports, n4 = n_super(Pn);
       const float sj = a.sig_s[blockIdx.x + (size_t)k * gridDim.x];
-      if (tid == 64) vstop = mbar_wait_bounded(&sready[k & 1], (uint32_t)((k >> 1) & 1), a.wait_limit) ? 0 : 1;
+      if (tid == 64) flags[1] = mbar_wait_bounded(&sready[k & 1], (uint32_t)((k >> 1) & 1), a.wait_limit) ? 0 : 1;
       epi_sync();
-      stop = vstop != 0;
+      stop = flags[1] != 0;
       epi_sync();
       for (int I = n4 - 1; I >= 0 && !stop; --I) {
         // the four warps decide together: one lane waits, the named barrier publishes the outcome
         if (tid == 64) {
-          vstop = mbar_wait_bounded(&rready[I], (uses >> I) & 1u, a.wait_limit) ? 0 : 1;
+          flags[1] = mbar_wait_bounded(&rready[I], (uses >> I) & 1u, a.wait_limit) ? 0 : 1;
           uses ^= 1u << I;
         }
         epi_sync();
-        stop = vstop != 0;
+        stop = flags[1] != 0;
         epi_sync();
         if (stop) break;
         tc_fence_after();
         uint32_t v[R];
         tmem_ld<R>(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(I * R), v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowread[I]);
         const int p = I * kSB + 32 * q + lane;
-        if (p < P) {
+        if (p < Pn) {
           const int port = pd.port_off + p;
           const float4* ub = reinterpret_cast<const float4*>(a.ubase + (size_t)port * R);
           const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
@@ -478,12 +583,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         if (tid == 64) abort_flag = 1;
         break;
       }
-      tc_fence_before();
       epi_sync();
-      if (tid == 64) {
-        mbar_arrive(accempty);
-        mbar_arrive(&slotfree[k & 1]);
-      }
+      if (tid == 64) mbar_arrive(&slotfree[k & 1]);
     }
   } else {
     // ---- vector warps: the port vectors s of subgraph k, one gather pass (FP32 values to a
@@ -494,9 +595,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     const int vw = vt >> 5;
     for (int k = 0; k < npc; ++k) {
       if (k >= 2) {
-        if (vt == 0) vstop_v = mbar_wait_bounded(&slotfree[k & 1], (uint32_t)(((k >> 1) - 1) & 1), a.wait_limit) ? 0 : 1;
+        if (vt == 0) flags[2] = mbar_wait_bounded(&slotfree[k & 1], (uint32_t)(((k >> 1) - 1) & 1), a.wait_limit) ? 0 : 1;
         vec_sync();
-        const bool stop = vstop_v != 0;
+        const bool stop = flags[2] != 0;
         vec_sync();
         if (stop) {
           if (vt == 0) abort_flag = 1;
@@ -504,11 +605,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         }
       }
       const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
-      const int P = pd.nports, np = n_super(P) * kSB;
+      const int Pn = pd.nports, np = n_super(Pn) * kSB;
       float mx[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) mx[r] = 0.f;
-      for (int p = vt; p < P; p += kVecThreads) {
+      for (int p = vt; p < Pn; p += kVecThreads) {
         float v[R];
         port_vector<R>(a, pd.port_off + p, v);
         const float gp = a.gscale[pd.port_off + p];  // s' = D^-1 s, D = diag(1 / g)
@@ -542,13 +643,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       vec_sync();
       unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
       for (int p = vt; p < np; p += kVecThreads) {
-        unsigned char* tile = slot + (size_t)(p / kSB) * G::kVec;
+        unsigned char* tile = slot + (size_t)(p / kSB) * P::kVec;
         const int c = p % kSB;
         const uint32_t pn = (uint32_t)(c / 64) * R * 128;
         const float4* src = reinterpret_cast<const float4*>(stage32 + (size_t)p * R);
 #pragma unroll
         for (int k4 = 0; k4 < R / 4; ++k4) {
-          const float4 x4 = (p < P) ? src[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 x4 = (p < Pn) ? src[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
           const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
