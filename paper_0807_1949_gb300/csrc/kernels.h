@@ -134,6 +134,8 @@ struct PortTCArgs {
   const int32_t* twin;
   const float* invz;
   CoupleRef<float> cpl;        // coupled lines (cpl.ptr == nullptr: none)
+  const int4* prec;            // per port 3 x int4: first four entries' wave rows, their coefficients
+                               // (float bits), {next end, e1, next coupling, k1} (launch_port_records)
   int* status;
   long wait_limit;
 };
@@ -142,6 +144,9 @@ constexpr int kTcMaxSuper = 16;       // 128-port super-rows per subgraph on the
 int64_t port_f16_bytes(int nports);   // fp16 hi / lo blocks of one subgraph (1 KB multiple)
 int64_t port_f32_blocks(int nports);  // 128 x 128 FP32 blocks of the lower triangle (setup)
 size_t port_tc_smem_bytes(int R, bool lo);
+// Per-port gather records of the tensor-core port sweep (3 int4 per port, nports of them).
+cudaError_t launch_port_records(int nports, const int32_t* port_end_ptr, const int32_t* twin, const float* invz,
+                                CoupleRef<float> cpl, int4* rec, cudaStream_t st);
 cudaError_t port_tc_configure(int R);
 // One persistent launch per sweep (grid <= SMs); lo = use the lo half of S_j (FP32-accurate).
 cudaError_t launch_port_sweep_tc(const PortTCArgs& a, int R, bool lo, int grid, cudaStream_t st);

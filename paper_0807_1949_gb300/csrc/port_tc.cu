@@ -178,36 +178,62 @@ __device__ __forceinline__ void block_mmas(uint32_t hiA, uint32_t loA, uint32_t 
 }
 
 // s_p for one port and all R columns: sum over its ends of w_in / Z_e plus the coupling currents.
+// The loads wait on a busy HBM, so they come in few dependent steps: the port's gather record
+// (loaded one port ahead by the caller) gives the wave rows and coefficients of its first four
+// entries, whose rows are read two at a time; entries past the fourth (rare) follow the per-port
+// lists.  The additions keep the order ends-then-coupling.
 template <int R>
-__device__ __forceinline__ void port_vector(const PortTCArgs& a, int port, float (&v)[R]) {
+__device__ __forceinline__ void port_vector(const PortTCArgs& a, const int4 (&rec)[3], float (&v)[R]) {
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = 0.f;
-  const int e0 = a.port_end_ptr[port], e1 = a.port_end_ptr[port + 1];
-  for (int e = e0; e < e1; ++e) {
+  const int row[4] = {rec[0].x, rec[0].y, rec[0].z, rec[0].w};
+  const float c[4] = {__int_as_float(rec[1].x), __int_as_float(rec[1].y), __int_as_float(rec[1].z),
+                      __int_as_float(rec[1].w)};
+#pragma unroll
+  for (int j = 0; j < 4; j += 2) {
+    if (row[j] < 0) break;  // entries are packed, absent ones at the end
+    const bool two = row[j + 1] >= 0;
+    const float4* w0 = reinterpret_cast<const float4*>(a.wprev + (size_t)row[j] * R);
+    const float4* w1 = reinterpret_cast<const float4*>(a.wprev + (size_t)(two ? row[j + 1] : row[j]) * R);
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      const float4 x = w0[q], y = w1[q];
+      v[4 * q] += x.x * c[j];
+      v[4 * q + 1] += x.y * c[j];
+      v[4 * q + 2] += x.z * c[j];
+      v[4 * q + 3] += x.w * c[j];
+      if (two) {
+        v[4 * q] += y.x * c[j + 1];
+        v[4 * q + 1] += y.y * c[j + 1];
+        v[4 * q + 2] += y.z * c[j + 1];
+        v[4 * q + 3] += y.w * c[j + 1];
+      }
+    }
+  }
+  for (int e = rec[2].x; e < rec[2].y; ++e) {
     const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.twin[e] * R);
     const float iz = a.invz[e];
 #pragma unroll
-    for (int k = 0; k < R / 4; ++k) {
-      const float4 x = w[k];
-      v[4 * k] += x.x * iz;
-      v[4 * k + 1] += x.y * iz;
-      v[4 * k + 2] += x.z * iz;
-      v[4 * k + 3] += x.w * iz;
+    for (int q = 0; q < R / 4; ++q) {
+      const float4 x = w[q];
+      v[4 * q] += x.x * iz;
+      v[4 * q + 1] += x.y * iz;
+      v[4 * q + 2] += x.z * iz;
+      v[4 * q + 3] += x.w * iz;
     }
   }
-  if (a.cpl.ptr)
-    for (int k = a.cpl.ptr[port]; k < a.cpl.ptr[port + 1]; ++k) {
-      const float yk = a.cpl.y[k];
-      const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
+  for (int k = rec[2].z; k < rec[2].w; ++k) {
+    const float yk = a.cpl.y[k];
+    const float4* w = reinterpret_cast<const float4*>(a.wprev + (size_t)a.cpl.oth[k] * R);
 #pragma unroll
-      for (int kk = 0; kk < R / 4; ++kk) {
-        const float4 x = w[kk];
-        v[4 * kk] += yk * x.x;
-        v[4 * kk + 1] += yk * x.y;
-        v[4 * kk + 2] += yk * x.z;
-        v[4 * kk + 3] += yk * x.w;
-      }
+    for (int q = 0; q < R / 4; ++q) {
+      const float4 x = w[q];
+      v[4 * q] += yk * x.x;
+      v[4 * q + 1] += yk * x.y;
+      v[4 * q + 2] += yk * x.z;
+      v[4 * q + 3] += yk * x.w;
     }
+  }
 }
 
 }  // namespace
@@ -315,6 +341,7 @@ template <int R, bool LO>
 __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArgs a) {
   using P = Plan<R>;
   constexpr int NS = P::kSlots;
+  static_assert(kVecThreads % (R / 4) == 0 && 32 % (R / 4) == 0, "column groups of the maxima pass");
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -373,8 +400,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
   volatile int& abort_flag = flags[0];
 
   if (warp == 0) {
-    // ---- copies: super-rows in descending order; per row the s_I tile, per block (I, J),
-    // J = I .. 0, its panels and (off the diagonal) the s_J tile.  Each piece goes out as soon as
+    // ---- copies: super-rows in descending order; per block (I, J), J = I .. 0, its panels and
+    // (off the diagonal) the s_J tile; the s_I tile of the next super-row a few blocks ahead.  Each piece goes out as soon as
     // its slots are free (the MMAs of the stage that last filled them are complete), so the next
     // blocks stream in while the current one is multiplied; the stage's full barrier counts the
     // bytes of every piece and completes after the last piece has been issued and has landed.
@@ -404,15 +431,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
         }
         const unsigned char* slot = scratch + (size_t)(k & 1) * slot_bytes;
         const unsigned char* Sp = a.S16 + pd.h_off;
-        for (int I = n4 - 1; I >= 0 && !abort_flag; --I) {
+        // s_I tile of super-row I into the row buffer grow & 1, once the MMAs of the row two
+        // before it (same buffer) are done
+        auto issue_row = [&](int I) -> bool {
           const int rb = (int)(grow & 1);
-          if (grow >= 2 && !mbar_wait_bounded(&rowempty[rb], (uint32_t)(((grow >> 1) - 1) & 1), a.wait_limit)) {
-            abort_flag = 1;
-            break;
-          }
+          if (grow >= 2 && !mbar_wait_bounded(&rowempty[rb], (uint32_t)(((grow >> 1) - 1) & 1), a.wait_limit))
+            return false;
           mbar_arrive_expect_tx(&rowfull[rb], P::kVec);
           bulk_g2s(row0 + rb * P::kVec, slot + (size_t)I * P::kVec, P::kVec, &rowfull[rb]);
           ++grow;
+          return true;
+        };
+        if (n4 > 0 && !issue_row(n4 - 1)) {
+          abort_flag = 1;
+          break;
+        }
+        for (int I = n4 - 1; I >= 0 && !abort_flag; --I) {
           const int h = sb_rows(Pn, I);
           const uint32_t pbytes = (uint32_t)h * 128;  // one panel
           for (int J = I; J >= 0; --J) {
@@ -447,6 +481,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
             }
             mbar_arrive(&full[st]);  // completes once what was issued has landed
             ++gblk;
+            // the next row's tile goes out a few blocks ahead: by the third block of this row the
+            // MMAs have finished the row before it, whose buffer it takes
+            if (ok && I > 0 && J == (I >= 2 ? I - 2 : 0)) ok = issue_row(I - 1);
             if (!ok) {
               abort_flag = 1;
               break;
@@ -606,31 +643,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
       }
       const PieceDesc pd = a.pieces[blockIdx.x + (size_t)k * gridDim.x];
       const int Pn = pd.nports, np = n_super(Pn) * kSB;
-      float mx[R];
+      // gather: s' = D^-1 s per port into the FP32 staging area; the next port's record is
+      // loaded before this port's wave rows
+      int4 rec[3];
+      if (vt < Pn)
 #pragma unroll
-      for (int r = 0; r < R; ++r) mx[r] = 0.f;
+        for (int i = 0; i < 3; ++i) rec[i] = a.prec[3 * (size_t)(pd.port_off + vt) + i];
       for (int p = vt; p < Pn; p += kVecThreads) {
-        float v[R];
-        port_vector<R>(a, pd.port_off + p, v);
-        const float gp = a.gscale[pd.port_off + p];  // s' = D^-1 s, D = diag(1 / g)
+        int4 nrec[3];
+        if (p + kVecThreads < Pn)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] *= gp;
+          for (int i = 0; i < 3; ++i) nrec[i] = a.prec[3 * (size_t)(pd.port_off + p + kVecThreads) + i];
+        float v[R];
+        port_vector<R>(a, rec, v);
+        const float gp = a.gscale[pd.port_off + p];  // s' = D^-1 s, D = diag(1 / g)
         float4* o = reinterpret_cast<float4*>(stage32 + (size_t)p * R);
 #pragma unroll
-        for (int k4 = 0; k4 < R / 4; ++k4) {
-          o[k4] = make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
-          mx[4 * k4] = fmaxf(mx[4 * k4], fabsf(v[4 * k4]));
-          mx[4 * k4 + 1] = fmaxf(mx[4 * k4 + 1], fabsf(v[4 * k4 + 1]));
-          mx[4 * k4 + 2] = fmaxf(mx[4 * k4 + 2], fabsf(v[4 * k4 + 2]));
-          mx[4 * k4 + 3] = fmaxf(mx[4 * k4 + 3], fabsf(v[4 * k4 + 3]));
-        }
+        for (int k4 = 0; k4 < R / 4; ++k4)
+          o[k4] = make_float4(v[4 * k4] * gp, v[4 * k4 + 1] * gp, v[4 * k4 + 2] * gp, v[4 * k4 + 3] * gp);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) rec[i] = nrec[i];
       }
+      vec_sync();
+      // column maxima in a coalesced pass over the staged values: the thread stride is a multiple
+      // of R / 4, so every float4 a thread reads holds the same four columns
+      {
+        float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4* s4 = reinterpret_cast<const float4*>(stage32);
+        for (int i = vt; i < Pn * (R / 4); i += kVecThreads) {
+          const float4 x = s4[i];
+          m4 = make_float4(fmaxf(m4.x, fabsf(x.x)), fmaxf(m4.y, fabsf(x.y)), fmaxf(m4.z, fabsf(x.z)),
+                           fmaxf(m4.w, fabsf(x.w)));
+        }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float m = mx[r];
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) red[vw][r] = m;
+        for (int o = R / 4; o < 32; o <<= 1) {
+          m4.x = fmaxf(m4.x, __shfl_xor_sync(0xffffffffu, m4.x, o));
+          m4.y = fmaxf(m4.y, __shfl_xor_sync(0xffffffffu, m4.y, o));
+          m4.z = fmaxf(m4.z, __shfl_xor_sync(0xffffffffu, m4.z, o));
+          m4.w = fmaxf(m4.w, __shfl_xor_sync(0xffffffffu, m4.w, o));
+        }
+        if (lane < R / 4) {
+          red[vw][4 * lane] = m4.x;
+          red[vw][4 * lane + 1] = m4.y;
+          red[vw][4 * lane + 2] = m4.z;
+          red[vw][4 * lane + 3] = m4.w;
+        }
       }
       vec_sync();
       if (vt < R) {
@@ -678,6 +735,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_port_sweep_tc(const PortTCArg
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
   }
+}
+
+// Gather record of port q: the wave rows and coefficients of its first four entries in the order
+// the sweep adds them (ends e0 .. e1 - 1 with 1 / Z_e, then coupling entries k0 .. k1 - 1 with y;
+// row -1 and coefficient 0 past the last one), and where the remaining entries resume.
+__global__ void k_port_records(int nports, const int32_t* __restrict__ port_end_ptr, const int32_t* __restrict__ twin,
+                               const float* __restrict__ invz, CoupleRef<float> cpl, int4* __restrict__ rec) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nports) return;
+  const int e0 = port_end_ptr[q], e1 = port_end_ptr[q + 1];
+  const int k0 = cpl.ptr ? cpl.ptr[q] : 0, k1 = cpl.ptr ? cpl.ptr[q + 1] : 0;
+  int row[4] = {-1, -1, -1, -1};
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  int n = 0, e = e0, k = k0;
+  for (; e < e1 && n < 4; ++e, ++n) {
+    row[n] = twin[e];
+    c[n] = invz[e];
+  }
+  for (; e == e1 && k < k1 && n < 4; ++k, ++n) {
+    row[n] = cpl.oth[k];
+    c[n] = cpl.y[k];
+  }
+  rec[3 * (size_t)q] = make_int4(row[0], row[1], row[2], row[3]);
+  rec[3 * (size_t)q + 1] = make_int4(__float_as_int(c[0]), __float_as_int(c[1]), __float_as_int(c[2]), __float_as_int(c[3]));
+  rec[3 * (size_t)q + 2] = make_int4(e, e1, k, k1);
+}
+
+cudaError_t launch_port_records(int nports, const int32_t* port_end_ptr, const int32_t* twin, const float* invz,
+                                CoupleRef<float> cpl, int4* rec, cudaStream_t st) {
+  if (nports <= 0) return cudaSuccess;
+  k_port_records<<<(nports + 255) / 256, 256, 0, st>>>(nports, port_end_ptr, twin, invz, cpl, rec);
+  return cudaGetLastError();
 }
 
 cudaError_t port_tc_configure(int R) {

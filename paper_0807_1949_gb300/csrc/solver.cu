@@ -90,7 +90,7 @@ struct vtm_solver {
   int32_t npieces = 0, nports = 0;
   size_t elem = 8;
 
-  DevBuf pieces, factor, factor_u, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status;
+  DevBuf pieces, factor, factor_u, bt, xc, w[2], port_local, port_end_ptr, twin, invz_t, status, port_rec;
   DevBuf a_rowptr, a_col, a_val, vc_ptr, vc_copy, copy_vertex, share;
   DevBuf vb, vx, vxt, vr, vrt, norms, nparts;  // nparts: per-block partial sums of the residual norms
   double* h_norms = nullptr;  // pinned: [R] residual^2, [R] b^2 ... plus status
@@ -1026,6 +1026,7 @@ static void launch_port(vtm_solver* s) {
       t.twin = s->twin.as<int32_t>();
       t.invz = s->invz_t.as<float>();
       t.cpl = couple_ref<float>(s);
+      t.prec = s->port_rec.as<int4>();
       t.status = s->status.as<int>();
       t.wait_limit = s->wait_limit;
       VTM_CUDA(launch_port_sweep_tc(t, s->R, !s->port_half, s->tc_grid, s->stream));
@@ -1144,6 +1145,9 @@ static void choose_form(vtm_solver* s, const vtm_setup_opts* o, int64_t s_tiles,
     VTM_CUDA(cudaMemsetAsync(s->gscale.p, 0, s->gscale.bytes, s->stream));
     s->tc_bytes_all = h_bytes;
     s->tc_bytes_hi = h_bytes / 2;
+    s->port_rec.alloc((size_t)std::max(1, s->nports) * 3 * sizeof(int4));
+    VTM_CUDA(launch_port_records(s->nports, s->port_end_ptr.as<int32_t>(), s->twin.as<int32_t>(),
+                                 s->invz_t.as<float>(), couple_ref<float>(s), s->port_rec.as<int4>(), s->stream));
     VTM_CUDA(port_tc_configure(s->R));
   } else {
     VTM_CUDA(port_sweep_configure<T>(s->R, smem, det));
