@@ -1572,8 +1572,10 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       }
     }
     // a correction phase usually ends on its FP32 floor, which only a second check can show: after a
-    // long batch in such a phase the next check comes after m sweeps
-    if (s->port_form && refine && restarts > 0 && last_inner > 0 && batch > 4 * m) next_k = m;
+    // long batch in such a phase the next check comes after m / 2 sweeps (at the floor the inner
+    // residual moves by about a percent over them, a phase still converging gains a factor of
+    // several, so the slow rule tells the two apart)
+    if (s->port_form && refine && restarts > 0 && last_inner > 0 && batch > 4 * m) next_k = std::max(2, m / 2);
     last_inner = inner;
     last_inner_sweeps = inner_sweeps;
     // accept the trial only when it improves on the residual it started from
