@@ -1499,6 +1499,7 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
   double last_inner = -1.0;
   int last_inner_sweeps = 0;
   double phase_rate = -1.0;  // per-sweep contraction of the inner residual, last measured
+  double phase_rate_before = -1.0;  // phase_rate before its last update
   // port form: the first sweep of every phase also gives u_base (first_sweep_typed)
   auto phase_start = [&]() {
     if (!s->port_form) return;
@@ -1559,7 +1560,10 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
       // (on the log scale) is a stall
       slow = phase_rate > 0.0 && inner < 1.0 && std::log(r_obs) > 0.25 * std::log(phase_rate);
       if (inner < last_inner) rate = r_obs;
-      if (inner <= 0.5 * last_inner) phase_rate = r_obs;  // an interval of real progress
+      if (inner <= 0.5 * last_inner) {  // an interval of real progress
+        phase_rate_before = phase_rate;
+        phase_rate = r_obs;
+      }
     } else if (s->port_form && last_inner < 0 && restarts > 0 && inner > 0) {
       rate = phase_rate;  // first check of a correction phase
     }
@@ -1592,8 +1596,12 @@ int solver_solve(vtm_solver* s, const double* b, double* x, int64_t ld, double r
     // coupled lines on FP16 responses: while such a phase makes progress it gains far more than a
     // factor 2 per check, so a check that gains less has met the FP16 floor
     const bool half_floor = s->port_half && s->coupled && inner > 0.5 * prev_inner && inner_sweeps >= 2 * m;
-    if (refine && inner < 1.0 &&
-        (inner <= reduction || (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || half_floor || slow)) {
+    const bool stalled = (inner >= 0.98 * prev_inner && inner_sweeps >= 2 * m) || half_floor || slow;
+    if (refine && inner < 1.0 && (inner <= reduction || stalled)) {
+      // a phase that ends on a stall spent the end of its last long interval on its floor, so the
+      // rate measured over that interval is too slow for sizing the next phase's batches
+      if (stalled && inner > reduction && phase_rate_before > 0.0 && phase_rate_before < phase_rate)
+        phase_rate = phase_rate_before;
       // defect correction: accept the trial iterate and restart the sweeps on its FP64 residual
       s->vx.swap(s->vxt);
       s->vr.swap(s->vrt);
