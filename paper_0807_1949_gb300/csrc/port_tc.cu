@@ -29,15 +29,16 @@
 //  * warp 0 streams the blocks (and the s_J tile of off-diagonal blocks) through a ring of 16 KB
 //    shared-memory slots by bulk copies (mbarrier complete_tx).  A block's panels go out one pair
 //    at a time, each as soon as its slots are free, so that the next blocks stream in while the
-//    current one is multiplied; the s_I tile of each super-row goes into a 2-slot row buffer;
+//    current one is multiplied; the s_I tile of each super-row goes into a 2-slot row buffer a few
+//    blocks before its row starts;
 //  * warp 1 issues the MMAs: y_I at tensor-memory columns I R .. I R + R - 1, lane = port, all
 //    super-rows of a subgraph held at once (n4 R <= 512 columns); tcgen05.commit releases stages
 //    and row buffers and hands each finished y_I to the epilogue;
 //  * warps 2-5 run the epilogue of the current subgraph: tcgen05.ld of each y_I (released at once
 //    for the next subgraph's MMAs), u = u_base + sigma_j sigma_r y, w_out[e] = 2u - w_in[e];
-//  * warps 6-13 compute the next subgraph's s (one gather pass: FP32 values to a staging area and
-//    the column maxima, then the split values written to a per-CTA global scratch slot that stays
-//    in L2).
+//  * warps 6-13 compute the next subgraph's s: a gather pass driven by per-port records (FP32
+//    values to a staging area), a coalesced pass over that area for the column maxima, then the
+//    split values written to a per-CTA global scratch slot that stays in L2.
 // Every wait is bounded; a CTA that gives up records VTM_ERR_TIMEOUT, lets its copies and MMAs
 // finish, frees its tensor memory and returns.
 #include <cuda_fp16.h>
