@@ -212,11 +212,13 @@ def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: 
         for cn in conns:                             # reset the per-subgraph clocks
             cn.send("times")
             cn.recv()
-        t0 = time.perf_counter()
-        for _ in range(sweeps):
+        per = []
+        for _ in range(sweeps):                      # median of single sweeps: robust to a stray stall
+            t0 = time.perf_counter()
             sweep(cur)
+            per.append(time.perf_counter() - t0)
             cur ^= 1
-        t_sweep = (time.perf_counter() - t0) / sweeps
+        t_sweep = float(np.median(per))
         spent = {}
         for cn in conns:
             cn.send("times")
