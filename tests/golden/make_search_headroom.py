@@ -1,0 +1,225 @@
+"""Write tests/golden/search_headroom.json: how much a richer impedance search gains over the
+learned part's three-parameter search family, with the FP64 oracle as the solver.
+
+The learned impedances are trained on targets from a search over the family
+log Z_t = th0 + th1 (g_t - median g) + th2 (m_t - 1) (learned_z.search).  Here, on small 2D 5-point
+problems of the learned family's kind (log-normal coefficients, sigma ~ U[0.5, 2]), that search is
+followed by coordinate descent with far more freedom, on the same objective (the relative residual
+after K sweeps):
+  face  one factor per subgraph interface (all lines joining the same two subgraphs), 24 on a
+        4 x 4 split;
+  line  one factor per line (per-port impedances), from the face result; only with --line.
+Each descent multiplies one group's impedances by 2 or 1/2, keeps a change that lowers the
+objective and repeats until nothing improves, then does the same with sqrt(2).  Every impedance set
+is then judged by what the method is for: sweeps to a relative residual of 1e-8 (checked every 5
+sweeps), next to Z = 1 and the best uniform Z (a scan of 22 values).  On the 64 x 64 problems both
+searches are repeated on that quantity itself (family_tol, face_tol): the objective is the sweep
+count to 1e-8 with the residual checked after every sweep, interpolated in log residual between
+the two sweeps around 1e-8 so that it varies smoothly with Z.  §7 makes Z the preconditioner and
+leaves its choice open; this measures what per-interface and per-port freedom would add to the
+training targets.
+
+Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
+                                                             30 min on 8 cores)
+     python tests/golden/make_search_headroom.py --line     (5 problems of 32 x 32, faces and lines)
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def problem(n: int, blk: int, seed: int):
+    """The seeded 2D problem: sigma drawn as in the learned 2D family, coefficients and b from inputs."""
+    from oracle import evs
+    from paper_0807_1949_gb300 import inputs
+
+    sigma = float(np.random.default_rng(10_000 + seed).uniform(0.5, 2.0))
+    A = inputs.grid_poisson((n, n), sigma=sigma, seed=seed)
+    b = inputs.rhs_uniform(A.n, 1, seed=seed)
+    return A, evs.split_grid(A, (n, n), (blk, blk)), b, sigma
+
+
+class OracleSolves:
+    """The FP64 oracle iterated for a per-line impedance vector (objective cached by its value)."""
+
+    def __init__(self, A, split, b, horizon: int):
+        from oracle import features
+
+        self.A, self.split, self.b, self.K = A, split, b, horizon
+        self.feats = features.line_features(split, A).astype(np.float32)
+        self.lines = len(split.vtl)
+        self.cache = {}
+
+    def residual_after(self, z, sweeps: int | None = None) -> float:
+        from oracle import vtm as ovtm
+
+        z = np.broadcast_to(np.asarray(z, dtype=np.float64), (self.lines,)).copy()
+        K = self.K if sweeps is None else sweeps
+        key = (K, np.round(np.log(z), 6).tobytes())
+        if key not in self.cache:
+            m = ovtm.VTM(self.split, z)
+            st = m.initial_state()
+            for _ in range(K):
+                st = m.sweep(st, self.b)
+            r = float(ovtm.relative_residual(self.A, self.b, m.assemble(st))[0])
+            self.cache[key] = r if math.isfinite(r) else 1e30
+        return self.cache[key]
+
+    def fractional_sweeps(self, z, rtol: float = 1e-8, maxit: int = 6000) -> float:
+        """Sweeps to reach rtol, interpolated in log residual between the two sweeps around it
+        (the residual is checked after every sweep), so that the count varies smoothly with z."""
+        from oracle import vtm as ovtm
+
+        z = np.broadcast_to(np.asarray(z, dtype=np.float64), (self.lines,)).copy()
+        key = ("tol", np.round(np.log(z), 6).tobytes())
+        if key not in self.cache:
+            m = ovtm.VTM(self.split, z)
+            st = m.initial_state()
+            prev, val = 1.0, float(maxit)
+            for k in range(1, maxit + 1):
+                st = m.sweep(st, self.b)
+                r = float(ovtm.relative_residual(self.A, self.b, m.assemble(st))[0])
+                if not math.isfinite(r):
+                    break
+                if r <= rtol:
+                    val = k - 1 + (math.log(prev / rtol) / math.log(prev / r) if prev > r else 1.0)
+                    break
+                prev = r
+            self.cache[key] = val
+        return self.cache[key]
+
+    def to_tolerance(self, z, rtol: float = 1e-8, maxit: int = 6000, every: int = 5) -> int:
+        from oracle import vtm as ovtm
+
+        m = ovtm.VTM(self.split, np.broadcast_to(np.asarray(z, dtype=np.float64), (self.lines,)).copy())
+        st = m.initial_state()
+        for k in range(1, maxit + 1):
+            st = m.sweep(st, self.b)
+            if k % every == 0 and ovtm.relative_residual(self.A, self.b, m.assemble(st))[0] <= rtol:
+                return k
+        return maxit
+
+
+def interfaces(split) -> list[list[int]]:
+    """Lines grouped by the unordered pair of subgraphs they join."""
+    groups = {}
+    for t, (ja, _, jb, _) in enumerate(split.vtl):
+        groups.setdefault((min(int(ja), int(jb)), max(int(ja), int(jb))), []).append(t)
+    return [groups[k] for k in sorted(groups)]
+
+
+def descend(objective, z: np.ndarray, groups, steps=(2.0, math.sqrt(2.0))):
+    """Coordinate descent of objective(z) over multiplicative factors of the groups' impedances."""
+    z = z.copy()
+    best = objective(z)
+    evals = 0
+    for step in steps:
+        improved = True
+        while improved:
+            improved = False
+            for idx in groups:
+                for f in (step, 1.0 / step):
+                    zt = z.copy()
+                    zt[idx] *= f
+                    r = objective(zt)
+                    evals += 1
+                    if r < best:
+                        best, z, improved = r, zt, True
+                        break
+    return z, best, evals
+
+
+def run(args) -> dict:
+    n, blk, seed, K, per_line, true_objective = args
+    from paper_0807_1949_gb300 import learned_z
+
+    A, split, b, sigma = problem(n, blk, seed)
+    ev = OracleSolves(A, split, b, K)
+    L = ev.lines
+    zs = np.exp(np.linspace(np.log(0.25), np.log(32.0), 22))
+    ru = [ev.residual_after(np.full(L, z)) for z in zs]
+    z_uni = float(zs[int(np.argmin(ru))])
+    theta, _ = learned_z.search(ev, sweeps=K)
+    z_fam = learned_z.family_z(ev.feats, theta)
+    groups = interfaces(split)
+    z_face, r_face, n_face = descend(ev.residual_after, z_fam, groups)
+    out = dict(n=n, block=blk, seed=seed, sigma=round(sigma, 4), horizon=K, lines=L, interfaces=len(groups),
+               z_uniform=round(z_uni, 4), theta=[round(v, 4) for v in theta],
+               objective=dict(uniform=min(ru), family=ev.residual_after(z_fam), face=r_face),
+               face_evals=n_face,
+               sweeps=dict(z1=ev.to_tolerance(np.ones(L)), uniform=ev.to_tolerance(np.full(L, z_uni)),
+                           family=ev.to_tolerance(z_fam), face=ev.to_tolerance(z_face)))
+    if true_objective:
+        # the same two searches on the quantity the impedances are for: sweeps to 1e-8
+        class _Tol:
+            feats = ev.feats
+
+            @staticmethod
+            def residual_after(z, sweeps):
+                return ev.fractional_sweeps(z)
+
+        theta_t, _ = learned_z.search(_Tol, sweeps=K)
+        z_ft = learned_z.family_z(ev.feats, theta_t)
+        z_gt, s_gt, n_gt = descend(ev.fractional_sweeps, z_ft, groups)
+        out["theta_tol"] = [round(v, 4) for v in theta_t]
+        out["fractional_sweeps"] = dict(family=ev.fractional_sweeps(z_fam), face=ev.fractional_sweeps(z_face),
+                                        family_tol=ev.fractional_sweeps(z_ft), face_tol=s_gt)
+        out["face_tol_evals"] = n_gt
+        out["sweeps"].update(family_tol=ev.to_tolerance(z_ft), face_tol=ev.to_tolerance(z_gt))
+    if per_line:
+        z_line, r_line, n_line = descend(ev.residual_after, z_face, [[t] for t in range(L)])
+        out["objective"]["line"] = r_line
+        out["line_evals"] = n_line
+        out["sweeps"]["line"] = ev.to_tolerance(z_line)
+        out["line_log_spread"] = round(float(np.std(np.log(z_line / z_face))), 4)
+    return out
+
+
+def summary(rows, keys) -> dict:
+    fam = np.array([r["sweeps"]["family"] for r in rows], dtype=float)
+    s = {"median_sweeps": {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}}
+    s["median_sweep_ratio_to_family"] = {k: round(float(np.median(np.array([r["sweeps"][k] for r in rows]) / fam)), 4)
+                                         for k in keys if k != "family"}
+    s["min_sweep_ratio_to_family"] = {k: round(float(np.min(np.array([r["sweeps"][k] for r in rows]) / fam)), 4)
+                                      for k in keys if k != "family"}
+    s["median_objective_gain_over_family"] = {
+        k: round(float(np.median([r["objective"]["family"] / r["objective"][k] for r in rows])), 3)
+        for k in keys if k in rows[0]["objective"] and k != "family"}
+    return s
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--line", action="store_true", help="also descend per line (32 x 32, 8^2 blocks)")
+    ap.add_argument("--procs", type=int, default=min(8, os.cpu_count() or 1))
+    a = ap.parse_args()
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    if a.line:
+        name, jobs, keys = "line32", [(32, 8, s, 50, True, False) for s in range(1, 6)], \
+            ("z1", "uniform", "family", "face", "line")
+    else:
+        name, jobs, keys = "face64", [(64, 16, s, 100, False, True) for s in range(1, 9)], \
+            ("z1", "uniform", "family", "face", "family_tol", "face_tol")
+    with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:
+        rows = sorted(pool.map(run, jobs), key=lambda r: r["seed"])
+    path = os.path.join(HERE, "search_headroom.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    out[name] = dict(rows=rows, summary=summary(rows, keys))
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out[name]["summary"], indent=1))
+
+
+if __name__ == "__main__":
+    main()
