@@ -220,7 +220,7 @@ def train(model: vtm.MLP, X: np.ndarray, y: np.ndarray, epochs: int = 40, batch:
     return hist
 
 
-def build_dataset(family: str, seeds, sweeps: int, verbose=True):
+def build_dataset(family: str, seeds, sweeps: int, verbose=True, profile: bool = False):
     X, y, meta = [], [], []
     for sd in seeds:
         t0 = time.time()
@@ -230,7 +230,7 @@ def build_dataset(family: str, seeds, sweeps: int, verbose=True):
         # of the defect correction early, where the residual no longer ranks the candidates)
         k1 = ev.to_tolerance(1.0)["sweeps"]
         horizon = int(min(sweeps, max(40, 10 * round(0.05 * k1))))
-        th, log = search(ev, horizon, wide_scan=family.startswith("fem"))
+        th, log = search(ev, horizon, wide_scan=family.startswith("fem"), profile=profile)
         zl = family_z(ev.feats, th)
         X.append(ev.feats)
         y.append(np.repeat(np.log(zl), 2).astype(np.float32))
@@ -490,6 +490,8 @@ def main():
                     help="keep the trained model; on the held-out seeds compare the plain search with the "
                          "profiled one (sweeps to 1e-8 of each family result, Z = 1 and the network); "
                          "JSON lines to --out")
+    ap.add_argument("--profile-search", action="store_true",
+                    help="training targets from the profiled search (search(profile=True))")
     a = ap.parse_args()
     if a.compare_search:
         model = load(os.path.join(MODELS, f"z_{a.family}.json"))
@@ -519,7 +521,7 @@ def main():
             json.dump(meta, f)
         return
     t0 = time.time()
-    X, y, meta = build_dataset(a.family, range(a.train), a.sweeps)
+    X, y, meta = build_dataset(a.family, range(a.train), a.sweeps, profile=a.profile_search)
     t_search = time.time() - t0
     model = vtm.MLP(seed=1)
     hist = train(model, X, y, epochs=a.epochs)
@@ -531,7 +533,8 @@ def main():
     out = a.out or os.path.join(MODELS, f"z_{a.family}.json")
     save(model, out, family=a.family, train_seeds=a.train, test_seeds=a.test, search_sweeps=a.sweeps,
          search_seconds=round(t_search, 1), loss=hist, search=meta, eval=rows, median_sweeps=summ,
-         features="vtm_line_features (8 per end)", target="log Z of the searched family, both ends")
+         features="vtm_line_features (8 per end)", target="log Z of the searched family, both ends",
+         search_walk="profiled" if a.profile_search else "plain")
 
 
 if __name__ == "__main__":
