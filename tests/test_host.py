@@ -193,6 +193,32 @@ def test_committed_models_are_well_formed():
         assert 8 <= len(c["eval"]) <= d["test_seeds"]
 
 
+def test_profiled_search_records():
+    """The recorded GPU comparison of the plain and the profiled search walks (held-out seeds of the
+    2D family) and the network trained on profiled-walk targets, evaluated on the same seeds."""
+    import json
+    import os
+    from paper_0807_1949_gb300 import learned_z
+    with open(os.path.join(learned_z.MODELS, "z_poisson2d-256.json")) as f:
+        shipped = json.load(f)
+    with open(os.path.join(learned_z.MODELS, "z_poisson2d-256-profiled.json")) as f:
+        prof = json.load(f)
+    p = np.asarray(prof["params"])
+    assert p.shape == (4801,) and np.all(np.isfinite(p))
+    assert prof["search_walk"] == "profiled" and len(prof["search"]) == prof["train_seeds"] == 24
+    cmp_rows = {r["seed"]: r for r in shipped["search_compare"]["rows"]}
+    assert len(cmp_rows) == 8
+    # per problem, the profiled walk's own family impedances against the plain walk's
+    ratio = [r["profiled"]["sweeps"] / r["plain"]["sweeps"] for r in cmp_rows.values()]
+    assert np.median(ratio) < 0.8 and all(r["profiled"]["evals"] > r["plain"]["evals"] for r in cmp_rows.values())
+    # the networks on the same held-out seeds: Z = 1 agrees between the two runs (same solver)
+    new = {e["seed"]: e for e in prof["eval"]}
+    assert set(new) == set(cmp_rows)
+    assert all(new[s]["z1"]["sweeps"] == cmp_rows[s]["z1"] for s in new)
+    assert np.median([new[s]["learned"]["sweeps"] for s in new]) < 0.8 * np.median(
+        [cmp_rows[s]["learned"] for s in new])
+
+
 @pytest.mark.parametrize("dims,block,sigma", [((32, 32), (16, 16), 0.0), ((12, 11), (4, 5), 1.0),
                                                ((9, 8, 7), (4, 4, 3), 0.7)])
 def test_line_pairs_match_oracle(vtmlib, dims, block, sigma):
