@@ -19,9 +19,14 @@ the two sweeps around 1e-8 so that it varies smoothly with Z.  §7 makes Z the p
 leaves its choice open; this measures what per-interface and per-port freedom would add to the
 training targets.
 
+With --profiled the 64 x 64 rows also get the search with its profiled walk (learned_z.search with
+profile=True: th0 re-refined at every step of the th1 / th2 walks) and per-interface descent from
+that result (family_profiled, face_profiled).
+
 Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
                                                              30 min on 8 cores)
      python tests/golden/make_search_headroom.py --line     (5 problems of 32 x 32, faces and lines)
+     python tests/golden/make_search_headroom.py --profiled (after the first; about 10 min)
 """
 import argparse
 import json
@@ -185,6 +190,21 @@ def run(args) -> dict:
     return out
 
 
+def run_profiled(args) -> dict:
+    """The profiled search (th0 re-refined at every walk step) and per-interface descent from it."""
+    n, blk, seed, K = args
+    from paper_0807_1949_gb300 import learned_z
+
+    A, split, b, _ = problem(n, blk, seed)
+    ev = OracleSolves(A, split, b, K)
+    theta, log = learned_z.search(ev, sweeps=K, profile=True)
+    z_p = learned_z.family_z(ev.feats, theta)
+    z_pf, r_pf, n_pf = descend(ev.residual_after, z_p, interfaces(split))
+    return dict(seed=seed, theta_profiled=[round(v, 4) for v in theta], profiled_evals=len(log),
+                profiled_face_evals=n_pf, objective=dict(family_profiled=ev.residual_after(z_p), face_profiled=r_pf),
+                sweeps=dict(family_profiled=ev.to_tolerance(z_p), face_profiled=ev.to_tolerance(z_pf)))
+
+
 def summary(rows, keys) -> dict:
     fam = np.array([r["sweeps"]["family"] for r in rows], dtype=float)
     s = {"median_sweeps": {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}}
@@ -201,9 +221,30 @@ def summary(rows, keys) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--line", action="store_true", help="also descend per line (32 x 32, 8^2 blocks)")
+    ap.add_argument("--profiled", action="store_true",
+                    help="add the profiled search and per-interface descent from it to the stored 64 x 64 rows")
     ap.add_argument("--procs", type=int, default=min(8, os.cpu_count() or 1))
     a = ap.parse_args()
     os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    path = os.path.join(HERE, "search_headroom.json")
+    if a.profiled:
+        out = json.load(open(path))
+        rows = out["face64"]["rows"]
+        with mp.get_context("spawn").Pool(min(a.procs, len(rows))) as pool:
+            extra = pool.map(run_profiled, [(r["n"], r["block"], r["seed"], r["horizon"]) for r in rows])
+        for r, e in zip(rows, extra):
+            assert r["seed"] == e["seed"]
+            r["theta_profiled"], r["profiled_evals"] = e["theta_profiled"], e["profiled_evals"]
+            r["profiled_face_evals"] = e["profiled_face_evals"]
+            r["objective"].update(e["objective"])
+            r["sweeps"].update(e["sweeps"])
+        keys = ("z1", "uniform", "family", "face", "family_tol", "face_tol", "family_profiled", "face_profiled")
+        out["face64"]["summary"] = summary(rows, keys)
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+            f.write("\n")
+        print(json.dumps(out["face64"]["summary"], indent=1))
+        return
     if a.line:
         name, jobs, keys = "line32", [(32, 8, s, 50, True, False) for s in range(1, 6)], \
             ("z1", "uniform", "family", "face", "line")
@@ -212,7 +253,6 @@ def main():
             ("z1", "uniform", "family", "face", "family_tol", "face_tol")
     with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:
         rows = sorted(pool.map(run, jobs), key=lambda r: r["seed"])
-    path = os.path.join(HERE, "search_headroom.json")
     out = json.load(open(path)) if os.path.exists(path) else {}
     out[name] = dict(rows=rows, summary=summary(rows, keys))
     with open(path, "w") as f:

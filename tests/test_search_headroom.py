@@ -3,11 +3,13 @@
 The targets come from a three-parameter search family (learned_z.search).  Freeing one impedance
 factor per subgraph interface, or per line (port), and descending on the same objective (the FP64
 residual after a fixed number of sweeps) lowers that objective further, but the sweeps to 1e-8 --
-what the impedances are for (§7: Z is the preconditioner) -- barely move: the gain at the search
-horizon is a transient that the asymptotic contraction does not keep.  One small case runs live
-with the FP64 oracle as the solver; the stored experiment (tests/golden/make_search_headroom.py,
-oracle only) covers 8 problems of 64 x 64 with per-interface freedom and 5 of 32 x 32 with per-line
-freedom.
+what the impedances are for (§7: Z is the preconditioner) -- move much less: most of the gain at
+the search horizon is a transient that the asymptotic contraction does not keep, and what remains
+comes from problems where the search's plain coordinate walk stalled (a step in th1 or th2 needed a
+new th0).  The profiled walk (th0 re-refined at every step) removes those stalls, and per-interface
+freedom then adds next to nothing.  One small case runs live with the FP64 oracle as the solver;
+the stored experiment (tests/golden/make_search_headroom.py, oracle only) covers 8 problems of
+64 x 64 with per-interface freedom and 5 of 32 x 32 with per-line freedom.
 """
 import json
 import math
@@ -48,6 +50,11 @@ def test_interface_descent_lowers_the_objective_but_not_the_sweeps(vtmlib):
     k_face = ev.to_tolerance(z_face)
     assert k_fam <= 0.7 * k1                               # the family search itself pays
     assert k_face >= 0.8 * k_fam, (k1, k_fam, k_face, r_fam / r_face)
+    # the profiled walk (th0 re-refined at every th1 / th2 step) gets past the plain walk's stall
+    theta_p, _ = learned_z.search(ev, sweeps=50, profile=True)
+    z_p = learned_z.family_z(ev.feats, theta_p)
+    assert ev.residual_after(z_p) <= r_fam
+    assert ev.to_tolerance(z_p) <= 0.8 * k_fam            # recorded: 100 against 160
 
 
 def test_stored_experiment_shows_little_headroom():
@@ -63,5 +70,17 @@ def test_stored_experiment_shows_little_headroom():
     # family searched on that rugged objective settles worse than on the residual after K sweeps
     assert 0.8 <= s["median_sweep_ratio_to_family"]["face_tol"] <= 1.0
     assert s["median_sweep_ratio_to_family"]["family_tol"] >= 1.0
-    for r in face["rows"]:
+    # the profiled walk (th0 re-refined at every th1 / th2 step) removes the plain walk's stalls, and
+    # per-interface freedom then adds next to nothing
+    assert s["median_sweep_ratio_to_family"]["family_profiled"] <= 0.7
+    assert s["median_sweeps"]["family_profiled"] < s["median_sweeps"]["face_tol"]
+    extra = [r["sweeps"]["face_profiled"] / r["sweeps"]["family_profiled"] for r in face["rows"]]
+    assert np.median(extra) >= 0.95 and min(extra) >= 0.8
+    line = g["line32"]
+    assert len(line["rows"]) == 5 and all(r["interfaces"] == 24 for r in line["rows"])
+    s = line["summary"]
+    # per-line freedom: the objective drops far more than per interface, the sweeps much less
+    assert s["median_objective_gain_over_family"]["line"] >= 4 * s["median_objective_gain_over_family"]["face"]
+    assert 0.75 <= s["median_sweep_ratio_to_family"]["line"] <= 1.0
+    for r in face["rows"] + line["rows"]:
         assert all(math.isfinite(v) for v in r["objective"].values())
