@@ -21,7 +21,8 @@ training targets.
 
 With --profiled the 64 x 64 rows also get the search with its profiled walk (learned_z.search with
 profile=True: th0 re-refined at every step of the th1 / th2 walks) and per-interface descent from
-that result (family_profiled, face_profiled).
+that result (family_profiled, face_profiled), and one fixed parameter set for all problems: the
+component-wise median of the other problems' profiled parameters (global_profiled, leave one out).
 
 Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
                                                              30 min on 8 cores)
@@ -205,6 +206,16 @@ def run_profiled(args) -> dict:
                 sweeps=dict(family_profiled=ev.to_tolerance(z_p), face_profiled=ev.to_tolerance(z_pf)))
 
 
+def run_global(args) -> int:
+    """Sweeps to 1e-8 of one fixed parameter set of the family on one problem."""
+    n, blk, seed, theta = args
+    from paper_0807_1949_gb300 import learned_z
+
+    A, split, b, _ = problem(n, blk, seed)
+    ev = OracleSolves(A, split, b, 0)
+    return ev.to_tolerance(learned_z.family_z(ev.feats, theta))
+
+
 def summary(rows, keys) -> dict:
     fam = np.array([r["sweeps"]["family"] for r in rows], dtype=float)
     s = {"median_sweeps": {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}}
@@ -232,13 +243,22 @@ def main():
         rows = out["face64"]["rows"]
         with mp.get_context("spawn").Pool(min(a.procs, len(rows))) as pool:
             extra = pool.map(run_profiled, [(r["n"], r["block"], r["seed"], r["horizon"]) for r in rows])
-        for r, e in zip(rows, extra):
-            assert r["seed"] == e["seed"]
-            r["theta_profiled"], r["profiled_evals"] = e["theta_profiled"], e["profiled_evals"]
-            r["profiled_face_evals"] = e["profiled_face_evals"]
-            r["objective"].update(e["objective"])
-            r["sweeps"].update(e["sweeps"])
-        keys = ("z1", "uniform", "family", "face", "family_tol", "face_tol", "family_profiled", "face_profiled")
+            for r, e in zip(rows, extra):
+                assert r["seed"] == e["seed"]
+                r["theta_profiled"], r["profiled_evals"] = e["theta_profiled"], e["profiled_evals"]
+                r["profiled_face_evals"] = e["profiled_face_evals"]
+                r["objective"].update(e["objective"])
+                r["sweeps"].update(e["sweeps"])
+            # one fixed parameter set for every problem: the component-wise median of the other
+            # problems' profiled parameters (leave one out), i.e. the method without a network
+            th = np.array([r["theta_profiled"] for r in rows])
+            glob = [tuple(float(v) for v in np.median(np.delete(th, i, axis=0), axis=0)) for i in range(len(rows))]
+            sw = pool.map(run_global, [(r["n"], r["block"], r["seed"], g) for r, g in zip(rows, glob)])
+        for r, g, k in zip(rows, glob, sw):
+            r["theta_global_profiled"] = [round(v, 4) for v in g]
+            r["sweeps"]["global_profiled"] = k
+        keys = ("z1", "uniform", "family", "face", "family_tol", "face_tol", "family_profiled", "face_profiled",
+                "global_profiled")
         out["face64"]["summary"] = summary(rows, keys)
         with open(path, "w") as f:
             json.dump(out, f, indent=1)

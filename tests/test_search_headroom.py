@@ -76,6 +76,8 @@ def test_stored_experiment_shows_little_headroom():
     assert s["median_sweeps"]["family_profiled"] < s["median_sweeps"]["face_tol"]
     extra = [r["sweeps"]["face_profiled"] / r["sweeps"]["family_profiled"] for r in face["rows"]]
     assert np.median(extra) >= 0.95 and min(extra) >= 0.8
+    # and one parameter set for all problems (leave one out) does nearly as well as the per-problem one
+    assert s["median_sweeps"]["global_profiled"] <= 1.1 * s["median_sweeps"]["family_profiled"]
     line = g["line32"]
     assert len(line["rows"]) == 5 and all(r["interfaces"] == 24 for r in line["rows"])
     s = line["summary"]
