@@ -23,11 +23,14 @@ With --profiled the 64 x 64 rows also get the search with its profiled walk (lea
 profile=True: th0 re-refined at every step of the th1 / th2 walks) and per-interface descent from
 that result (family_profiled, face_profiled), and one fixed parameter set for all problems: the
 component-wise median of the other problems' profiled parameters (global_profiled, leave one out).
+With --three-d the plain and the profiled walk are compared the same way on eight 3D problems of the
+kind of the 256^3 run's family (33^3 in 8^3 blocks, sigma ~ U[0.75, 1.75], horizon 60 sweeps).
 
 Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
                                                              30 min on 8 cores)
      python tests/golden/make_search_headroom.py --line     (5 problems of 32 x 32, faces and lines)
      python tests/golden/make_search_headroom.py --profiled (after the first; about 10 min)
+     python tests/golden/make_search_headroom.py --three-d  (about 30 min on 8 cores)
 """
 import argparse
 import json
@@ -44,15 +47,46 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 
-def problem(n: int, blk: int, seed: int):
-    """The seeded 2D problem: sigma drawn as in the learned 2D family, coefficients and b from inputs."""
+def problem(n: int, blk: int, seed: int, dim: int = 2):
+    """The seeded problem: 2D with sigma drawn as in the learned 2D family, or 3D (n^3, blocks of
+    blk^3) with sigma ~ U[0.75, 1.75] as in the family of the 256^3 run; coefficients and b from
+    inputs."""
     from oracle import evs
     from paper_0807_1949_gb300 import inputs
 
-    sigma = float(np.random.default_rng(10_000 + seed).uniform(0.5, 2.0))
-    A = inputs.grid_poisson((n, n), sigma=sigma, seed=seed)
+    lo, hi = (0.5, 2.0) if dim == 2 else (0.75, 1.75)
+    sigma = float(np.random.default_rng(10_000 + seed).uniform(lo, hi))
+    A = inputs.grid_poisson((n,) * dim, sigma=sigma, seed=seed)
     b = inputs.rhs_uniform(A.n, 1, seed=seed)
-    return A, evs.split_grid(A, (n, n), (blk, blk)), b, sigma
+    return A, evs.split_grid(A, (n,) * dim, (blk,) * dim), b, sigma
+
+
+def run_3d(args) -> dict:
+    """3D: the plain and the profiled walk of the family search, judged by sweeps to 1e-8."""
+    n, blk, seed, K = args
+    from paper_0807_1949_gb300 import learned_z
+
+    A, split, b, sigma = problem(n, blk, seed, dim=3)
+    ev = OracleSolves(A, split, b, K)
+    L = ev.lines
+    th, log = learned_z.search(ev, sweeps=K)
+    tp, logp = learned_z.search(ev, sweeps=K, profile=True)
+    return dict(n=n, block=blk, seed=seed, sigma=round(sigma, 4), horizon=K, lines=L,
+                theta=[round(v, 4) for v in th], theta_profiled=[round(v, 4) for v in tp],
+                evals=len(log), profiled_evals=len(logp),
+                objective=dict(family=ev.residual_after(learned_z.family_z(ev.feats, th)),
+                               family_profiled=ev.residual_after(learned_z.family_z(ev.feats, tp))),
+                sweeps=dict(z1=ev.to_tolerance(np.ones(L)), family=ev.to_tolerance(learned_z.family_z(ev.feats, th)),
+                            family_profiled=ev.to_tolerance(learned_z.family_z(ev.feats, tp))))
+
+
+def run_global3(args) -> int:
+    n, blk, seed, theta = args
+    from paper_0807_1949_gb300 import learned_z
+
+    A, split, b, _ = problem(n, blk, seed, dim=3)
+    ev = OracleSolves(A, split, b, 0)
+    return ev.to_tolerance(learned_z.family_z(ev.feats, theta))
 
 
 class OracleSolves:
@@ -234,10 +268,29 @@ def main():
     ap.add_argument("--line", action="store_true", help="also descend per line (32 x 32, 8^2 blocks)")
     ap.add_argument("--profiled", action="store_true",
                     help="add the profiled search and per-interface descent from it to the stored 64 x 64 rows")
+    ap.add_argument("--three-d", action="store_true",
+                    help="plain against profiled walk on eight 3D problems (33^3 in 8^3 blocks, 64 subgraphs)")
     ap.add_argument("--procs", type=int, default=min(8, os.cpu_count() or 1))
     a = ap.parse_args()
     os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
     path = os.path.join(HERE, "search_headroom.json")
+    if a.three_d:
+        jobs = [(33, 8, s, 60) for s in range(1, 9)]
+        with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:
+            rows = sorted(pool.map(run_3d, jobs), key=lambda r: r["seed"])
+            th = np.array([r["theta_profiled"] for r in rows])
+            glob = [tuple(float(v) for v in np.median(np.delete(th, i, axis=0), axis=0)) for i in range(len(rows))]
+            sw = pool.map(run_global3, [(r["n"], r["block"], r["seed"], g) for r, g in zip(rows, glob)])
+        for r, g, k in zip(rows, glob, sw):
+            r["theta_global_profiled"] = [round(v, 4) for v in g]
+            r["sweeps"]["global_profiled"] = k
+        out = json.load(open(path)) if os.path.exists(path) else {}
+        out["profiled3d"] = dict(rows=rows, summary=summary(rows, ("z1", "family", "family_profiled", "global_profiled")))
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+            f.write("\n")
+        print(json.dumps(out["profiled3d"]["summary"], indent=1))
+        return
     if a.profiled:
         out = json.load(open(path))
         rows = out["face64"]["rows"]

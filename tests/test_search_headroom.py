@@ -84,5 +84,11 @@ def test_stored_experiment_shows_little_headroom():
     # per-line freedom: the objective drops far more than per interface, the sweeps much less
     assert s["median_objective_gain_over_family"]["line"] >= 4 * s["median_objective_gain_over_family"]["face"]
     assert 0.75 <= s["median_sweep_ratio_to_family"]["line"] <= 1.0
-    for r in face["rows"] + line["rows"]:
+    # 3D (the family of the 256^3 run, 33^3 in 8^3 blocks): the same stall and the same one-theta rule
+    d3 = g["profiled3d"]
+    assert len(d3["rows"]) == 8 and all(r["theta_profiled"][1] == -1.0 for r in d3["rows"])
+    s = d3["summary"]
+    assert s["median_sweep_ratio_to_family"]["family_profiled"] <= 0.75
+    assert s["median_sweeps"]["global_profiled"] <= 1.1 * s["median_sweeps"]["family_profiled"]
+    for r in face["rows"] + line["rows"] + d3["rows"]:
         assert all(math.isfinite(v) for v in r["objective"].values())
