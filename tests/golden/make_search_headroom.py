@@ -25,12 +25,15 @@ that result (family_profiled, face_profiled), and one fixed parameter set for al
 component-wise median of the other problems' profiled parameters (global_profiled, leave one out).
 With --three-d the plain and the profiled walk are compared the same way on eight 3D problems of the
 kind of the 256^3 run's family (33^3 in 8^3 blocks, sigma ~ U[0.75, 1.75], horizon 60 sweeps).
+With --networks the two trained 2D networks (plain-walk and profiled-walk targets) and one parameter
+set of each walk are compared on eight held-out 256^2 problems of their family.
 
 Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
                                                              30 min on 8 cores)
      python tests/golden/make_search_headroom.py --line     (5 problems of 32 x 32, faces and lines)
      python tests/golden/make_search_headroom.py --profiled (after the first; about 10 min)
      python tests/golden/make_search_headroom.py --three-d  (about 30 min on 8 cores)
+     python tests/golden/make_search_headroom.py --networks (about 5 min on 8 cores)
 """
 import argparse
 import json
@@ -250,6 +253,27 @@ def run_global(args) -> int:
     return ev.to_tolerance(learned_z.family_z(ev.feats, theta))
 
 
+def run_networks(args) -> dict:
+    """256^2 (the 2D family's own size): sweeps to 1e-8 of the two trained networks (their forward
+    pass taken by the oracle's FP64 perceptron on the BF16-rounded weights; both ends of a line
+    agree on the geometric mean) and of one parameter set of each walk (the median of the model
+    file's training-set parameters), all with the FP64 oracle as the solver."""
+    seed, models = args
+    from oracle import evs, mlp
+    from paper_0807_1949_gb300 import learned_z
+
+    A, dims, block, sigma, b = learned_z.problem("poisson2d-256", seed)
+    split = evs.split_grid(A, dims, block)
+    ev = OracleSolves(A, split, b, 0)
+    row = dict(seed=seed, sigma=round(sigma, 4), lines=ev.lines, sweeps={})
+    for name, (params, theta) in models.items():
+        y, _ = mlp.forward(mlp.bf16_round(params), ev.feats.astype(np.float64))
+        z_net = np.exp(np.clip(0.5 * (y[0::2] + y[1::2]), -30.0, 30.0))
+        row["sweeps"][name + "_network"] = ev.to_tolerance(z_net)
+        row["sweeps"][name + "_one_theta"] = ev.to_tolerance(learned_z.family_z(ev.feats, theta))
+    return row
+
+
 def summary(rows, keys) -> dict:
     fam = np.array([r["sweeps"]["family"] for r in rows], dtype=float)
     s = {"median_sweeps": {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}}
@@ -268,12 +292,37 @@ def main():
     ap.add_argument("--line", action="store_true", help="also descend per line (32 x 32, 8^2 blocks)")
     ap.add_argument("--profiled", action="store_true",
                     help="add the profiled search and per-interface descent from it to the stored 64 x 64 rows")
+    ap.add_argument("--networks", action="store_true",
+                    help="the two trained 2D networks against one parameter set of each walk, on 8 held-out "
+                         "256^2 problems")
     ap.add_argument("--three-d", action="store_true",
                     help="plain against profiled walk on eight 3D problems (33^3 in 8^3 blocks, 64 subgraphs)")
     ap.add_argument("--procs", type=int, default=min(8, os.cpu_count() or 1))
     a = ap.parse_args()
     os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
     path = os.path.join(HERE, "search_headroom.json")
+    if a.networks:
+        from paper_0807_1949_gb300 import learned_z
+
+        models = {}
+        for name, fname in (("plain", "z_poisson2d-256.json"), ("profiled", "z_poisson2d-256-profiled.json")):
+            with open(os.path.join(learned_z.MODELS, fname)) as f:
+                m = json.load(f)
+            th = np.median(np.array([list(r["theta"]) + [0.0] * (4 - len(r["theta"])) for r in m["search"]]), axis=0)
+            models[name] = (np.asarray(m["params"], dtype=np.float64), tuple(float(v) for v in th))
+        jobs = [(sd, models) for sd in range(100_000, 100_008)]
+        with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:
+            rows = pool.map(run_networks, jobs)
+        keys = ("plain_network", "plain_one_theta", "profiled_network", "profiled_one_theta")
+        med = {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}
+        out = json.load(open(path)) if os.path.exists(path) else {}
+        out["networks256"] = dict(rows=rows, theta={k: [round(v, 4) for v in t] for k, (_, t) in models.items()},
+                                  median_sweeps=med)
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+            f.write("\n")
+        print(json.dumps(med, indent=1))
+        return
     if a.three_d:
         jobs = [(33, 8, s, 60) for s in range(1, 9)]
         with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:

@@ -90,5 +90,11 @@ def test_stored_experiment_shows_little_headroom():
     s = d3["summary"]
     assert s["median_sweep_ratio_to_family"]["family_profiled"] <= 0.75
     assert s["median_sweeps"]["global_profiled"] <= 1.1 * s["median_sweeps"]["family_profiled"]
+    # 256^2, held-out seeds of the 2D family, FP64 oracle: the one-theta rule of the profiled walk
+    # needs fewer sweeps than either trained network
+    net = g["networks256"]
+    assert len(net["rows"]) == 8 and net["theta"]["profiled"][1] == -1.0
+    m = net["median_sweeps"]
+    assert m["profiled_one_theta"] < min(m["plain_network"], m["profiled_network"], m["plain_one_theta"])
     for r in face["rows"] + line["rows"] + d3["rows"]:
         assert all(math.isfinite(v) for v in r["objective"].values())
