@@ -490,32 +490,36 @@ void line_features(const vtm_partition* p, float* out) {
       else *off += std::fabs(p->l_val[k]);
     }
   };
-  for (int64_t e = 0; e < 2 * nl; ++e) {
-    const int64_t c = (e & 1) ? p->line_b[e >> 1] : p->line_a[e >> 1];
-    const int64_t tw = (e & 1) ? p->line_a[e >> 1] : p->line_b[e >> 1];
-    const int64_t i = p->copy_vertex[c];
-    double aii = 0, amax = 0, amin = INFINITY;
-    for (int64_t k = p->a_rowptr[i]; k < p->a_rowptr[i + 1]; ++k) {
-      if (p->a_col[k] == i) aii = p->a_val[k];
-      else {
-        amax = std::max(amax, std::fabs(p->a_val[k]));
-        amin = std::min(amin, std::fabs(p->a_val[k]));
+  // every end writes its own row: blocks of consecutive ends on the host threads
+  const int64_t E = 2 * nl, kBlock = 4096;
+  parallel_for((E + kBlock - 1) / kBlock, [&](int64_t blk) {
+    for (int64_t e = blk * kBlock; e < std::min(E, (blk + 1) * kBlock); ++e) {
+      const int64_t c = (e & 1) ? p->line_b[e >> 1] : p->line_a[e >> 1];
+      const int64_t tw = (e & 1) ? p->line_a[e >> 1] : p->line_b[e >> 1];
+      const int64_t i = p->copy_vertex[c];
+      double aii = 0, amax = 0, amin = INFINITY;
+      for (int64_t k = p->a_rowptr[i]; k < p->a_rowptr[i + 1]; ++k) {
+        if (p->a_col[k] == i) aii = p->a_val[k];
+        else {
+          amax = std::max(amax, std::fabs(p->a_val[k]));
+          amin = std::min(amin, std::fabs(p->a_val[k]));
+        }
       }
+      double dc, offc, dt, offt;
+      copy_diag_and_off(c, &dc, &offc);
+      copy_diag_and_off(tw, &dt, &offt);
+      const int64_t nj = p->piece_ptr[piece[c] + 1] - p->piece_ptr[piece[c]];
+      float* f = out + e * VTM_MLP_IN;
+      f[0] = (float)safe_log(aii);
+      f[1] = (float)safe_log(dc);
+      f[2] = (float)std::log((double)ncopies[i]);
+      f[3] = (float)nlines[c];
+      f[4] = (float)safe_log(offc);
+      f[5] = (float)safe_log(dt);
+      f[6] = (amax > 0 && std::isfinite(amin) && amin > 0) ? (float)std::log(amax / amin) : 0.f;
+      f[7] = (float)std::log((double)p->n / (double)nj);
     }
-    double dc, offc, dt, offt;
-    copy_diag_and_off(c, &dc, &offc);
-    copy_diag_and_off(tw, &dt, &offt);
-    const int64_t nj = p->piece_ptr[piece[c] + 1] - p->piece_ptr[piece[c]];
-    float* f = out + e * VTM_MLP_IN;
-    f[0] = (float)safe_log(aii);
-    f[1] = (float)safe_log(dc);
-    f[2] = (float)std::log((double)ncopies[i]);
-    f[3] = (float)nlines[c];
-    f[4] = (float)safe_log(offc);
-    f[5] = (float)safe_log(dt);
-    f[6] = (amax > 0 && std::isfinite(amin) && amin > 0) ? (float)std::log(amax / amin) : 0.f;
-    f[7] = (float)std::log((double)p->n / (double)nj);
-  }
+  });
 }
 
 }  // namespace vtm
