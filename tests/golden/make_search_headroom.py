@@ -26,7 +26,9 @@ component-wise median of the other problems' profiled parameters (global_profile
 With --three-d the plain and the profiled walk are compared the same way on eight 3D problems of the
 kind of the 256^3 run's family (33^3 in 8^3 blocks, sigma ~ U[0.75, 1.75], horizon 60 sweeps).
 With --networks the two trained 2D networks (plain-walk and profiled-walk targets) and one parameter
-set of each walk are compared on eight held-out 256^2 problems of their family.
+set of each walk are compared on eight held-out 256^2 problems of their family; with --refined as
+well, the solves run FP32 factors and sweeps inside FP64 defect correction (oracle.mixed, the
+structure of the library's FP32 solve) instead of the FP64 iteration.
 
 Run: python tests/golden/make_search_headroom.py            (8 problems of 64 x 64, faces; about
                                                              30 min on 8 cores)
@@ -258,19 +260,25 @@ def run_networks(args) -> dict:
     pass taken by the oracle's FP64 perceptron on the BF16-rounded weights; both ends of a line
     agree on the geometric mean) and of one parameter set of each walk (the median of the model
     file's training-set parameters), all with the FP64 oracle as the solver."""
-    seed, models = args
-    from oracle import evs, mlp
+    seed, models, refined = args
+    from oracle import evs, mixed, mlp
     from paper_0807_1949_gb300 import learned_z
 
     A, dims, block, sigma, b = learned_z.problem("poisson2d-256", seed)
     split = evs.split_grid(A, dims, block)
     ev = OracleSolves(A, split, b, 0)
+    if refined:
+        # FP32 factors and sweeps inside FP64 defect correction (oracle.mixed), checked every 10
+        def sweeps(z):
+            return mixed.solve_refined(split, A, b, z, kind="fp32", rtol=1e-8, maxit=6000, check_every=10).sweeps
+    else:
+        sweeps = ev.to_tolerance
     row = dict(seed=seed, sigma=round(sigma, 4), lines=ev.lines, sweeps={})
     for name, (params, theta) in models.items():
         y, _ = mlp.forward(mlp.bf16_round(params), ev.feats.astype(np.float64))
         z_net = np.exp(np.clip(0.5 * (y[0::2] + y[1::2]), -30.0, 30.0))
-        row["sweeps"][name + "_network"] = ev.to_tolerance(z_net)
-        row["sweeps"][name + "_one_theta"] = ev.to_tolerance(learned_z.family_z(ev.feats, theta))
+        row["sweeps"][name + "_network"] = sweeps(z_net)
+        row["sweeps"][name + "_one_theta"] = sweeps(learned_z.family_z(ev.feats, theta))
     return row
 
 
@@ -295,6 +303,8 @@ def main():
     ap.add_argument("--networks", action="store_true",
                     help="the two trained 2D networks against one parameter set of each walk, on 8 held-out "
                          "256^2 problems")
+    ap.add_argument("--refined", action="store_true",
+                    help="with --networks: FP32 sweeps inside FP64 defect correction (oracle.mixed) instead of FP64")
     ap.add_argument("--three-d", action="store_true",
                     help="plain against profiled walk on eight 3D problems (33^3 in 8^3 blocks, 64 subgraphs)")
     ap.add_argument("--procs", type=int, default=min(8, os.cpu_count() or 1))
@@ -310,13 +320,13 @@ def main():
                 m = json.load(f)
             th = np.median(np.array([list(r["theta"]) + [0.0] * (4 - len(r["theta"])) for r in m["search"]]), axis=0)
             models[name] = (np.asarray(m["params"], dtype=np.float64), tuple(float(v) for v in th))
-        jobs = [(sd, models) for sd in range(100_000, 100_008)]
+        jobs = [(sd, models, a.refined) for sd in range(100_000, 100_008)]
         with mp.get_context("spawn").Pool(min(a.procs, len(jobs))) as pool:
             rows = pool.map(run_networks, jobs)
         keys = ("plain_network", "plain_one_theta", "profiled_network", "profiled_one_theta")
         med = {k: float(np.median([r["sweeps"][k] for r in rows])) for k in keys}
         out = json.load(open(path)) if os.path.exists(path) else {}
-        out["networks256"] = dict(rows=rows, theta={k: [round(v, 4) for v in t] for k, (_, t) in models.items()},
+        out["networks256_fp32" if a.refined else "networks256"] = dict(rows=rows, theta={k: [round(v, 4) for v in t] for k, (_, t) in models.items()},
                                   median_sweeps=med)
         with open(path, "w") as f:
             json.dump(out, f, indent=1)

@@ -96,5 +96,11 @@ def test_stored_experiment_shows_little_headroom():
     assert len(net["rows"]) == 8 and net["theta"]["profiled"][1] == -1.0
     m = net["median_sweeps"]
     assert m["profiled_one_theta"] < min(m["plain_network"], m["profiled_network"], m["plain_one_theta"])
+    # the same with FP32 sweeps inside FP64 defect correction (the structure of the library's solve),
+    # where the network of profiled targets beats the shipped one but not the one-theta rule
+    net = g["networks256_fp32"]
+    m = net["median_sweeps"]
+    assert m["profiled_network"] < 0.8 * m["plain_network"]
+    assert m["profiled_one_theta"] < min(m["plain_network"], m["profiled_network"], m["plain_one_theta"])
     for r in face["rows"] + line["rows"] + d3["rows"]:
         assert all(math.isfinite(v) for v in r["objective"].values())
