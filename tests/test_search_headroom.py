@@ -7,9 +7,12 @@ what the impedances are for (§7: Z is the preconditioner) -- move much less: mo
 the search horizon is a transient that the asymptotic contraction does not keep, and what remains
 comes from problems where the search's plain coordinate walk stalled (a step in th1 or th2 needed a
 new th0).  The profiled walk (th0 re-refined at every step) removes those stalls, and per-interface
-freedom then adds next to nothing.  One small case runs live with the FP64 oracle as the solver;
-the stored experiment (tests/golden/make_search_headroom.py, oracle only) covers 8 problems of
-64 x 64 with per-interface freedom and 5 of 32 x 32 with per-line freedom.
+freedom then adds next to nothing.  One parameter set of the profiled walk for all problems does
+about as well as the per-problem search, and at 256^2 it beats both trained 2D networks.  One small
+case runs live with the FP64 oracle as the solver; the stored experiment
+(tests/golden/make_search_headroom.py, oracle only) covers 8 problems of 64 x 64 with per-interface
+freedom, 5 of 32 x 32 with per-line freedom, 8 of 33^3 in 3D, and the networks on 8 held-out
+256^2 problems (FP64, and FP32 sweeps inside FP64 defect correction).
 """
 import json
 import math
