@@ -128,15 +128,16 @@ def _ow_main(conn, dims, block, sigma, nrhs, pieces, shm_names, shapes, coff):
     shm = {k: shared_memory.SharedMemory(name=n) for k, n in shm_names.items()}
     arr = {k: np.ndarray(shapes[k], dtype=np.float64, buffer=shm[k].buf) for k in shm}
     import time as _time
-    spent = {j: 0.0 for j in pieces}  # seconds in each subgraph's step since the last report
+    spent = {j: [] for j in pieces}   # seconds of each subgraph's step, one entry per sweep since the last report
     conn.send("ready")
     while True:
         msg = conn.recv()
         if msg is None:
             break
         if msg == "times":
-            conn.send(dict(spent))
-            spent = {j: 0.0 for j in pieces}
+            # median of single steps: a stall of the host during one sweep moves no subgraph's time
+            conn.send({j: (float(np.median(v)) if v else 0.0) for j, v in spent.items()})
+            spent = {j: [] for j in pieces}
             continue
         cur = msg
         u, om = arr["u%d" % cur], arr["o%d" % cur]
@@ -144,7 +145,7 @@ def _ow_main(conn, dims, block, sigma, nrhs, pieces, shm_names, shapes, coff):
         for j in pieces:
             t0 = _time.perf_counter()
             x = m.piece_step(j, u, om, b, nu, no)
-            spent[j] += _time.perf_counter() - t0
+            spent[j].append(_time.perf_counter() - t0)
             arr["x"][:, coff[j]:coff[j + 1]] = x
         conn.send("done")
     for v in shm.values():
@@ -253,7 +254,7 @@ def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: 
     total = int(np.prod(nbw))
     # The work of a subgraph grows with its ports, i.e. with the number of block faces it shares with
     # neighbours; a small sample has more boundary subgraphs than the workload.  Scale the sample's
-    # time by the workload's work over the sample's, with the mean step time of each class measured
+    # time by the workload's work over the sample's, with the step time of each class measured
     # in the sample (classes by neighbour count; a missing class from a linear fit in that count).
     def faces(idx, nb):
         return sum((i > 0) + (i < m - 1) for i, m in zip(idx, nb))
@@ -270,7 +271,7 @@ def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: 
     for j, g in enumerate(split.subgraphs):
         coord = np.array(np.unravel_index(int(np.min(g.vertices)), dims))
         idx = tuple(int(v) for v in np.minimum(coord // blk, np.array(nbs) - 1))
-        per_class.setdefault(faces(idx, nbs), []).append(spent.get(j, 0.0) / sweeps)
+        per_class.setdefault(faces(idx, nbs), []).append(spent.get(j, 0.0))
     mean = {k: float(np.mean(v)) for k, v in per_class.items()}
     ks = sorted(mean)
     if len(ks) >= 2:
