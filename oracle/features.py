@@ -16,7 +16,10 @@ import scipy.sparse as sp
 from .evs import SplitGraph, _as_csr
 
 
-def line_features(split: SplitGraph, A) -> np.ndarray:
+def line_features(split: SplitGraph, A, lines=None) -> np.ndarray:
+    """Features of every end, rows in end order; with ``lines`` (indices into split.vtl) only the
+    ends of those lines, rows 2k and 2k + 1 for the k-th listed line (the counts of copies and of
+    lines at a copy still come from the whole split)."""
     A = _as_csr(A)
     m = len(split.vtl)
     ncopies = np.zeros(split.n, dtype=np.int64)
@@ -27,8 +30,10 @@ def line_features(split: SplitGraph, A) -> np.ndarray:
         nlines[(ja, ca)] = nlines.get((ja, ca), 0) + 1
         nlines[(jb, cb)] = nlines.get((jb, cb), 0) + 1
     diag = A.diagonal()
-    out = np.zeros((2 * m, 8))
-    for t, (ja, ca, jb, cb) in enumerate(split.vtl):
+    sel = range(m) if lines is None else [int(t) for t in lines]
+    out = np.zeros((2 * len(sel), 8))
+    for k, t in enumerate(sel):
+        ja, ca, jb, cb = split.vtl[t]
         for side, (j, c, jt, ct) in enumerate(((ja, ca, jb, cb), (jb, cb, ja, ca))):
             g = split.subgraphs[j]
             i = int(g.vertices[c])
@@ -38,7 +43,7 @@ def line_features(split: SplitGraph, A) -> np.ndarray:
             dt = split.subgraphs[jt].A[ct, ct]
             nb = A.getrow(i)
             vals = np.abs(nb.data[nb.indices != i])
-            f = out[2 * t + side]
+            f = out[2 * k + side]
             f[0] = np.log(diag[i])
             f[1] = np.log(dc)
             f[2] = np.log(ncopies[i])

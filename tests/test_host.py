@@ -137,6 +137,27 @@ def test_line_features_match_oracle(vtmlib, dims, block, sigma):
     assert np.allclose(got, ref[order], rtol=1e-6, atol=1e-6)
 
 
+def test_line_features_match_oracle_on_a_threaded_partition(vtmlib):
+    """65^3 in 4^3 blocks: 576,000 line ends, enough for the library to spread the ends over its host
+    threads; 2000 random lines (4000 ends) against the oracle."""
+    from oracle import features
+    dims, block = (65, 65, 65), (4, 4, 4)
+    A = inputs.grid_poisson(dims, sigma=1.0, seed=5)
+    part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
+    osplit = evs.split_grid(A, dims, block)
+    got = part.line_features()
+    assert got.shape == (2 * len(osplit.vtl), 8) and 2 * len(osplit.vtl) >= 64 * 4096
+    pos = {tuple(int(x) for x in q): t for t, q in enumerate(part.lines())}
+    rng = np.random.default_rng(11)
+    pick = rng.choice(len(osplit.vtl), size=2000, replace=False)
+    ref = features.line_features(osplit, A, lines=pick)
+    rows = []
+    for t in pick:
+        u = pos[tuple(int(x) for x in osplit.vtl[t])]
+        rows += [2 * u, 2 * u + 1]
+    assert np.allclose(got[rows], ref, rtol=1e-6, atol=1e-6)
+
+
 def test_rcb_is_identical_to_oracle(vtmlib):
     rng = np.random.default_rng(0)
     for dim, n, parts in [(2, 5000, 37), (3, 3000, 64), (2, 999, 2)]:
