@@ -445,26 +445,43 @@ void line_pairs(const vtm_partition* p, std::vector<int64_t>& pairs, std::vector
       if (p->a_col[q] == k) return std::fabs(p->a_val[q]);
     return 0.0;
   };
-  for (int64_t t = 0; t < nl; ++t) {
-    const int64_t ca = p->line_a[t], cb = p->line_b[t];
-    const int32_t ja = piece[ca], jb = piece[cb];
-    for (int64_t k = p->l_rowptr[ca]; k < p->l_rowptr[ca + 1]; ++k) {
-      const int64_t cn = p->piece_ptr[ja] + p->l_col[k];
-      if (cn == ca) continue;
-      for (int64_t q = lptr[cn]; q < lptr[cn + 1]; ++q) {
-        const int64_t u = lid[q];
-        if (u <= t) continue;
-        const int64_t ua = p->line_a[u], ub = p->line_b[u];
-        int64_t other;  // u's copy in jb
-        if (piece[ua] == ja && piece[ub] == jb) other = ub;
-        else if (piece[ub] == ja && piece[ua] == jb) other = ua;
-        else continue;
-        if (!has_col(cb, other - p->piece_ptr[jb])) continue;
-        pairs.push_back(t);
-        pairs.push_back(u);
-        wts.push_back(a_abs(p->copy_vertex[ca], p->copy_vertex[cn]));
+  // blocks of consecutive lines on the host threads, each into its own lists; joined in block
+  // order, so the pairs come out in the same order as from one loop over t
+  const int64_t kBlock = 4096, nblk = (nl + kBlock - 1) / kBlock;
+  std::vector<std::vector<int64_t>> bpairs(nblk);
+  std::vector<std::vector<double>> bwts(nblk);
+  parallel_for(nblk, [&](int64_t blk) {
+    std::vector<int64_t>& pp = bpairs[blk];
+    std::vector<double>& ww = bwts[blk];
+    for (int64_t t = blk * kBlock; t < std::min(nl, (blk + 1) * kBlock); ++t) {
+      const int64_t ca = p->line_a[t], cb = p->line_b[t];
+      const int32_t ja = piece[ca], jb = piece[cb];
+      for (int64_t k = p->l_rowptr[ca]; k < p->l_rowptr[ca + 1]; ++k) {
+        const int64_t cn = p->piece_ptr[ja] + p->l_col[k];
+        if (cn == ca) continue;
+        for (int64_t q = lptr[cn]; q < lptr[cn + 1]; ++q) {
+          const int64_t u = lid[q];
+          if (u <= t) continue;
+          const int64_t ua = p->line_a[u], ub = p->line_b[u];
+          int64_t other;  // u's copy in jb
+          if (piece[ua] == ja && piece[ub] == jb) other = ub;
+          else if (piece[ub] == ja && piece[ua] == jb) other = ua;
+          else continue;
+          if (!has_col(cb, other - p->piece_ptr[jb])) continue;
+          pp.push_back(t);
+          pp.push_back(u);
+          ww.push_back(a_abs(p->copy_vertex[ca], p->copy_vertex[cn]));
+        }
       }
     }
+  });
+  size_t total = 0;
+  for (const auto& v : bwts) total += v.size();
+  pairs.reserve(2 * total);
+  wts.reserve(total);
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    pairs.insert(pairs.end(), bpairs[blk].begin(), bpairs[blk].end());
+    wts.insert(wts.end(), bwts[blk].begin(), bwts[blk].end());
   }
 }
 

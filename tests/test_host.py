@@ -137,16 +137,25 @@ def test_line_features_match_oracle(vtmlib, dims, block, sigma):
     assert np.allclose(got, ref[order], rtol=1e-6, atol=1e-6)
 
 
-def test_line_features_match_oracle_on_a_threaded_partition(vtmlib):
-    """65^3 in 4^3 blocks: 576,000 line ends, enough for the library to spread the ends over its host
-    threads; 2000 random lines (4000 ends) against the oracle."""
-    from oracle import features
+@pytest.fixture(scope="module")
+def threaded_split(vtmlib):
+    """65^3 in 4^3 blocks: 288,000 lines (576,000 ends), enough for the library to spread the lines
+    and ends over its host threads (it does so from 64 blocks of 4096); the library's partition
+    and the oracle's split of the same matrix."""
     dims, block = (65, 65, 65), (4, 4, 4)
     A = inputs.grid_poisson(dims, sigma=1.0, seed=5)
     part = vtmlib.partition_evs(A, "grid", dims=dims, block=block)
     osplit = evs.split_grid(A, dims, block)
+    assert len(osplit.vtl) >= 64 * 4096
+    return A, part, osplit
+
+
+def test_line_features_match_oracle_on_a_threaded_partition(threaded_split):
+    """2000 random lines (4000 ends) of the threaded partition against the oracle."""
+    from oracle import features
+    A, part, osplit = threaded_split
     got = part.line_features()
-    assert got.shape == (2 * len(osplit.vtl), 8) and 2 * len(osplit.vtl) >= 64 * 4096
+    assert got.shape == (2 * len(osplit.vtl), 8)
     pos = {tuple(int(x) for x in q): t for t, q in enumerate(part.lines())}
     rng = np.random.default_rng(11)
     pick = rng.choice(len(osplit.vtl), size=2000, replace=False)
@@ -156,6 +165,22 @@ def test_line_features_match_oracle_on_a_threaded_partition(vtmlib):
         u = pos[tuple(int(x) for x in osplit.vtl[t])]
         rows += [2 * u, 2 * u + 1]
     assert np.allclose(got[rows], ref, rtol=1e-6, atol=1e-6)
+
+
+def test_line_pairs_match_oracle_on_a_threaded_partition(threaded_split):
+    """The candidate couplings of the threaded partition: the oracle's set of pairs with |a_ik|,
+    listed in increasing order of the first line as from one loop over the lines."""
+    from oracle import coupled
+    A, part, osplit = threaded_split
+    pr, w = part.line_pairs()
+    opr, ow = coupled.adjacent_line_pairs(osplit, A)
+    assert len(pr) == len(opr) > 0
+    q, oq = part.lines(), osplit.vtl
+    got = {frozenset((tuple(q[t]), tuple(q[u]))): x for (t, u), x in zip(pr, w)}
+    ref = {frozenset((tuple(int(v) for v in oq[t]), tuple(int(v) for v in oq[u]))): x for (t, u), x in zip(opr, ow)}
+    assert got.keys() == ref.keys()
+    assert all(got[k] == ref[k] for k in ref)
+    assert np.all(pr[:, 0] < pr[:, 1]) and np.all(np.diff(pr[:, 0]) >= 0)
 
 
 def test_rcb_is_identical_to_oracle(vtmlib):
