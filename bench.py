@@ -152,141 +152,174 @@ def _ow_main(conn, dims, block, sigma, nrhs, pieces, shm_names, shapes, coff):
         v.close()
 
 
-def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: int | None = None) -> dict:
-    """Seconds per sweep and per residual check of the FP64 oracle on all host cores (see above)."""
-    import multiprocessing as mp
-    from multiprocessing import shared_memory
+class OracleSampler:
+    """The FP64 oracle on all host cores over a bounded sample of a workload (see above): the
+    workers, the sample's split and its factors are made once; each time() call times sweeps and
+    one residual check of the running iteration."""
 
-    import numpy as np
+    def __init__(self, workload: str, cores: int | None = None, nb: int | None = None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
 
-    from oracle import evs
-    from oracle import vtm as ovtm
-    from paper_0807_1949_gb300 import inputs
+        import numpy as np
 
-    w = WORKLOADS[workload]
-    d = len(w["dims"])
-    if nb is None:
-        nb = 4 if d == 3 else 8                     # 64 subgraphs
-    dims = tuple(min(n, nb * s + 1) for n, s in zip(w["dims"], w["block"]))
-    R = w["nrhs"]
-    A = inputs.grid_poisson(dims, sigma=w["sigma"], seed=0)
-    b = inputs.rhs_uniform(A.n, R, seed=0)
-    split = evs.split_grid(A, dims, w["block"])
-    P = len(split.subgraphs)
-    E = 2 * len(split.vtl)
-    sizes = [len(g.vertices) for g in split.subgraphs]
-    coff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    if cores is None:
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    cores = max(1, min(cores, P))
-    shapes = {"u0": (R, E), "o0": (R, E), "u1": (R, E), "o1": (R, E), "x": (R, int(coff[-1]))}
-    shm = {k: shared_memory.SharedMemory(create=True, size=max(8, int(np.prod(v)) * 8)) for k, v in shapes.items()}
-    arr = {k: np.ndarray(shapes[k], dtype=np.float64, buffer=shm[k].buf) for k in shm}
-    for v in arr.values():
-        v[...] = 0.0
-    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in env_keep:
-        os.environ[k] = "1"
-    ctx = mp.get_context("spawn")
-    procs, conns = [], []
-    try:
-        for c in range(cores):
-            mine = list(range(c, P, cores))
-            pa, pb = ctx.Pipe()
-            pr = ctx.Process(target=_ow_main, args=(pb, dims, w["block"], w["sigma"], R, mine,
-                                                    {k: v.name for k, v in shm.items()}, shapes, coff))
-            pr.start()
-            procs.append(pr)
-            conns.append(pa)
-        for cn in conns:
-            assert cn.recv() == "ready"
+        from oracle import evs
+        from paper_0807_1949_gb300 import inputs
 
-        def sweep(cur):
-            for cn in conns:
-                cn.send(cur)
-            for cn in conns:
-                assert cn.recv() == "done"
+        self.workload = workload
+        w = self.w = WORKLOADS[workload]
+        d = len(w["dims"])
+        if nb is None:
+            nb = 4 if d == 3 else 8                 # 64 subgraphs
+        dims = self.dims = tuple(min(n, nb * s + 1) for n, s in zip(w["dims"], w["block"]))
+        R = self.R = w["nrhs"]
+        self.A = inputs.grid_poisson(dims, sigma=w["sigma"], seed=0)
+        self.b = inputs.rhs_uniform(self.A.n, R, seed=0)
+        split = self.split = evs.split_grid(self.A, dims, w["block"])
+        P = self.P = len(split.subgraphs)
+        E = 2 * len(split.vtl)
+        sizes = [len(g.vertices) for g in split.subgraphs]
+        self.coff = coff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        if cores is None:
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.cores = cores = max(1, min(cores, P))
+        shapes = {"u0": (R, E), "o0": (R, E), "u1": (R, E), "o1": (R, E), "x": (R, int(coff[-1]))}
+        self.shm, self.procs, self.conns = {}, [], []
+        self.cur, self.warm = 0, False
+        env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env_keep:
+            os.environ[k] = "1"
+        try:
+            self.shm = {k: shared_memory.SharedMemory(create=True, size=max(8, int(np.prod(v)) * 8))
+                        for k, v in shapes.items()}
+            self.arr = {k: np.ndarray(shapes[k], dtype=np.float64, buffer=self.shm[k].buf) for k in self.shm}
+            for v in self.arr.values():
+                v[...] = 0.0
+            ctx = mp.get_context("spawn")
+            for c in range(cores):
+                mine = list(range(c, P, cores))
+                pa, pb = ctx.Pipe()
+                pr = ctx.Process(target=_ow_main, args=(pb, dims, w["block"], w["sigma"], R, mine,
+                                                        {k: v.name for k, v in self.shm.items()}, shapes, coff))
+                pr.start()
+                self.procs.append(pr)
+                self.conns.append(pa)
+            for cn in self.conns:
+                assert cn.recv() == "ready"
+        except BaseException:
+            self.close()
+            raise
+        finally:
+            for k, v in env_keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
-        cur = 0
-        sweep(cur)                                   # warm-up
-        cur ^= 1
-        for cn in conns:                             # reset the per-subgraph clocks
+    def _sweep(self):
+        for cn in self.conns:
+            cn.send(self.cur)
+        for cn in self.conns:
+            assert cn.recv() == "done"
+        self.cur ^= 1
+
+    def time(self, sweeps: int) -> dict:
+        """Seconds per sweep (median of single sweeps) and per residual check, and the work ratio of
+        the workload to the sample (by class of subgraph)."""
+        import numpy as np
+
+        from oracle import vtm as ovtm
+
+        if not self.warm:
+            self._sweep()                            # warm-up
+            self.warm = True
+        for cn in self.conns:                        # reset the per-subgraph clocks
             cn.send("times")
             cn.recv()
         per = []
         for _ in range(sweeps):                      # median of single sweeps: robust to a stray stall
             t0 = time.perf_counter()
-            sweep(cur)
+            self._sweep()
             per.append(time.perf_counter() - t0)
-            cur ^= 1
         t_sweep = float(np.median(per))
         spent = {}
-        for cn in conns:
+        for cn in self.conns:
             cn.send("times")
             spent.update(cn.recv())
         t0 = time.perf_counter()
+        arr, coff, cur = self.arr, self.coff, self.cur
         st = ovtm.State(u=arr["u%d" % cur], omega=arr["o%d" % cur],
-                        x_local=[arr["x"][:, coff[j]:coff[j + 1]] for j in range(P)])
-        x = ovtm.assemble(split, st)
-        rr = ovtm.relative_residual(A, b, x)
+                        x_local=[arr["x"][:, coff[j]:coff[j + 1]] for j in range(self.P)])
+        x = ovtm.assemble(self.split, st)
+        rr = ovtm.relative_residual(self.A, self.b, x)
         t_check = time.perf_counter() - t0
         assert np.all(np.isfinite(rr))
-    finally:
-        for cn in conns:
+        w, dims = self.w, self.dims
+        nbw = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(w["dims"], w["block"])]
+        nbs = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(dims, w["block"])]
+        total = int(np.prod(nbw))
+
+        # The work of a subgraph grows with its ports, i.e. with the number of block faces it shares
+        # with neighbours; a small sample has more boundary subgraphs than the workload.  Scale the
+        # sample's time by the workload's work over the sample's, with the step time of each class
+        # measured in the sample (classes by neighbour count; a missing class from a linear fit in
+        # that count).
+        def faces(idx, nb):
+            return sum((i > 0) + (i < m - 1) for i, m in zip(idx, nb))
+
+        def class_counts(nb):
+            cnt = {}
+            for idx in np.ndindex(*nb):
+                k = faces(idx, nb)
+                cnt[k] = cnt.get(k, 0) + 1
+            return cnt
+
+        blk = np.array(w["block"])
+        per_class = {}
+        for j, g in enumerate(self.split.subgraphs):
+            coord = np.array(np.unravel_index(int(np.min(g.vertices)), dims))
+            idx = tuple(int(v) for v in np.minimum(coord // blk, np.array(nbs) - 1))
+            per_class.setdefault(faces(idx, nbs), []).append(spent.get(j, 0.0))
+        mean = {k: float(np.mean(v)) for k, v in per_class.items()}
+        ks = sorted(mean)
+        if len(ks) >= 2:
+            slope, icpt = np.polyfit(ks, [mean[k] for k in ks], 1)
+        else:
+            slope, icpt = 0.0, (mean[ks[0]] if ks else 1.0)
+
+        def cost(k):
+            return mean[k] if k in mean else max(icpt + slope * k, 1e-12)
+
+        work = lambda cnt: sum(c * cost(k) for k, c in cnt.items())
+        ratio = work(class_counts(nbw)) / max(work(class_counts(nbs)), 1e-30)
+        return dict(t_sweep=t_sweep, t_check=t_check, sample_pieces=self.P, total_pieces=total, sample_dims=dims,
+                    sweeps=sweeps, cores=self.cores, nrhs=self.R, work_ratio=ratio,
+                    n_ratio=float(np.prod(w["dims"])) / float(np.prod(dims)))
+
+    def close(self):
+        for cn in self.conns:
             try:
                 cn.send(None)
             except Exception:
                 pass
-        for pr in procs:
+        for pr in self.procs:
             pr.join(timeout=60)
             if pr.is_alive():
                 pr.kill()
-        for v in shm.values():
+        for v in self.shm.values():
             v.close()
             v.unlink()
-        for k, v in env_keep.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    nbw = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(w["dims"], w["block"])]
-    nbs = [max(1, -(-(n - 1) // s)) if n > 1 else 1 for n, s in zip(dims, w["block"])]
-    total = int(np.prod(nbw))
-    # The work of a subgraph grows with its ports, i.e. with the number of block faces it shares with
-    # neighbours; a small sample has more boundary subgraphs than the workload.  Scale the sample's
-    # time by the workload's work over the sample's, with the step time of each class measured
-    # in the sample (classes by neighbour count; a missing class from a linear fit in that count).
-    def faces(idx, nb):
-        return sum((i > 0) + (i < m - 1) for i, m in zip(idx, nb))
+        self.conns, self.procs, self.shm = [], [], {}
 
-    def class_counts(nb):
-        cnt = {}
-        for idx in np.ndindex(*nb):
-            k = faces(idx, nb)
-            cnt[k] = cnt.get(k, 0) + 1
-        return cnt
 
-    blk = np.array(w["block"])
-    per_class = {}
-    for j, g in enumerate(split.subgraphs):
-        coord = np.array(np.unravel_index(int(np.min(g.vertices)), dims))
-        idx = tuple(int(v) for v in np.minimum(coord // blk, np.array(nbs) - 1))
-        per_class.setdefault(faces(idx, nbs), []).append(spent.get(j, 0.0))
-    mean = {k: float(np.mean(v)) for k, v in per_class.items()}
-    ks = sorted(mean)
-    if len(ks) >= 2:
-        slope, icpt = np.polyfit(ks, [mean[k] for k in ks], 1)
-    else:
-        slope, icpt = 0.0, (mean[ks[0]] if ks else 1.0)
-
-    def cost(k):
-        return mean[k] if k in mean else max(icpt + slope * k, 1e-12)
-
-    work = lambda cnt: sum(c * cost(k) for k, c in cnt.items())
-    ratio = work(class_counts(nbw)) / max(work(class_counts(nbs)), 1e-30)
-    return dict(t_sweep=t_sweep, t_check=t_check, sample_pieces=P, total_pieces=total, sample_dims=dims,
-                sweeps=sweeps, cores=cores, nrhs=R, work_ratio=ratio,
-                n_ratio=float(np.prod(w["dims"])) / float(np.prod(dims)))
+def oracle_timing(workload: str, sweeps: int = 4, cores: int | None = None, nb: int | None = None) -> dict:
+    """Seconds per sweep and per residual check of the FP64 oracle on all host cores (see above),
+    from a sampler made for this one measurement."""
+    smp = OracleSampler(workload, cores, nb)
+    try:
+        return smp.time(sweeps)
+    finally:
+        smp.close()
 
 
 def oracle_time_to_tol(t: dict, sweeps_to_tol: int, check_every: int = 10) -> float:
@@ -432,14 +465,20 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "no recorded sweep count of the plain method for "
                           + args.workload}))
         return 0
-    for _ in range(args.warmup):
-        oracle_timing(args.workload, 1)
     t0 = time.perf_counter()
+    smp = OracleSampler(args.workload)      # workers, split and factors once (factorisation excluded)
+    t_make = time.perf_counter() - t0
     vals, t = [], None
-    for _ in range(args.steps):
-        t = oracle_timing(args.workload, 2)
-        vals.append(oracle_time_to_tol(t, ksweeps))
-    dt = time.perf_counter() - t0
+    try:
+        for _ in range(args.warmup):
+            smp.time(1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            t = smp.time(2)
+            vals.append(oracle_time_to_tol(t, ksweeps))
+        dt = time.perf_counter() - t0
+    finally:
+        smp.close()
     v = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": args.gpus,
@@ -453,7 +492,8 @@ def run_reference(args):
                                     f"residual check of a {list(t['sample_dims'])} grid ({t['sample_pieces']} "
                                     f"subgraphs of the workload's block shape, {t['nrhs']} right-hand sides), scaled "
                                     f"to {t['total_pieces']} subgraphs and {ksweeps} sweeps ({ksrc}); wall "
-                                    f"{dt:.1f} s for {args.steps} steps")},
+                                    f"{dt:.1f} s for {args.steps} steps, after {t_make:.1f} s to split and "
+                                    f"factor the sample once")},
         "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

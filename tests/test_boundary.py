@@ -33,12 +33,13 @@ def test_package_never_imports_the_oracle():
 
 def test_bench_imports_the_oracle_only_in_its_sampler():
     """bench.py runs the oracle only to time it (the cpu_baseline / reference leg): the sampler
-    oracle_timing and its worker processes _ow_main."""
+    (OracleSampler, oracle_timing) and its worker processes _ow_main."""
     found, tree = _oracle_imports(os.path.join(ROOT, "bench.py"))
     assert found
     inside = set()
     for n in ast.walk(tree):
-        if isinstance(n, ast.FunctionDef) and n.name in ("oracle_timing", "_ow_main"):
+        if (isinstance(n, ast.FunctionDef) and n.name in ("oracle_timing", "_ow_main")) or \
+                (isinstance(n, ast.ClassDef) and n.name == "OracleSampler"):
             inside |= {m.lineno for m in ast.walk(n) if isinstance(m, (ast.Import, ast.ImportFrom))}
     assert all(line in inside for line, _ in found)
 
