@@ -83,3 +83,33 @@ def test_sample_extrapolation_matches_a_whole_oracle_solve():
         del bench.WORKLOADS[name]
     assert 0.8 <= est / whole <= 1.25, (ests, whole, sum(t_sw) + sum(t_ck), k)
     assert np.isfinite(est)
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """With two ranks (torchrun, as the benchmark is launched for N > 1) rank 0 alone times the
+    oracle and prints one line; the other rank exits 0 without work."""
+    import socket
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+                          "--gpus", "2", "--steps", "1", "--warmup", "0", "--workload", "laplace2d-32"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-800:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout[-800:]
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_reference_arm_without_a_sweep_count_says_unavailable():
+    """A workload with no recorded sweep count of the plain method (neither a whole oracle run nor
+    the GPU's plain arm) gives the contract's one-line unavailable record and exit code 0."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--workload", "poisson2d-256"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-500:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "poisson2d-256" in line["unavailable"]
