@@ -20,6 +20,7 @@ from paper_0807_1949_gb300 import inputs  # noqa: E402
 WORKLOADS = {
     "poisson3d-128": dict(dims=(128, 128, 128), block=(16, 16, 16), sigma=1.0),
     "laplace2d-32": dict(dims=(32, 32), block=(16, 16), sigma=0.0),
+    "poisson2d-256": dict(dims=(256, 256), block=(32, 32), sigma=1.25),
 }
 
 

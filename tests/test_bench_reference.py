@@ -108,8 +108,8 @@ def test_reference_arm_without_a_sweep_count_says_unavailable():
     """A workload with no recorded sweep count of the plain method (neither a whole oracle run nor
     the GPU's plain arm) gives the contract's one-line unavailable record and exit code 0."""
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--workload", "poisson2d-256"], capture_output=True, text=True,
+                          "--warmup", "0", "--workload", "poisson3d-64"], capture_output=True, text=True,
                          timeout=300, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-500:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
-    assert line["impl"] == "reference" and "poisson2d-256" in line["unavailable"]
+    assert line["impl"] == "reference" and "poisson3d-64" in line["unavailable"]
