@@ -28,38 +28,6 @@ double boundary_excess(double aii, double offabs) {
   return d;
 }
 
-void copy_and_check_matrix(const vtm_csr* A, vtm_partition* p) {
-  if (!A || A->n <= 0 || !A->rowptr || !A->col || !A->val) fail(VTM_ERR_INVALID, "A: null or empty matrix");
-  const int64_t n = A->n;
-  if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) fail(VTM_ERR_INVALID, "A: rowptr inconsistent with nnz");
-  p->n = n;
-  p->a_rowptr.assign(A->rowptr, A->rowptr + n + 1);
-  p->a_col.assign(A->col, A->col + A->nnz);
-  p->a_val.assign(A->val, A->val + A->nnz);
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t lo = A->rowptr[i], hi = A->rowptr[i + 1];
-    if (hi < lo) fail(VTM_ERR_INVALID, "A: rowptr not monotone");
-    bool diag = false;
-    for (int64_t k = lo; k < hi; ++k) {
-      int32_t j = A->col[k];
-      if (j < 0 || j >= n) fail(VTM_ERR_INVALID, "A: column index out of range");
-      if (k > lo && A->col[k - 1] >= j) fail(VTM_ERR_INVALID, "A: columns not strictly ascending in a row");
-      if (j == i) {
-        diag = true;
-        if (!(A->val[k] > 0)) fail(VTM_ERR_INVALID, "A: non-positive diagonal");
-        continue;
-      }
-      // symmetric partner
-      const int32_t* b = A->col + A->rowptr[j];
-      const int32_t* e = A->col + A->rowptr[j + 1];
-      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
-      if (f == e || *f != i || A->val[A->rowptr[j] + (f - b)] != A->val[k])
-        fail(VTM_ERR_NOT_SYMMETRIC, "A is not symmetric");
-    }
-    if (!diag) fail(VTM_ERR_INVALID, "A: missing diagonal entry");
-  }
-}
-
 template <class F>
 void parallel_for(int64_t count, F&& f) {
   unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
@@ -83,6 +51,57 @@ void parallel_for(int64_t count, F&& f) {
   for (auto& x : th) x.join();
   for (unsigned t = 0; t < nt; ++t)
     if (bad[t]) throw errs[t];
+}
+
+void copy_and_check_matrix(const vtm_csr* A, vtm_partition* p) {
+  if (!A || A->n <= 0 || !A->rowptr || !A->col || !A->val) fail(VTM_ERR_INVALID, "A: null or empty matrix");
+  const int64_t n = A->n;
+  if (A->nnz < 0 || A->rowptr[0] != 0 || A->rowptr[n] != A->nnz)
+    fail(VTM_ERR_INVALID, "A: rowptr inconsistent with nnz");
+  // every row's range first: a row's symmetric partner may lie in a later row, whose range must
+  // already be known to lie inside [0, nnz]
+  for (int64_t i = 0; i < n; ++i)
+    if (A->rowptr[i + 1] < A->rowptr[i]) fail(VTM_ERR_INVALID, "A: rowptr not monotone");
+  p->n = n;
+  p->a_rowptr.assign(A->rowptr, A->rowptr + n + 1);
+  p->a_col.assign(A->col, A->col + A->nnz);
+  p->a_val.assign(A->val, A->val + A->nnz);
+  // then the entries, blocks of consecutive rows on the host threads; each block keeps its first
+  // error and the lowest block's is reported, so the error is the one a loop over the rows meets
+  // first
+  const int64_t kRows = 16384, nblk = (n + kRows - 1) / kRows;
+  std::vector<int> ecode(nblk, 0);
+  std::vector<std::string> emsg(nblk);
+  parallel_for(nblk, [&](int64_t blk) {
+    try {
+      for (int64_t i = blk * kRows; i < std::min(n, (blk + 1) * kRows); ++i) {
+        const int64_t lo = A->rowptr[i], hi = A->rowptr[i + 1];
+        bool diag = false;
+        for (int64_t k = lo; k < hi; ++k) {
+          int32_t j = A->col[k];
+          if (j < 0 || j >= n) fail(VTM_ERR_INVALID, "A: column index out of range");
+          if (k > lo && A->col[k - 1] >= j) fail(VTM_ERR_INVALID, "A: columns not strictly ascending in a row");
+          if (j == i) {
+            diag = true;
+            if (!(A->val[k] > 0)) fail(VTM_ERR_INVALID, "A: non-positive diagonal");
+            continue;
+          }
+          // symmetric partner
+          const int32_t* b = A->col + A->rowptr[j];
+          const int32_t* e = A->col + A->rowptr[j + 1];
+          const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+          if (f == e || *f != i || A->val[A->rowptr[j] + (f - b)] != A->val[k])
+            fail(VTM_ERR_NOT_SYMMETRIC, "A is not symmetric");
+        }
+        if (!diag) fail(VTM_ERR_INVALID, "A: missing diagonal entry");
+      }
+    } catch (const vtm::Error& e) {
+      ecode[blk] = e.code;
+      emsg[blk] = e.msg;
+    }
+  });
+  for (int64_t blk = 0; blk < nblk; ++blk)
+    if (ecode[blk]) fail(ecode[blk], emsg[blk]);
 }
 
 // ----------------------------------------------------------------------------------- GRID

@@ -121,6 +121,37 @@ def test_errors_are_reported(vtmlib):
     assert e.value.code == 3
 
 
+def test_malformed_rowptr_is_an_error_before_any_partner_lookup(vtmlib):
+    """Row 19 of a 6 x 6 grid made to end before it starts: row 14's symmetric partner, row 20,
+    would be read through that range; the library reports the bad row pointer instead."""
+    A = inputs.grid_poisson((6, 6))
+    rp = A.rowptr.copy()
+    rp[20] = rp[19] - 1
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(inputs.CSR(n=A.n, rowptr=rp, col=A.col, val=A.val), "grid", dims=(6, 6), block=(3, 3))
+    assert e.value.code == 1 and "monotone" in str(e.value)
+
+
+def test_first_error_of_a_threaded_matrix_check(vtmlib):
+    """1024^2 rows (checked in 64 blocks on the host threads) with two defects: a column index out of
+    range in row 100 and an unsymmetric value in row 900000; the error of row 100 is reported, as
+    from one loop over the rows."""
+    A = inputs.grid_poisson((1024, 1024))
+    col, val = A.col.copy(), A.val.copy()
+    col[A.rowptr[101] - 1] = A.n + 5
+    val[A.rowptr[900000]] *= 2
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(inputs.CSR(n=A.n, rowptr=A.rowptr, col=col, val=val), "grid", dims=(1024, 1024),
+                             block=(512, 512))
+    assert e.value.code == 1 and "out of range" in str(e.value)
+    val2 = A.val.copy()
+    val2[A.rowptr[900000]] *= 2
+    with pytest.raises(vtmlib.VTMError) as e:
+        vtmlib.partition_evs(inputs.CSR(n=A.n, rowptr=A.rowptr, col=A.col, val=val2), "grid", dims=(1024, 1024),
+                             block=(512, 512))
+    assert e.value.code == 2
+
+
 @pytest.mark.parametrize("dims,block,sigma", [((9, 7, 6), (4, 3, 5), 0.7), ((17, 12), (8, 5), 1.3)])
 def test_line_features_match_oracle(vtmlib, dims, block, sigma):
     from oracle import features
