@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <thread>
 #include <tuple>
 
@@ -35,22 +36,27 @@ void parallel_for(int64_t count, F&& f) {
     for (int64_t i = 0; i < count; ++i) f(i);
     return;
   }
+  // any exception of a worker (an Error, or bad_alloc from a growing list) is carried back to
+  // the calling thread and rethrown there, where the C ABI turns it into an error code
   std::vector<std::thread> th;
-  std::vector<vtm::Error> errs(nt);
-  std::vector<char> bad(nt, 0);
-  for (unsigned t = 0; t < nt; ++t) {
-    th.emplace_back([&, t] {
-      try {
-        for (int64_t i = t; i < count; i += nt) f(i);
-      } catch (const vtm::Error& e) {
-        errs[t] = e;
-        bad[t] = 1;
-      }
-    });
+  std::vector<std::exception_ptr> errs(nt);
+  try {
+    for (unsigned t = 0; t < nt; ++t) {
+      th.emplace_back([&, t] {
+        try {
+          for (int64_t i = t; i < count; i += nt) f(i);
+        } catch (...) {
+          errs[t] = std::current_exception();
+        }
+      });
+    }
+  } catch (...) {  // a thread that could not start: wait for those that did, then report
+    for (auto& x : th) x.join();
+    throw;
   }
   for (auto& x : th) x.join();
   for (unsigned t = 0; t < nt; ++t)
-    if (bad[t]) throw errs[t];
+    if (errs[t]) std::rethrow_exception(errs[t]);
 }
 
 void copy_and_check_matrix(const vtm_csr* A, vtm_partition* p) {
