@@ -161,8 +161,8 @@ typedef struct vtm_partition_info {
 /* §4 steps 1-4.  A: host CSR (copied).  On success *out owns the split.
  * A is checked first: rowptr must start at 0, end at nnz >= 0 and never decrease (checked for
  * every row before any entry is read), columns in range and strictly ascending, a positive
- * diagonal in every row, and a_ij = a_ji; with several defects the one in the lowest row is
- * reported.  Errors: VTM_ERR_INVALID (a malformed A / bad spec / an edge in no common subgraph /
+ * diagonal in every row, and a_ij = a_ji; a bad rowptr is reported before any entry defect, and
+ * of several entry defects the one in the lowest row.  Errors: VTM_ERR_INVALID (a malformed A / bad spec / an edge in no common subgraph /
  * a line between copies that do not exist), VTM_ERR_NOT_SYMMETRIC, VTM_ERR_NOT_CONFORMAL,
  * VTM_ERR_OOM (host memory). */
 int vtm_partition_evs(const vtm_csr* A, const vtm_partition_spec* spec, vtm_partition** out);
