@@ -190,8 +190,8 @@ class OracleSampler:
         for k in env_keep:
             os.environ[k] = "1"
         try:
-            self.shm = {k: shared_memory.SharedMemory(create=True, size=max(8, int(np.prod(v)) * 8))
-                        for k, v in shapes.items()}
+            for k, v in shapes.items():              # one at a time, so that close() frees every one made
+                self.shm[k] = shared_memory.SharedMemory(create=True, size=max(8, int(np.prod(v)) * 8))
             self.arr = {k: np.ndarray(shapes[k], dtype=np.float64, buffer=self.shm[k].buf) for k in self.shm}
             for v in self.arr.values():
                 v[...] = 0.0
