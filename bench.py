@@ -758,7 +758,9 @@ def run_vtm(args):
     if rank != 0:
         return 0
     cpu = None
-    if not args.no_cpu_baseline and w["kind"] == "grid":
+    if ws > 1:
+        cpu = {"value": None, "unit": "ms", "kind": "oracle", "note": "the oracle is timed at one GPU (N = 1) only"}
+    elif not args.no_cpu_baseline and w["kind"] == "grid":
         ks, src = reference_sweeps(args.workload)
         if ks <= 0 and plain:
             ks, src = plain["sweeps"], "the plain FP64 method's count on this GPU"
